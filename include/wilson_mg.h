@@ -1,0 +1,204 @@
+/*
+ * wilson_mg.h -- C ABI of the GB300 adaptive-multigrid solver for the 4D SU(3)
+ * Wilson-Dirac system D x = b.
+ *
+ * Paper: M. A. Clark, J. Brannick, R. C. Brower, S. F. McCormick,
+ * T. A. Manteuffel, J. C. Osborn, C. Rebbi, "The removal of critical slowing
+ * down", Lattice 2008 (arXiv:0811.4331).
+ *
+ * Operator (Sec. 1, Eq. 1.1 and the paragraph after it), lattice spacing 1,
+ * Wilson parameter r = 1, periodic boundaries:
+ *   (D psi)(n) = (4 + m) psi(n)
+ *       - 1/2 sum_mu [(1 - gamma_mu) U_mu(n) psi(n+mu) + (1 + gamma_mu) U_mu(n-mu)^+ psi(n-mu)]
+ * with the chiral gamma basis gamma_k = [[0, -i sigma_k], [i sigma_k, 0]]
+ * (k = x, y, z), gamma_t = [[0, 1], [1, 0]], gamma_5 = diag(1, 1, -1, -1).
+ *
+ * ---------------------------------------------------------------- layouts
+ * Complex numbers are interleaved (re, im).  dims = {Lx, Ly, Lz, Lt}; the
+ * site index is lexicographic with x fastest:
+ *   site = x + Lx * (y + Ly * (z + Lz * t)),  V = Lx Ly Lz Lt.
+ * EXTERNAL layouts (what mg_setup / mg_solve / the field converters take):
+ *   gauge   : double complex [4][V][3][3]  (mu = x, y, z, t; row, column)
+ *   spinor  : double complex [nrhs][V][4][3]  (spin, colour) = [nrhs][V][12]
+ *   level-l field (l >= 1): double complex [nrhs][V_l][2 Nv_l]; components
+ *             [0, Nv_l) have chirality +, [Nv_l, 2 Nv_l) chirality -.
+ * INTERNAL layout (what dslash_apply / coarse_apply / restrict / prolong /
+ * mr_apply operate on, in the precision named by `prec`): component-major,
+ *   [nrhs][ncomp][V_l] complex, element (r, c, s) at (r * ncomp + c) * V_l + s,
+ * with ncomp = 12 on level 0 (c = spin * 3 + colour) and 2 Nv_l on level l.
+ * Complex element types: MG_F64 = 2 x double, MG_F32 = 2 x float,
+ * MG_F16 = 2 x IEEE binary16, MG_BF16 = 2 x bfloat16.  mg_field_to_internal /
+ * mg_field_from_internal convert between the two.
+ *
+ * ---------------------------------------------------------------- conventions
+ * Every call returns an mg_status.  No exception crosses the ABI.  On error
+ * mg_last_error() returns a static, thread-local message.  `stream` is a
+ * cudaStream_t (NULL = legacy default stream); all device work of a call is
+ * enqueued on it.  Calls that take or return host data, or that return
+ * results to the host (mg_setup, mg_solve, the getters), synchronise the
+ * stream before returning; the *_apply calls do not.  A handle is not
+ * thread-safe.  Device pointers passed in must stay valid until the work
+ * enqueued on `stream` has finished.
+ */
+#ifndef WILSON_MG_H
+#define WILSON_MG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MG_OK = 0,
+  MG_EINVAL = 1,      /* bad argument: sizes, level, precision, layout, null pointer */
+  MG_ENOMEM = 2,      /* device allocation failed */
+  MG_ECUDA = 3,       /* a CUDA call failed (message in mg_last_error) */
+  MG_ERANK = 4,       /* block Gram-Schmidt lost rank (a candidate fell below 1e-12 of its norm) */
+  MG_ENOCONV = 5,     /* solver hit max_iter; x holds the last iterate, stats its true residual */
+  MG_EBREAKDOWN = 6,  /* GCR breakdown (||A z|| = 0) */
+  MG_ENAN = 7         /* a residual norm became NaN or Inf */
+} mg_status;
+
+typedef enum { MG_F64 = 0, MG_F32 = 1, MG_F16 = 2, MG_BF16 = 3 } mg_precision;
+
+#define MG_MAX_LEVELS 4
+
+/* Solver parameters.  mg_default_params fills the paper's choices:
+ * V(2,2) (Sec. 4, Sec. 5), omega = 0.8 (Sec. 3), 4 next-level V-cycles per
+ * fine coarse correction (Sec. 5), GCR(50) (Sec. 5), 4^4 blocks (Sec. 3,
+ * Sec. 5), Nv = 20 (Sec. 5). */
+typedef struct {
+  int n_levels;                       /* 1 = no preconditioner (plain GCR), 2..MG_MAX_LEVELS */
+  int block[MG_MAX_LEVELS - 1][4];    /* aggregate of level l -> l+1, {bx, by, bz, bt} */
+  int nv[MG_MAX_LEVELS - 1];          /* null vectors of level l (coarse ncomp = 2 nv) */
+  int setup_sweeps[MG_MAX_LEVELS - 1];/* MR steps on A x = 0 per candidate (Sec. 2, "l") */
+  int coarse_cycles[MG_MAX_LEVELS - 1];/* next-level V-cycles per coarse correction of level l */
+  int nu_pre, nu_post;                /* MR smoothing steps before / after the coarse correction */
+  double omega;                       /* MR under-relaxation */
+  int gcr_restart;                    /* outer flexible GCR restart length */
+  int max_iter;                       /* outer GCR iteration cap (all restarts) */
+  int mixed;                          /* 0 = plain FP64 everywhere; 1 = mixed precision */
+  int fine_prec;                      /* mixed: storage of level-0 smoother work (MG_F16/MG_BF16/MG_F32) */
+  int coarse_prec;                    /* mixed: storage of levels 1..L-2 (MG_F32/MG_F16/MG_BF16) */
+  double reliable_delta;              /* mixed: inner FP32 GCR reduces ||r|| by this factor before an FP64 update */
+  uint64_t seed;                      /* on-device start vectors: level l uses stream seed + l */
+} mg_params;
+
+/* Per right-hand side solve statistics. */
+typedef struct {
+  int iters;                 /* outer GCR iterations */
+  int restarts;              /* GCR restarts */
+  int reliable_updates;      /* FP64 true-residual recomputations (mixed) */
+  long long fine_dslash;     /* level-0 operator applications, all precisions */
+  long long fine_dslash_f64; /* of which in FP64 */
+  double true_rel_residual;  /* ||b - D x|| / ||b||, recomputed in FP64 at exit */
+  double solve_seconds;      /* wall time of this right-hand side's solve */
+} mg_stats;
+
+typedef struct mg_handle mg_handle;
+
+/* Last error message of this thread (never NULL). */
+const char* mg_last_error(void);
+
+/* Fill `p` with defaults: 2 levels, 4^4 blocks, Nv = 20, 20 setup sweeps,
+ * V(2,2), omega 0.8, 4 coarse cycles, GCR(50), max_iter 2000, plain FP64. */
+int mg_default_params(mg_params* p);
+
+/* Build the solver for gauge field `gauge` and mass `mass`.
+ *   h            : out, a new handle owning every device buffer of the hierarchy.
+ *   gauge        : external layout, FP64; host memory if gauge_on_device == 0,
+ *                  device memory otherwise.  Copied; the caller keeps ownership.
+ *   dims         : {Lx, Ly, Lz, Lt}, each >= 1.
+ *   p            : parameters (copied).  For every level l < n_levels - 1 the
+ *                  level's extent must be divisible by block[l], and
+ *                  nv[l] <= (components per chirality) * (sites per block).
+ *   starts       : NULL, or an array of n_levels - 1 host pointers; starts[l]
+ *                  holds nv[l] FP64 start vectors of level l in the external
+ *                  layout [nv][V_l][ncomp_l].  NULL entries (or NULL starts)
+ *                  use the on-device counter generator (seed p->seed + l).
+ * Setup per level (Sec. 2 adaptive steps 1-3, Eq. 2.3; Sec. 3): setup_sweeps
+ * MR steps (omega) on A x = 0 from each start, unit-normalise, blockwise
+ * FP64 modified Gram-Schmidt (two passes, candidate order) per aggregate and
+ * chirality into P, then A_{l+1} = P^+ A_l P as a 9-point stencil of
+ * 2Nv x 2Nv blocks; the coarsest level gets a dense FP64 inverse.
+ * Errors: MG_EINVAL, MG_ENOMEM, MG_ERANK, MG_ECUDA.  On error *h is NULL. */
+int mg_setup(mg_handle** h, const double* gauge, int gauge_on_device, const int dims[4],
+             double mass, const mg_params* p, const double* const* starts, void* stream);
+
+/* Free every device buffer of `h` (NULL is allowed). */
+int mg_destroy(mg_handle* h);
+
+/* Solve D x_r = b_r for r = 0..nrhs-1 to ||b - D x|| / ||b|| <= tol with
+ * flexible GCR(gcr_restart) preconditioned by one modified multigrid V-cycle
+ * (Sec. 5), or unpreconditioned when n_levels == 1.
+ *   b, x  : external spinor layout, FP64, [nrhs][V][12]; device memory if
+ *           on_device != 0, else host memory.  x is the initial guess on
+ *           entry (zero it for none) and the solution on return.
+ *   stats : NULL or an array of nrhs mg_stats.
+ * Every returned x is judged by its true FP64 residual, recomputed at exit.
+ * Errors: MG_EINVAL, MG_ENOCONV (x and stats still filled), MG_EBREAKDOWN,
+ * MG_ENAN, MG_ECUDA. */
+int mg_solve(mg_handle* h, const double* b, double* x, int nrhs, int on_device, double tol,
+             mg_stats* stats, void* stream);
+
+/* out = D in on level 0 (Sec. 1 operator above) for nrhs internal-layout
+ * spinors of precision `prec` (device memory; in and out must not overlap).
+ * Arithmetic is FP64 for MG_F64 and FP32 otherwise.  Errors: MG_EINVAL. */
+int dslash_apply(mg_handle* h, int prec, const void* in, void* out, int nrhs, void* stream);
+
+/* out = A_level in for the coarse stencil operator of `level` >= 1
+ * (A_l = P^+ A_{l-1} P, Sec. 2), internal layout, device memory.
+ * Precisions: MG_F64 and MG_F32 (storage of operator and vectors).
+ * Errors: MG_EINVAL (no such level / precision). */
+int coarse_apply(mg_handle* h, int level, int prec, const void* in, void* out, int nrhs,
+                 void* stream);
+
+/* out (level l+1) = P_l^+ in (level l)  -- restriction R = P^+ (Sec. 3).
+ * Internal layouts, precision `prec` for both vectors (MG_F64 or MG_F32). */
+int restrict_apply(mg_handle* h, int level, int prec, const void* in, void* out, int nrhs,
+                   void* stream);
+
+/* out (level l) = P_l in (level l+1)  -- prolongation (Sec. 2). */
+int prolong_apply(mg_handle* h, int level, int prec, const void* in, void* out, int nrhs,
+                  void* stream);
+
+/* `steps` under-relaxed MR steps (Sec. 3, omega from the params) on
+ * A_level x = b starting from x (internal layout, precision prec; x is
+ * updated in place, r receives b - A x as updated by the iteration). */
+int mr_apply(mg_handle* h, int level, int prec, const void* b, void* x, void* r, int steps,
+             void* stream);
+
+/* e = M r: one modified V-cycle of the hierarchy applied to the level-0
+ * internal-layout FP64 residual r (plain FP64 hierarchy only). */
+int vcycle_apply(mg_handle* h, const void* r, void* e, void* stream);
+
+/* Copy nrhs FP64 external-layout fields of `level` (host if on_device == 0)
+ * to the internal layout in precision prec on the device, and back. */
+int mg_field_to_internal(mg_handle* h, int level, int prec, const double* ext, int on_device,
+                         void* internal, int nrhs, void* stream);
+int mg_field_from_internal(mg_handle* h, int level, int prec, const void* internal,
+                           double* ext, int on_device, int nrhs, void* stream);
+
+/* Sizes of level `level`: sites, components per site, null vectors (0 on
+ * the coarsest level). */
+int mg_level_info(mg_handle* h, int level, int dims_out[4], int* ncomp, int* nv);
+
+/* Copy the FP64 prolongator of level l to host memory, external layout
+ * [nv][V_l][ncomp_l]: vector k holds, on every aggregate B and chirality
+ * chi, column chi * nv + k of P restricted to B (Eq. 2.3). */
+int mg_get_prolongator(mg_handle* h, int level, double* out);
+
+/* Copy the FP64 coarse stencil of level l >= 1 to host memory as
+ * [9][V_l][ncomp][ncomp] complex (row i, column j); direction d = 0 is the
+ * site itself, d = 1 + 2 mu the hop to n + mu, d = 2 + 2 mu to n - mu. */
+int mg_get_coarse_op(mg_handle* h, int level, double* out);
+
+/* Device bytes that mg_setup + mg_solve(nrhs) need for these sizes. */
+size_t mg_footprint(const int dims[4], const mg_params* p, int nrhs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

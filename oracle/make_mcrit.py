@@ -1,0 +1,75 @@
+"""Write tests/golden/mcrit.json: the critical mass of each seeded beta = 6.0 workload field.
+
+Test infrastructure: calls only the oracle and the seeded input generators.
+
+m_crit is read as minus the smallest real part of the spectrum of the
+Wilson-Dirac operator at m = 0 on the given gauge field, so that
+D(m_crit + delta) has smallest real eigenvalue part delta (Sec. 1: the
+eigenvalues satisfy Re(lambda) > 0 and D turns singular as
+Re(lambda_min) -> 0; Sec. 5 quotes m_crit = -0.8049 for its own beta = 6.0,
+16^3 x 32 ensemble).  The eigenvalues come from implicitly restarted Arnoldi
+(scipy's ARPACK binding, which='SR') on the oracle operator.
+
+Usage: python -m oracle.make_mcrit [--dims 8 8 8 16] [--sweeps 200] [--seed 0]
+"""
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+import scipy.sparse.linalg as sla
+
+from oracle import dirac
+from paper_0811_4331_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "..", "tests", "golden", "mcrit.json")
+
+
+def smallest_real_part(U, nev=4, tol=1e-8):
+    lat = U.shape[1:5]
+    n = int(np.prod(lat)) * 12
+
+    def mv(v):
+        return dirac.wilson_dirac(U, v.reshape(lat + (4, 3)), 0.0).reshape(n)
+
+    op = sla.LinearOperator((n, n), matvec=mv, dtype=np.complex128)
+    vals = sla.eigs(op, k=nev, which="SR", ncv=64, tol=tol, maxiter=100000,
+                    return_eigenvectors=False)
+    return float(np.min(vals.real)), [complex(v) for v in vals]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dims", type=int, nargs=4, default=[8, 8, 8, 16])
+    ap.add_argument("--beta", type=float, default=6.0)
+    ap.add_argument("--sweeps", type=int, default=200)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args()
+    t0 = time.time()
+    U = inputs.heatbath_gauge(tuple(a.dims), a.beta, a.sweeps, a.seed)
+    t1 = time.time()
+    lam, vals = smallest_real_part(U)
+    t2 = time.time()
+    key = "%dx%dx%dx%d_beta%.1f_sweeps%d_seed%d" % (*a.dims, a.beta, a.sweeps, a.seed)
+    data = {}
+    if os.path.exists(GOLDEN):
+        with open(GOLDEN) as f:
+            data = json.load(f)
+    data[key] = {
+        "dims": a.dims, "beta": a.beta, "sweeps": a.sweeps, "seed": a.seed,
+        "plaquette": inputs.plaquette(U),
+        "min_re_lambda_m0": lam,
+        "m_crit": -lam,
+        "lowest_eigenvalues_m0": [[v.real, v.imag] for v in vals],
+        "how": "python -m oracle.make_mcrit --dims %d %d %d %d --sweeps %d --seed %d"
+               % (*a.dims, a.sweeps, a.seed),
+        "seconds": {"heatbath": round(t1 - t0, 1), "arnoldi": round(t2 - t1, 1)},
+    }
+    with open(GOLDEN, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    print(key, data[key]["m_crit"], data[key]["plaquette"])
+
+
+if __name__ == "__main__":
+    main()

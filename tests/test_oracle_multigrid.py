@@ -1,0 +1,219 @@
+"""Pins of the oracle multigrid pieces against mathematics the paper fixes.
+
+* MR: exact residual-decrease identity and the least-squares optimality of alpha.
+* Block QR: equals numpy's Householder QR up to column phases (a library
+  routine), P^+ P = 1, structural chirality zeros, P P^+ v_i = v_i (Eq. 2.3).
+* Restriction / prolongation: adjoint pair and R P = 1.
+* Coarse stencil: equals the brute-force dense P^+ D P, for coarse extents
+  1, 2 and 3, and on the second coarsening; coarse gamma5-Hermiticity.
+* Two-grid special case: with Nv = 6 |b| the prolongator is square unitary,
+  the coarse solve is exact and one MG-preconditioned GCR step solves.
+* GCR: matches dense LU, minimal-residual monotonicity.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import dirac
+from oracle import multigrid as mg
+from paper_0811_4331_gb300 import inputs
+
+
+def _lat(dims):
+    Lx, Ly, Lz, Lt = dims
+    return (Lt, Lz, Ly, Lx)
+
+
+def _fine_apply(U, m):
+    lat = U.shape[1:5]
+    return lambda y: dirac.wilson_dirac(U, y.reshape(lat + (4, 3)), m).reshape(lat + (12,))
+
+
+def test_alpha_is_least_squares_minimiser():
+    rng = np.random.default_rng(0)
+    p = rng.standard_normal(50) + 1j * rng.standard_normal(50)
+    r = rng.standard_normal(50) + 1j * rng.standard_normal(50)
+    a = mg.minimal_residual_coefficient(p, r)
+    ls = np.linalg.lstsq(p[:, None], r, rcond=None)[0][0]
+    assert abs(a - ls) < 1e-14 * abs(ls)
+    assert mg.minimal_residual_coefficient(np.zeros(3, complex), r[:3]) == 0.0
+
+
+def test_mr_residual_identity_and_monotone():
+    """||r'||^2 = ||r||^2 - omega (2 - omega) |<p|r>|^2 / ||p||^2 per step, r' = b - D x' recomputed."""
+    dims = (4, 4, 2, 2)
+    U = inputs.random_gauge(dims, 1)
+    A = _fine_apply(U, 0.1)
+    lat = _lat(dims)
+    b = inputs.gaussian_spinor(dims, 2).reshape(lat + (12,))
+    omega = 0.8
+    x = np.zeros_like(b)
+    r = b.copy()
+    for _ in range(5):
+        p = A(r)
+        pr = np.vdot(p, r)
+        pp = np.vdot(p, p).real
+        x1, r1 = mg.mr_relax(A, b, x, 1, omega)
+        true = b - A(x1)
+        assert np.allclose(r1, true, atol=1e-12)
+        expect = np.vdot(r, r).real - omega * (2 - omega) * abs(pr) ** 2 / pp
+        assert abs(np.vdot(true, true).real - expect) < 1e-11 * expect
+        assert np.vdot(true, true).real < np.vdot(r, r).real
+        x, r = x1, true
+
+
+def test_mgs2_matches_householder_qr():
+    rng = np.random.default_rng(3)
+    Vb = rng.standard_normal((40, 7)) + 1j * rng.standard_normal((40, 7))
+    Q = mg.mgs2(Vb)
+    Qh, R = np.linalg.qr(Vb)
+    ph = np.diag(R) / np.abs(np.diag(R))
+    assert np.max(np.abs(Q - Qh * ph)) < 1e-13
+    assert np.max(np.abs(Q.conj().T @ Q - np.eye(7))) < 1e-14
+    with pytest.raises(ArithmeticError):
+        Vb[:, 3] = Vb[:, 0] * (0.5 - 2j)
+        mg.mgs2(Vb)
+
+
+def _hierarchy_pieces(dims, block, nv, sweeps, seed=0, m=0.1):
+    U = inputs.random_gauge(dims, seed)
+    lat = _lat(dims)
+    A = _fine_apply(U, m)
+    starts = inputs.null_vector_starts(lat, 12, nv, 100 + seed)
+    cands = mg.relax_null_vectors(A, starts, sweeps)
+    blk = mg.Blocking(lat, block, 12)
+    P = mg.block_orthonormalize(cands, blk)
+    return U, A, cands, blk, P
+
+
+def test_prolongator_properties():
+    dims = (4, 4, 4, 4)
+    nv = 6
+    U, A, cands, blk, P = _hierarchy_pieces(dims, (2, 2, 2, 2), nv, 4)
+    # structural chirality zeros: [gamma5, P] = 0
+    assert np.all(P[..., :6, nv:] == 0) and np.all(P[..., 6:, :nv] == 0)
+    # P^+ P = 1 on the coarse space
+    G = blk.block_sum(np.einsum("...ci,...cj->...ij", np.conj(P), P))
+    assert np.max(np.abs(G - np.eye(2 * nv))) < 1e-14
+    # P V_c = V: every candidate lies in the range of P (Eq. 2.3)
+    for v in cands:
+        proj = mg.prolong(P, blk, mg.restrict(P, blk, v))
+        assert np.max(np.abs(proj - v)) < 1e-13
+
+
+def test_restrict_prolong_adjoint():
+    dims = (4, 4, 2, 4)
+    U, A, cands, blk, P = _hierarchy_pieces(dims, (2, 2, 2, 2), 5, 3, seed=4)
+    rng = np.random.default_rng(1)
+    r = rng.standard_normal(blk.lattice + (12,)) + 1j * rng.standard_normal(blk.lattice + (12,))
+    xc = rng.standard_normal(blk.coarse + (10,)) + 1j * rng.standard_normal(blk.coarse + (10,))
+    lhs = np.vdot(mg.prolong(P, blk, xc), r)
+    rhs = np.vdot(xc, mg.restrict(P, blk, r))
+    assert abs(lhs - rhs) < 1e-13 * abs(lhs)
+    assert np.max(np.abs(mg.restrict(P, blk, mg.prolong(P, blk, xc)) - xc)) < 1e-13
+
+
+def _dense_check(dims, block, nv, sweeps, seed):
+    U, A, cands, blk, P = _hierarchy_pieces(dims, block, nv, sweeps, seed)
+    lat = _lat(dims)
+    Af = dirac.wilson_stencil(U, 0.1)
+    Ac = mg.coarse_stencil(Af, P, blk)
+    D = dirac.dense_matrix(A, lat + (12,))
+    Pd = dirac.dense_matrix(lambda xc: mg.prolong(P, blk, xc), blk.coarse + (2 * nv,))
+    brute = Pd.conj().T @ D @ Pd
+    dense = mg.dense_from_stencil(Ac)
+    assert np.max(np.abs(brute - dense)) < 1e-13 * np.max(np.abs(brute))
+    return Ac, blk
+
+
+@pytest.mark.parametrize("dims,block", [((4, 4, 4, 4), (2, 2, 2, 2)),   # coarse extent 2
+                                        ((6, 2, 2, 2), (2, 2, 2, 2)),   # extents 3 and 1
+                                        ((2, 2, 2, 2), (2, 2, 2, 2))])  # a single aggregate
+def test_coarse_stencil_equals_brute_force(dims, block):
+    _dense_check(dims, block, 4, 3, seed=2)
+
+
+def test_coarse_gamma5_hermiticity():
+    """Gamma5 = diag(+1_Nv, -1_Nv) per coarse site: Gamma5 A_c Gamma5 = A_c^+ (from [gamma5, P] = 0)."""
+    Ac, blk = _dense_check((4, 4, 4, 4), (2, 2, 2, 2), 4, 3, seed=5)
+    Dc = mg.dense_from_stencil(Ac)
+    nc = 8
+    g5 = np.tile(np.r_[np.ones(nc // 2), -np.ones(nc // 2)], Dc.shape[0] // nc)
+    lhs = g5[:, None] * Dc * g5[None, :]
+    assert np.max(np.abs(lhs - Dc.conj().T)) < 1e-13
+
+
+def test_second_coarsening_equals_brute_force():
+    dims = (4, 4, 4, 4)
+    nv0, nv1 = 4, 3
+    U = inputs.random_gauge(dims, 8)
+    lat = _lat(dims)
+    starts = [inputs.null_vector_starts(lat, 12, nv0, 21),
+              inputs.null_vector_starts((2, 2, 2, 2), 2 * nv0, nv1, 22)]
+    levels = [dict(block=(2, 2, 2, 2), nv=nv0, sweeps=3), dict(block=(2, 2, 1, 1), nv=nv1, sweeps=3)]
+    h = mg.mg_setup(U, 0.1, levels, starts)
+    A1 = mg.dense_from_stencil(h[1].stencil)
+    Pd = dirac.dense_matrix(lambda xc: mg.prolong(h[1].P, h[1].blk, xc), h[2].lattice + (2 * nv1,))
+    brute = Pd.conj().T @ A1 @ Pd
+    assert np.max(np.abs(brute - mg.dense_from_stencil(h[2].stencil))) < 1e-13 * np.max(np.abs(brute))
+    # the coarse level keeps chirality in its own split (first nv0 comps +, last nv0 -)
+    assert np.all(h[1].P[..., :nv0, nv1:] == 0) and np.all(h[1].P[..., nv0:, :nv1] == 0)
+
+
+def test_unitary_prolongator_solves_in_one_step():
+    """Nv = 6 |b|: P is square unitary, the coarse solve is exact, GCR converges in one step."""
+    dims = (2, 2, 2, 2)
+    U = inputs.random_gauge(dims, 0)
+    lat = _lat(dims)
+    starts = [inputs.null_vector_starts(lat, 12, 96, 7)]
+    h = mg.mg_setup(U, 0.1, [dict(block=(2, 2, 2, 2), nv=96, sweeps=0)], starts)
+    b = inputs.gaussian_spinor(dims, 3).reshape(lat + (12,))
+    x, info = mg.mg_solve(h, b, tol=1e-11)
+    assert info["iters"] == 1
+    assert info["true_rel_residual"] < 1e-12
+
+
+def test_gcr_matches_lu_and_is_monotone():
+    dims = (2, 2, 2, 2)
+    U = inputs.random_gauge(dims, 1)
+    lat = _lat(dims)
+    A = _fine_apply(U, 0.05)
+    b = inputs.gaussian_spinor(dims, 2).reshape(lat + (12,))
+    x, info = mg.fgcr(A, b, None, tol=1e-12, restart=200)
+    D = dirac.dense_matrix(A, lat + (12,))
+    xl = scipy.linalg.solve(D, b.reshape(-1)).reshape(b.shape)
+    assert np.linalg.norm(x - xl) < 1e-10 * np.linalg.norm(xl)
+    assert info["iters"] <= 192
+    h = np.array(info["history"])
+    assert np.all(np.diff(h) <= 1e-15)
+
+
+def test_two_level_mg_solve_small_workload():
+    """4^4, U = exp(0.3 i H), m = 0.1, 2^4 blocks, Nv = 8, 10 setup sweeps, tol 1e-10."""
+    dims = (4, 4, 4, 4)
+    U = inputs.random_gauge(dims, 0)
+    lat = _lat(dims)
+    starts = [inputs.null_vector_starts(lat, 12, 8, 2)]
+    h = mg.mg_setup(U, 0.1, [dict(block=(2, 2, 2, 2), nv=8, sweeps=10)], starts)
+    b = inputs.gaussian_spinor(dims, 1).reshape(lat + (12,))
+    x, info = mg.mg_solve(h, b, tol=1e-10)
+    assert info["true_rel_residual"] <= 1e-10
+    D = dirac.dense_matrix(h[0].apply, lat + (12,))
+    xl = scipy.linalg.solve(D, b.reshape(-1)).reshape(b.shape)
+    assert np.linalg.norm(x - xl) < 1e-8 * np.linalg.norm(xl)
+    # preconditioning pays: fewer outer iterations than plain GCR
+    _, plain = mg.fgcr(h[0].apply, b, None, tol=1e-10)
+    assert info["iters"] < plain["iters"]
+
+
+def test_three_level_mg_solve():
+    dims = (4, 4, 4, 4)
+    U = inputs.random_gauge(dims, 3)
+    lat = _lat(dims)
+    starts = [inputs.null_vector_starts(lat, 12, 6, 31),
+              inputs.null_vector_starts((2, 2, 2, 2), 12, 4, 32)]
+    h = mg.mg_setup(U, 0.1, [dict(block=(2, 2, 2, 2), nv=6, sweeps=6),
+                             dict(block=(2, 2, 1, 1), nv=4, sweeps=6)], starts)
+    b = inputs.gaussian_spinor(dims, 4).reshape(lat + (12,))
+    x, info = mg.mg_solve(h, b, tol=1e-10)
+    assert info["true_rel_residual"] <= 1e-10
