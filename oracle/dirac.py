@@ -136,3 +136,28 @@ def stencil_apply(A, y):
         mu, step = stencil_offset(d)
         out = out + np.einsum("...ij,...j->...i", A[d], shift(y, mu, step))
     return out
+
+
+def wilson_dirac_site(U, psi, mass, site):
+    """(D psi)(n) at one site n = (x, y, z, t), from the same definition (Sec. 1).
+
+    Used to check sampled outputs of lattices too large for the whole-field
+    oracle.  Neighbour coordinates wrap periodically.
+    """
+    Lt, Lz, Ly, Lx = psi.shape[:4]
+    L = (Lx, Ly, Lz, Lt)
+    x = list(site)
+
+    def at(c):
+        return (c[3] % L[3], c[2] % L[2], c[1] % L[1], c[0] % L[0])
+
+    out = (4.0 + mass) * psi[at(x)]
+    for mu in range(4):
+        up = list(x)
+        up[mu] += 1
+        dn = list(x)
+        dn[mu] -= 1
+        fwd = psi[at(up)] @ U[mu][at(x)].T               # U_mu(n) psi(n + mu), colour on the right
+        bwd = psi[at(dn)] @ np.conj(U[mu][at(dn)])       # U_mu(n - mu)^+ psi(n - mu)
+        out = out - 0.5 * ((IDENTITY4 - GAMMA[mu]) @ fwd + (IDENTITY4 + GAMMA[mu]) @ bwd)
+    return out

@@ -1,0 +1,883 @@
+// C ABI of the library and the host-side orchestration of the solver:
+// setup of the multigrid hierarchy (Sec. 2 adaptive steps, Eq. 2.3, Sec. 3),
+// the modified V(2,2) cycle with the alpha-damped coarse-grid correction
+// (Sec. 3 Eq. 3.5, Sec. 5) and flexible GCR(50) (Sec. 5), plain FP64 or
+// mixed precision with FP64 reliable updates.  All arithmetic runs in the
+// kernels of this library; the host only sequences launches and reads the
+// residual norms that decide when to stop.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+
+namespace wmg {
+
+static thread_local std::string g_err = "";
+void set_error(const std::string& msg) { g_err = msg; }
+
+}  // namespace wmg
+
+using namespace wmg;
+
+#define CK(x)                                                                          \
+  do {                                                                                 \
+    cudaError_t e_ = (x);                                                              \
+    if (e_ != cudaSuccess) {                                                           \
+      set_error(std::string(#x) + ": " + cudaGetErrorString(e_));                      \
+      return MG_ECUDA;                                                                 \
+    }                                                                                  \
+  } while (0)
+#define LK(x)                                                                          \
+  do {                                                                                 \
+    if ((x) != 0) {                                                                    \
+      cudaError_t e_ = cudaGetLastError();                                             \
+      set_error(std::string("launch failed: ") + #x + ": " + cudaGetErrorString(e_));  \
+      return e_ == cudaSuccess ? MG_EINVAL : MG_ECUDA;                                 \
+    }                                                                                  \
+  } while (0)
+#define RET(x)                      \
+  do {                              \
+    int r_ = (x);                   \
+    if (r_ != MG_OK) return r_;     \
+  } while (0)
+
+namespace {
+
+// Result-slot map (doubles) inside the reducer's slot array.
+const int kMaxRhs = 64;
+const int kMaxBasis = 64;  // GCR restart length cap (multiple of 8)
+inline size_t slot_level(int l) { return (size_t)l * 4 * kMaxRhs; }
+inline size_t slot_gcr_wr() { return slot_level(MG_MAX_LEVELS); }
+inline size_t slot_gcr_rn() { return slot_gcr_wr() + 4 * kMaxRhs; }
+inline size_t slot_gcr_bn() { return slot_gcr_rn() + 4 * kMaxRhs; }
+inline size_t slot_misc() { return slot_gcr_bn() + 4 * kMaxRhs; }
+inline size_t slot_beta() { return slot_misc() + 4 * kMaxRhs; }
+inline size_t slot_total() { return slot_beta() + (size_t)2 * kMaxBasis * kMaxRhs; }
+
+enum { WV_E, WV_RES, WV_P, WV_XC, WV_AXC, WV_RC, WV_EC, WV_T, WV_DT, WV_IN, WV_A, WV_B, WV_COUNT };
+
+int prec_of(const mg_handle* h, int l) {
+  if (!h->p.mixed) return MG_F64;
+  const int L = (int)h->lev.size();
+  if (l == 0) return h->p.fine_prec;
+  if (l == L - 1) return MG_F32;  // coarsest vectors; the inverse stays FP64
+  return h->p.coarse_prec;
+}
+
+Agg agg_of(const Level& a) {
+  Agg g;
+  for (int m = 0; m < 4; ++m) {
+    g.L[m] = a.L[m];
+    g.blk[m] = a.blk[m];
+    g.Lc[m] = a.Lc[m];
+  }
+  g.V = a.V;
+  g.ncomp = a.ncomp;
+  g.nhalf = a.nhalf;
+  g.nv = a.nv;
+  g.bsites = a.bsites;
+  g.Vc = a.Vc;
+  return g;
+}
+
+size_t bytes_of(int prec) { return prec == MG_F64 ? 16 : (prec == MG_F32 ? 8 : 4); }
+
+int check_prec(int prec) { return (prec >= 0 && prec <= 3) ? MG_OK : MG_EINVAL; }
+
+void* work(mg_handle* h, int l, int prec, int idx, int nrhs) {
+  if ((int)h->work.size() <= l) h->work.resize(l + 1);
+  auto& byprec = h->work[l];
+  if (byprec.empty()) byprec.resize(4);
+  auto& vecs = byprec[prec];
+  if ((int)vecs.size() <= idx) vecs.resize(idx + 1);
+  if (!vecs[idx]) vecs[idx].reset(new DevBuf());
+  const size_t need = h->lev[l]->n() * (size_t)nrhs * bytes_of(prec);
+  if (!vecs[idx]->ensure(need)) return nullptr;
+  return vecs[idx]->p;
+}
+
+int ensure_reducer(mg_handle* h, int nrhs) {
+  if (nrhs > kMaxRhs) {
+    set_error("nrhs above the library limit of 64");
+    return MG_EINVAL;
+  }
+  size_t need = (size_t)kMaxVecBlocks * 16 * ((kMaxBasis / 8) * (size_t)nrhs + 1);
+  for (auto& lp : h->lev) {
+    const Level& a = *lp;
+    size_t b = a.ncomp == 12 ? (size_t)wilson_blocks(a.V) : (size_t)coarse_blocks(a.ncomp, a.V);
+    need = std::max(need, b * 3 * (size_t)nrhs);
+  }
+  if (need <= h->red.max_partials && h->red.nslots) return MG_OK;
+  cudaStreamSynchronize(h->st);
+  if (!h->red.init(need, (int)slot_total(), 4096)) {
+    set_error("out of device memory for reduction scratch");
+    return MG_ENOMEM;
+  }
+  return MG_OK;
+}
+
+// out = a_ * (A_l in) + c_ * y; optional dots <out|z>, ||out||^2 into slot.
+int op_apply(mg_handle* h, int l, int prec, const void* in, void* out, const void* y, double a_, double c_,
+             const void* z, size_t slot, int nrhs) {
+  Level& a = *h->lev[l];
+  if (l == 0) {
+    if (!a.links[prec].p) {
+      set_error("level-0 operator not stored in this precision");
+      return MG_EINVAL;
+    }
+    DslashCall d;
+    d.prec = prec;
+    d.in = in;
+    d.out = out;
+    d.y = y;
+    d.z = z;
+    d.links = a.links[prec].p;
+    for (int m = 0; m < 4; ++m) d.L[m] = a.L[m];
+    d.a = a_ * (4.0 + h->mass);
+    d.b = -0.5 * a_;
+    d.c = c_;
+    d.nrhs = nrhs;
+    d.red = h->red.at(slot, 4);
+    LK(launch_wilson(d, h->st));
+  } else {
+    if (!a.cop[prec].p) {
+      set_error("coarse operator not stored in this precision");
+      return MG_EINVAL;
+    }
+    CoarseCall k;
+    k.prec = prec;
+    k.C = a.cop[prec].p;
+    k.in = in;
+    k.out = out;
+    k.y = y;
+    k.z = z;
+    for (int m = 0; m < 4; ++m) k.L[m] = a.L[m];
+    k.ncomp = a.ncomp;
+    k.a = a_;
+    k.c = c_;
+    k.nrhs = nrhs;
+    k.red = h->red.at(slot, 4);
+    LK(launch_coarse_apply(k, h->st));
+  }
+  return MG_OK;
+}
+
+int mr_update(mg_handle* h, int l, int prec, void* x_out, const void* x_in, const void* u, void* r_out,
+              const void* r_in, const void* p, size_t slot, double omega, int nrhs) {
+  MrUpdate m;
+  m.prec = prec;
+  m.n = h->lev[l]->n();
+  m.nrhs = nrhs;
+  m.x_out = x_out;
+  m.x_in = x_in;
+  m.u = u;
+  m.r_out = r_out;
+  m.r_in = r_in;
+  m.p = p;
+  m.dots = h->red.slot(slot);
+  m.dstride = 4;
+  m.omega = omega;
+  m.red = h->red.at(0, 0);
+  m.red.result = nullptr;
+  LK(launch_mr_update(m, h->st));
+  return MG_OK;
+}
+
+// `steps` MR steps on A_l x = b continuing from (x, res): if x_zero the
+// iterate is 0 and res is taken from b without an operator application.
+int mr_steps(mg_handle* h, int l, int prec, const void* b, void* x, bool x_zero, void* res, int steps, int nrhs) {
+  const size_t sl = slot_level(l);
+  void* p = work(h, l, prec, WV_P, nrhs);
+  if (!p) return MG_ENOMEM;
+  const double omega = h->p.omega;
+  if (steps == 0) {
+    if (x_zero) {
+      CK(cudaMemsetAsync(x, 0, h->lev[l]->n() * nrhs * bytes_of(prec), h->st));
+      CK(cudaMemcpyAsync(res, b, h->lev[l]->n() * nrhs * bytes_of(prec), cudaMemcpyDeviceToDevice, h->st));
+    }
+    return MG_OK;
+  }
+  for (int s = 0; s < steps; ++s) {
+    const void* rcur = (s == 0 && x_zero) ? b : res;
+    RET(op_apply(h, l, prec, rcur, p, nullptr, 1.0, 0.0, rcur, sl, nrhs));
+    RET(mr_update(h, l, prec, x, (s == 0 && x_zero) ? nullptr : x, rcur, res, rcur, p, sl, omega, nrhs));
+  }
+  return MG_OK;
+}
+
+int coarsest_solve(mg_handle* h, int l, int prec, const void* r, void* e, int nrhs) {
+  Level& a = *h->lev[l];
+  LK(launch_dense_matvec(prec, prec, a.N(), a.inv.as<double2>(), r, e, nrhs, h->st));
+  return MG_OK;
+}
+
+// e = V_l(r): one modified V(nu_pre, nu_post) cycle on level l.
+int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
+  const int L = (int)h->lev.size();
+  const int prec = prec_of(h, l);
+  if (l == L - 1) return coarsest_solve(h, l, prec, r, e, nrhs);
+  Level& a = *h->lev[l];
+  const int pc = prec_of(h, l + 1);
+  void* res = work(h, l, prec, WV_RES, nrhs);
+  void* xc = work(h, l, prec, WV_XC, nrhs);
+  void* axc = work(h, l, prec, WV_AXC, nrhs);
+  void* rc = work(h, l + 1, pc, WV_RC, nrhs);
+  void* ec = work(h, l + 1, pc, WV_EC, nrhs);
+  if (!res || !xc || !axc || !rc || !ec) {
+    set_error("out of device memory for V-cycle work vectors");
+    return MG_ENOMEM;
+  }
+  // pre-smoothing from e = 0
+  RET(mr_steps(h, l, prec, r, e, true, res, h->p.nu_pre, nrhs));
+  // restrict, coarse solve, prolong
+  const Agg g = agg_of(a);
+  LK(launch_restrict(prec, prec, pc, g, a.P[prec].p, res, rc, nrhs, h->st));
+  if (l + 1 == L - 1) {
+    RET(coarsest_solve(h, l + 1, pc, rc, ec, nrhs));
+  } else {
+    RET(vcycle(h, l + 1, rc, ec, nrhs));
+    void* t = work(h, l + 1, pc, WV_T, nrhs);
+    void* dt = work(h, l + 1, pc, WV_DT, nrhs);
+    if (!t || !dt) return MG_ENOMEM;
+    for (int c = 1; c < a.cycles; ++c) {
+      RET(op_apply(h, l + 1, pc, ec, t, rc, -1.0, 1.0, nullptr, 0, nrhs));
+      RET(vcycle(h, l + 1, t, dt, nrhs));
+      LK(launch_convert(pc, pc, h->lev[l + 1]->n(), nrhs, dt, ec, 1.0, nullptr, 0, 0.0, 1, h->st));
+    }
+  }
+  LK(launch_prolong(pc, prec, prec, g, a.P[prec].p, ec, xc, nrhs, h->st));
+  // alpha = <A x_c|r0> / <A x_c|A x_c>  (Eq. 3.5);  e += alpha x_c, r0 -= alpha A x_c
+  const size_t sl = slot_level(l);
+  RET(op_apply(h, l, prec, xc, axc, nullptr, 1.0, 0.0, res, sl, nrhs));
+  RET(mr_update(h, l, prec, e, e, xc, res, res, axc, sl, 1.0, nrhs));
+  // post-smoothing
+  RET(mr_steps(h, l, prec, res, e, false, res, h->p.nu_post, nrhs));
+  return MG_OK;
+}
+
+int read_slots(mg_handle* h, size_t off, int count) {
+  CK(cudaMemcpyAsync(h->host_slots, h->red.slot(off), count * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return MG_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+const char* mg_last_error(void) { return g_err.c_str(); }
+
+int mg_default_params(mg_params* p) {
+  if (!p) return MG_EINVAL;
+  memset(p, 0, sizeof(*p));
+  p->n_levels = 2;
+  for (int l = 0; l < MG_MAX_LEVELS - 1; ++l) {
+    for (int m = 0; m < 4; ++m) p->block[l][m] = 4;
+    p->nv[l] = 20;
+    p->setup_sweeps[l] = 20;
+    p->coarse_cycles[l] = 1;
+  }
+  p->coarse_cycles[0] = 4;
+  p->nu_pre = 2;
+  p->nu_post = 2;
+  p->omega = 0.8;
+  p->gcr_restart = 50;
+  p->max_iter = 2000;
+  p->mixed = 0;
+  p->fine_prec = MG_F16;
+  p->coarse_prec = MG_F32;
+  p->reliable_delta = 1e-4;
+  p->seed = 0;
+  return MG_OK;
+}
+
+int mg_destroy(mg_handle* h) {
+  if (!h) return MG_OK;
+  if (h->st) cudaStreamSynchronize(h->st);
+  if (h->host_slots) cudaFreeHost(h->host_slots);
+  delete h;
+  return MG_OK;
+}
+
+static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, const double* const* starts) {
+  const mg_params& p = h->p;
+  cudaStream_t st = h->st;
+  const int Lv = p.n_levels;
+  // ---- level 0 and the gauge field
+  h->lev.emplace_back(new Level());
+  Level& f = *h->lev[0];
+  for (int m = 0; m < 4; ++m) f.L[m] = h->dims[m];
+  f.V = f.L[0] * f.L[1] * f.L[2] * f.L[3];
+  f.ncomp = 12;
+  {
+    DevBuf ext;
+    const double* gdev = gauge;
+    const size_t gbytes = (size_t)4 * f.V * 9 * 16;
+    if (!gauge_on_device) {
+      if (!ext.ensure(gbytes)) return MG_ENOMEM;
+      CK(cudaMemcpyAsync(ext.p, gauge, gbytes, cudaMemcpyHostToDevice, st));
+      gdev = ext.as<double>();
+    }
+    std::vector<int> precs = {MG_F64};
+    if (p.mixed) {
+      precs.push_back(MG_F32);
+      if (p.fine_prec != MG_F32 && p.fine_prec != MG_F64) precs.push_back(p.fine_prec);
+    }
+    for (int pr : precs) {
+      const int NL = pr == MG_F64 ? 9 : 6;
+      if (!f.links[pr].ensure((size_t)4 * NL * f.V * bytes_of(pr))) return MG_ENOMEM;
+      LK(launch_pack_links(pr, gdev, f.links[pr].p, f.V, st));
+    }
+    CK(cudaStreamSynchronize(st));
+  }
+  RET(ensure_reducer(h, 1));
+  DevBuf errflag;
+  if (!errflag.ensure(sizeof(int))) return MG_ENOMEM;
+  CK(cudaMemsetAsync(errflag.p, 0, sizeof(int), st));
+  // ---- coarser levels
+  for (int l = 0; l + 1 < Lv; ++l) {
+    Level& a = *h->lev[l];
+    a.nv = p.nv[l];
+    a.sweeps = p.setup_sweeps[l];
+    a.cycles = p.coarse_cycles[l] < 1 ? 1 : p.coarse_cycles[l];
+    a.nhalf = a.ncomp / 2;
+    a.bsites = 1;
+    a.Vc = 1;
+    for (int m = 0; m < 4; ++m) {
+      a.blk[m] = p.block[l][m];
+      if (a.blk[m] < 1 || a.L[m] % a.blk[m]) {
+        set_error("level " + std::to_string(l) + ": extent not divisible by the block size");
+        return MG_EINVAL;
+      }
+      a.Lc[m] = a.L[m] / a.blk[m];
+      a.bsites *= a.blk[m];
+      a.Vc *= a.Lc[m];
+    }
+    if (a.nv < 1 || a.nv > a.nhalf * a.bsites) {
+      set_error("level " + std::to_string(l) + ": nv must be in [1, ncomp/2 * block sites]");
+      return MG_EINVAL;
+    }
+    RET(ensure_reducer(h, a.nv));
+    // candidates, FP64 internal [nv][ncomp][V]
+    DevBuf cand, rr, pp;
+    const size_t vb = a.n() * 16;
+    if (!cand.ensure(vb * a.nv) || !rr.ensure(vb * a.nv) || !pp.ensure(vb * a.nv)) return MG_ENOMEM;
+    if (starts && starts[l]) {
+      DevBuf ext;
+      if (!ext.ensure(vb * a.nv)) return MG_ENOMEM;
+      CK(cudaMemcpyAsync(ext.p, starts[l], vb * a.nv, cudaMemcpyHostToDevice, st));
+      LK(launch_ext_to_int(MG_F64, a.ncomp, a.V, a.nv, ext.p, cand.p, st));
+      CK(cudaStreamSynchronize(st));
+    } else {
+      LK(launch_gaussian_starts(p.seed + (uint64_t)l, a.nv, a.ncomp, a.V, cand.p, st));
+    }
+    // relax A x = 0 (Sec. 2 step 1-2): r = -A x, then MR steps
+    const size_t sl = slot_level(l);
+    if (a.sweeps > 0) {
+      RET(op_apply(h, l, MG_F64, cand.p, rr.p, nullptr, -1.0, 0.0, nullptr, 0, a.nv));
+      for (int s = 0; s < a.sweeps; ++s) {
+        RET(op_apply(h, l, MG_F64, rr.p, pp.p, nullptr, 1.0, 0.0, rr.p, sl, a.nv));
+        RET(mr_update(h, l, MG_F64, cand.p, cand.p, rr.p, rr.p, rr.p, pp.p, sl, p.omega, a.nv));
+      }
+    }
+    // unit-normalise every candidate
+    LK(launch_dot(MG_F64, a.n(), a.nv, cand.p, cand.p, h->red.at(slot_misc(), 4), st));
+    LK(launch_convert(MG_F64, MG_F64, a.n(), a.nv, cand.p, cand.p, 1.0, h->red.slot(slot_misc() + 2), 4, -0.5, 0,
+                      st));
+    // blockwise Gram-Schmidt into P (Eq. 2.3)
+    const Agg g = agg_of(a);
+    if (!a.P[MG_F64].ensure((size_t)a.Vc * 2 * a.nv * a.nhalf * a.bsites * 16)) return MG_ENOMEM;
+    LK(launch_block_gs(g, cand.as<double2>(), a.P[MG_F64].as<double2>(), errflag.as<int>(), st));
+    // Galerkin coarse operator, one column at a time
+    h->lev.emplace_back(new Level());
+    Level& c = *h->lev[l + 1];
+    for (int m = 0; m < 4; ++m) c.L[m] = a.Lc[m];
+    c.V = a.Vc;
+    c.ncomp = 2 * a.nv;
+    const int nc = c.ncomp;
+    if (!c.cop[MG_F64].ensure((size_t)9 * nc * nc * c.V * 16)) return MG_ENOMEM;
+    for (int j = 0; j < nc; ++j) {
+      LK(launch_p_column(g, a.P[MG_F64].as<double2>(), j, rr.as<double2>(), st));
+      if (l == 0)
+        LK(launch_galerkin_wilson(g, a.links[MG_F64].as<double2>(), h->mass, rr.as<double2>(),
+                                  a.P[MG_F64].as<double2>(), j, c.cop[MG_F64].as<double2>(), st));
+      else
+        LK(launch_galerkin_stencil(g, a.cop[MG_F64].as<double2>(), rr.as<double2>(), a.P[MG_F64].as<double2>(), j,
+                                   c.cop[MG_F64].as<double2>(), st));
+    }
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr == 2) {
+      set_error("block Gram-Schmidt lost rank on level " + std::to_string(l));
+      return MG_ERANK;
+    }
+  }
+  // ---- precision copies for the mixed V-cycle
+  for (int l = 0; l < Lv; ++l) {
+    Level& a = *h->lev[l];
+    const int pr = prec_of(h, l);
+    if (pr == MG_F64) continue;
+    if (l + 1 < Lv) {
+      const size_t np = (size_t)a.Vc * 2 * a.nv * a.nhalf * a.bsites;
+      if (!a.P[pr].ensure(np * bytes_of(pr))) return MG_ENOMEM;
+      LK(launch_convert(MG_F64, pr, np, 1, a.P[MG_F64].p, a.P[pr].p, 1.0, nullptr, 0, 0.0, 0, st));
+    }
+    if (l >= 1 && l + 1 < Lv) {
+      const size_t nc = (size_t)9 * a.ncomp * a.ncomp * a.V;
+      if (!a.cop[pr].ensure(nc * bytes_of(pr))) return MG_ENOMEM;
+      LK(launch_convert(MG_F64, pr, nc, 1, a.cop[MG_F64].p, a.cop[pr].p, 1.0, nullptr, 0, 0.0, 0, st));
+    }
+  }
+  // ---- coarsest level: dense FP64 inverse
+  if (Lv >= 2) {
+    Level& c = *h->lev[Lv - 1];
+    const size_t N = c.n();
+    if (N > 8192) {
+      set_error("coarsest level has " + std::to_string(N) + " unknowns; the dense solve takes at most 8192");
+      return MG_EINVAL;
+    }
+    DevBuf aug, col;
+    if (!aug.ensure(N * 2 * N * 16) || !col.ensure(N * 16) || !c.inv.ensure(N * N * 16)) return MG_ENOMEM;
+    CK(cudaMemsetAsync(errflag.p, 0, sizeof(int), st));
+    LK(dense_inverse(c.cop[MG_F64].as<double2>(), c.L, c.ncomp, aug.as<double2>(), col.as<double2>(),
+                     errflag.as<int>(), c.inv.as<double2>(), st));
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr) {
+      set_error("coarsest operator is singular (zero pivot)");
+      return MG_EINVAL;
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+int mg_setup(mg_handle** hout, const double* gauge, int gauge_on_device, const int dims[4], double mass,
+             const mg_params* p, const double* const* starts, void* stream) {
+  if (!hout) return MG_EINVAL;
+  *hout = nullptr;
+  if (!gauge || !dims || !p) {
+    set_error("null argument");
+    return MG_EINVAL;
+  }
+  for (int m = 0; m < 4; ++m)
+    if (dims[m] < 1) {
+      set_error("dims must be >= 1");
+      return MG_EINVAL;
+    }
+  if (p->n_levels < 1 || p->n_levels > MG_MAX_LEVELS || p->nu_pre < 0 || p->nu_post < 0 || p->gcr_restart < 1 ||
+      p->gcr_restart > kMaxBasis || !(p->omega > 0.0)) {
+    set_error("invalid mg_params (levels 1..4, restart 1..64, nu >= 0, omega > 0)");
+    return MG_EINVAL;
+  }
+  if (p->mixed && (check_prec(p->fine_prec) || p->fine_prec == MG_F64 || check_prec(p->coarse_prec) ||
+                   p->coarse_prec == MG_F64)) {
+    set_error("mixed precision needs fine_prec and coarse_prec in {F32, F16, BF16}");
+    return MG_EINVAL;
+  }
+  mg_handle* h = new mg_handle();
+  h->p = *p;
+  h->mass = mass;
+  for (int m = 0; m < 4; ++m) h->dims[m] = dims[m];
+  h->st = (cudaStream_t)stream;
+  if (cudaMallocHost((void**)&h->host_slots, slot_total() * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    set_error("pinned host allocation failed");
+    return MG_ENOMEM;
+  }
+  int rc = setup_impl(h, gauge, gauge_on_device, starts);
+  if (rc != MG_OK) {
+    mg_destroy(h);
+    return rc;
+  }
+  *hout = h;
+  return MG_OK;
+}
+
+int dslash_apply(mg_handle* h, int prec, const void* in, void* out, int nrhs, void* stream) {
+  if (!h || !in || !out || nrhs < 1 || check_prec(prec)) {
+    set_error("dslash_apply: bad argument");
+    return MG_EINVAL;
+  }
+  cudaStream_t keep = h->st;
+  h->st = (cudaStream_t)stream;
+  int rc = ensure_reducer(h, nrhs);
+  if (rc == MG_OK) rc = op_apply(h, 0, prec, in, out, nullptr, 1.0, 0.0, nullptr, 0, nrhs);
+  h->st = keep;
+  return rc;
+}
+
+int coarse_apply(mg_handle* h, int level, int prec, const void* in, void* out, int nrhs, void* stream) {
+  if (!h || level < 1 || level >= (int)h->lev.size() || !in || !out || nrhs < 1 || check_prec(prec)) {
+    set_error("coarse_apply: bad argument");
+    return MG_EINVAL;
+  }
+  cudaStream_t keep = h->st;
+  h->st = (cudaStream_t)stream;
+  int rc = ensure_reducer(h, nrhs);
+  if (rc == MG_OK) rc = op_apply(h, level, prec, in, out, nullptr, 1.0, 0.0, nullptr, 0, nrhs);
+  h->st = keep;
+  return rc;
+}
+
+int restrict_apply(mg_handle* h, int level, int prec, const void* in, void* out, int nrhs, void* stream) {
+  if (!h || level < 0 || level + 1 >= (int)h->lev.size() || !in || !out || nrhs < 1 || check_prec(prec) ||
+      !h->lev[level]->P[prec].p) {
+    set_error("restrict_apply: bad argument or prolongator not stored in this precision");
+    return MG_EINVAL;
+  }
+  Level& a = *h->lev[level];
+  const int pout = prec == MG_F64 ? MG_F64 : MG_F32;
+  LK(launch_restrict(prec, prec, pout, agg_of(a), a.P[prec].p, in, out, nrhs, (cudaStream_t)stream));
+  return MG_OK;
+}
+
+int prolong_apply(mg_handle* h, int level, int prec, const void* in, void* out, int nrhs, void* stream) {
+  if (!h || level < 0 || level + 1 >= (int)h->lev.size() || !in || !out || nrhs < 1 || check_prec(prec) ||
+      !h->lev[level]->P[prec].p) {
+    set_error("prolong_apply: bad argument or prolongator not stored in this precision");
+    return MG_EINVAL;
+  }
+  Level& a = *h->lev[level];
+  const int pin = prec == MG_F64 ? MG_F64 : MG_F32;
+  LK(launch_prolong(pin, prec, prec, agg_of(a), a.P[prec].p, in, out, nrhs, (cudaStream_t)stream));
+  return MG_OK;
+}
+
+int mr_apply(mg_handle* h, int level, int prec, const void* b, void* x, void* r, int steps, void* stream) {
+  if (!h || level < 0 || level >= (int)h->lev.size() || !b || !x || !r || steps < 0 || check_prec(prec)) {
+    set_error("mr_apply: bad argument");
+    return MG_EINVAL;
+  }
+  cudaStream_t keep = h->st;
+  h->st = (cudaStream_t)stream;
+  int rc = ensure_reducer(h, 1);
+  if (rc == MG_OK) rc = op_apply(h, level, prec, x, r, b, -1.0, 1.0, nullptr, 0, 1);
+  if (rc == MG_OK) rc = mr_steps(h, level, prec, b, x, false, r, steps, 1);
+  h->st = keep;
+  return rc;
+}
+
+int vcycle_apply(mg_handle* h, const void* r, void* e, void* stream) {
+  if (!h || !r || !e || h->lev.size() < 2 || h->p.mixed) {
+    set_error("vcycle_apply: needs a plain FP64 hierarchy with >= 2 levels");
+    return MG_EINVAL;
+  }
+  cudaStream_t keep = h->st;
+  h->st = (cudaStream_t)stream;
+  int rc = ensure_reducer(h, 1);
+  if (rc == MG_OK) rc = vcycle(h, 0, r, e, 1);
+  h->st = keep;
+  return rc;
+}
+
+int mg_field_to_internal(mg_handle* h, int level, int prec, const double* ext, int on_device, void* internal,
+                         int nrhs, void* stream) {
+  if (!h || level < 0 || level >= (int)h->lev.size() || !ext || !internal || nrhs < 1 || check_prec(prec)) {
+    set_error("mg_field_to_internal: bad argument");
+    return MG_EINVAL;
+  }
+  Level& a = *h->lev[level];
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf tmp;
+  const void* src = ext;
+  if (!on_device) {
+    if (!tmp.ensure(a.n() * nrhs * 16)) return MG_ENOMEM;
+    CK(cudaMemcpyAsync(tmp.p, ext, a.n() * nrhs * 16, cudaMemcpyHostToDevice, st));
+    src = tmp.p;
+  }
+  LK(launch_ext_to_int(prec, a.ncomp, a.V, nrhs, src, internal, st));
+  if (!on_device) CK(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+int mg_field_from_internal(mg_handle* h, int level, int prec, const void* internal, double* ext, int on_device,
+                           int nrhs, void* stream) {
+  if (!h || level < 0 || level >= (int)h->lev.size() || !ext || !internal || nrhs < 1 || check_prec(prec)) {
+    set_error("mg_field_from_internal: bad argument");
+    return MG_EINVAL;
+  }
+  Level& a = *h->lev[level];
+  cudaStream_t st = (cudaStream_t)stream;
+  if (on_device) {
+    LK(launch_int_to_ext(prec, a.ncomp, a.V, nrhs, internal, ext, st));
+    return MG_OK;
+  }
+  DevBuf tmp;
+  if (!tmp.ensure(a.n() * nrhs * 16)) return MG_ENOMEM;
+  LK(launch_int_to_ext(prec, a.ncomp, a.V, nrhs, internal, tmp.p, st));
+  CK(cudaMemcpyAsync(ext, tmp.p, a.n() * nrhs * 16, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+int mg_level_info(mg_handle* h, int level, int dims_out[4], int* ncomp, int* nv) {
+  if (!h || level < 0 || level >= (int)h->lev.size()) return MG_EINVAL;
+  Level& a = *h->lev[level];
+  if (dims_out)
+    for (int m = 0; m < 4; ++m) dims_out[m] = a.L[m];
+  if (ncomp) *ncomp = a.ncomp;
+  if (nv) *nv = a.nv;
+  return MG_OK;
+}
+
+int mg_get_prolongator(mg_handle* h, int level, double* out) {
+  if (!h || level < 0 || level + 1 >= (int)h->lev.size() || !out) return MG_EINVAL;
+  Level& a = *h->lev[level];
+  cudaStream_t st = h->st;
+  DevBuf f, tot, ext;
+  if (!f.ensure(a.n() * 16) || !tot.ensure(a.n() * 16) || !ext.ensure(a.n() * 16)) return MG_ENOMEM;
+  const Agg g = agg_of(a);
+  for (int k = 0; k < a.nv; ++k) {
+    LK(launch_p_column(g, a.P[MG_F64].as<double2>(), k, tot.as<double2>(), st));
+    LK(launch_p_column(g, a.P[MG_F64].as<double2>(), a.nv + k, f.as<double2>(), st));
+    LK(launch_convert(MG_F64, MG_F64, a.n(), 1, f.p, tot.p, 1.0, nullptr, 0, 0.0, 1, st));
+    LK(launch_int_to_ext(MG_F64, a.ncomp, a.V, 1, tot.p, ext.p, st));
+    CK(cudaMemcpyAsync(out + (size_t)k * a.n() * 2, ext.p, a.n() * 16, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+int mg_get_coarse_op(mg_handle* h, int level, double* out) {
+  if (!h || level < 1 || level >= (int)h->lev.size() || !out) return MG_EINVAL;
+  Level& a = *h->lev[level];
+  const size_t n = a.ncomp, V = a.V;
+  std::vector<double> tmp((size_t)9 * n * n * V * 2);
+  CK(cudaMemcpyAsync(tmp.data(), a.cop[MG_F64].p, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  // [9][i][j][B] -> [9][B][i][j]
+  for (size_t d = 0; d < 9; ++d)
+    for (size_t i = 0; i < n; ++i)
+      for (size_t j = 0; j < n; ++j)
+        for (size_t B = 0; B < V; ++B) {
+          const size_t src = (((d * n + i) * n + j) * V + B) * 2;
+          const size_t dst = (((d * V + B) * n + i) * n + j) * 2;
+          out[dst] = tmp[src];
+          out[dst + 1] = tmp[src + 1];
+        }
+  return MG_OK;
+}
+
+size_t mg_footprint(const int dims[4], const mg_params* p, int nrhs) {
+  if (!dims || !p) return 0;
+  size_t V = (size_t)dims[0] * dims[1] * dims[2] * dims[3];
+  size_t bytes = (size_t)4 * V * 9 * 16 * 2;                      // links + upload staging
+  const size_t vec = V * 12 * 16;                                  // one FP64 fine vector
+  bytes += vec * (size_t)nrhs * (2 * (size_t)p->gcr_restart + 8);  // GCR basis + work
+  size_t Vl = V, nc = 12;
+  for (int l = 0; l + 1 < p->n_levels; ++l) {
+    size_t bs = (size_t)p->block[l][0] * p->block[l][1] * p->block[l][2] * p->block[l][3];
+    bytes += Vl * nc * 16 * (size_t)p->nv[l] * 4;  // candidates, relaxation work, P
+    Vl /= bs;
+    nc = 2 * (size_t)p->nv[l];
+    bytes += 9 * nc * nc * Vl * 16 * 2;            // coarse stencil
+    bytes += Vl * nc * 16 * (size_t)nrhs * 10;     // coarse work vectors
+  }
+  if (p->n_levels >= 2) bytes += (Vl * nc) * (Vl * nc) * 16 * 3;  // dense inverse + scratch
+  return bytes;
+}
+
+}  // extern "C"
+
+// ====================================================================== solve
+namespace {
+
+int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on_device, double tol,
+              mg_stats* stats) {
+  cudaStream_t st = h->st;
+  Level& f = *h->lev[0];
+  const size_t n = f.n();
+  const bool mixed = h->p.mixed != 0;
+  const int pin = mixed ? MG_F32 : MG_F64;   // inner (Krylov) precision
+  const size_t bi = bytes_of(pin);
+  const int restart = h->p.gcr_restart;
+  RET(ensure_reducer(h, nrhs));
+  auto t0 = std::chrono::steady_clock::now();
+  // FP64 x, b, r in the internal layout
+  if (!h->gx64.ensure(n * nrhs * 16) || !h->gb64.ensure(n * nrhs * 16) || !h->gr64.ensure(n * nrhs * 16) ||
+      !h->gtmp.ensure(n * nrhs * 16))
+    return MG_ENOMEM;
+  {
+    const void* bsrc = b_ext;
+    const void* xsrc = x_ext;
+    DevBuf stage;
+    if (!on_device) {
+      if (!stage.ensure(n * nrhs * 16 * 2)) return MG_ENOMEM;
+      CK(cudaMemcpyAsync(stage.p, b_ext, n * nrhs * 16, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync((char*)stage.p + n * nrhs * 16, x_ext, n * nrhs * 16, cudaMemcpyHostToDevice, st));
+      bsrc = stage.p;
+      xsrc = (char*)stage.p + n * nrhs * 16;
+    }
+    LK(launch_ext_to_int(MG_F64, 12, f.V, nrhs, bsrc, h->gb64.p, st));
+    LK(launch_ext_to_int(MG_F64, 12, f.V, nrhs, xsrc, h->gx64.p, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  // Krylov buffers in precision pin: basis W, Z [restart][nrhs][n], x, r
+  const size_t vbytes = n * nrhs * bi;
+  if (!h->gW.ensure(vbytes * restart) || !h->gZ.ensure(vbytes * restart) || !h->gx.ensure(vbytes) ||
+      !h->gr.ensure(vbytes))
+    return MG_ENOMEM;
+  double* hs = h->host_slots;
+  std::vector<double> bn(nrhs), rn(nrhs);
+  LK(launch_dot(MG_F64, n, nrhs, h->gb64.p, h->gb64.p, h->red.at(slot_gcr_bn(), 4), st));
+  RET(read_slots(h, slot_gcr_bn(), 4 * nrhs));
+  for (int r = 0; r < nrhs; ++r) bn[r] = sqrt(hs[4 * r + 2]);
+  for (int r = 0; r < nrhs; ++r)
+    if (bn[r] == 0.0) {
+      set_error("mg_solve: zero right-hand side");
+      return MG_EINVAL;
+    }
+  std::vector<int> iters(nrhs, 0), done(nrhs, 0);
+  int restarts = 0, reliable = 0, status = MG_OK;
+  long long fine = 0, fine64 = 0;
+  const long long per_cycle = (h->lev.size() >= 2) ? (h->p.nu_pre + h->p.nu_post + 1) : 0;
+  int total_iters = 0;
+  // true residual r64 = b - D x64 (FP64)
+  auto true_residual = [&]() -> int {
+    RET(op_apply(h, 0, MG_F64, h->gx64.p, h->gr64.p, h->gb64.p, -1.0, 1.0, nullptr, 0, nrhs));
+    ++fine;
+    ++fine64;
+    LK(launch_dot(MG_F64, n, nrhs, h->gr64.p, h->gr64.p, h->red.at(slot_gcr_rn(), 4), st));
+    RET(read_slots(h, slot_gcr_rn(), 4 * nrhs));
+    for (int r = 0; r < nrhs; ++r) rn[r] = sqrt(h->host_slots[4 * r + 2]);
+    return MG_OK;
+  };
+  RET(true_residual());
+  bool all_done = true;
+  for (int r = 0; r < nrhs; ++r) {
+    if (!isfinite(rn[r])) return MG_ENAN;
+    done[r] = rn[r] <= tol * bn[r];
+    all_done &= (bool)done[r];
+  }
+  while (!all_done) {
+    if (total_iters >= h->p.max_iter) {
+      status = MG_ENOCONV;
+      break;
+    }
+    // start of a cycle: Krylov residual r = r64 (converted), x = 0
+    LK(launch_convert(MG_F64, pin, n, nrhs, h->gr64.p, h->gr.p, 1.0, nullptr, 0, 0.0, 0, st));
+    CK(cudaMemsetAsync(h->gx.p, 0, vbytes, st));
+    LK(launch_dot(pin, n, nrhs, h->gr.p, h->gr.p, h->red.at(slot_gcr_rn(), 4), st));
+    std::vector<double> r0 = rn;
+    int k = 0;
+    for (;;) {
+      char* zk = (char*)h->gZ.p + (size_t)k * vbytes;
+      char* wk = (char*)h->gW.p + (size_t)k * vbytes;
+      // z = M r
+      if (h->lev.size() >= 2) {
+        const int pf = prec_of(h, 0);
+        if (pf == pin) {
+          RET(vcycle(h, 0, h->gr.p, zk, nrhs));
+        } else {
+          void* rin = work(h, 0, pf, WV_IN, nrhs);
+          void* eout = work(h, 0, pf, WV_A, nrhs);
+          if (!rin || !eout) return MG_ENOMEM;
+          // scale the residual to RMS 1/8 per component for 16-bit storage
+          const double sig = sqrt((double)n) / 8.0;
+          LK(launch_convert(pin, pf, n, nrhs, h->gr.p, rin, sig, h->red.slot(slot_gcr_rn() + 2), 4, -0.5, 0, st));
+          RET(vcycle(h, 0, rin, eout, nrhs));
+          LK(launch_convert(pf, pin, n, nrhs, eout, zk, 1.0 / sig, h->red.slot(slot_gcr_rn() + 2), 4, 0.5, 0, st));
+        }
+        fine += per_cycle;
+      } else {
+        CK(cudaMemcpyAsync(zk, h->gr.p, vbytes, cudaMemcpyDeviceToDevice, st));
+      }
+      // w = D z
+      RET(op_apply(h, 0, pin, zk, wk, nullptr, 1.0, 0.0, nullptr, 0, nrhs));
+      ++fine;
+      if (pin == MG_F64) ++fine64;
+      // classical Gram-Schmidt, twice, against the previous w's
+      if (k == 0) {
+        LK(launch_dot(pin, n, nrhs, wk, h->gr.p, h->red.at(slot_gcr_wr(), 4), st));
+      } else {
+        for (int pass = 0; pass < 2; ++pass) {
+          LK(launch_multidot(pin, n, nrhs, k, kMaxBasis, h->gW.p, n * nrhs, wk, h->red.at(slot_beta(), 0), st));
+          RedArgs r2 = h->red.at(slot_gcr_wr(), 4);
+          LK(launch_multiaxpy(pin, n, nrhs, k, kMaxBasis, h->red.slot(slot_beta()), h->gW.p, h->gZ.p, n * nrhs, wk,
+                              zk, h->gr.p, r2, st));
+        }
+      }
+      LK(launch_gcr_update(pin, pin, n, nrhs, h->red.slot(slot_gcr_wr()), 4, wk, zk, h->gx.p, h->gr.p,
+                           h->red.at(slot_gcr_rn() + 2, 4), st));
+      RET(read_slots(h, slot_gcr_rn(), 4 * nrhs));
+      ++k;
+      ++total_iters;
+      bool inner_done = true;
+      for (int r = 0; r < nrhs; ++r) {
+        const double v = sqrt(hs[4 * r + 2]);
+        if (!isfinite(v)) {
+          set_error("mg_solve: residual norm is not finite");
+          return MG_ENAN;
+        }
+        if (!done[r]) ++iters[r];
+        const double target = mixed ? std::max(tol * bn[r] * 0.5, h->p.reliable_delta * r0[r]) : tol * bn[r];
+        if (!done[r] && v > target) inner_done = false;
+      }
+      if (inner_done || k == restart || total_iters >= h->p.max_iter) break;
+    }
+    // x64 += x (the cycle's correction), then the true residual in FP64
+    LK(launch_convert(pin, MG_F64, n, nrhs, h->gx.p, h->gx64.p, 1.0, nullptr, 0, 0.0, 1, st));
+    RET(true_residual());
+    if (k == restart) ++restarts;
+    ++reliable;
+    all_done = true;
+    for (int r = 0; r < nrhs; ++r) {
+      if (!isfinite(rn[r])) {
+        set_error("mg_solve: true residual is not finite");
+        return MG_ENAN;
+      }
+      if (!done[r] && rn[r] <= tol * bn[r]) done[r] = 1;
+      all_done &= (bool)done[r];
+    }
+  }
+  // result back to the external layout
+  {
+    DevBuf stage;
+    void* dst = x_ext;
+    if (!on_device) {
+      if (!stage.ensure(n * nrhs * 16)) return MG_ENOMEM;
+      dst = stage.p;
+    }
+    LK(launch_int_to_ext(MG_F64, 12, f.V, nrhs, h->gx64.p, dst, st));
+    if (!on_device) CK(cudaMemcpyAsync(x_ext, stage.p, n * nrhs * 16, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) {
+    for (int r = 0; r < nrhs; ++r) {
+      stats[r].iters = iters[r];
+      stats[r].restarts = restarts;
+      stats[r].reliable_updates = reliable;
+      stats[r].fine_dslash = fine;
+      stats[r].fine_dslash_f64 = fine64;
+      stats[r].true_rel_residual = rn[r] / bn[r];
+      stats[r].solve_seconds = secs;
+    }
+  }
+  return status;
+}
+
+}  // namespace
+
+extern "C" int mg_solve(mg_handle* h, const double* b, double* x, int nrhs, int on_device, double tol,
+                        mg_stats* stats, void* stream) {
+  if (!h || !b || !x || nrhs < 1 || !(tol > 0.0)) {
+    set_error("mg_solve: bad argument");
+    return MG_EINVAL;
+  }
+  cudaStream_t keep = h->st;
+  h->st = (cudaStream_t)stream;
+  int rc = gcr_solve(h, b, x, nrhs, on_device, tol, stats);
+  h->st = keep;
+  return rc;
+}

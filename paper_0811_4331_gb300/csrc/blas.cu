@@ -1,0 +1,400 @@
+// Vector kernels of the solver: MR and alpha-step updates (Sec. 3), GCR
+// Gram-Schmidt and updates (Sec. 5), precision conversion, layout transposes
+// and the counter-based start vectors of the null-vector setup (Sec. 2).
+//
+// All reductions are deterministic (fixed grid, last-block finish, see
+// grid_reduce) and accumulate in FP64 per thread.  Grids are capped at
+// 8 blocks per SM (1216 on 152 SMs) with grid-stride loops, so every vector
+// kernel is one coalesced streaming pass over its operands.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace wmg {
+
+int vec_blocks(size_t n) {
+  size_t b = (n + kVecThreads - 1) / kVecThreads;
+  if (b > (size_t)kMaxVecBlocks) b = kMaxVecBlocks;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+static inline bool launched() { return cudaGetLastError() == cudaSuccess; }
+
+// ------------------------------------------------------------------ MR update
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads) mr_update_kernel(const MrUpdate m) {
+  typedef typename Store<S>::R R;
+  const int rhs = blockIdx.y;
+  const double* d = m.dots + (size_t)rhs * m.dstride;
+  const double den = d[2];
+  double ar = 0.0, ai = 0.0;
+  if (den > 0.0 && isfinite(den)) {
+    ar = m.omega * d[0] / den;
+    ai = m.omega * d[1] / den;
+  }
+  const cx<R> alpha = mk<R>((R)ar, (R)ai);
+  const size_t off = (size_t)rhs * m.n;
+  S* xo = (S*)m.x_out + off;
+  const S* xi = m.x_in ? (const S*)m.x_in + off : nullptr;
+  const S* u = (const S*)m.u + off;
+  S* ro = (S*)m.r_out + off;
+  const S* ri = (const S*)m.r_in + off;
+  const S* p = (const S*)m.p + off;
+  double red[1] = {0.0};
+  for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < m.n; i += (size_t)gridDim.x * kVecThreads) {
+    cx<R> x = xi ? ldc<R>(xi, i) : zero<R>();
+    x = cfma(alpha, ldc<R>(u, i), x);
+    cx<R> r = ldc<R>(ri, i);
+    r = r - alpha * ldc<R>(p, i);
+    stc(xo, i, x);
+    stc(ro, i, r);
+    red[0] += (double)norm2(as_stored<S>(r));
+  }
+  if (m.red.result) grid_reduce<1, kVecThreads>(red, m.red, rhs);
+}
+
+int launch_mr_update(const MrUpdate& m, cudaStream_t st) {
+  dim3 grid(vec_blocks(m.n), m.nrhs);
+  switch (m.prec) {
+    case 0: mr_update_kernel<double2><<<grid, kVecThreads, 0, st>>>(m); break;
+    case 1: mr_update_kernel<float2><<<grid, kVecThreads, 0, st>>>(m); break;
+    case 2: mr_update_kernel<__half2><<<grid, kVecThreads, 0, st>>>(m); break;
+    case 3: mr_update_kernel<__nv_bfloat162><<<grid, kVecThreads, 0, st>>>(m); break;
+    default: return -1;
+  }
+  return launched() ? 0 : -1;
+}
+
+// ------------------------------------------------------------------ dot
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads) dot_kernel(size_t n, const S* a, const S* b, RedArgs ra) {
+  typedef typename Store<S>::R R;
+  const int rhs = blockIdx.y;
+  a += (size_t)rhs * n;
+  b += (size_t)rhs * n;
+  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
+    cx<R> x = ldc<R>(a, i), y = ldc<R>(b, i);
+    cx<R> d = cmul_conj(x, y);
+    red[0] += (double)d.re;
+    red[1] += (double)d.im;
+    red[2] += (double)norm2(x);
+    red[3] += (double)norm2(y);
+  }
+  grid_reduce<4, kVecThreads>(red, ra, rhs);
+}
+
+int launch_dot(int prec, size_t n, int nrhs, const void* a, const void* b, RedArgs red, cudaStream_t st) {
+  dim3 grid(vec_blocks(n), nrhs);
+  switch (prec) {
+    case 0: dot_kernel<double2><<<grid, kVecThreads, 0, st>>>(n, (const double2*)a, (const double2*)b, red); break;
+    case 1: dot_kernel<float2><<<grid, kVecThreads, 0, st>>>(n, (const float2*)a, (const float2*)b, red); break;
+    case 2: dot_kernel<__half2><<<grid, kVecThreads, 0, st>>>(n, (const __half2*)a, (const __half2*)b, red); break;
+    case 3:
+      dot_kernel<__nv_bfloat162>
+          <<<grid, kVecThreads, 0, st>>>(n, (const __nv_bfloat162*)a, (const __nv_bfloat162*)b, red);
+      break;
+    default: return -1;
+  }
+  return launched() ? 0 : -1;
+}
+
+// ------------------------------------------------------------------ GCR Gram-Schmidt
+// One block row computes CH dots <W_j|w> for j in [chunk * CH, chunk * CH + CH).
+constexpr int kChunk = 8;
+
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads)
+    multidot_kernel(size_t n, int k, int kmax, const S* W, size_t jstride, const S* w, RedArgs ra) {
+  typedef typename Store<S>::R R;
+  const int chunk = blockIdx.y, rhs = blockIdx.z;
+  const int j0 = chunk * kChunk;
+  const S* wr = w + (size_t)rhs * n;
+  double red[2 * kChunk];
+#pragma unroll
+  for (int q = 0; q < 2 * kChunk; ++q) red[q] = 0.0;
+  for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
+    const cx<R> x = ldc<R>(wr, i);
+#pragma unroll
+    for (int q = 0; q < kChunk; ++q) {
+      if (j0 + q < k) {
+        cx<R> d = cmul_conj(ldc<R>(W + (size_t)(j0 + q) * jstride + (size_t)rhs * n, i), x);
+        red[2 * q] += (double)d.re;
+        red[2 * q + 1] += (double)d.im;
+      }
+    }
+  }
+  // lane = rhs * nchunks + chunk; the result is laid out so that beta_j of
+  // rhs r sits at result[(r * kmax + j) * 2]: stride between lanes is 2 CH
+  // within one rhs, 2 kmax between rhs.
+  RedArgs r2 = ra;
+  r2.result = ra.result + (size_t)rhs * kmax * 2 + (size_t)chunk * 2 * kChunk - (size_t)(rhs * gridDim.y + chunk) * 2 * kChunk;
+  r2.stride = 2 * kChunk;
+  grid_reduce<2 * kChunk, kVecThreads>(red, r2, rhs * gridDim.y + chunk);
+}
+
+int launch_multidot(int prec, size_t n, int nrhs, int k, int kmax, const void* W, size_t jstride, const void* w,
+                    RedArgs red, cudaStream_t st) {
+  if (k <= 0) return 0;
+  if (kmax % kChunk) return -1;
+  dim3 grid(vec_blocks(n), (k + kChunk - 1) / kChunk, nrhs);
+  switch (prec) {
+    case 0:
+      multidot_kernel<double2><<<grid, kVecThreads, 0, st>>>(n, k, kmax, (const double2*)W, jstride, (const double2*)w, red);
+      break;
+    case 1:
+      multidot_kernel<float2><<<grid, kVecThreads, 0, st>>>(n, k, kmax, (const float2*)W, jstride, (const float2*)w, red);
+      break;
+    default: return -1;
+  }
+  return launched() ? 0 : -1;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads)
+    multiaxpy_kernel(size_t n, int k, int kmax, const double* beta, const S* W, const S* Zb, size_t jstride, S* w,
+                     S* z, const S* r, RedArgs ra) {
+  typedef typename Store<S>::R R;
+  const int rhs = blockIdx.y;
+  const size_t off = (size_t)rhs * n;
+  const double* bt = beta + (size_t)rhs * kmax * 2;
+  double red[3] = {0.0, 0.0, 0.0};
+  for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
+    cx<R> wv = ldc<R>(w + off, i), zv = ldc<R>(z + off, i);
+    for (int j = 0; j < k; ++j) {
+      const cx<R> b = mk<R>((R)bt[2 * j], (R)bt[2 * j + 1]);
+      wv = wv - b * ldc<R>(W + (size_t)j * jstride + off, i);
+      zv = zv - b * ldc<R>(Zb + (size_t)j * jstride + off, i);
+    }
+    stc(w + off, i, wv);
+    stc(z + off, i, zv);
+    const cx<R> ws = as_stored<S>(wv);
+    const cx<R> d = cmul_conj(ws, ldc<R>(r + off, i));
+    red[0] += (double)d.re;
+    red[1] += (double)d.im;
+    red[2] += (double)norm2(ws);
+  }
+  if (ra.result) grid_reduce<3, kVecThreads>(red, ra, rhs);
+}
+
+int launch_multiaxpy(int prec, size_t n, int nrhs, int k, int kmax, const double* beta, const void* W,
+                     const void* Zb, size_t jstride, void* w, void* z, const void* r, RedArgs red2, cudaStream_t st) {
+  dim3 grid(vec_blocks(n), nrhs);
+  switch (prec) {
+    case 0:
+      multiaxpy_kernel<double2><<<grid, kVecThreads, 0, st>>>(n, k, kmax, beta, (const double2*)W, (const double2*)Zb,
+                                                              jstride, (double2*)w, (double2*)z, (const double2*)r, red2);
+      break;
+    case 1:
+      multiaxpy_kernel<float2><<<grid, kVecThreads, 0, st>>>(n, k, kmax, beta, (const float2*)W, (const float2*)Zb,
+                                                             jstride, (float2*)w, (float2*)z, (const float2*)r, red2);
+      break;
+    default: return -1;
+  }
+  return launched() ? 0 : -1;
+}
+
+template <typename S, typename SX>
+__global__ void __launch_bounds__(kVecThreads)
+    gcr_update_kernel(size_t n, const double* dots, int dstride, S* w, S* z, SX* x, S* r, RedArgs ra) {
+  typedef typename Store<S>::R R;
+  typedef typename Store<SX>::R RX;
+  const int rhs = blockIdx.y;
+  const double* d = dots + (size_t)rhs * dstride;
+  const double nw2 = d[2];
+  double inv = 0.0, ar = 0.0, ai = 0.0;
+  if (nw2 > 0.0 && isfinite(nw2)) {
+    inv = 1.0 / sqrt(nw2);
+    ar = d[0] * inv;
+    ai = d[1] * inv;
+  }
+  const R s = (R)inv;
+  const cx<R> a = mk<R>((R)ar, (R)ai);
+  const cx<RX> ax = mk<RX>((RX)ar, (RX)ai);
+  const size_t off = (size_t)rhs * n;
+  double red[1] = {0.0};
+  for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
+    const cx<R> wv = as_stored<S>(s * ldc<R>(w + off, i));
+    const cx<R> zv = as_stored<S>(s * ldc<R>(z + off, i));
+    stc(w + off, i, wv);
+    stc(z + off, i, zv);
+    cx<RX> xv = ldc<RX>(x + off, i);
+    xv = cfma(ax, mk<RX>((RX)zv.re, (RX)zv.im), xv);
+    stc(x + off, i, xv);
+    cx<R> rv = ldc<R>(r + off, i) - a * wv;
+    stc(r + off, i, rv);
+    red[0] += (double)norm2(as_stored<S>(rv));
+  }
+  grid_reduce<1, kVecThreads>(red, ra, rhs);
+}
+
+int launch_gcr_update(int prec, int xprec, size_t n, int nrhs, const double* dots, int dstride, void* w, void* z,
+                      void* x, void* r, RedArgs red, cudaStream_t st) {
+  dim3 grid(vec_blocks(n), nrhs);
+  if (prec == 0 && xprec == 0)
+    gcr_update_kernel<double2, double2><<<grid, kVecThreads, 0, st>>>(n, dots, dstride, (double2*)w, (double2*)z,
+                                                                       (double2*)x, (double2*)r, red);
+  else if (prec == 1 && xprec == 1)
+    gcr_update_kernel<float2, float2><<<grid, kVecThreads, 0, st>>>(n, dots, dstride, (float2*)w, (float2*)z,
+                                                                     (float2*)x, (float2*)r, red);
+  else if (prec == 1 && xprec == 0)
+    gcr_update_kernel<float2, double2><<<grid, kVecThreads, 0, st>>>(n, dots, dstride, (float2*)w, (float2*)z,
+                                                                      (double2*)x, (float2*)r, red);
+  else
+    return -1;
+  return launched() ? 0 : -1;
+}
+
+// ------------------------------------------------------------------ conversions
+template <typename SI, typename SO>
+__global__ void __launch_bounds__(kVecThreads) convert_kernel(size_t n, const SI* in, SO* out, double s0,
+                                                              const double* slot, int sstride, double sexp, int acc) {
+  const int rhs = blockIdx.y;
+  double s = s0;
+  if (slot) {
+    const double v = slot[(size_t)rhs * sstride];
+    s *= (sexp == 0.5) ? sqrt(v) : (sexp == -0.5 ? (v > 0.0 ? 1.0 / sqrt(v) : 0.0) : pow(v, sexp));
+  }
+  const size_t off = (size_t)rhs * n;
+  for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
+    if (sizeof(typename Store<SI>::R) == 8 || sizeof(typename Store<SO>::R) == 8) {
+      cx<double> v = ldc<double>(in + off, i);
+      v = s * v;
+      if (acc) v = v + ldc<double>(out + off, i);
+      stc(out + off, i, v);
+    } else {
+      cx<float> v = ldc<float>(in + off, i);
+      v = (float)s * v;
+      if (acc) v = v + ldc<float>(out + off, i);
+      stc(out + off, i, v);
+    }
+  }
+}
+
+template <typename SI>
+static int convert_to(int pout, dim3 grid, size_t n, const void* in, void* out, double s0, const double* slot,
+                      int sstride, double sexp, int acc, cudaStream_t st) {
+  const SI* i = (const SI*)in;
+  switch (pout) {
+    case 0: convert_kernel<SI, double2><<<grid, kVecThreads, 0, st>>>(n, i, (double2*)out, s0, slot, sstride, sexp, acc); break;
+    case 1: convert_kernel<SI, float2><<<grid, kVecThreads, 0, st>>>(n, i, (float2*)out, s0, slot, sstride, sexp, acc); break;
+    case 2: convert_kernel<SI, __half2><<<grid, kVecThreads, 0, st>>>(n, i, (__half2*)out, s0, slot, sstride, sexp, acc); break;
+    case 3:
+      convert_kernel<SI, __nv_bfloat162>
+          <<<grid, kVecThreads, 0, st>>>(n, i, (__nv_bfloat162*)out, s0, slot, sstride, sexp, acc);
+      break;
+    default: return -1;
+  }
+  return launched() ? 0 : -1;
+}
+
+int launch_convert(int pin, int pout, size_t n, int nrhs, const void* in, void* out, double s0, const double* slot,
+                   int sstride, double sexp, int accumulate, cudaStream_t st) {
+  dim3 grid(vec_blocks(n), nrhs);
+  switch (pin) {
+    case 0: return convert_to<double2>(pout, grid, n, in, out, s0, slot, sstride, sexp, accumulate, st);
+    case 1: return convert_to<float2>(pout, grid, n, in, out, s0, slot, sstride, sexp, accumulate, st);
+    case 2: return convert_to<__half2>(pout, grid, n, in, out, s0, slot, sstride, sexp, accumulate, st);
+    case 3: return convert_to<__nv_bfloat162>(pout, grid, n, in, out, s0, slot, sstride, sexp, accumulate, st);
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------------ layouts
+template <typename S>
+__global__ void ext_to_int_kernel(int ncomp, int V, int nrhs, const double2* ext, S* out) {
+  const size_t tot = (size_t)nrhs * ncomp * V;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
+    // i indexes the internal layout [r][c][s]
+    const int s = (int)(i % V);
+    const size_t rc = i / V;
+    const int c = (int)(rc % ncomp);
+    const size_t r = rc / ncomp;
+    const double2 v = ext[(r * V + s) * ncomp + c];
+    stc(out, i, mk<double>(v.x, v.y));
+  }
+}
+
+template <typename S>
+__global__ void int_to_ext_kernel(int ncomp, int V, int nrhs, const S* in, double2* ext) {
+  const size_t tot = (size_t)nrhs * ncomp * V;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
+    // i indexes the external layout [r][s][c]
+    const int c = (int)(i % ncomp);
+    const size_t rs = i / ncomp;
+    const int s = (int)(rs % V);
+    const size_t r = rs / V;
+    const cx<double> v = ldc<double>(in, (r * ncomp + c) * V + s);
+    ext[i] = make_double2(v.re, v.im);
+  }
+}
+
+static unsigned grid_for(size_t tot) {
+  size_t b = (tot + 255) / 256;
+  if (b > 8192) b = 8192;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+int launch_ext_to_int(int prec, int ncomp, int V, int nrhs, const void* ext, void* internal, cudaStream_t st) {
+  const unsigned g = grid_for((size_t)nrhs * ncomp * V);
+  const double2* e = (const double2*)ext;
+  switch (prec) {
+    case 0: ext_to_int_kernel<double2><<<g, 256, 0, st>>>(ncomp, V, nrhs, e, (double2*)internal); break;
+    case 1: ext_to_int_kernel<float2><<<g, 256, 0, st>>>(ncomp, V, nrhs, e, (float2*)internal); break;
+    case 2: ext_to_int_kernel<__half2><<<g, 256, 0, st>>>(ncomp, V, nrhs, e, (__half2*)internal); break;
+    case 3: ext_to_int_kernel<__nv_bfloat162><<<g, 256, 0, st>>>(ncomp, V, nrhs, e, (__nv_bfloat162*)internal); break;
+    default: return -1;
+  }
+  return launched() ? 0 : -1;
+}
+
+int launch_int_to_ext(int prec, int ncomp, int V, int nrhs, const void* internal, void* ext, cudaStream_t st) {
+  const unsigned g = grid_for((size_t)nrhs * ncomp * V);
+  double2* e = (double2*)ext;
+  switch (prec) {
+    case 0: int_to_ext_kernel<double2><<<g, 256, 0, st>>>(ncomp, V, nrhs, (const double2*)internal, e); break;
+    case 1: int_to_ext_kernel<float2><<<g, 256, 0, st>>>(ncomp, V, nrhs, (const float2*)internal, e); break;
+    case 2: int_to_ext_kernel<__half2><<<g, 256, 0, st>>>(ncomp, V, nrhs, (const __half2*)internal, e); break;
+    case 3:
+      int_to_ext_kernel<__nv_bfloat162><<<g, 256, 0, st>>>(ncomp, V, nrhs, (const __nv_bfloat162*)internal, e);
+      break;
+    default: return -1;
+  }
+  return launched() ? 0 : -1;
+}
+
+// ------------------------------------------------------------------ start vectors
+__device__ __forceinline__ uint64_t splitmix64_out(uint64_t state, uint64_t m) {
+  uint64_t z = state + (m + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void gaussian_starts_kernel(uint64_t seed, int nv, int ncomp, int V, double2* out) {
+  const size_t tot = (size_t)nv * ncomp * V;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
+    // i indexes the internal layout [k][c][s]; the stream index is k V ncomp + s ncomp + c
+    const int s = (int)(i % V);
+    const size_t kc = i / V;
+    const int c = (int)(kc % ncomp);
+    const size_t k = kc / ncomp;
+    const uint64_t e = (k * V + s) * ncomp + c;
+    const uint64_t x1 = splitmix64_out(seed, 2 * e), x2 = splitmix64_out(seed, 2 * e + 1);
+    const double u1 = ((double)(x1 >> 11) + 1.0) * 0x1.0p-53;
+    const double u2 = ((double)(x2 >> 11) + 1.0) * 0x1.0p-53;
+    const double rad = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    out[i] = make_double2(rad * cs, rad * sn);
+  }
+}
+
+int launch_gaussian_starts(uint64_t seed, int nv, int ncomp, int V, void* out, cudaStream_t st) {
+  gaussian_starts_kernel<<<grid_for((size_t)nv * ncomp * V), 256, 0, st>>>(seed, nv, ncomp, V, (double2*)out);
+  return launched() ? 0 : -1;
+}
+
+}  // namespace wmg

@@ -1,0 +1,116 @@
+// Internal state of an mg_handle and device-memory helpers (host code).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/wilson_mg.h"
+#include "kernels.h"
+
+namespace wmg {
+
+void set_error(const std::string& msg);
+
+// Owning device buffer.  The library allocates with cudaMalloc and frees on
+// destruction; nothing is shared between handles.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  // (Re)allocate to at least n bytes; returns false on failure.
+  bool ensure(size_t n) {
+    if (n <= bytes && p) return true;
+    release();
+    if (n == 0) n = 16;
+    if (cudaMalloc(&p, n) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return false;
+    }
+    bytes = n;
+    return true;
+  }
+  template <typename T>
+  T* as() const {
+    return (T*)p;
+  }
+};
+
+struct Level {
+  int L[4] = {0, 0, 0, 0};
+  int V = 0;
+  int ncomp = 0;  // 12 on level 0, 2 nv_{l-1} on level l >= 1
+  // coarsening to level l+1 (nv == 0 on the coarsest level)
+  int nv = 0;
+  int blk[4] = {1, 1, 1, 1};
+  int bsites = 0;  // sites per aggregate
+  int nhalf = 0;   // components per chirality = ncomp / 2
+  int Lc[4] = {0, 0, 0, 0};
+  int Vc = 0;
+  int sweeps = 0;
+  int cycles = 1;
+  // operator of this level, per storage precision (index = precision code)
+  DevBuf links[4];  // level 0: [4][NL][V]
+  DevBuf cop[4];    // level >= 1: stencil [9][ncomp][ncomp][V]
+  // prolongator to level l+1, per precision: [Vc][2][nv][nhalf][bsites]
+  DevBuf P[4];
+  // coarsest level: dense FP64 inverse [N][N], N = ncomp V
+  DevBuf inv;
+  int N() const { return ncomp * V; }
+  size_t n() const { return (size_t)ncomp * V; }
+};
+
+struct Reducer {
+  DevBuf partials, tickets, slots;
+  size_t max_partials = 0;  // doubles
+  int nslots = 0;
+  bool init(size_t partial_doubles, int slots_doubles, int ntickets) {
+    if (!partials.ensure(partial_doubles * sizeof(double))) return false;
+    if (!tickets.ensure((size_t)ntickets * sizeof(unsigned))) return false;
+    if (!slots.ensure((size_t)slots_doubles * sizeof(double))) return false;
+    if (cudaMemset(tickets.p, 0, (size_t)ntickets * sizeof(unsigned)) != cudaSuccess) return false;
+    if (cudaMemset(slots.p, 0, (size_t)slots_doubles * sizeof(double)) != cudaSuccess) return false;
+    max_partials = partial_doubles;
+    nslots = slots_doubles;
+    return true;
+  }
+  // Reduction descriptor writing into result slot `slot` (doubles offset).
+  RedArgs at(size_t slot, int stride) const {
+    RedArgs r;
+    r.partials = partials.as<double>();
+    r.tickets = tickets.as<unsigned>();
+    r.result = slots.as<double>() + slot;
+    r.stride = stride;
+    return r;
+  }
+  double* slot(size_t off) const { return slots.as<double>() + off; }
+};
+
+}  // namespace wmg
+
+struct mg_handle {
+  mg_params p;
+  double mass = 0.0;
+  int dims[4] = {0, 0, 0, 0};
+  cudaStream_t st = nullptr;
+  std::vector<std::unique_ptr<wmg::Level>> lev;
+  wmg::Reducer red;
+  // work vectors: [level][precision][index]
+  std::vector<std::vector<std::vector<std::unique_ptr<wmg::DevBuf>>>> work;
+  int work_nrhs = 0;
+  // outer solver buffers
+  wmg::DevBuf gx, gr, gw, gz, gW, gZ, gb64, gx64, gr64, gtmp;
+  int basis_cap = 0;  // vectors held by gW / gZ per rhs
+  wmg::DevBuf err_flag;  // device int set by setup kernels on failure
+  double* host_slots = nullptr;  // pinned mirror for read-backs
+};

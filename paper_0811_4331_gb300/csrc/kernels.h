@@ -1,0 +1,144 @@
+// Host-side launch interface shared by the translation units of the library.
+// Precision codes: 0 = FP64, 1 = FP32, 2 = FP16, 3 = BF16 (storage of complex
+// elements); arithmetic is FP64 for code 0 and FP32 otherwise.  Every
+// launcher returns 0 on success and -1 on an invalid argument or launch error.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace wmg {
+
+// ------------------------------------------------------------------ fine stencil
+struct DslashCall {
+  int prec;
+  const void* in;
+  void* out;
+  const void* y;      // optional: out += c * y
+  const void* z;      // optional: reduce <out|z>, ||out||^2 into red.result
+  const void* links;  // packed links of precision prec
+  int L[4];
+  double a, b, c;     // out = a in + b Hop(in) + c y
+  int nrhs;
+  RedArgs red;        // lane = right-hand side, 3 values
+};
+int launch_wilson(const DslashCall& d, cudaStream_t st);
+int wilson_blocks(int V);
+int launch_pack_links(int prec, const void* ext, void* out, int V, cudaStream_t st);
+
+// ------------------------------------------------------------------ vectors
+// Every vector kernel works on nrhs vectors of n complex elements each,
+// right-hand side r at offset r * n.  Grid sizes are a pure function of n.
+int vec_blocks(size_t n);
+const int kVecThreads = 256;
+const int kMaxVecBlocks = 1216;  // 152 SMs x 8
+
+// x_out = (x_in or 0) + alpha u;  r_out = r_in - alpha p, with per-rhs
+// alpha = omega * (d[0] + i d[1]) / d[2] read from dots[rhs * dstride]
+// (alpha = 0 when d[2] is 0 or not finite).  Optional reduction of
+// ||r_out||^2 into red (lane rhs, 1 value).
+struct MrUpdate {
+  int prec;
+  size_t n;
+  int nrhs;
+  void* x_out;
+  const void* x_in;  // may be null (zero) or equal to x_out
+  const void* u;
+  void* r_out;
+  const void* r_in;  // may equal r_out
+  const void* p;
+  const double* dots;
+  int dstride;
+  double omega;
+  RedArgs red;  // red.result == null: no reduction
+};
+int launch_mr_update(const MrUpdate& m, cudaStream_t st);
+
+// <a|b>, ||a||^2, ||b||^2 per rhs into red (4 values: re, im, |a|^2, |b|^2).
+int launch_dot(int prec, size_t n, int nrhs, const void* a, const void* b, RedArgs red, cudaStream_t st);
+
+// Classical Gram-Schmidt pieces for flexible GCR.
+// Basis vector j of rhs r at base + j * jstride + r * n (elements).
+// multidot: beta_j = <W_j|w> for j < k -> result[(r * kmax + j) * 2 + {0,1}] (red.stride
+// ignored; result holds kmax complex per rhs).
+int launch_multidot(int prec, size_t n, int nrhs, int k, int kmax, const void* W, size_t jstride,
+                    const void* w, RedArgs red, cudaStream_t st);
+// w -= sum_j beta_j W_j, z -= sum_j beta_j Z_j (beta from multidot result);
+// then reduce ||w||^2 and <w|r> per rhs into red2 (3 values: re, im, |w|^2).
+int launch_multiaxpy(int prec, size_t n, int nrhs, int k, int kmax, const double* beta, const void* W,
+                     const void* Zb, size_t jstride, void* w, void* z, const void* r, RedArgs red2,
+                     cudaStream_t st);
+// GCR step from dots = (<w|r>, ||w||^2) per rhs: w /= |w|, z /= |w|,
+// a = <w|r> / |w|, x += a z, r -= a w; reduce ||r||^2 into red (1 value).
+// x may have a different precision (xprec) than the others.
+int launch_gcr_update(int prec, int xprec, size_t n, int nrhs, const double* dots, int dstride, void* w,
+                      void* z, void* x, void* r, RedArgs red, cudaStream_t st);
+
+// out = scale * in (+ out if accumulate), converting precision.  scale =
+// s0 * (slot ? pow(slot[rhs * sstride], sexp) : 1).
+int launch_convert(int pin, int pout, size_t n, int nrhs, const void* in, void* out, double s0,
+                   const double* slot, int sstride, double sexp, int accumulate, cudaStream_t st);
+
+// External [nrhs][V][ncomp] FP64 complex <-> internal [nrhs][ncomp][V] of precision prec.
+int launch_ext_to_int(int prec, int ncomp, int V, int nrhs, const void* ext, void* internal, cudaStream_t st);
+int launch_int_to_ext(int prec, int ncomp, int V, int nrhs, const void* internal, void* ext, cudaStream_t st);
+
+// Counter-based Gaussian start vectors (SplitMix64 + Box-Muller), FP64
+// internal layout [nv][ncomp][V]; element (k, site, comp) is stream element
+// k V ncomp + site ncomp + comp of stream `seed`.
+int launch_gaussian_starts(uint64_t seed, int nv, int ncomp, int V, void* out, cudaStream_t st);
+
+// ------------------------------------------------------------------ coarse levels
+struct CoarseCall {
+  int prec;
+  const void* C;  // [9][ncomp][ncomp][V]
+  const void* in;
+  void* out;
+  const void* y;  // optional: out = a A in + c y
+  const void* z;  // optional dots <out|z>, ||out||^2
+  int L[4];
+  int ncomp;
+  double a, c;
+  int nrhs;
+  RedArgs red;
+};
+int launch_coarse_apply(const CoarseCall& k, cudaStream_t st);
+int coarse_blocks(int ncomp, int V);
+
+// Aggregation of level l (fine side) into level l+1 (coarse side).
+struct Agg {
+  int L[4];
+  int V;
+  int ncomp;
+  int nhalf;
+  int nv;
+  int blk[4];
+  int bsites;
+  int Lc[4];
+  int Vc;
+};
+int launch_restrict(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
+                    cudaStream_t st);
+int launch_prolong(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
+                   cudaStream_t st);
+
+// Coarsest level: dense inverse (Gauss-Jordan, partial pivoting, FP64) of
+// a stencil operator; aug is [N][2N] scratch, colbuf [N], inv [N][N];
+// *err = 1 on a zero pivot.
+int dense_inverse(const double2* C, const int L[4], int n, double2* aug, double2* colbuf, int* err, double2* inv,
+                  cudaStream_t st);
+int launch_dense_matvec(int pin, int pout, int N, const double2* inv, const void* x, void* y, int nrhs,
+                        cudaStream_t st);
+
+// Setup: blockwise Gram-Schmidt (err = 2 on rank loss), prolongator
+// columns as fields, Galerkin coarse stencil column j.
+int launch_block_gs(const Agg& g, const double2* cand, double2* P, int* err, cudaStream_t st);
+int launch_p_column(const Agg& g, const double2* P, int j, double2* v, cudaStream_t st);
+int launch_galerkin_wilson(const Agg& g, const double2* links64, double mass, const double2* vj, const double2* P,
+                           int j, double2* Cout, cudaStream_t st);
+int launch_galerkin_stencil(const Agg& g, const double2* Cfine, const double2* vj, const double2* P, int j,
+                            double2* Cout, cudaStream_t st);
+
+}  // namespace wmg

@@ -1,0 +1,278 @@
+// Setup kernels of the adaptive multigrid (FP64 throughout):
+//
+// * blockwise Gram-Schmidt of the candidate vectors into P (Sec. 2, adaptive
+//   step 3 and Eq. 2.3: P V_c = V with P^+ P = 1), one aggregate and
+//   chirality per CTA (chirality kept intact, Sec. 3 after Eq. 3.2 and the
+//   blocking of Sec. 5), modified Gram-Schmidt applied twice in candidate
+//   order;
+// * the Galerkin coarse operator A_c = P^+ A P (Sec. 2) as a 9-point stencil:
+//   column j of every block C_d'(B) comes from one CTA per aggregate that
+//   applies each fine hop A_d to the prolongator column j and projects the
+//   result onto the rows of P, sorting each fine hop into the coarse
+//   direction d' it crosses (d' = 0 when it stays inside the aggregate).
+#include "common.cuh"
+#include "kernels.h"
+#include "wilson_hop.cuh"
+
+namespace wmg {
+
+static inline bool launched() { return cudaGetLastError() == cudaSuccess; }
+
+__device__ __forceinline__ int agg_site2(const Agg& g, int B, int s) {
+  int cb[4], cl[4], cf[4];
+  site_coords(B, g.Lc, cb);
+  site_coords(s, g.blk, cl);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) cf[m] = cb[m] * g.blk[m] + cl[m];
+  return site_index(cf, g.L);
+}
+
+// Deterministic block sum of one complex value (FP64); result valid in all threads.
+template <int NT>
+__device__ __forceinline__ cx<double> block_csum(cx<double> v, double* sm) {
+  double a[2] = {v.re, v.im};
+  block_sum<2, NT>(a, sm);
+  __shared__ double out[2];
+  if (threadIdx.x == 0) {
+    out[0] = a[0];
+    out[1] = a[1];
+  }
+  __syncthreads();
+  cx<double> r = mk<double>(out[0], out[1]);
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------------ block Gram-Schmidt
+template <int NT>
+__global__ void __launch_bounds__(NT) block_gs_kernel(const Agg g, const double2* cand, double2* P, int* err) {
+  __shared__ double sm[2 * (NT / 32)];
+  const int B = blockIdx.x >> 1, chi = blockIdx.x & 1;
+  const int nv = g.nv, nh = g.nhalf, bs = g.bsites;
+  const int len = nh * bs;
+  double2* base = P + ((size_t)B * 2 + chi) * nv * len;
+  for (int k = 0; k < nv; ++k) {
+    double2* q = base + (size_t)k * len;
+    // gather candidate k restricted to (B, chi)
+    double nrm0 = 0.0;
+    for (int e = threadIdx.x; e < len; e += NT) {
+      const int c = e / bs, s = e - c * bs;
+      const double2 v = cand[((size_t)k * g.ncomp + chi * nh + c) * g.V + agg_site2(g, B, s)];
+      q[e] = v;
+      nrm0 += v.x * v.x + v.y * v.y;
+    }
+    const double orig = block_csum<NT>(mk<double>(nrm0, 0.0), sm).re;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int j = 0; j < k; ++j) {
+        const double2* pj = base + (size_t)j * len;
+        cx<double> d = zero<double>();
+        for (int e = threadIdx.x; e < len; e += NT)
+          d = cfma_conj(mk<double>(pj[e].x, pj[e].y), mk<double>(q[e].x, q[e].y), d);
+        d = block_csum<NT>(d, sm);
+        for (int e = threadIdx.x; e < len; e += NT) {
+          const cx<double> v = mk<double>(q[e].x, q[e].y) - d * mk<double>(pj[e].x, pj[e].y);
+          q[e] = make_double2(v.re, v.im);
+        }
+        __syncthreads();
+      }
+    }
+    double nrm = 0.0;
+    for (int e = threadIdx.x; e < len; e += NT) nrm += q[e].x * q[e].x + q[e].y * q[e].y;
+    nrm = block_csum<NT>(mk<double>(nrm, 0.0), sm).re;
+    const double nq = sqrt(nrm);
+    if (!(nq > 1e-12 * sqrt(orig))) {
+      if (threadIdx.x == 0) atomicExch(err, 2);
+      return;
+    }
+    const double inv = 1.0 / nq;
+    for (int e = threadIdx.x; e < len; e += NT) q[e] = make_double2(q[e].x * inv, q[e].y * inv);
+    __syncthreads();
+  }
+}
+
+int launch_block_gs(const Agg& g, const double2* cand, double2* P, int* err, cudaStream_t st) {
+  block_gs_kernel<256><<<g.Vc * 2, 256, 0, st>>>(g, cand, P, err);
+  return launched() ? 0 : -1;
+}
+
+// Column j of P (j = chi' nv + k') as a level-l field [ncomp][V]: the k'-th
+// orthonormal vector on its chirality chi' half, zero on the other half.
+__global__ void p_column_kernel(const Agg g, const double2* P, int j, double2* v) {
+  const size_t tot = (size_t)g.ncomp * g.V;
+  const int chi = j / g.nv, k = j - chi * g.nv;
+  const int len = g.nhalf * g.bsites;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / g.V), site = (int)(e % g.V);
+    double2 val = make_double2(0.0, 0.0);
+    if (c / g.nhalf == chi) {
+      int cf[4], cb[4], cl[4];
+      site_coords(site, g.L, cf);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        cb[m] = cf[m] / g.blk[m];
+        cl[m] = cf[m] - cb[m] * g.blk[m];
+      }
+      const int B = site_index(cb, g.Lc), s = site_index(cl, g.blk);
+      val = P[(((size_t)B * 2 + chi) * g.nv + k) * len + (size_t)(c - chi * g.nhalf) * g.bsites + s];
+    }
+    v[e] = val;
+  }
+}
+
+int launch_p_column(const Agg& g, const double2* P, int j, double2* v, cudaStream_t st) {
+  size_t tot = (size_t)g.ncomp * g.V;
+  size_t b = (tot + 255) / 256;
+  if (b > 8192) b = 8192;
+  p_column_kernel<<<(unsigned)b, 256, 0, st>>>(g, P, j, v);
+  return launched() ? 0 : -1;
+}
+
+// ------------------------------------------------------------------ Galerkin build
+// h = A_d(n) v(n + e_d) on every site of aggregate B into sm_h[c][s].
+struct WilsonHopOp {
+  const double2* U;  // FP64 links, 18 reals: [4][9][V]
+  double mass;
+  __device__ void apply(const Agg& g, int B, int d, const double2* v, cx<double>* h, int nt) const {
+    for (int s = threadIdx.x; s < g.bsites; s += nt) {
+      const int n = agg_site2(g, B, s);
+      cx<double> acc[4][3];
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[sp][a] = zero<double>();
+      if (d == 0) {
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) acc[sp][a] = (4.0 + mass) * ldc<double>(v, (size_t)(sp * 3 + a) * g.V + n);
+      } else {
+        int c[4];
+        site_coords(n, g.L, c);
+        const int nb = neighbor(c, g.L, d);
+        const int mu = (d - 1) >> 1;
+        const bool fwd = d & 1;
+        Link<double> u;
+        load_link<double, double2, 9>(u, U, mu, g.V, fwd ? n : nb);
+        switch (d) {
+          case 1: hop<0, true>(acc, v, g.V, nb, u); break;
+          case 2: hop<0, false>(acc, v, g.V, nb, u); break;
+          case 3: hop<1, true>(acc, v, g.V, nb, u); break;
+          case 4: hop<1, false>(acc, v, g.V, nb, u); break;
+          case 5: hop<2, true>(acc, v, g.V, nb, u); break;
+          case 6: hop<2, false>(acc, v, g.V, nb, u); break;
+          case 7: hop<3, true>(acc, v, g.V, nb, u); break;
+          default: hop<3, false>(acc, v, g.V, nb, u); break;
+        }
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) acc[sp][a] = -0.5 * acc[sp][a];
+      }
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) h[(sp * 3 + a) * g.bsites + s] = acc[sp][a];
+    }
+  }
+};
+
+struct StencilHopOp {
+  const double2* C;  // [9][n][n][V] of the level being coarsened
+  __device__ void apply(const Agg& g, int B, int d, const double2* v, cx<double>* h, int nt) const {
+    const int n = g.ncomp;
+    for (int e = threadIdx.x; e < n * g.bsites; e += nt) {
+      const int i = e / g.bsites, s = e - i * g.bsites;
+      const int site = agg_site2(g, B, s);
+      int c[4];
+      site_coords(site, g.L, c);
+      const int nb = neighbor(c, g.L, d);
+      cx<double> acc = zero<double>();
+      const double2* row = C + ((size_t)(d * n + i) * n) * g.V + site;
+      for (int j = 0; j < n; ++j) acc = cfma(ldc<double>(row, (size_t)j * g.V), ldc<double>(v, (size_t)j * g.V + nb), acc);
+      h[e] = acc;
+    }
+  }
+};
+
+// Does the hop d from aggregate-local site s leave the aggregate?
+__device__ __forceinline__ bool crosses(const Agg& g, int s, int d) {
+  if (d == 0) return false;
+  int cl[4];
+  site_coords(s, g.blk, cl);
+  const int mu = (d - 1) >> 1;
+  return (d & 1) ? (cl[mu] == g.blk[mu] - 1) : (cl[mu] == 0);
+}
+
+template <typename Op, int NT>
+__global__ void __launch_bounds__(NT) galerkin_kernel(const Agg g, Op op, const double2* vj, const double2* P, int j,
+                                                      double2* Cout) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<double>* h = (cx<double>*)smem_raw;                     // [ncomp][bsites]
+  cx<double>* acc0 = h + (size_t)g.ncomp * g.bsites;         // [2 nv]
+  const int B = blockIdx.x;
+  const int nc = 2 * g.nv;  // coarse components
+  const int len = g.nhalf * g.bsites;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < nc; i += NT) acc0[i] = zero<double>();
+  __syncthreads();
+  for (int d = 0; d < 9; ++d) {
+    op.apply(g, B, d, vj, h, NT);
+    __syncthreads();
+    for (int row = warp; row < nc; row += NT / 32) {
+      const int chi = row / g.nv;
+      const double2* pr = P + ((size_t)B * 2 * g.nv + row) * len;
+      const cx<double>* hv = h + (size_t)chi * len;
+      cx<double> in = zero<double>(), out = zero<double>();
+      for (int e = lane; e < len; e += 32) {
+        const int s = e % g.bsites;
+        const cx<double> t = cmul_conj(ldc<double>(pr, e), hv[e]);
+        if (crosses(g, s, d))
+          out = out + t;
+        else
+          in = in + t;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        in.re += __shfl_down_sync(0xffffffffu, in.re, o);
+        in.im += __shfl_down_sync(0xffffffffu, in.im, o);
+        out.re += __shfl_down_sync(0xffffffffu, out.re, o);
+        out.im += __shfl_down_sync(0xffffffffu, out.im, o);
+      }
+      if (lane == 0) {
+        acc0[row] = acc0[row] + in;
+        if (d > 0) Cout[((size_t)(d * nc + row) * nc + j) * g.Vc + B] = make_double2(out.re, out.im);
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < nc; i += NT) Cout[((size_t)(0 * nc + i) * nc + j) * g.Vc + B] = make_double2(acc0[i].re, acc0[i].im);
+}
+
+template <typename Op>
+static int galerkin_t(const Agg& g, const Op& op, const double2* vj, const double2* P, int j, double2* Cout,
+                      cudaStream_t st) {
+  constexpr int NT = 256;
+  const size_t sm = ((size_t)g.ncomp * g.bsites + 2 * g.nv) * sizeof(cx<double>);
+  if (sm > 200 * 1024) return -1;
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(galerkin_kernel<Op, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  galerkin_kernel<Op, NT><<<g.Vc, NT, sm, st>>>(g, op, vj, P, j, Cout);
+  return launched() ? 0 : -1;
+}
+
+int launch_galerkin_wilson(const Agg& g, const double2* links64, double mass, const double2* vj, const double2* P,
+                           int j, double2* Cout, cudaStream_t st) {
+  WilsonHopOp op;
+  op.U = links64;
+  op.mass = mass;
+  return galerkin_t(g, op, vj, P, j, Cout, st);
+}
+
+int launch_galerkin_stencil(const Agg& g, const double2* Cfine, const double2* vj, const double2* P, int j,
+                            double2* Cout, cudaStream_t st) {
+  StencilHopOp op;
+  op.C = Cfine;
+  return galerkin_t(g, op, vj, P, j, Cout, st);
+}
+
+}  // namespace wmg

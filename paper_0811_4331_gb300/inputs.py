@@ -87,6 +87,21 @@ def random_gauge(dims, seed, eps=0.3):
     return random_su3(rng, 4 * V, eps).reshape((4,) + lat + (3, 3))
 
 
+def random_gauge_fast(dims, seed, eps=0.3):
+    """SU(3) field reunitarize(1 + eps (A - A^+)/2) with A Gaussian complex.
+
+    A cheap generator for lattices where the eigen-decomposition of every
+    link would take minutes; used where only the memory traffic of the
+    operator matters, not the distribution of the links.
+    """
+    rng = np.random.default_rng(seed)
+    lat = _shape(dims)
+    shp = (4,) + lat + (3, 3)
+    A = rng.standard_normal(shp) + 1j * rng.standard_normal(shp)
+    M = np.eye(3) + 0.5 * eps * (A - np.conj(np.swapaxes(A, -1, -2)))
+    return reunitarize(M)
+
+
 def unit_gauge(dims):
     lat = _shape(dims)
     U = np.zeros((4,) + lat + (3, 3), dtype=np.complex128)

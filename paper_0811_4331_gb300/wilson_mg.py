@@ -1,0 +1,298 @@
+"""Thin ctypes binding of the C ABI in include/wilson_mg.h (argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Host arrays are
+numpy (C-contiguous); device arrays are torch CUDA tensors (contiguous).  No
+arithmetic of the solver happens here: if the CUDA library is missing the
+import of this module fails, there is no fallback.
+
+Layouts (see the header): external spinors are complex128 arrays shaped
+(nrhs, Lt, Lz, Ly, Lx, 4, 3) (or without the leading nrhs); internal fields
+are (nrhs, ncomp, V) complex in the precision named by ``prec``: complex128
+(MG_F64), complex64 (MG_F32), or a trailing pair of float16 / bfloat16
+(MG_F16 / MG_BF16).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwilsonmg.so")
+
+MG_OK, MG_EINVAL, MG_ENOMEM, MG_ECUDA, MG_ERANK, MG_ENOCONV, MG_EBREAKDOWN, MG_ENAN = range(8)
+MG_F64, MG_F32, MG_F16, MG_BF16 = range(4)
+MG_MAX_LEVELS = 4
+STATUS_NAMES = ["MG_OK", "MG_EINVAL", "MG_ENOMEM", "MG_ECUDA", "MG_ERANK", "MG_ENOCONV", "MG_EBREAKDOWN", "MG_ENAN"]
+
+
+class mg_params(ctypes.Structure):
+    _fields_ = [
+        ("n_levels", ctypes.c_int),
+        ("block", (ctypes.c_int * 4) * (MG_MAX_LEVELS - 1)),
+        ("nv", ctypes.c_int * (MG_MAX_LEVELS - 1)),
+        ("setup_sweeps", ctypes.c_int * (MG_MAX_LEVELS - 1)),
+        ("coarse_cycles", ctypes.c_int * (MG_MAX_LEVELS - 1)),
+        ("nu_pre", ctypes.c_int),
+        ("nu_post", ctypes.c_int),
+        ("omega", ctypes.c_double),
+        ("gcr_restart", ctypes.c_int),
+        ("max_iter", ctypes.c_int),
+        ("mixed", ctypes.c_int),
+        ("fine_prec", ctypes.c_int),
+        ("coarse_prec", ctypes.c_int),
+        ("reliable_delta", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class mg_stats(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int),
+        ("restarts", ctypes.c_int),
+        ("reliable_updates", ctypes.c_int),
+        ("fine_dslash", ctypes.c_longlong),
+        ("fine_dslash_f64", ctypes.c_longlong),
+        ("true_rel_residual", ctypes.c_double),
+        ("solve_seconds", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class MgError(RuntimeError):
+    def __init__(self, status, msg, stats=None):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 8 else status, msg))
+        self.status = status
+        self.stats = stats
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libwilsonmg.so is not built (run __graft_entry__.build()); no fallback exists")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, VP = ctypes.POINTER, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    sig = {
+        "mg_last_error": (ctypes.c_char_p, []),
+        "mg_default_params": (I, [P(mg_params)]),
+        "mg_setup": (I, [P(VP), VP, I, P(I), D, P(mg_params), VP, VP]),
+        "mg_destroy": (I, [VP]),
+        "mg_solve": (I, [VP, VP, VP, I, I, D, P(mg_stats), VP]),
+        "dslash_apply": (I, [VP, I, VP, VP, I, VP]),
+        "coarse_apply": (I, [VP, I, I, VP, VP, I, VP]),
+        "restrict_apply": (I, [VP, I, I, VP, VP, I, VP]),
+        "prolong_apply": (I, [VP, I, I, VP, VP, I, VP]),
+        "mr_apply": (I, [VP, I, I, VP, VP, VP, I, VP]),
+        "vcycle_apply": (I, [VP, VP, VP, VP]),
+        "mg_field_to_internal": (I, [VP, I, I, VP, I, VP, I, VP]),
+        "mg_field_from_internal": (I, [VP, I, I, VP, VP, I, I, VP]),
+        "mg_level_info": (I, [VP, I, P(I), P(I), P(I)]),
+        "mg_get_prolongator": (I, [VP, I, VP]),
+        "mg_get_coarse_op": (I, [VP, I, VP]),
+        "mg_footprint": (ctypes.c_size_t, [P(I), P(mg_params), I]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+# every entry point declared in include/wilson_mg.h
+EXPORTS = ["mg_last_error", "mg_default_params", "mg_setup", "mg_destroy", "mg_solve", "dslash_apply",
+           "coarse_apply", "restrict_apply", "prolong_apply", "mr_apply", "vcycle_apply", "mg_field_to_internal",
+           "mg_field_from_internal", "mg_level_info", "mg_get_prolongator", "mg_get_coarse_op", "mg_footprint"]
+
+
+def mg_last_error():
+    return LIB.mg_last_error().decode()
+
+
+def _check(status, stats=None):
+    if status != MG_OK:
+        raise MgError(status, mg_last_error(), stats)
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data), 0
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(a.data_ptr()), (1 if a.is_cuda else 0)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def mg_default_params(**kw):
+    p = mg_params()
+    _check(LIB.mg_default_params(ctypes.byref(p)))
+    for k, v in kw.items():
+        if k in ("block",):
+            for l, b in enumerate(v):
+                for m in range(4):
+                    p.block[l][m] = int(b[m])
+        elif k in ("nv", "setup_sweeps", "coarse_cycles"):
+            arr = getattr(p, k)
+            for l, x in enumerate(v):
+                arr[l] = int(x)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Handle:
+    """Owns an mg_handle*; freed by mg_destroy (explicitly or on garbage collection)."""
+
+    def __init__(self, ptr, dims):
+        self.ptr = ptr
+        self.dims = tuple(dims)
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                LIB.mg_destroy(self.ptr)
+        except Exception:
+            pass
+        self.ptr = None
+
+
+def mg_setup(gauge, dims, mass, params, starts=None, stream=None):
+    """Build the hierarchy.  gauge: (4, Lt, Lz, Ly, Lx, 3, 3) complex128, numpy or CUDA tensor.
+
+    starts: None or a list (one entry per coarsening) of numpy arrays of nv start
+    vectors in the external layout of that level (None entries use the
+    on-device generator).
+    """
+    gp, gdev = _ptr(gauge)
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    keep = []
+    sp = None
+    if starts is not None:
+        arr = (ctypes.c_void_p * (MG_MAX_LEVELS - 1))()
+        for l, s in enumerate(starts):
+            if s is None:
+                arr[l] = None
+            else:
+                s = np.ascontiguousarray(s, dtype=np.complex128)
+                keep.append(s)
+                arr[l] = s.ctypes.data
+        sp = ctypes.cast(arr, ctypes.c_void_p)
+        keep.append(arr)
+    h = ctypes.c_void_p()
+    _check(LIB.mg_setup(ctypes.byref(h), gp, gdev, d, float(mass), ctypes.byref(params), sp, _stream(stream)))
+    return Handle(h, dims)
+
+
+def mg_destroy(h):
+    if h.ptr:
+        _check(LIB.mg_destroy(h.ptr))
+        h.ptr = None
+
+
+def mg_solve(h, b, x, tol, stream=None, raise_on_noconv=True):
+    """Solve D x = b in place on x.  Returns (status, [stats dict per rhs])."""
+    shp = b.shape
+    nrhs = 1 if len(shp) == 6 else int(shp[0])
+    st = (mg_stats * nrhs)()
+    bp, bdev = _ptr(b)
+    xp, xdev = _ptr(x)
+    if bdev != xdev:
+        raise ValueError("b and x must both be host arrays or both device tensors")
+    status = LIB.mg_solve(h.ptr, bp, xp, nrhs, bdev, float(tol), st, _stream(stream))
+    stats = [s.as_dict() for s in st]
+    if status != MG_OK and (status != MG_ENOCONV or raise_on_noconv):
+        raise MgError(status, mg_last_error(), stats)
+    return status, stats
+
+
+def dslash_apply(h, prec, inp, out, nrhs=1, stream=None):
+    _check(LIB.dslash_apply(h.ptr, prec, _ptr(inp)[0], _ptr(out)[0], nrhs, _stream(stream)))
+
+
+def coarse_apply(h, level, prec, inp, out, nrhs=1, stream=None):
+    _check(LIB.coarse_apply(h.ptr, level, prec, _ptr(inp)[0], _ptr(out)[0], nrhs, _stream(stream)))
+
+
+def restrict_apply(h, level, prec, inp, out, nrhs=1, stream=None):
+    _check(LIB.restrict_apply(h.ptr, level, prec, _ptr(inp)[0], _ptr(out)[0], nrhs, _stream(stream)))
+
+
+def prolong_apply(h, level, prec, inp, out, nrhs=1, stream=None):
+    _check(LIB.prolong_apply(h.ptr, level, prec, _ptr(inp)[0], _ptr(out)[0], nrhs, _stream(stream)))
+
+
+def mr_apply(h, level, prec, b, x, r, steps, stream=None):
+    _check(LIB.mr_apply(h.ptr, level, prec, _ptr(b)[0], _ptr(x)[0], _ptr(r)[0], steps, _stream(stream)))
+
+
+def vcycle_apply(h, r, e, stream=None):
+    _check(LIB.vcycle_apply(h.ptr, _ptr(r)[0], _ptr(e)[0], _stream(stream)))
+
+
+def mg_field_to_internal(h, level, prec, ext, internal, nrhs=1, stream=None):
+    ep, edev = _ptr(ext)
+    _check(LIB.mg_field_to_internal(h.ptr, level, prec, ep, edev, _ptr(internal)[0], nrhs, _stream(stream)))
+
+
+def mg_field_from_internal(h, level, prec, internal, ext, nrhs=1, stream=None):
+    ep, edev = _ptr(ext)
+    _check(LIB.mg_field_from_internal(h.ptr, level, prec, _ptr(internal)[0], ep, edev, nrhs, _stream(stream)))
+
+
+def mg_level_info(h, level):
+    d = (ctypes.c_int * 4)()
+    nc = ctypes.c_int()
+    nv = ctypes.c_int()
+    _check(LIB.mg_level_info(h.ptr, level, d, ctypes.byref(nc), ctypes.byref(nv)))
+    return tuple(d), nc.value, nv.value
+
+
+def mg_get_prolongator(h, level):
+    dims, nc, nv = mg_level_info(h, level)
+    V = int(np.prod(dims))
+    out = np.empty((nv, V, nc), dtype=np.complex128)
+    _check(LIB.mg_get_prolongator(h.ptr, level, ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def mg_get_coarse_op(h, level):
+    dims, nc, _ = mg_level_info(h, level)
+    V = int(np.prod(dims))
+    out = np.empty((9, V, nc, nc), dtype=np.complex128)
+    _check(LIB.mg_get_coarse_op(h.ptr, level, ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def mg_footprint(dims, params, nrhs):
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    return int(LIB.mg_footprint(d, ctypes.byref(params), int(nrhs)))
+
+
+def internal_empty(h, level, prec, nrhs=1, device="cuda"):
+    """Allocate an internal-layout field of `level` (torch CUDA tensor)."""
+    import torch
+    dims, nc, _ = mg_level_info(h, level)
+    V = int(np.prod(dims))
+    if prec == MG_F64:
+        return torch.empty((nrhs, nc, V), dtype=torch.complex128, device=device)
+    if prec == MG_F32:
+        return torch.empty((nrhs, nc, V), dtype=torch.complex64, device=device)
+    dt = torch.float16 if prec == MG_F16 else torch.bfloat16
+    return torch.empty((nrhs, nc, V, 2), dtype=dt, device=device)

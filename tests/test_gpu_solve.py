@@ -1,0 +1,144 @@
+"""GPU MG-GCR solves, judged by the true FP64 residual (recomputed by the oracle) and
+against the unique solution x = D^-1 b (dense LU where the lattice is small).
+
+The solution of D x = b is unique (Sec. 1: Re(lambda) > 0 at these masses), so
+the multigrid internals (precision, batching) may change iteration counts but
+not x.  Tolerance on x: ||x - x_LU|| / ||x_LU|| <= 1e-8 (residual 1e-10 times
+the condition number of these small systems).
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+from gpu_util import lattice, rel_err, require_gpu, torch
+from oracle import dirac
+from oracle import multigrid as mg
+from paper_0811_4331_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _true_rel(U, mass, x, b):
+    return float(np.linalg.norm(b - dirac.wilson_dirac(U, x, mass)) / np.linalg.norm(b))
+
+
+def _small_workload():
+    dims = (4, 4, 4, 4)
+    U = inputs.random_gauge(dims, 0)
+    b = inputs.gaussian_spinor(dims, 1)
+    starts = [np.stack(inputs.null_vector_starts(lattice(dims), 12, 8, 2)).reshape(8, -1, 12)]
+    return dims, U, b, starts
+
+
+@pytest.fixture(scope="module")
+def lu_small():
+    dims, U, b, starts = _small_workload()
+    D = dirac.dense_matrix(lambda y: dirac.wilson_dirac(U, y, 0.1), lattice(dims) + (4, 3))
+    return scipy.linalg.lu_factor(D)
+
+
+@pytest.mark.parametrize("mixed,fine", [(0, 0), (1, 2), (1, 3), (1, 1)])
+def test_small_two_level_solve(mixed, fine, lu_small):
+    """4^4, U = exp(0.3 i H), m = 0.1, 2^4 blocks, Nv = 8, 10 setup sweeps, tol 1e-10."""
+    wm = require_gpu()
+    dims, U, b, starts = _small_workload()
+    p = wm.mg_default_params(n_levels=2, block=[(2, 2, 2, 2)], nv=[8], setup_sweeps=[10], mixed=mixed,
+                             fine_prec=fine if mixed else 2)
+    h = wm.mg_setup(U, dims, 0.1, p, starts=starts)
+    x = np.zeros_like(b)
+    status, st = wm.mg_solve(h, b, x, 1e-10)
+    assert status == wm.MG_OK
+    assert st[0]["true_rel_residual"] <= 1e-10
+    assert _true_rel(U, 0.1, x, b) <= 1e-10
+    xl = scipy.linalg.lu_solve(lu_small, b.reshape(-1)).reshape(b.shape)
+    assert rel_err(x, xl) < 1e-8
+    if mixed:
+        assert st[0]["fine_dslash_f64"] <= st[0]["reliable_updates"] + 1
+
+
+def test_plain_gpu_iterations_match_oracle():
+    """Plain FP64: same hierarchy and same arithmetic, so the outer iteration count equals the oracle's."""
+    wm = require_gpu()
+    dims, U, b, starts = _small_workload()
+    p = wm.mg_default_params(n_levels=2, block=[(2, 2, 2, 2)], nv=[8], setup_sweeps=[10])
+    h = wm.mg_setup(U, dims, 0.1, p, starts=starts)
+    x = np.zeros_like(b)
+    _, st = wm.mg_solve(h, b, x, 1e-10)
+    hier = mg.mg_setup(U, 0.1, [dict(block=(2, 2, 2, 2), nv=8, sweeps=10)],
+                       [list(starts[0].reshape((8,) + lattice(dims) + (12,)))])
+    xo, info = mg.mg_solve(hier, b.reshape(lattice(dims) + (12,)), tol=1e-10)
+    assert abs(st[0]["iters"] - info["iters"]) <= 1
+    assert rel_err(x.reshape(xo.shape), xo) < 1e-9
+
+
+def test_unpreconditioned_gcr(lu_small):
+    wm = require_gpu()
+    dims, U, b, _ = _small_workload()
+    p = wm.mg_default_params(n_levels=1)
+    h = wm.mg_setup(U, dims, 0.1, p)
+    x = np.zeros_like(b)
+    _, st = wm.mg_solve(h, b, x, 1e-10)
+    assert _true_rel(U, 0.1, x, b) <= 1e-10
+    xl = scipy.linalg.lu_solve(lu_small, b.reshape(-1)).reshape(b.shape)
+    assert rel_err(x, xl) < 1e-8
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_three_level_solve_and_multi_rhs(mixed):
+    wm = require_gpu()
+    dims = (8, 8, 8, 8)
+    mass = -0.2
+    U = inputs.random_gauge(dims, 4)
+    nrhs = 3
+    b = np.stack([inputs.gaussian_spinor(dims, 20 + r) for r in range(nrhs)])
+    b[1] = inputs.point_source(dims, 2, 1)
+    p = wm.mg_default_params(n_levels=3, block=[(2, 2, 2, 2), (2, 2, 2, 2)], nv=[8, 6], setup_sweeps=[8, 8],
+                             mixed=mixed)
+    h = wm.mg_setup(U, dims, mass, p)
+    x = np.zeros_like(b)
+    _, st = wm.mg_solve(h, b, x, 1e-10)
+    for r in range(nrhs):
+        assert _true_rel(U, mass, x[r], b[r]) <= 1e-10, r
+        assert st[r]["true_rel_residual"] <= 1e-10
+    # the batched solve and a solve of one rhs alone give the same x
+    x1 = np.zeros_like(b[1])
+    wm.mg_solve(h, np.ascontiguousarray(b[1]), x1, 1e-10)
+    assert rel_err(x1, x[1]) < 1e-8
+
+
+def test_device_buffers_and_initial_guess():
+    wm = require_gpu()
+    dims, U, b, starts = _small_workload()
+    p = wm.mg_default_params(n_levels=2, block=[(2, 2, 2, 2)], nv=[8], setup_sweeps=[10], mixed=1)
+    h = wm.mg_setup(torch.from_numpy(U).cuda(), dims, 0.1, p, starts=starts)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    wm.mg_solve(h, bd, xd, 1e-10)
+    assert _true_rel(U, 0.1, xd.cpu().numpy(), b) <= 1e-10
+    # starting from the solution needs no iteration
+    _, st = wm.mg_solve(h, bd, xd, 1e-10)
+    assert st[0]["iters"] == 0
+
+
+def test_iteration_cap_reports_no_convergence():
+    wm = require_gpu()
+    dims, U, b, _ = _small_workload()
+    p = wm.mg_default_params(n_levels=1, max_iter=3)
+    h = wm.mg_setup(U, dims, 0.1, p)
+    x = np.zeros_like(b)
+    status, st = wm.mg_solve(h, b, x, 1e-10, raise_on_noconv=False)
+    assert status == wm.MG_ENOCONV
+    assert st[0]["iters"] == 3
+    assert abs(st[0]["true_rel_residual"] - _true_rel(U, 0.1, x, b)) < 1e-12
+
+
+def test_bad_arguments():
+    wm = require_gpu()
+    dims, U, b, _ = _small_workload()
+    p = wm.mg_default_params(n_levels=2, block=[(3, 2, 2, 2)], nv=[8])
+    with pytest.raises(wm.MgError) as e:
+        wm.mg_setup(U, dims, 0.1, p)
+    assert e.value.status == wm.MG_EINVAL
+    p = wm.mg_default_params(n_levels=2, block=[(2, 2, 2, 2)], nv=[97])
+    with pytest.raises(wm.MgError):
+        wm.mg_setup(U, dims, 0.1, p)

@@ -143,3 +143,13 @@ def test_dense_lu_solve_2x4():
     assert np.linalg.norm(r) <= 1e-13 * np.linalg.norm(b)
     # Re(lambda) > 0 for this field and mass (Sec. 1)
     assert np.min(np.linalg.eigvals(D).real) > 0
+
+
+def test_single_site_operator_matches_field_operator():
+    dims = (3, 4, 2, 5)
+    U = inputs.random_gauge(dims, 1)
+    psi = inputs.gaussian_spinor(dims, 2)
+    full = dirac.wilson_dirac(U, psi, 0.3)
+    for site in [(0, 0, 0, 0), (2, 3, 1, 4), (1, 0, 1, 2), (2, 0, 0, 0)]:
+        x, y, z, t = site
+        assert np.max(np.abs(dirac.wilson_dirac_site(U, psi, 0.3, site) - full[t, z, y, x])) < 1e-13
