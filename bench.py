@@ -1,0 +1,497 @@
+#!/usr/bin/env python
+"""MG-GCR time-to-solution benchmark (one JSON line on rank 0).
+
+Workload (the mixed-vs-FP64 configuration): an 8^3 x 16 lattice with a seeded
+beta = 6.0 Wilson-action heatbath gauge field (200 sweeps, cold start),
+Wilson mass swept over m_crit + {0.1, 0.03, 0.01, 0.003} (m_crit of this
+field from tests/golden/mcrit.json), two-level adaptive MG with 4^4
+aggregates and Nv = 20 null vectors, one Gaussian right-hand side, outer
+flexible GCR(50) to a true FP64 relative residual of 1e-10.
+
+One step = the whole hot path for the four masses: mg_setup (null-vector
+relaxation, block Gram-Schmidt, Galerkin coarse operator, coarsest inverse)
+and mg_solve, in the chosen mixed-precision form (FP16 fine smoother,
+FP32 Krylov, FP64 reliable updates / Gram-Schmidt / coarsest solve).  The
+plain-FP64 form of the same step is timed beside it.  `value` is seconds
+per step (lower is better) with the gauge field and sources resident on the
+device; `e2e` is the same step through the C ABI with host buffers.
+
+Also reported: dslash HBM bandwidth on a 32^3 x 64 lattice (working set
+larger than L2) per storage precision, the roofline of the dominant kernel
+(CUDA events around each of its launches inside a profiled step), SM clocks
+sampled during the timed steps, and the FP64 CPU oracle timed on a bounded
+sample (`cpu_baseline`).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0811_4331_gb300 import inputs  # noqa: E402
+
+DIMS = (8, 8, 8, 16)
+BETA, HB_SWEEPS, HB_SEED = 6.0, 200, 0
+DMASSES = (0.1, 0.03, 0.01, 0.003)
+NV, BLOCK, SETUP_SWEEPS = 20, (4, 4, 4, 4), 300
+TOL = 1e-10
+RHS_SEED = 1
+BW_DIMS = (32, 32, 32, 64)
+WORKLOAD = "8^3x16 beta=6.0 heatbath (200 sweeps, seed 0), 2-level MG 4^4 blocks Nv=20 (300 MR setup sweeps), " \
+           "mass sweep m_crit+{0.1,0.03,0.01,0.003}, 1 Gaussian RHS, tol 1e-10"
+
+
+def mcrit():
+    key = "%dx%dx%dx%d_beta%.1f_sweeps%d_seed%d" % (*DIMS, BETA, HB_SWEEPS, HB_SEED)
+    with open(os.path.join(ROOT, "tests", "golden", "mcrit.json")) as f:
+        return json.load(f)[key]["m_crit"]
+
+
+def make_inputs():
+    U = inputs.heatbath_gauge(DIMS, BETA, HB_SWEEPS, HB_SEED)
+    b = inputs.gaussian_spinor(DIMS, RHS_SEED)
+    return U, b
+
+
+def params(wm, mixed):
+    return wm.mg_default_params(n_levels=2, block=[BLOCK], nv=[NV], setup_sweeps=[SETUP_SWEEPS], mixed=mixed,
+                                fine_prec=wm.MG_F16, seed=7)
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- native arm
+def native(args, rank, world, U, b):
+    import torch
+    from paper_0811_4331_gb300 import wilson_mg as wm
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    mc = mcrit()
+    masses = [mc + d for d in DMASSES]
+    Ud = torch.from_numpy(U).cuda()
+    bd = torch.from_numpy(b).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step(mixed, host=False, stats_out=None):
+        p = params(wm, mixed)
+        for m in masses:
+            if host:
+                h = wm.mg_setup(U, DIMS, m, p, stream=stream)
+                x = np.zeros_like(b)
+                _, st = wm.mg_solve(h, b, x, TOL, stream=stream)
+            else:
+                h = wm.mg_setup(Ud, DIMS, m, p, stream=stream)
+                x = torch.zeros_like(bd)
+                _, st = wm.mg_solve(h, bd, x, TOL, stream=stream)
+            if stats_out is not None:
+                stats_out.append((m, st[0], x if host else x.cpu().numpy()))
+            del h
+
+    def timed(mixed, K, W, host=False):
+        for _ in range(W):
+            step(mixed, host)
+        times = []
+        for _ in range(K):
+            flush.zero_()
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(mixed, host)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        t = np.array(times)
+        if world > 1:
+            tt = torch.tensor(t, device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            t = tt.cpu().numpy()
+        return t
+
+    clk = ClockSampler(dev)
+    clk.start()
+    n0 = wm.mg_launch_count()
+    t_mixed = timed(1, args.steps, args.warmup)
+    n_launch = wm.mg_launch_count() - n0
+    clocks = clk.stop()
+    res = {"mixed_s": t_mixed.tolist()}
+    if args.only_timed:
+        return {"value": float(np.median(t_mixed)), "mixed_s": res["mixed_s"], "clocks": clocks}
+    # correctness of the timed form: true FP64 residual recomputed by the library and re-checked on the host
+    chk = []
+    step(1, stats_out=chk)
+    from oracle import dirac
+    per_mass = []
+    for m, st, x in chk:
+        rel = float(np.linalg.norm(b - dirac.wilson_dirac(U, x, m)) / np.linalg.norm(b))
+        per_mass.append({"dm": round(m - mc, 4), "iters": st["iters"], "fine_dslash": st["fine_dslash"],
+                         "fine_dslash_f64": st["fine_dslash_f64"], "true_rel_residual": rel})
+        assert rel <= TOL * 1.0001, ("mixed solve missed the tolerance", m, rel)
+    out = {"per_mass_mixed": per_mass}
+    # plain FP64 beside it
+    if not args.no_plain:
+        t_plain = timed(0, max(1, min(args.steps, 2)), 1)
+        chk = []
+        step(0, stats_out=chk)
+        out["fp64_plain"] = {"value": float(np.median(t_plain)), "unit": "s per 4-mass sweep",
+                             "per_mass": [{"dm": round(m - mc, 4), "iters": st["iters"],
+                                           "fine_dslash": st["fine_dslash"],
+                                           "true_rel_residual": st["true_rel_residual"]} for m, st, _ in chk]}
+        out["speedup_mixed_vs_fp64"] = float(np.median(t_plain) / np.median(t_mixed))
+    # end to end through the C ABI with host buffers
+    t_e2e = timed(1, max(1, min(args.steps, 3)), 1, host=True)
+    V = int(np.prod(DIMS))
+    h2d = len(masses) * (U.nbytes + 2 * b.nbytes)
+    d2h = len(masses) * b.nbytes
+    out["e2e"] = {"value": float(np.median(t_e2e)), "unit": "s per 4-mass sweep", "h2d_bytes_per_step": h2d,
+                  "d2h_bytes_per_step": d2h}
+    # roofline of the dominant kernel, from events around each of its launches in one profiled step
+    out["roofline"], out["kernel_shares"] = profiled_step(wm, torch, Ud, bd, masses, stream)
+    out["clocks"] = clocks
+    out["mixed_s"] = res["mixed_s"]
+    out["value"] = float(np.median(t_mixed))
+    # launches of the warm-up + timed steps; report those of the K timed steps
+    out["gpu_launches"] = int(round(n_launch * args.steps / (args.steps + args.warmup)))
+    if not args.no_dslash_hbm and rank == 0:
+        out["dslash_hbm"] = dslash_bandwidth(wm, torch, stream)
+    return out
+
+
+def profiled_step(wm, torch, Ud, bd, masses, stream):
+    """One extra step (setup + solve) with the per-launch event profiler on every kernel class.
+
+    Returns the roofline of the dominant kernel and the device-time share of every class.
+    """
+    prec_names = ["f64", "f32", "f16", "bf16"]
+    p = params(wm, 1)
+    tot = {}
+    wm.mg_profile(None, (1 << len(wm.KERNEL_CLASS_NAMES)) - 1)
+    try:
+        for m in masses:
+            h = wm.mg_setup(Ud, DIMS, m, p, stream=stream)
+            x = torch.zeros_like(bd)
+            wm.mg_solve(h, bd, x, TOL, stream=stream)
+            for k, nm in enumerate(wm.KERNEL_CLASS_NAMES):
+                for prec in range(4):
+                    n, ms = wm.mg_profile_read(h, k, prec)
+                    if n:
+                        a = tot.get((nm, prec), [0, 0.0])
+                        tot[(nm, prec)] = [a[0] + n, a[1] + ms]
+            del h
+    finally:
+        wm.mg_profile(None, 0)
+    all_ms = sum(v[1] for v in tot.values())
+    shares = {"%s/%s" % (k[0], prec_names[k[1]]): {"launches": v[0], "ms": round(v[1], 4),
+                                                    "share": round(v[1] / all_ms, 4)}
+              for k, v in sorted(tot.items(), key=lambda kv: -kv[1][1])}
+    V = int(np.prod(DIMS))
+    peaks = measured_peaks()
+    (top, tprec), (n, ms) = max(tot.items(), key=lambda kv: kv[1][1])
+    avg_s = ms / 1e3 / max(n, 1)
+    roof = {"kernel": "%s/%s" % (top, prec_names[tprec]), "launches": n, "avg_us": round(avg_s * 1e6, 3),
+            "traffic": None}
+    if top == "dslash":
+        bps = {0: 960, 1: 384, 2: 192, 3: 192}[tprec]
+        ach = bps * V / avg_s / 1e9
+        roof.update(bound="hbm", achieved=round(ach, 1), peak=peaks.get("hbm_gbs"), unit="GB/s",
+                    frac=round(ach / peaks.get("hbm_gbs"), 4),
+                    algorithmic="%d B/site x %d sites per launch" % (bps, V))
+    elif top == "galerkin":
+        # per (coarse site, column): 9 directions x (hop on |b| sites, ~170 flop/site,
+        # + 2Nv x 6|b| complex MACs of the projection)
+        bs = int(np.prod(BLOCK))
+        fl = 9 * (bs * 170 + 2 * NV * 6 * bs * 8) * (V // bs) * 2 * NV
+        ach = fl / avg_s / 1e12
+        roof.update(bound="alu", achieved=round(ach, 3), peak=1.196, unit="TFLOP/s (FP64)",
+                    frac=round(ach / 1.196, 4), algorithmic="%.3g FP64 flop per launch" % fl)
+    elif top == "inverse":
+        N = 2 * NV * (V // int(np.prod(BLOCK)))
+        fl = 8.0 * N ** 3
+        ach = fl / avg_s / 1e12
+        roof.update(bound="alu", achieved=round(ach, 3), peak=74.6 if tprec == 1 else 1.196,
+                    unit="TFLOP/s", frac=round(ach / (74.6 if tprec == 1 else 1.196), 4),
+                    algorithmic="Gauss-Jordan, 8 N^3 flop, N = %d" % N)
+    else:
+        roof.update(bound="latency", achieved=None, peak=None, unit=None, frac=None)
+    return roof, shares
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def dslash_bandwidth(wm, torch, stream):
+    """Achieved GB/s of dslash_apply on 32^3 x 64 (inputs + links + output > L2) per storage precision."""
+    U = inputs.random_gauge_fast(BW_DIMS, 5)
+    Ud = torch.from_numpy(U).cuda()
+    del U
+    V = int(np.prod(BW_DIMS))
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
+    out = {"dims": list(BW_DIMS), "peak_gbs": peak}
+    # algorithmic bytes per site: spinor in + out (24 complex) + 4 stored links per site
+    per_site = {wm.MG_F64: 24 * 16 + 4 * 9 * 16, wm.MG_F32: 24 * 8 + 4 * 6 * 8,
+                wm.MG_F16: 24 * 4 + 4 * 6 * 4, wm.MG_BF16: 24 * 4 + 4 * 6 * 4}
+    flops_site = 1320 + 48
+    for prec, name in ((wm.MG_F16, "f16"), (wm.MG_BF16, "bf16"), (wm.MG_F32, "f32"), (wm.MG_F64, "f64")):
+        p = wm.mg_default_params(n_levels=1, mixed=0 if prec == wm.MG_F64 else 1,
+                                 fine_prec=prec if prec != wm.MG_F64 else wm.MG_F16)
+        h = wm.mg_setup(Ud, BW_DIMS, -0.79, p, stream=stream)
+        a = wm.internal_empty(h, 0, prec)
+        c = wm.internal_empty(h, 0, prec)
+        if a.is_complex():
+            a.copy_(torch.randn(a.shape, dtype=a.dtype, device="cuda"))
+        else:
+            a.copy_(torch.randn(a.shape, device="cuda").to(a.dtype))
+        for _ in range(3):
+            wm.dslash_apply(h, prec, a, c, 1, stream)
+        reps = 20 if prec != wm.MG_F64 else 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(reps):
+            wm.dslash_apply(h, prec, a if i % 2 == 0 else c, c if i % 2 == 0 else a, 1, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        gbs = per_site[prec] * V / t / 1e9
+        ent = {"us": round(t * 1e6, 2), "bytes_per_site": per_site[prec], "achieved_gbs": round(gbs, 1),
+               "frac_of_measured_hbm": round(gbs / peak, 4), "tflops": round(flops_site * V / t / 1e12, 3)}
+        if prec == wm.MG_F64:
+            ent["bound"] = "alu"
+            ent["fp64_peak_tflops"] = 1.196
+            ent["frac_of_fp64_peak"] = round(flops_site * V / t / 1e12 / 1.196, 4)
+        out[name] = ent
+        del h, a, c
+        torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------------------- oracle (cpu) arm
+RELAX_SAMPLE, ITER_SAMPLE = 10, 3
+ORACLE_SAMPLE = ("FP64 numpy oracle, single thread, on the same inputs: %d of the %d setup MR sweeps (all %d "
+                 "candidates), then block QR + Galerkin P^+DP + dense LU in full, then %d GCR iterations; "
+                 "value = 4 x (relaxation x %d/%d + QR/Galerkin/LU) + sum over the 4 masses of (oracle "
+                 "iteration count from tests/golden/c2_reference.json) x (time per iteration)"
+                 % (RELAX_SAMPLE, SETUP_SWEEPS, NV, ITER_SAMPLE, SETUP_SWEEPS, RELAX_SAMPLE))
+
+
+def oracle_iters():
+    with open(os.path.join(ROOT, "tests", "golden", "c2_reference.json")) as f:
+        ref = json.load(f)
+    return [m["iters"] for m in ref["masses"]]
+
+
+def oracle_sample(U, b, m):
+    """Time the oracle on a bounded sample of one step; returns (extrapolated seconds per step, parts)."""
+    import scipy.linalg
+    from oracle import dirac
+    from oracle import multigrid as mg
+    lat = (DIMS[3], DIMS[2], DIMS[1], DIMS[0])
+    bb = b.reshape(lat + (12,))
+    starts = inputs.null_vector_starts(lat, 12, NV, 7)
+
+    def apply(y):
+        return dirac.wilson_dirac(U, y.reshape(lat + (4, 3)), m).reshape(lat + (12,))
+
+    t0 = time.perf_counter()
+    cands = mg.relax_null_vectors(apply, starts, RELAX_SAMPLE)
+    t1 = time.perf_counter()
+    blk = mg.Blocking(lat, BLOCK, 12)
+    P = mg.block_orthonormalize(cands, blk)
+    Ac = mg.coarse_stencil(dirac.wilson_stencil(U, m), P, blk)
+    lu = scipy.linalg.lu_factor(mg.dense_from_stencil(Ac))
+    t2 = time.perf_counter()
+    fine = mg.Level(apply, lat, 12)
+    fine.P, fine.blk = P, blk
+    coarse = mg.Level(lambda y: dirac.stencil_apply(Ac, y), blk.coarse, 2 * NV)
+    coarse.stencil, coarse.lu = Ac, lu
+    hier = [fine, coarse]
+    t3 = time.perf_counter()
+    try:
+        mg.fgcr(apply, bb, lambda r: mg.vcycle(hier, 0, r), tol=1e-300, restart=ITER_SAMPLE, max_restarts=1)
+    except ArithmeticError:
+        pass
+    t4 = time.perf_counter()
+    relax = (t1 - t0) * SETUP_SWEEPS / RELAX_SAMPLE
+    rest = t2 - t1
+    per_iter = (t4 - t3) / ITER_SAMPLE
+    total = len(DMASSES) * (relax + rest) + sum(oracle_iters()) * per_iter
+    return total, {"relax_sample_s": round(t1 - t0, 3), "qr_galerkin_lu_s": round(rest, 3),
+                   "per_iter_s": round(per_iter, 4), "sampled_s": round(t4 - t0 - (t3 - t2), 3)}
+
+
+def cpu_baseline_subprocess(U):
+    """The oracle timed in a child process pinned to one thread (BLAS included)."""
+    import tempfile
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "gauge.npy")
+        np.save(path, U)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", path], env=env,
+                           capture_output=True, text=True)
+    if r.returncode != 0:
+        return {"error": r.stderr[-500:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": round(d["seconds"], 3), "unit": "s per 4-mass sweep", "cores": 1, "kind": "oracle",
+            "sample": ORACLE_SAMPLE, "parts": d["parts"]}
+
+
+def oracle_sample_main(path):
+    U = np.load(path)
+    b = inputs.gaussian_spinor(DIMS, RHS_SEED)
+    s, parts = oracle_sample(U, b, mcrit() + DMASSES[0])
+    print(json.dumps({"seconds": s, "parts": parts}))
+
+
+def reference_arm(args, rank, world):
+    """--impl reference: the oracle as it stands, on the host cores, same metric and unit."""
+    if rank != 0:
+        return None
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
+    U, b = make_inputs()
+    m = mcrit() + DMASSES[0]
+    for _ in range(args.warmup):
+        oracle_sample(U, b, m)
+    ts = []
+    parts = None
+    for _ in range(args.steps):
+        s, parts = oracle_sample(U, b, m)
+        ts.append(s)
+    v = float(np.median(ts))
+    return {"impl": "reference", "metric": "MG-GCR time-to-solution @1e-10 rel residual, mixed vs FP64; "
+                                          "dslash HBM GB/s",
+            "value": round(v, 3), "unit": "s per 4-mass sweep (setup + solve)", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 1), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded beta=6.0 heatbath gauge field, Gaussian source)",
+            "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "s per 4-mass sweep", "cores": 1, "kind": "oracle",
+                             "sample": ORACLE_SAMPLE, "parts": parts},
+            "e2e": {"value": round(v, 3), "unit": "s per 4-mass sweep", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-dslash-hbm", action="store_true")
+    ap.add_argument("--only-timed", action="store_true", help="time the mixed step only (for profiler runs)")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.oracle_sample:
+        oracle_sample_main(args.oracle_sample)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        out = reference_arm(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    import torch
+    if world > 1:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    U, b = make_inputs()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.only_timed:
+        cpu = cpu_baseline_subprocess(U)
+    r = native(args, rank, world, U, b)
+    if rank == 0:
+        v = r.pop("value")
+        line = {"metric": "MG-GCR time-to-solution @1e-10 rel residual, mixed vs FP64; dslash HBM GB/s",
+                "value": round(v, 5), "unit": "s per 4-mass sweep (setup + solve)", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 3),
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded beta=6.0 heatbath gauge field, Gaussian source)",
+                "config": {"workload": WORKLOAD, "l2": "256 MB buffer written between timed steps",
+                           "precision": "fine smoother FP16 storage / FP32 math, Krylov FP32, FP64 reliable "
+                                        "updates, Gram-Schmidt and coarsest solve"},
+                "solves_per_s": round(world * len(DMASSES) / v, 3)}
+        line.update(r)
+        line["cpu_baseline"] = cpu
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

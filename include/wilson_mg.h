@@ -84,6 +84,7 @@ typedef struct {
   int coarse_prec;                    /* mixed: storage of levels 1..L-2 (MG_F32/MG_F16/MG_BF16) */
   double reliable_delta;              /* mixed: inner FP32 GCR reduces ||r|| by this factor before an FP64 update */
   uint64_t seed;                      /* on-device start vectors: level l uses stream seed + l */
+  int use_graphs;                     /* 1: replay the V-cycle as a captured CUDA graph; 0: launch eagerly */
 } mg_params;
 
 /* Per right-hand side solve statistics. */
@@ -103,7 +104,8 @@ typedef struct mg_handle mg_handle;
 const char* mg_last_error(void);
 
 /* Fill `p` with defaults: 2 levels, 4^4 blocks, Nv = 20, 20 setup sweeps,
- * V(2,2), omega 0.8, 4 coarse cycles, GCR(50), max_iter 2000, plain FP64. */
+ * V(2,2), omega 0.8, 4 coarse cycles, GCR(50), max_iter 2000, plain FP64,
+ * CUDA graphs on. */
 int mg_default_params(mg_params* p);
 
 /* Build the solver for gauge field `gauge` and mass `mass`.
@@ -194,6 +196,37 @@ int mg_get_prolongator(mg_handle* h, int level, double* out);
  * [9][V_l][ncomp][ncomp] complex (row i, column j); direction d = 0 is the
  * site itself, d = 1 + 2 mu the hop to n + mu, d = 2 + 2 mu to n - mu. */
 int mg_get_coarse_op(mg_handle* h, int level, double* out);
+
+/* Kernel classes of the profiler. */
+typedef enum {
+  MG_K_DSLASH = 0,   /* level-0 Wilson stencil */
+  MG_K_COARSE = 1,   /* coarse 9-point stencil */
+  MG_K_RESTRICT = 2, /* P^+ */
+  MG_K_PROLONG = 3,  /* P */
+  MG_K_VECTOR = 4,   /* MR / GCR vector updates, dots, conversions */
+  MG_K_COARSEST = 5, /* dense coarsest solve */
+  MG_K_SETUP = 6,    /* start vectors, block Gram-Schmidt, prolongator columns, copies */
+  MG_K_GALERKIN = 7, /* Galerkin build of the coarse stencil */
+  MG_K_INVERSE = 8,  /* dense coarsest inverse (the whole elimination as one interval) */
+  MG_K_CLASSES = 9
+} mg_kernel_class;
+
+/* Enable (mask != 0, bit c = class c) or disable the per-launch profiler
+ * of handle h and clear its counters.  While enabled, every launch of a
+ * selected class is bracketed by two CUDA events recorded on the stream it
+ * runs on (no extra synchronisation), and the V-cycle is launched eagerly
+ * rather than replayed as a graph.  h == NULL sets the mask that handles
+ * created afterwards start with (so that mg_setup itself is profiled). */
+int mg_profile(mg_handle* h, unsigned mask);
+
+/* Synchronise and return the number of launches and their summed event
+ * time (milliseconds) of class `kclass` with storage precision `prec`
+ * since the last mg_profile call. */
+int mg_profile_read(mg_handle* h, int kclass, int prec, long long* launches, double* ms);
+
+/* Number of kernels this library has launched since it was loaded, over
+ * all handles and threads (a monotonic counter). */
+unsigned long long mg_launch_count(void);
 
 /* Device bytes that mg_setup + mg_solve(nrhs) need for these sizes. */
 size_t mg_footprint(const int dims[4], const mg_params* p, int nrhs);

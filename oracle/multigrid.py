@@ -218,11 +218,11 @@ def coarse_stencil(A, P, blk):
     Pc = np.conj(P)
     for d in range(9):
         if d == 0:
-            M = np.einsum("...ci,...cd,...dj->...ij", Pc, A[0], P)
+            M = np.einsum("...ci,...cd,...dj->...ij", Pc, A[0], P, optimize=True)
             Ac[0] += blk.block_sum(M)
             continue
         mu, step = dirac.stencil_offset(d)
-        M = np.einsum("...ci,...cd,...dj->...ij", Pc, A[d], dirac.shift(P, mu, step))
+        M = np.einsum("...ci,...cd,...dj->...ij", Pc, A[d], dirac.shift(P, mu, step), optimize=True)
         b = blk.block[mu]
         n = blk.coords(mu) % b
         leaves = (n == b - 1) if step > 0 else (n == 0)

@@ -19,6 +19,11 @@ namespace wmg {
 
 static thread_local std::string g_err = "";
 void set_error(const std::string& msg) { g_err = msg; }
+// kernels launched by this library since it was loaded (all handles, all threads)
+static unsigned long long g_launches = 0;
+// profiler mask that new handles start with (mg_profile(NULL, mask))
+static unsigned g_default_prof_mask = 0;
+inline void count_launches(unsigned long long n) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
 
 }  // namespace wmg
 
@@ -34,6 +39,7 @@ using namespace wmg;
   } while (0)
 #define LK(x)                                                                          \
   do {                                                                                 \
+    count_launches(1);                                                                 \
     if ((x) != 0) {                                                                    \
       cudaError_t e_ = cudaGetLastError();                                             \
       set_error(std::string("launch failed: ") + #x + ": " + cudaGetErrorString(e_));  \
@@ -45,6 +51,8 @@ using namespace wmg;
     int r_ = (x);                   \
     if (r_ != MG_OK) return r_;     \
   } while (0)
+
+extern "C" unsigned long long mg_launch_count(void);
 
 namespace {
 
@@ -97,6 +105,10 @@ void* work(mg_handle* h, int l, int prec, int idx, int nrhs) {
   if ((int)vecs.size() <= idx) vecs.resize(idx + 1);
   if (!vecs[idx]) vecs[idx].reset(new DevBuf());
   const size_t need = h->lev[l]->n() * (size_t)nrhs * bytes_of(prec);
+  if (need > vecs[idx]->bytes || !vecs[idx]->p) {
+    if (h->capturing) return nullptr;  // never allocate inside a capture
+    ++h->buf_gen;
+  }
   if (!vecs[idx]->ensure(need)) return nullptr;
   return vecs[idx]->p;
 }
@@ -113,13 +125,45 @@ int ensure_reducer(mg_handle* h, int nrhs) {
     need = std::max(need, b * 3 * (size_t)nrhs);
   }
   if (need <= h->red.max_partials && h->red.nslots) return MG_OK;
+  if (h->capturing) return MG_EINVAL;
   cudaStreamSynchronize(h->st);
+  ++h->buf_gen;
   if (!h->red.init(need, (int)slot_total(), 4096)) {
     set_error("out of device memory for reduction scratch");
     return MG_ENOMEM;
   }
   return MG_OK;
 }
+
+// Per-launch event profiler (mg_profile): brackets each launch of a selected
+// kernel class with a pair of events on the handle's stream.
+struct Prof {
+  mg_handle* h;
+  bool on;
+  size_t idx = 0;
+  int key;
+  Prof(mg_handle* hh, int cls, int prec)
+      : h(hh), on(((hh->prof_mask >> cls) & 1u) && !hh->capturing), key(cls * 4 + prec) {
+    if (!on) return;
+    while (h->prof_used + 2 > h->prof_pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        on = false;
+        return;
+      }
+      h->prof_pool.push_back(e);
+    }
+    idx = h->prof_used;
+    h->prof_used += 2;
+    cudaEventRecord(h->prof_pool[idx], h->st);
+  }
+  ~Prof() {
+    if (!on) return;
+    cudaEventRecord(h->prof_pool[idx + 1], h->st);
+    h->prof_marks.push_back(std::make_pair(key, idx));
+  }
+};
 
 // out = a_ * (A_l in) + c_ * y; optional dots <out|z>, ||out||^2 into slot.
 int op_apply(mg_handle* h, int l, int prec, const void* in, void* out, const void* y, double a_, double c_,
@@ -143,6 +187,7 @@ int op_apply(mg_handle* h, int l, int prec, const void* in, void* out, const voi
     d.c = c_;
     d.nrhs = nrhs;
     d.red = h->red.at(slot, 4);
+    Prof pf(h, MG_K_DSLASH, prec);
     LK(launch_wilson(d, h->st));
   } else {
     if (!a.cop[prec].p) {
@@ -162,6 +207,7 @@ int op_apply(mg_handle* h, int l, int prec, const void* in, void* out, const voi
     k.c = c_;
     k.nrhs = nrhs;
     k.red = h->red.at(slot, 4);
+    Prof pf(h, MG_K_COARSE, prec);
     LK(launch_coarse_apply(k, h->st));
   }
   return MG_OK;
@@ -184,6 +230,7 @@ int mr_update(mg_handle* h, int l, int prec, void* x_out, const void* x_in, cons
   m.omega = omega;
   m.red = h->red.at(0, 0);
   m.red.result = nullptr;
+  Prof pf(h, MG_K_VECTOR, prec);
   LK(launch_mr_update(m, h->st));
   return MG_OK;
 }
@@ -210,11 +257,45 @@ int mr_steps(mg_handle* h, int l, int prec, const void* b, void* x, bool x_zero,
   return MG_OK;
 }
 
+// Setup relaxation in FP32: steps between recomputations of the true residual.
+const int kTrueResidualEvery = 25;
+
+// Number of FP64 iterative-refinement steps of the mixed-precision coarsest solve.
+const int kCoarsestRefine = 2;
+
+// Exact solve on the coarsest level.  Plain: e = A^-1 r with the FP64
+// inverse.  Mixed: the inverse is FP32; the solve runs in FP64 as
+// e = X r, then kCoarsestRefine times e += X (r - A e) with the FP64 stencil.
 int coarsest_solve(mg_handle* h, int l, int prec, const void* r, void* e, int nrhs) {
   Level& a = *h->lev[l];
-  LK(launch_dense_matvec(prec, prec, a.N(), a.inv.as<double2>(), r, e, nrhs, h->st));
+  if (a.inv_prec == MG_F64 && prec == MG_F64) {
+    Prof pf(h, MG_K_COARSEST, prec);
+    LK(launch_dense_matvec(0, 0, 0, a.N(), a.inv.p, r, e, nrhs, 0, h->st));
+    return MG_OK;
+  }
+  void* r64 = work(h, l, MG_F64, WV_A, nrhs);
+  void* e64 = work(h, l, MG_F64, WV_B, nrhs);
+  void* t64 = work(h, l, MG_F64, WV_T, nrhs);
+  if (!r64 || !e64 || !t64) return MG_ENOMEM;
+  const size_t n = a.n();
+  {
+    Prof pf(h, MG_K_VECTOR, prec);
+    LK(launch_convert(prec, MG_F64, n, nrhs, r, r64, 1.0, nullptr, 0, 0.0, 0, h->st));
+  }
+  {
+    Prof pf(h, MG_K_COARSEST, MG_F32);
+    LK(launch_dense_matvec(a.inv_prec, 0, 0, a.N(), a.inv.p, r64, e64, nrhs, 0, h->st));
+  }
+  for (int it = 0; it < kCoarsestRefine; ++it) {
+    RET(op_apply(h, l, MG_F64, e64, t64, r64, -1.0, 1.0, nullptr, 0, nrhs));
+    Prof pf(h, MG_K_COARSEST, MG_F32);
+    LK(launch_dense_matvec(a.inv_prec, 0, 0, a.N(), a.inv.p, t64, e64, nrhs, 1, h->st));
+  }
+  Prof pf(h, MG_K_VECTOR, prec);
+  LK(launch_convert(MG_F64, prec, n, nrhs, e64, e, 1.0, nullptr, 0, 0.0, 0, h->st));
   return MG_OK;
 }
+
 
 // e = V_l(r): one modified V(nu_pre, nu_post) cycle on level l.
 int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
@@ -236,7 +317,10 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
   RET(mr_steps(h, l, prec, r, e, true, res, h->p.nu_pre, nrhs));
   // restrict, coarse solve, prolong
   const Agg g = agg_of(a);
-  LK(launch_restrict(prec, prec, pc, g, a.P[prec].p, res, rc, nrhs, h->st));
+  {
+    Prof pf(h, MG_K_RESTRICT, prec);
+    LK(launch_restrict(prec, prec, pc, g, a.P[prec].p, res, rc, nrhs, h->st));
+  }
   if (l + 1 == L - 1) {
     RET(coarsest_solve(h, l + 1, pc, rc, ec, nrhs));
   } else {
@@ -247,16 +331,78 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
     for (int c = 1; c < a.cycles; ++c) {
       RET(op_apply(h, l + 1, pc, ec, t, rc, -1.0, 1.0, nullptr, 0, nrhs));
       RET(vcycle(h, l + 1, t, dt, nrhs));
+      Prof pf(h, MG_K_VECTOR, pc);
       LK(launch_convert(pc, pc, h->lev[l + 1]->n(), nrhs, dt, ec, 1.0, nullptr, 0, 0.0, 1, h->st));
     }
   }
-  LK(launch_prolong(pc, prec, prec, g, a.P[prec].p, ec, xc, nrhs, h->st));
+  {
+    Prof pf(h, MG_K_PROLONG, prec);
+    LK(launch_prolong(pc, prec, prec, g, a.P[prec].p, ec, xc, nrhs, h->st));
+  }
   // alpha = <A x_c|r0> / <A x_c|A x_c>  (Eq. 3.5);  e += alpha x_c, r0 -= alpha A x_c
   const size_t sl = slot_level(l);
   RET(op_apply(h, l, prec, xc, axc, nullptr, 1.0, 0.0, res, sl, nrhs));
   RET(mr_update(h, l, prec, e, e, xc, res, res, axc, sl, 1.0, nrhs));
   // post-smoothing
   RET(mr_steps(h, l, prec, res, e, false, res, h->p.nu_post, nrhs));
+  return MG_OK;
+}
+
+// e = V_0(r) through a CUDA graph of the whole cycle.  The first call for a
+// given (nrhs, r, e) runs the cycle eagerly (so every work buffer exists),
+// then captures it on a private stream; later calls replay the graph on the
+// handle's stream.  Any buffer reallocation invalidates the cached graphs.
+int vcycle_graph(mg_handle* h, const void* r, void* e, int nrhs) {
+  if (!h->use_graphs || h->prof_mask) return vcycle(h, 0, r, e, nrhs);  // the profiler times launches one by one
+  for (auto& g : h->graphs) {
+    if (g.nrhs == nrhs && g.in == r && g.out == e && g.gen == h->buf_gen) {
+      CK(cudaGraphLaunch(g.exec, h->st));
+      count_launches(g.nodes);
+      return MG_OK;
+    }
+  }
+  RET(vcycle(h, 0, r, e, nrhs));  // eager run: allocates and warms every buffer
+  if (!h->cap_st) CK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+  CK(cudaStreamSynchronize(h->st));
+  cudaStream_t keep = h->st;
+  const unsigned long long gen = h->buf_gen;
+  const unsigned long long n0 = mg_launch_count();
+  h->st = h->cap_st;
+  h->capturing = true;
+  cudaGraph_t graph = nullptr;
+  int rc = MG_OK;
+  cudaError_t ce = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal);
+  if (ce == cudaSuccess) {
+    rc = vcycle(h, 0, r, e, nrhs);
+    ce = cudaStreamEndCapture(h->cap_st, &graph);
+  }
+  h->capturing = false;
+  h->st = keep;
+  const unsigned long long nodes = mg_launch_count() - n0;
+  if (ce != cudaSuccess || rc != MG_OK || gen != h->buf_gen) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    h->use_graphs = false;  // fall back to eager launches for this handle
+    return rc != MG_OK ? rc : MG_OK;
+  }
+  cudaGraphExec_t exec = nullptr;
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    h->use_graphs = false;
+    return MG_OK;
+  }
+  // drop graphs of older generations
+  for (auto it = h->graphs.begin(); it != h->graphs.end();) {
+    if (it->gen != h->buf_gen) {
+      cudaGraphExecDestroy(it->exec);
+      it = h->graphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  h->graphs.push_back({nrhs, r, e, gen, nodes, exec});
   return MG_OK;
 }
 
@@ -294,6 +440,7 @@ int mg_default_params(mg_params* p) {
   p->coarse_prec = MG_F32;
   p->reliable_delta = 1e-4;
   p->seed = 0;
+  p->use_graphs = 1;
   return MG_OK;
 }
 
@@ -301,6 +448,9 @@ int mg_destroy(mg_handle* h) {
   if (!h) return MG_OK;
   if (h->st) cudaStreamSynchronize(h->st);
   if (h->host_slots) cudaFreeHost(h->host_slots);
+  for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
   delete h;
   return MG_OK;
 }
@@ -364,10 +514,11 @@ static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, co
       return MG_EINVAL;
     }
     RET(ensure_reducer(h, a.nv));
-    // candidates, FP64 internal [nv][ncomp][V]
-    DevBuf cand, rr, pp;
+    // candidates, FP64 internal [nv][ncomp][V]; relaxed in FP32 in the mixed form
+    const int rp = p.mixed ? MG_F32 : MG_F64;
+    DevBuf cand, candr, rr, pp;
     const size_t vb = a.n() * 16;
-    if (!cand.ensure(vb * a.nv) || !rr.ensure(vb * a.nv) || !pp.ensure(vb * a.nv)) return MG_ENOMEM;
+    if (!cand.ensure(vb * a.nv)) return MG_ENOMEM;
     if (starts && starts[l]) {
       DevBuf ext;
       if (!ext.ensure(vb * a.nv)) return MG_ENOMEM;
@@ -375,26 +526,46 @@ static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, co
       LK(launch_ext_to_int(MG_F64, a.ncomp, a.V, a.nv, ext.p, cand.p, st));
       CK(cudaStreamSynchronize(st));
     } else {
+      Prof pf(h, MG_K_SETUP, MG_F64);
       LK(launch_gaussian_starts(p.seed + (uint64_t)l, a.nv, a.ncomp, a.V, cand.p, st));
     }
-    // relax A x = 0 (Sec. 2 step 1-2): r = -A x, then MR steps
+    void* x = cand.p;
+    const size_t vr = a.n() * bytes_of(rp);
+    if (rp != MG_F64) {
+      if (!candr.ensure(vr * a.nv)) return MG_ENOMEM;
+      LK(launch_convert(MG_F64, rp, a.n(), a.nv, cand.p, candr.p, 1.0, nullptr, 0, 0.0, 0, st));
+      x = candr.p;
+    }
+    if (!rr.ensure(vr * a.nv) || !pp.ensure(vr * a.nv)) return MG_ENOMEM;
+    // relax A x = 0 (Sec. 2 steps 1-2): r = -A x, then MR steps, all candidates at once
     const size_t sl = slot_level(l);
     if (a.sweeps > 0) {
-      RET(op_apply(h, l, MG_F64, cand.p, rr.p, nullptr, -1.0, 0.0, nullptr, 0, a.nv));
+      RET(op_apply(h, l, rp, x, rr.p, nullptr, -1.0, 0.0, nullptr, 0, a.nv));
       for (int s = 0; s < a.sweeps; ++s) {
-        RET(op_apply(h, l, MG_F64, rr.p, pp.p, nullptr, 1.0, 0.0, rr.p, sl, a.nv));
-        RET(mr_update(h, l, MG_F64, cand.p, cand.p, rr.p, rr.p, rr.p, pp.p, sl, p.omega, a.nv));
+        // FP32 relaxation: the recursively updated residual drifts from -A x
+        // once it has shrunk by a few orders, so it is recomputed every
+        // kTrueResidualEvery steps (FP64 follows the plain recursion).
+        if (rp != MG_F64 && s > 0 && s % kTrueResidualEvery == 0)
+          RET(op_apply(h, l, rp, x, rr.p, nullptr, -1.0, 0.0, nullptr, 0, a.nv));
+        RET(op_apply(h, l, rp, rr.p, pp.p, nullptr, 1.0, 0.0, rr.p, sl, a.nv));
+        RET(mr_update(h, l, rp, x, x, rr.p, rr.p, rr.p, pp.p, sl, p.omega, a.nv));
       }
     }
     // unit-normalise every candidate
-    LK(launch_dot(MG_F64, a.n(), a.nv, cand.p, cand.p, h->red.at(slot_misc(), 4), st));
-    LK(launch_convert(MG_F64, MG_F64, a.n(), a.nv, cand.p, cand.p, 1.0, h->red.slot(slot_misc() + 2), 4, -0.5, 0,
-                      st));
-    // blockwise Gram-Schmidt into P (Eq. 2.3)
+    LK(launch_dot(rp, a.n(), a.nv, x, x, h->red.at(slot_misc(), 4), st));
+    LK(launch_convert(rp, MG_F64, a.n(), a.nv, x, cand.p, 1.0, h->red.slot(slot_misc() + 2), 4, -0.5, 0, st));
+    CK(cudaStreamSynchronize(st));
+    candr.release();
+    pp.release();
+    rr.release();
+    // blockwise Gram-Schmidt into P (Eq. 2.3), FP64
     const Agg g = agg_of(a);
     if (!a.P[MG_F64].ensure((size_t)a.Vc * 2 * a.nv * a.nhalf * a.bsites * 16)) return MG_ENOMEM;
-    LK(launch_block_gs(g, cand.as<double2>(), a.P[MG_F64].as<double2>(), errflag.as<int>(), st));
-    // Galerkin coarse operator, one column at a time
+    {
+      Prof pf(h, MG_K_SETUP, MG_F64);
+      LK(launch_block_gs(g, cand.as<double2>(), a.P[MG_F64].as<double2>(), errflag.as<int>(), st));
+    }
+    // Galerkin coarse operator, FP64, columns in batches of at most 1 GB of fields
     h->lev.emplace_back(new Level());
     Level& c = *h->lev[l + 1];
     for (int m = 0; m < 4; ++m) c.L[m] = a.Lc[m];
@@ -402,14 +573,22 @@ static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, co
     c.ncomp = 2 * a.nv;
     const int nc = c.ncomp;
     if (!c.cop[MG_F64].ensure((size_t)9 * nc * nc * c.V * 16)) return MG_ENOMEM;
-    for (int j = 0; j < nc; ++j) {
-      LK(launch_p_column(g, a.P[MG_F64].as<double2>(), j, rr.as<double2>(), st));
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(nc, ((size_t)1 << 30) / vb));
+    DevBuf cols;
+    if (!cols.ensure(vb * chunk)) return MG_ENOMEM;
+    for (int j0 = 0; j0 < nc; j0 += chunk) {
+      const int ncols = std::min(chunk, nc - j0);
+      {
+        Prof pf(h, MG_K_SETUP, MG_F64);
+        LK(launch_p_column(g, a.P[MG_F64].as<double2>(), j0, ncols, cols.as<double2>(), st));
+      }
+      Prof pf(h, MG_K_GALERKIN, MG_F64);
       if (l == 0)
-        LK(launch_galerkin_wilson(g, a.links[MG_F64].as<double2>(), h->mass, rr.as<double2>(),
-                                  a.P[MG_F64].as<double2>(), j, c.cop[MG_F64].as<double2>(), st));
+        LK(launch_galerkin_wilson(g, a.links[MG_F64].as<double2>(), h->mass, cols.as<double2>(),
+                                  a.P[MG_F64].as<double2>(), j0, ncols, c.cop[MG_F64].as<double2>(), st));
       else
-        LK(launch_galerkin_stencil(g, a.cop[MG_F64].as<double2>(), rr.as<double2>(), a.P[MG_F64].as<double2>(), j,
-                                   c.cop[MG_F64].as<double2>(), st));
+        LK(launch_galerkin_stencil(g, a.cop[MG_F64].as<double2>(), cols.as<double2>(), a.P[MG_F64].as<double2>(),
+                                   j0, ncols, c.cop[MG_F64].as<double2>(), st));
     }
     int herr = 0;
     CK(cudaMemcpyAsync(&herr, errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -418,24 +597,25 @@ static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, co
       set_error("block Gram-Schmidt lost rank on level " + std::to_string(l));
       return MG_ERANK;
     }
-  }
-  // ---- precision copies for the mixed V-cycle
-  for (int l = 0; l < Lv; ++l) {
-    Level& a = *h->lev[l];
+    // precision copies: this level's P for the cycle; the next level's
+    // operator for its cycle and (mixed) its FP32 relaxation
     const int pr = prec_of(h, l);
-    if (pr == MG_F64) continue;
-    if (l + 1 < Lv) {
+    if (pr != MG_F64) {
       const size_t np = (size_t)a.Vc * 2 * a.nv * a.nhalf * a.bsites;
       if (!a.P[pr].ensure(np * bytes_of(pr))) return MG_ENOMEM;
       LK(launch_convert(MG_F64, pr, np, 1, a.P[MG_F64].p, a.P[pr].p, 1.0, nullptr, 0, 0.0, 0, st));
     }
-    if (l >= 1 && l + 1 < Lv) {
-      const size_t nc = (size_t)9 * a.ncomp * a.ncomp * a.V;
-      if (!a.cop[pr].ensure(nc * bytes_of(pr))) return MG_ENOMEM;
-      LK(launch_convert(MG_F64, pr, nc, 1, a.cop[MG_F64].p, a.cop[pr].p, 1.0, nullptr, 0, 0.0, 0, st));
+    if (p.mixed && l + 2 < Lv) {
+      const size_t ncop = (size_t)9 * nc * nc * c.V;
+      const int want[2] = {MG_F32, p.coarse_prec};
+      for (int q : want) {
+        if (c.cop[q].p) continue;
+        if (!c.cop[q].ensure(ncop * bytes_of(q))) return MG_ENOMEM;
+        LK(launch_convert(MG_F64, q, ncop, 1, c.cop[MG_F64].p, c.cop[q].p, 1.0, nullptr, 0, 0.0, 0, st));
+      }
     }
   }
-  // ---- coarsest level: dense FP64 inverse
+  // ---- coarsest level: dense inverse (FP64, or FP32 refined in FP64 in the mixed form)
   if (Lv >= 2) {
     Level& c = *h->lev[Lv - 1];
     const size_t N = c.n();
@@ -443,11 +623,17 @@ static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, co
       set_error("coarsest level has " + std::to_string(N) + " unknowns; the dense solve takes at most 8192");
       return MG_EINVAL;
     }
+    c.inv_prec = p.mixed ? MG_F32 : MG_F64;
+    const size_t eb = bytes_of(c.inv_prec);
     DevBuf aug, col;
-    if (!aug.ensure(N * 2 * N * 16) || !col.ensure(N * 16) || !c.inv.ensure(N * N * 16)) return MG_ENOMEM;
+    if (!aug.ensure(N * 2 * N * eb) || !col.ensure(dense_inverse_scratch_bytes(c.inv_prec, (int)N)) ||
+        !c.inv.ensure(N * N * eb))
+      return MG_ENOMEM;
     CK(cudaMemsetAsync(errflag.p, 0, sizeof(int), st));
-    LK(dense_inverse(c.cop[MG_F64].as<double2>(), c.L, c.ncomp, aug.as<double2>(), col.as<double2>(),
-                     errflag.as<int>(), c.inv.as<double2>(), st));
+    Prof pf(h, MG_K_INVERSE, c.inv_prec);
+    LK(dense_inverse(c.inv_prec, c.cop[MG_F64].as<double2>(), c.L, c.ncomp, aug.p, col.p, errflag.as<int>(), c.inv.p,
+                     st));
+    count_launches(N + 2);  // stencil-to-dense, init, one per pivot, finish (one counted by LK)
     int herr = 0;
     CK(cudaMemcpyAsync(&herr, errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -488,6 +674,8 @@ int mg_setup(mg_handle** hout, const double* gauge, int gauge_on_device, const i
   h->mass = mass;
   for (int m = 0; m < 4; ++m) h->dims[m] = dims[m];
   h->st = (cudaStream_t)stream;
+  h->use_graphs = p->use_graphs != 0;
+  h->prof_mask = __atomic_load_n(&g_default_prof_mask, __ATOMIC_RELAXED);
   if (cudaMallocHost((void**)&h->host_slots, slot_total() * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -638,8 +826,8 @@ int mg_get_prolongator(mg_handle* h, int level, double* out) {
   if (!f.ensure(a.n() * 16) || !tot.ensure(a.n() * 16) || !ext.ensure(a.n() * 16)) return MG_ENOMEM;
   const Agg g = agg_of(a);
   for (int k = 0; k < a.nv; ++k) {
-    LK(launch_p_column(g, a.P[MG_F64].as<double2>(), k, tot.as<double2>(), st));
-    LK(launch_p_column(g, a.P[MG_F64].as<double2>(), a.nv + k, f.as<double2>(), st));
+    LK(launch_p_column(g, a.P[MG_F64].as<double2>(), k, 1, tot.as<double2>(), st));
+    LK(launch_p_column(g, a.P[MG_F64].as<double2>(), a.nv + k, 1, f.as<double2>(), st));
     LK(launch_convert(MG_F64, MG_F64, a.n(), 1, f.p, tot.p, 1.0, nullptr, 0, 0.0, 1, st));
     LK(launch_int_to_ext(MG_F64, a.ncomp, a.V, 1, tot.p, ext.p, st));
     CK(cudaMemcpyAsync(out + (size_t)k * a.n() * 2, ext.p, a.n() * 16, cudaMemcpyDeviceToHost, st));
@@ -665,6 +853,38 @@ int mg_get_coarse_op(mg_handle* h, int level, double* out) {
           out[dst] = tmp[src];
           out[dst + 1] = tmp[src + 1];
         }
+  return MG_OK;
+}
+
+unsigned long long mg_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+int mg_profile(mg_handle* h, unsigned mask) {
+  if (!h) {
+    __atomic_store_n(&g_default_prof_mask, mask, __ATOMIC_RELAXED);
+    return MG_OK;
+  }
+  CK(cudaStreamSynchronize(h->st));
+  h->prof_marks.clear();
+  h->prof_used = 0;
+  h->prof_mask = mask;
+  return MG_OK;
+}
+
+int mg_profile_read(mg_handle* h, int kclass, int prec, long long* launches, double* ms) {
+  if (!h || kclass < 0 || kclass >= MG_K_CLASSES || check_prec(prec)) return MG_EINVAL;
+  CK(cudaStreamSynchronize(h->st));
+  long long n = 0;
+  double tot = 0.0;
+  for (auto& m : h->prof_marks) {
+    if (m.first != kclass * 4 + prec) continue;
+    CK(cudaEventSynchronize(h->prof_pool[m.second + 1]));
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, h->prof_pool[m.second], h->prof_pool[m.second + 1]));
+    tot += t;
+    ++n;
+  }
+  if (launches) *launches = n;
+  if (ms) *ms = tot;
   return MG_OK;
 }
 
@@ -777,15 +997,22 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
       if (h->lev.size() >= 2) {
         const int pf = prec_of(h, 0);
         if (pf == pin) {
-          RET(vcycle(h, 0, h->gr.p, zk, nrhs));
+          void* eout = work(h, 0, pf, WV_A, nrhs);
+          if (!eout) return MG_ENOMEM;
+          RET(vcycle_graph(h, h->gr.p, eout, nrhs));
+          CK(cudaMemcpyAsync(zk, eout, vbytes, cudaMemcpyDeviceToDevice, st));
         } else {
           void* rin = work(h, 0, pf, WV_IN, nrhs);
           void* eout = work(h, 0, pf, WV_A, nrhs);
           if (!rin || !eout) return MG_ENOMEM;
           // scale the residual to RMS 1/8 per component for 16-bit storage
           const double sig = sqrt((double)n) / 8.0;
-          LK(launch_convert(pin, pf, n, nrhs, h->gr.p, rin, sig, h->red.slot(slot_gcr_rn() + 2), 4, -0.5, 0, st));
-          RET(vcycle(h, 0, rin, eout, nrhs));
+          {
+            Prof pf2(h, MG_K_VECTOR, pin);
+            LK(launch_convert(pin, pf, n, nrhs, h->gr.p, rin, sig, h->red.slot(slot_gcr_rn() + 2), 4, -0.5, 0, st));
+          }
+          RET(vcycle_graph(h, rin, eout, nrhs));
+          Prof pf2(h, MG_K_VECTOR, pin);
           LK(launch_convert(pf, pin, n, nrhs, eout, zk, 1.0 / sig, h->red.slot(slot_gcr_rn() + 2), 4, 0.5, 0, st));
         }
         fine += per_cycle;
@@ -798,8 +1025,10 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
       if (pin == MG_F64) ++fine64;
       // classical Gram-Schmidt, twice, against the previous w's
       if (k == 0) {
+        Prof pf2(h, MG_K_VECTOR, pin);
         LK(launch_dot(pin, n, nrhs, wk, h->gr.p, h->red.at(slot_gcr_wr(), 4), st));
       } else {
+        Prof pf2(h, MG_K_VECTOR, pin);
         for (int pass = 0; pass < 2; ++pass) {
           LK(launch_multidot(pin, n, nrhs, k, kMaxBasis, h->gW.p, n * nrhs, wk, h->red.at(slot_beta(), 0), st));
           RedArgs r2 = h->red.at(slot_gcr_wr(), 4);
@@ -807,8 +1036,11 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
                               zk, h->gr.p, r2, st));
         }
       }
-      LK(launch_gcr_update(pin, pin, n, nrhs, h->red.slot(slot_gcr_wr()), 4, wk, zk, h->gx.p, h->gr.p,
-                           h->red.at(slot_gcr_rn() + 2, 4), st));
+      {
+        Prof pf2(h, MG_K_VECTOR, pin);
+        LK(launch_gcr_update(pin, pin, n, nrhs, h->red.slot(slot_gcr_wr()), 4, wk, zk, h->gx.p, h->gr.p,
+                             h->red.at(slot_gcr_rn() + 2, 4), st));
+      }
       RET(read_slots(h, slot_gcr_rn(), 4 * nrhs));
       ++k;
       ++total_iters;

@@ -157,16 +157,34 @@ __global__ void __launch_bounds__(kVecThreads)
     multiaxpy_kernel(size_t n, int k, int kmax, const double* beta, const S* W, const S* Zb, size_t jstride, S* w,
                      S* z, const S* r, RedArgs ra) {
   typedef typename Store<S>::R R;
+  __shared__ cx<R> sb[64];
   const int rhs = blockIdx.y;
   const size_t off = (size_t)rhs * n;
   const double* bt = beta + (size_t)rhs * kmax * 2;
+  for (int j = threadIdx.x; j < k; j += kVecThreads) sb[j] = mk<R>((R)bt[2 * j], (R)bt[2 * j + 1]);
+  __syncthreads();
   double red[3] = {0.0, 0.0, 0.0};
   for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
     cx<R> wv = ldc<R>(w + off, i), zv = ldc<R>(z + off, i);
-    for (int j = 0; j < k; ++j) {
-      const cx<R> b = mk<R>((R)bt[2 * j], (R)bt[2 * j + 1]);
-      wv = wv - b * ldc<R>(W + (size_t)j * jstride + off, i);
-      zv = zv - b * ldc<R>(Zb + (size_t)j * jstride + off, i);
+    // four basis vectors per round: eight independent loads in flight
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {
+      cx<R> a0 = ldc<R>(W + (size_t)(j + 0) * jstride + off, i), c0 = ldc<R>(Zb + (size_t)(j + 0) * jstride + off, i);
+      cx<R> a1 = ldc<R>(W + (size_t)(j + 1) * jstride + off, i), c1 = ldc<R>(Zb + (size_t)(j + 1) * jstride + off, i);
+      cx<R> a2 = ldc<R>(W + (size_t)(j + 2) * jstride + off, i), c2 = ldc<R>(Zb + (size_t)(j + 2) * jstride + off, i);
+      cx<R> a3 = ldc<R>(W + (size_t)(j + 3) * jstride + off, i), c3 = ldc<R>(Zb + (size_t)(j + 3) * jstride + off, i);
+      wv = wv - sb[j] * a0;
+      zv = zv - sb[j] * c0;
+      wv = wv - sb[j + 1] * a1;
+      zv = zv - sb[j + 1] * c1;
+      wv = wv - sb[j + 2] * a2;
+      zv = zv - sb[j + 2] * c2;
+      wv = wv - sb[j + 3] * a3;
+      zv = zv - sb[j + 3] * c3;
+    }
+    for (; j < k; ++j) {
+      wv = wv - sb[j] * ldc<R>(W + (size_t)j * jstride + off, i);
+      zv = zv - sb[j] * ldc<R>(Zb + (size_t)j * jstride + off, i);
     }
     stc(w + off, i, wv);
     stc(z + off, i, zv);

@@ -33,32 +33,54 @@ struct CoarseArgs {
   RedArgs red;
 };
 
-template <typename S, int NT>
+// G lanes cooperate on one output (i, B): lane q of the group sums the
+// (d, j) terms q, q + G, ...; the group then reduces with shuffles.  Small
+// coarse grids use large G so that the launch still covers every SM.
+template <typename S, int NT, int G>
 __global__ void __launch_bounds__(NT) coarse_apply_kernel(const CoarseArgs<S> A) {
   typedef typename Store<S>::R R;
   const int V = A.V, n = A.n;
-  const int t = blockIdx.x * NT + threadIdx.x;  // t = i V + B
+  const int t = blockIdx.x * NT + threadIdx.x;
+  const int o = t / G, q = t % G;  // output index o = i V + B
   const int rhs = blockIdx.y;
   const size_t voff = (size_t)rhs * n * V;
   double red[3] = {0.0, 0.0, 0.0};
-  if (t < n * V) {
-    const int i = t / V, B = t - i * V;
+  const bool live = o < n * V;
+  cx<R> acc = zero<R>();
+  int i = 0, B = 0;
+  if (live) {
+    i = o / V;
+    B = o - i * V;
     int c[4];
     site_coords(B, A.L, c);
-    cx<R> acc = zero<R>();
-    for (int d = 0; d < 9; ++d) {
-      const int nb = neighbor(c, A.L, d);
-      const S* row = A.C + ((size_t)(d * n + i) * n) * V + B;
-      const S* x = A.in + voff + nb;
-      for (int j = 0; j < n; ++j) acc = cfma(ldc<R>(row, (size_t)j * V), ldc<R>(x, (size_t)j * V), acc);
+    const int terms = 9 * n;
+    int d = q / n, j = q - (q / n) * n;
+    int nb = (q < terms) ? neighbor(c, A.L, d) : 0;
+    for (int p = q; p < terms; p += G) {
+      acc = cfma(ldc<R>(A.C, (((size_t)(d * n + i) * n) + j) * V + B), ldc<R>(A.in, voff + (size_t)j * V + nb), acc);
+      j += G;
+      while (j >= n) {
+        j -= n;
+        ++d;
+        if (d < 9) nb = neighbor(c, A.L, d);
+      }
     }
-    const size_t o = voff + (size_t)i * V + B;
+  }
+  if (G > 1) {
+#pragma unroll
+    for (int w = G / 2; w > 0; w >>= 1) {
+      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, w);
+      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, w);
+    }
+  }
+  if (live && q == 0) {
+    const size_t oo = voff + (size_t)i * V + B;
     cx<R> v = (R)A.a * acc;
-    if (A.y) v = v + (R)A.c * ldc<R>(A.y, o);
-    stc(A.out, o, v);
+    if (A.y) v = v + (R)A.c * ldc<R>(A.y, oo);
+    stc(A.out, oo, v);
     if (A.z) {
       const cx<R> vs = as_stored<S>(v);
-      const cx<R> dd = cmul_conj(vs, ldc<R>(A.z, o));
+      const cx<R> dd = cmul_conj(vs, ldc<R>(A.z, oo));
       red[0] = (double)dd.re;
       red[1] = (double)dd.im;
       red[2] = (double)norm2(vs);
@@ -67,10 +89,20 @@ __global__ void __launch_bounds__(NT) coarse_apply_kernel(const CoarseArgs<S> A)
   if (A.z) grid_reduce<3, NT>(red, A.red, rhs);
 }
 
+// Lanes per output: enough threads for ~64K in flight, at most 32.
+static int coarse_group(int ncomp, int V) {
+  const long outs = (long)ncomp * V;
+  int G = 1;
+  while (G < 32 && outs * G < 65536) G *= 2;
+  return G;
+}
+
 int launch_coarse_apply(const CoarseCall& k, cudaStream_t st) {
   constexpr int NT = 128;
   const int V = k.L[0] * k.L[1] * k.L[2] * k.L[3];
-  dim3 grid((k.ncomp * V + NT - 1) / NT, k.nrhs);
+  const int G = coarse_group(k.ncomp, V);
+  dim3 grid((unsigned)(((long)k.ncomp * V * G + NT - 1) / NT), k.nrhs);
+#define WMG_COARSE_G(S, GG) coarse_apply_kernel<S, NT, GG><<<grid, NT, 0, st>>>(A)
 #define WMG_COARSE(S)                                        \
   {                                                          \
     CoarseArgs<S> A;                                         \
@@ -85,7 +117,14 @@ int launch_coarse_apply(const CoarseCall& k, cudaStream_t st) {
     A.a = k.a;                                               \
     A.c = k.c;                                               \
     A.red = k.red;                                           \
-    coarse_apply_kernel<S, NT><<<grid, NT, 0, st>>>(A);      \
+    switch (G) {                                             \
+      case 1: WMG_COARSE_G(S, 1); break;                     \
+      case 2: WMG_COARSE_G(S, 2); break;                     \
+      case 4: WMG_COARSE_G(S, 4); break;                     \
+      case 8: WMG_COARSE_G(S, 8); break;                     \
+      case 16: WMG_COARSE_G(S, 16); break;                   \
+      default: WMG_COARSE_G(S, 32); break;                   \
+    }                                                        \
   }
   switch (k.prec) {
     case 0: WMG_COARSE(double2); break;
@@ -95,10 +134,13 @@ int launch_coarse_apply(const CoarseCall& k, cudaStream_t st) {
     default: return -1;
   }
 #undef WMG_COARSE
+#undef WMG_COARSE_G
   return launched() ? 0 : -1;
 }
 
-int coarse_blocks(int ncomp, int V) { return (ncomp * V + 127) / 128; }
+int coarse_blocks(int ncomp, int V) {
+  return (int)(((long)ncomp * V * coarse_group(ncomp, V) + 127) / 128);
+}
 
 // ------------------------------------------------------------------ aggregates
 // Fine site of aggregate B, aggregate-local site s.
@@ -208,17 +250,18 @@ int launch_prolong(int pin, int pP, int pout, const Agg& g, const void* P, const
 }
 
 // ------------------------------------------------------------------ coarsest: dense inverse
-// Dense FP64 matrix of a stencil operator in the internal vector order
+// Dense matrix of a stencil operator in the internal vector order
 // (row i V + B, column j V + B'), written into the left half of an
-// augmented [N][2N] array whose right half is set to the identity.
-__global__ void stencil_to_dense_kernel(const double2* C, int L0, int L1, int L2, int L3, int n, double2* aug) {
+// augmented [N][2N] array (element type T) whose right half is the identity.
+template <typename T>
+__global__ void stencil_to_dense_kernel(const double2* C, int L0, int L1, int L2, int L3, int n, T* aug) {
   const int L[4] = {L0, L1, L2, L3};
   const int V = L0 * L1 * L2 * L3;
   const int N = n * V;
   const size_t tot = (size_t)N * 2 * N;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
     const int row = (int)(e / (2 * (size_t)N)), col = (int)(e % (2 * (size_t)N));
-    double2 v = make_double2(0.0, 0.0);
+    cx<double> v = zero<double>();
     if (col < N) {
       const int i = row / V, B = row % V, j = col / V, Bp = col % V;
       int c[4];
@@ -226,94 +269,118 @@ __global__ void stencil_to_dense_kernel(const double2* C, int L0, int L1, int L2
       for (int d = 0; d < 9; ++d) {
         if (neighbor(c, L, d) != Bp) continue;
         const double2 a = C[((size_t)(d * n + i) * n + j) * V + B];
-        v.x += a.x;
-        v.y += a.y;
+        v.re += a.x;
+        v.im += a.y;
       }
     } else if (col - N == row) {
-      v.x = 1.0;
+      v.re = 1.0;
     }
-    aug[e] = v;
+    stc(aug, e, v);
   }
 }
 
-// Gauss-Jordan step k, part 1 (one block): partial pivot on column k, swap
-// rows, scale the pivot row, save column k (zero at k) for the update.
-__global__ void gj_pivot_kernel(double2* aug, int N, int k, double2* colbuf, int* err) {
-  __shared__ double best[1024];
-  __shared__ int arg[1024];
-  const int tid = threadIdx.x, nt = blockDim.x;
+// Gauss-Jordan elimination with virtual partial pivoting: rows are never
+// swapped and pivot rows are never scaled during the sweep.  Step k takes the
+// unused row p_k with the largest |a_{i,k}| as pivot and subtracts
+// (a_ik / a_{p_k,k}) times row p_k from every other row; afterwards row p_k of
+// the left block is a_{p_k,k} e_k, so row k of the inverse is row p_k of the
+// right block divided by a_{p_k,k}.  One launch per step: the launch for
+// step k also snapshots column k+1 and finds the next pivot with a packed
+// 64-bit atomicMax (|a|^2 as float bits above, ~row below: ties go to the
+// smallest row, independently of scheduling).
+__device__ __forceinline__ unsigned long long pivot_key(float mag2, int row) {
+  return ((unsigned long long)__float_as_uint(mag2) << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)row);
+}
+__device__ __forceinline__ int pivot_row(unsigned long long key) { return (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFu)); }
+
+template <typename T>
+__global__ void gj_init_kernel(const T* aug, int N, T* col0, unsigned long long* keys) {
+  typedef typename Store<T>::R R;
   const size_t ld = 2 * (size_t)N;
-  double b = -1.0;
-  int a = N;
-  for (int i = k + tid; i < N; i += nt) {
-    const double2 v = aug[(size_t)i * ld + k];
-    const double m = v.x * v.x + v.y * v.y;
-    if (m > b) {
-      b = m;
-      a = i;
-    }
+  unsigned long long best = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const T v = aug[(size_t)i * ld];
+    col0[i] = v;
+    const cx<R> c = ldc<R>(&v, 0);
+    const unsigned long long key = pivot_key((float)norm2(c), i);
+    best = key > best ? key : best;
   }
-  best[tid] = b;
-  arg[tid] = a;
-  __syncthreads();
-  for (int o = nt / 2; o > 0; o >>= 1) {
-    if (tid < o) {
-      const double b2 = best[tid + o];
-      const int a2 = arg[tid + o];
-      if (b2 > best[tid] || (b2 == best[tid] && a2 < arg[tid])) {
-        best[tid] = b2;
-        arg[tid] = a2;
-      }
-    }
-    __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_down_sync(0xffffffffu, best, o);
+    best = other > best ? other : best;
   }
-  const int p = arg[0];
-  if (!(best[0] > 0.0)) {
-    if (tid == 0) *err = 1;
-    return;
-  }
-  if (p != k) {
-    for (size_t j = tid; j < ld; j += nt) {
-      const double2 t = aug[(size_t)k * ld + j];
-      aug[(size_t)k * ld + j] = aug[(size_t)p * ld + j];
-      aug[(size_t)p * ld + j] = t;
-    }
-  }
-  __syncthreads();
-  const double2 pv = aug[(size_t)k * ld + k];
-  const double den = pv.x * pv.x + pv.y * pv.y;
-  const double2 inv = make_double2(pv.x / den, -pv.y / den);
-  __syncthreads();
-  for (size_t j = tid; j < ld; j += nt) {
-    const double2 t = aug[(size_t)k * ld + j];
-    aug[(size_t)k * ld + j] = make_double2(t.x * inv.x - t.y * inv.y, t.x * inv.y + t.y * inv.x);
-  }
-  for (int i = tid; i < N; i += nt) colbuf[i] = (i == k) ? make_double2(0.0, 0.0) : aug[(size_t)i * ld + k];
+  if ((threadIdx.x & 31) == 0 && best) atomicMax(keys, best);
 }
 
-// Part 2: every row i != k subtracts colbuf[i] times the pivot row.
-__global__ void gj_update_kernel(double2* aug, int N, int k, const double2* colbuf, const int* err) {
+template <typename T>
+__global__ void gj_step_kernel(T* aug, int N, int k, const T* colk, T* colnext, int* used,
+                               unsigned long long* keys, int* err) {
+  typedef typename Store<T>::R R;
+  __shared__ unsigned long long wbest[32];
   if (*err) return;
   const size_t ld = 2 * (size_t)N;
-  const size_t tot = (size_t)N * ld;
+  const int p = pivot_row(keys[k]);
+  if (p < 0 || p >= N) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *err = 1;
+    return;
+  }
+  const cx<R> piv = ldc<R>(colk, p);
+  if (!(norm2(piv) > (R)0)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *err = 1;
+    return;
+  }
+  const R den = norm2(piv);
+  const cx<R> pinv = mk<R>(piv.re / den, -piv.im / den);
+  const size_t width = ld - (size_t)k;  // columns k .. 2N-1 (columns < k of row p are zero)
+  const size_t tot = (size_t)N * width;
+  unsigned long long best = 0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / ld);
-    const size_t j = e % ld;
-    if (i == k || j < (size_t)k) continue;  // columns < k of row k are already zero
-    const double2 f = colbuf[i];
-    const double2 pk = aug[(size_t)k * ld + j];
-    double2 v = aug[e];
-    v.x -= f.x * pk.x - f.y * pk.y;
-    v.y -= f.x * pk.y + f.y * pk.x;
-    aug[e] = v;
+    const int i = (int)(e / width);
+    const size_t j = (size_t)k + e % width;
+    const size_t o = (size_t)i * ld + j;
+    cx<R> v = ldc<R>(aug, o);
+    if (i != p) {
+      const cx<R> f = ldc<R>(colk, i) * pinv;
+      v = (j == (size_t)k) ? zero<R>() : v - f * ldc<R>(aug, (size_t)p * ld + j);
+      stc(aug, o, v);
+    }
+    if (j == (size_t)k + 1 && (int)j < N) {
+      stc(colnext, i, v);
+      if (i != p && !used[i]) {
+        const unsigned long long key = pivot_key((float)norm2(v), i);
+        best = key > best ? key : best;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_down_sync(0xffffffffu, best, o);
+    best = other > best ? other : best;
+  }
+  if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = wbest[w] > b ? wbest[w] : b;
+    if (b && k + 1 < N) atomicMax(keys + k + 1, b);
+    if (blockIdx.x == 0) used[p] = 1;
   }
 }
 
-__global__ void copy_right_half_kernel(const double2* aug, int N, double2* inv) {
+// inv[k][c] = aug[p_k][N + c] / aug[p_k][k]
+template <typename T>
+__global__ void gj_finish_kernel(const T* aug, int N, const unsigned long long* keys, T* inv) {
+  typedef typename Store<T>::R R;
   const size_t tot = (size_t)N * N;
+  const size_t ld = 2 * (size_t)N;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t i = e / N, j = e % N;
-    inv[e] = aug[i * 2 * (size_t)N + N + j];
+    const int k = (int)(e / N);
+    const size_t c = e % N;
+    const int p = pivot_row(keys[k]);
+    if (p < 0 || p >= N) continue;
+    const cx<R> piv = ldc<R>(aug, (size_t)p * ld + k);
+    const R den = norm2(piv);
+    const cx<R> pinv = mk<R>(piv.re / den, -piv.im / den);
+    stc(inv, e, ldc<R>(aug, (size_t)p * ld + N + c) * pinv);
   }
 }
 
@@ -323,48 +390,87 @@ static unsigned grid_for(size_t tot, size_t cap) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-int dense_inverse(const double2* C, const int L[4], int n, double2* aug, double2* colbuf, int* err, double2* inv,
-                  cudaStream_t st) {
+template <typename T>
+static int dense_inverse_t(const double2* C, const int L[4], int n, T* aug, T* cols, int* err, T* inv,
+                           unsigned long long* keys, int* used, cudaStream_t st) {
   const int V = L[0] * L[1] * L[2] * L[3];
   const int N = n * V;
-  stencil_to_dense_kernel<<<grid_for((size_t)N * 2 * N, 8192), 256, 0, st>>>(C, L[0], L[1], L[2], L[3], n, aug);
+  stencil_to_dense_kernel<T><<<grid_for((size_t)N * 2 * N, 8192), 256, 0, st>>>(C, L[0], L[1], L[2], L[3], n, aug);
+  cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (N + 1), st);
+  cudaMemsetAsync(used, 0, sizeof(int) * N, st);
+  gj_init_kernel<T><<<grid_for(N, 1024), 256, 0, st>>>(aug, N, cols, keys);
   if (!launched()) return -1;
   for (int k = 0; k < N; ++k) {
-    gj_pivot_kernel<<<1, 1024, 0, st>>>(aug, N, k, colbuf, err);
-    gj_update_kernel<<<grid_for((size_t)N * 2 * N, 4096), 256, 0, st>>>(aug, N, k, colbuf, err);
+    const T* colk = cols + (size_t)(k & 1) * N;
+    T* colnext = cols + (size_t)((k + 1) & 1) * N;
+    gj_step_kernel<T><<<grid_for((size_t)N * (2 * N - k), 2048), 256, 0, st>>>(aug, N, k, colk, colnext, used, keys,
+                                                                              err);
   }
-  copy_right_half_kernel<<<grid_for((size_t)N * N, 8192), 256, 0, st>>>(aug, N, inv);
+  gj_finish_kernel<T><<<grid_for((size_t)N * N, 8192), 256, 0, st>>>(aug, N, keys, inv);
   return launched() ? 0 : -1;
 }
 
-// y = inv x for nrhs vectors; one warp per row, FP64 matrix and arithmetic.
-template <typename SI, typename SO>
-__global__ void dense_matvec_kernel(int N, const double2* inv, const SI* x, SO* y) {
+int dense_inverse(int prec, const double2* C, const int L[4], int n, void* aug, void* scratch, int* err, void* inv,
+                  cudaStream_t st) {
+  // scratch: two column snapshots [2][N] of the element type, N + 1 pivot keys, N used-row flags
+  const int N = n * L[0] * L[1] * L[2] * L[3];
+  const size_t eb = prec == 0 ? 16 : 8;
+  char* sc = (char*)scratch;
+  unsigned long long* keys = (unsigned long long*)(sc + 2 * (size_t)N * eb);
+  int* used = (int*)(keys + N + 1);
+  if (prec == 0)
+    return dense_inverse_t<double2>(C, L, n, (double2*)aug, (double2*)sc, err, (double2*)inv, keys, used, st);
+  if (prec == 1) return dense_inverse_t<float2>(C, L, n, (float2*)aug, (float2*)sc, err, (float2*)inv, keys, used, st);
+  return -1;
+}
+
+size_t dense_inverse_scratch_bytes(int prec, int N) {
+  return 2 * (size_t)N * (prec == 0 ? 16 : 8) + 8 * ((size_t)N + 1) + 4 * (size_t)N + 64;
+}
+
+// y = inv x (+ y if acc) for nrhs vectors; one warp per row.  Arithmetic in
+// the matrix's precision.
+template <typename TM, typename SI, typename SO>
+__global__ void dense_matvec_kernel(int N, const TM* inv, const SI* x, SO* y, int acc) {
+  typedef typename Store<TM>::R R;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int rhs = blockIdx.y;
   if (warp >= N) return;
-  const double2* row = inv + (size_t)warp * N;
+  const TM* row = inv + (size_t)warp * N;
   const SI* xr = x + (size_t)rhs * N;
-  cx<double> acc = zero<double>();
-  for (int j = lane; j < N; j += 32) {
-    const double2 a = row[j];
-    acc = cfma(mk<double>(a.x, a.y), ldc<double>(xr, j), acc);
+  cx<R> a = zero<R>(), b = zero<R>();
+  int j = lane;
+  for (; j + 32 < N; j += 64) {  // two independent chains
+    a = cfma(ldc<R>(row, j), ldc<R>(xr, j), a);
+    b = cfma(ldc<R>(row, j + 32), ldc<R>(xr, j + 32), b);
   }
+  for (; j < N; j += 32) a = cfma(ldc<R>(row, j), ldc<R>(xr, j), a);
+  a = a + b;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    acc.re += __shfl_down_sync(0xffffffffu, acc.re, o);
-    acc.im += __shfl_down_sync(0xffffffffu, acc.im, o);
+    a.re += __shfl_down_sync(0xffffffffu, a.re, o);
+    a.im += __shfl_down_sync(0xffffffffu, a.im, o);
   }
-  if (lane == 0) stc(y, (size_t)rhs * N + warp, acc);
+  if (lane == 0) {
+    const size_t o = (size_t)rhs * N + warp;
+    cx<double> v = mk<double>((double)a.re, (double)a.im);
+    if (acc) v = v + ldc<double>(y, o);
+    stc(y, o, v);
+  }
 }
 
-int launch_dense_matvec(int pin, int pout, int N, const double2* inv, const void* x, void* y, int nrhs,
+int launch_dense_matvec(int pm, int pin, int pout, int N, const void* inv, const void* x, void* y, int nrhs, int acc,
                         cudaStream_t st) {
   dim3 grid((N * 32 + 255) / 256, nrhs);
-  if (pin == 0 && pout == 0)
-    dense_matvec_kernel<double2, double2><<<grid, 256, 0, st>>>(N, inv, (const double2*)x, (double2*)y);
-  else if (pin == 1 && pout == 1)
-    dense_matvec_kernel<float2, float2><<<grid, 256, 0, st>>>(N, inv, (const float2*)x, (float2*)y);
+  if (pm == 0 && pin == 0 && pout == 0)
+    dense_matvec_kernel<double2, double2, double2>
+        <<<grid, 256, 0, st>>>(N, (const double2*)inv, (const double2*)x, (double2*)y, acc);
+  else if (pm == 1 && pin == 0 && pout == 0)
+    dense_matvec_kernel<float2, double2, double2>
+        <<<grid, 256, 0, st>>>(N, (const float2*)inv, (const double2*)x, (double2*)y, acc);
+  else if (pm == 1 && pin == 1 && pout == 1)
+    dense_matvec_kernel<float2, float2, float2>
+        <<<grid, 256, 0, st>>>(N, (const float2*)inv, (const float2*)x, (float2*)y, acc);
   else
     return -1;
   return launched() ? 0 : -1;

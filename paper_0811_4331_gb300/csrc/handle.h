@@ -64,8 +64,10 @@ struct Level {
   DevBuf cop[4];    // level >= 1: stencil [9][ncomp][ncomp][V]
   // prolongator to level l+1, per precision: [Vc][2][nv][nhalf][bsites]
   DevBuf P[4];
-  // coarsest level: dense FP64 inverse [N][N], N = ncomp V
+  // coarsest level: dense inverse [N][N], N = ncomp V, FP64 (plain) or FP32
+  // (mixed: applied with FP64 iterative refinement)
   DevBuf inv;
+  int inv_prec = 0;
   int N() const { return ncomp * V; }
   size_t n() const { return (size_t)ncomp * V; }
 };
@@ -112,5 +114,24 @@ struct mg_handle {
   wmg::DevBuf gx, gr, gw, gz, gW, gZ, gb64, gx64, gr64, gtmp;
   int basis_cap = 0;  // vectors held by gW / gZ per rhs
   wmg::DevBuf err_flag;  // device int set by setup kernels on failure
+  // profiler: event pairs per (class, precision)
+  unsigned prof_mask = 0;
+  std::vector<cudaEvent_t> prof_pool;
+  size_t prof_used = 0;
+  std::vector<std::pair<int, size_t>> prof_marks;  // (class * 4 + prec, index of start event)
+  // CUDA graphs of the V-cycle, keyed by (nrhs, input, output, buffer generation)
+  struct CycleGraph {
+    int nrhs;
+    const void* in;
+    void* out;
+    unsigned long long gen;
+    unsigned long long nodes;
+    cudaGraphExec_t exec;
+  };
+  std::vector<CycleGraph> graphs;
+  unsigned long long buf_gen = 1;  // bumped whenever a work buffer or the reducer is reallocated
+  cudaStream_t cap_st = nullptr;   // private stream used only for capture
+  bool capturing = false;
+  bool use_graphs = true;
   double* host_slots = nullptr;  // pinned mirror for read-backs
 };

@@ -124,21 +124,25 @@ int launch_restrict(int pin, int pP, int pout, const Agg& g, const void* P, cons
 int launch_prolong(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
                    cudaStream_t st);
 
-// Coarsest level: dense inverse (Gauss-Jordan, partial pivoting, FP64) of
-// a stencil operator; aug is [N][2N] scratch, colbuf [N], inv [N][N];
-// *err = 1 on a zero pivot.
-int dense_inverse(const double2* C, const int L[4], int n, double2* aug, double2* colbuf, int* err, double2* inv,
+// Coarsest level: dense inverse (Gauss-Jordan, partial pivoting) of an FP64
+// stencil operator in precision prec (0 or 1); aug is [N][2N] of precision
+// prec, scratch holds dense_inverse_scratch_bytes(prec, N), inv is [N][N];
+// *err = 1 on a zero pivot.  N + 2 launches.
+int dense_inverse(int prec, const double2* C, const int L[4], int n, void* aug, void* scratch, int* err, void* inv,
                   cudaStream_t st);
-int launch_dense_matvec(int pin, int pout, int N, const double2* inv, const void* x, void* y, int nrhs,
-                        cudaStream_t st);
+size_t dense_inverse_scratch_bytes(int prec, int N);
+// y = inv x (+ y if acc); (matrix, in, out) precisions (0,0,0), (1,0,0), (1,1,1).
+int launch_dense_matvec(int pm, int pin, int pout, int N, const void* inv, const void* x, void* y, int nrhs,
+                        int acc, cudaStream_t st);
 
 // Setup: blockwise Gram-Schmidt (err = 2 on rank loss), prolongator
 // columns as fields, Galerkin coarse stencil column j.
 int launch_block_gs(const Agg& g, const double2* cand, double2* P, int* err, cudaStream_t st);
-int launch_p_column(const Agg& g, const double2* P, int j, double2* v, cudaStream_t st);
+// Columns j0 .. j0 + ncols - 1 at v + (j - j0) * ncomp * V.
+int launch_p_column(const Agg& g, const double2* P, int j0, int ncols, double2* v, cudaStream_t st);
 int launch_galerkin_wilson(const Agg& g, const double2* links64, double mass, const double2* vj, const double2* P,
-                           int j, double2* Cout, cudaStream_t st);
-int launch_galerkin_stencil(const Agg& g, const double2* Cfine, const double2* vj, const double2* P, int j,
-                            double2* Cout, cudaStream_t st);
+                           int j0, int ncols, double2* Cout, cudaStream_t st);
+int launch_galerkin_stencil(const Agg& g, const double2* Cfine, const double2* vj, const double2* P, int j0,
+                            int ncols, double2* Cout, cudaStream_t st);
 
 }  // namespace wmg

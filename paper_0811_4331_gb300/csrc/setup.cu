@@ -97,8 +97,10 @@ int launch_block_gs(const Agg& g, const double2* cand, double2* P, int* err, cud
 
 // Column j of P (j = chi' nv + k') as a level-l field [ncomp][V]: the k'-th
 // orthonormal vector on its chirality chi' half, zero on the other half.
-__global__ void p_column_kernel(const Agg g, const double2* P, int j, double2* v) {
+__global__ void p_column_kernel(const Agg g, const double2* P, int j0, double2* vbase) {
   const size_t tot = (size_t)g.ncomp * g.V;
+  const int j = j0 + blockIdx.y;
+  double2* v = vbase + (size_t)blockIdx.y * tot;
   const int chi = j / g.nv, k = j - chi * g.nv;
   const int len = g.nhalf * g.bsites;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
@@ -119,11 +121,11 @@ __global__ void p_column_kernel(const Agg g, const double2* P, int j, double2* v
   }
 }
 
-int launch_p_column(const Agg& g, const double2* P, int j, double2* v, cudaStream_t st) {
+int launch_p_column(const Agg& g, const double2* P, int j0, int ncols, double2* v, cudaStream_t st) {
   size_t tot = (size_t)g.ncomp * g.V;
   size_t b = (tot + 255) / 256;
   if (b > 8192) b = 8192;
-  p_column_kernel<<<(unsigned)b, 256, 0, st>>>(g, P, j, v);
+  p_column_kernel<<<dim3((unsigned)b, ncols), 256, 0, st>>>(g, P, j0, v);
   return launched() ? 0 : -1;
 }
 
@@ -204,8 +206,10 @@ __device__ __forceinline__ bool crosses(const Agg& g, int s, int d) {
 }
 
 template <typename Op, int NT>
-__global__ void __launch_bounds__(NT) galerkin_kernel(const Agg g, Op op, const double2* vj, const double2* P, int j,
-                                                      double2* Cout) {
+__global__ void __launch_bounds__(NT) galerkin_kernel(const Agg g, Op op, const double2* vbase, const double2* P,
+                                                      int j0, double2* Cout) {
+  const int j = j0 + blockIdx.y;
+  const double2* vj = vbase + (size_t)blockIdx.y * g.ncomp * g.V;
   extern __shared__ unsigned char smem_raw[];
   cx<double>* h = (cx<double>*)smem_raw;                     // [ncomp][bsites]
   cx<double>* acc0 = h + (size_t)g.ncomp * g.bsites;         // [2 nv]
@@ -249,30 +253,30 @@ __global__ void __launch_bounds__(NT) galerkin_kernel(const Agg g, Op op, const 
 }
 
 template <typename Op>
-static int galerkin_t(const Agg& g, const Op& op, const double2* vj, const double2* P, int j, double2* Cout,
-                      cudaStream_t st) {
+static int galerkin_t(const Agg& g, const Op& op, const double2* vj, const double2* P, int j0, int ncols,
+                      double2* Cout, cudaStream_t st) {
   constexpr int NT = 256;
   const size_t sm = ((size_t)g.ncomp * g.bsites + 2 * g.nv) * sizeof(cx<double>);
   if (sm > 200 * 1024) return -1;
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(galerkin_kernel<Op, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  galerkin_kernel<Op, NT><<<g.Vc, NT, sm, st>>>(g, op, vj, P, j, Cout);
+  galerkin_kernel<Op, NT><<<dim3(g.Vc, ncols), NT, sm, st>>>(g, op, vj, P, j0, Cout);
   return launched() ? 0 : -1;
 }
 
 int launch_galerkin_wilson(const Agg& g, const double2* links64, double mass, const double2* vj, const double2* P,
-                           int j, double2* Cout, cudaStream_t st) {
+                           int j0, int ncols, double2* Cout, cudaStream_t st) {
   WilsonHopOp op;
   op.U = links64;
   op.mass = mass;
-  return galerkin_t(g, op, vj, P, j, Cout, st);
+  return galerkin_t(g, op, vj, P, j0, ncols, Cout, st);
 }
 
-int launch_galerkin_stencil(const Agg& g, const double2* Cfine, const double2* vj, const double2* P, int j,
-                            double2* Cout, cudaStream_t st) {
+int launch_galerkin_stencil(const Agg& g, const double2* Cfine, const double2* vj, const double2* P, int j0,
+                            int ncols, double2* Cout, cudaStream_t st) {
   StencilHopOp op;
   op.C = Cfine;
-  return galerkin_t(g, op, vj, P, j, Cout, st);
+  return galerkin_t(g, op, vj, P, j0, ncols, Cout, st);
 }
 
 }  // namespace wmg

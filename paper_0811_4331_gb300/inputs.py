@@ -24,6 +24,10 @@ Layouts are the external ones of the C ABI: a spinor field is
 field is (4, Lt, Lz, Ly, Lx, 3, 3) with mu = 0..3 for x, y, z, t.  ``dims`` is
 always given as (Lx, Ly, Lz, Lt).
 """
+import ctypes
+import os
+import subprocess
+
 import numpy as np
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -129,19 +133,6 @@ def _roll(f, mu, step):
     return np.roll(f, -step, axis=3 - mu)
 
 
-def staple_sum(U, mu):
-    """Sum over nu != mu of the up and down staples attached to U_mu(n)."""
-    A = np.zeros_like(U[mu])
-    for nu in range(4):
-        if nu == mu:
-            continue
-        Unu_xmu = _roll(U[nu], mu, +1)
-        A += Unu_xmu @ _dag(_roll(U[mu], nu, +1)) @ _dag(U[nu])
-        Unu_xmu_mnu = _roll(Unu_xmu, nu, -1)
-        A += _dag(Unu_xmu_mnu) @ _dag(_roll(U[mu], nu, -1)) @ _roll(U[nu], nu, -1)
-    return A
-
-
 def plaquette(U):
     """Average of Re tr(U_mu(n) U_nu(n+mu) U_mu(n+nu)^+ U_nu(n)^+) / 3 over n and mu < nu."""
     tot = 0.0
@@ -154,89 +145,52 @@ def plaquette(U):
     return tot / cnt
 
 
-_SUBGROUPS = ((0, 1), (1, 2), (0, 2))
+# ------------------------------------------------------------------ heatbath
+# The heatbath is plain C (gen/heatbath.c), compiled with -ffp-contract=off
+# and restricted to correctly rounded operations, so that the field is the
+# same bit for bit on every machine (its critical mass and reference solves
+# are stored once).
+
+_GEN_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "gen")
+_GEN_LIB = os.path.join(_GEN_DIR, "libgen.so")
+_gen = None
 
 
-def _kp_sample_x0(rng, alpha):
-    """Kennedy-Pendleton: x0 in [-1, 1] with density ~ sqrt(1 - x0^2) exp(alpha x0)."""
-    n = alpha.shape[0]
-    x0 = np.empty(n)
-    todo = np.arange(n)
-    while todo.size:
-        a = alpha[todo]
-        r1 = 1.0 - rng.random(todo.size)
-        r2 = rng.random(todo.size)
-        r3 = 1.0 - rng.random(todo.size)
-        r4 = rng.random(todo.size)
-        delta = -(np.log(r1) + np.cos(2.0 * np.pi * r2) ** 2 * np.log(r3)) / a
-        ok = r4 * r4 <= 1.0 - 0.5 * delta
-        x0[todo[ok]] = 1.0 - delta[ok]
-        todo = todo[~ok]
-    return x0
+def build_generators():
+    """Compile gen/heatbath.c into gen/libgen.so (gcc, no FMA contraction)."""
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           os.path.join(_GEN_DIR, "heatbath.c"), "-o", _GEN_LIB + ".tmp", "-lm"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("building the gauge generator failed:\n" + r.stderr)
+    os.replace(_GEN_LIB + ".tmp", _GEN_LIB)
+    return _GEN_LIB
 
 
-def _su2_heatbath(rng, W, i, j, beta):
-    """SU(2) subgroup (i, j) update matrices R for links with W = U A (n, 3, 3)."""
-    n = W.shape[0]
-    w00, w01, w10, w11 = W[:, i, i], W[:, i, j], W[:, j, i], W[:, j, j]
-    b0 = 0.5 * (w00 + w11).real
-    b3 = 0.5 * (w00 - w11).imag
-    b1 = 0.5 * (w01 + w10).imag
-    b2 = 0.5 * (w01 - w10).real
-    k = np.sqrt(b0 * b0 + b1 * b1 + b2 * b2 + b3 * b3)
-    k = np.maximum(k, 1e-300)
-    Vm = np.empty((n, 2, 2), dtype=np.complex128)
-    Vm[:, 0, 0] = b0 + 1j * b3
-    Vm[:, 0, 1] = b2 + 1j * b1
-    Vm[:, 1, 0] = -b2 + 1j * b1
-    Vm[:, 1, 1] = b0 - 1j * b3
-    Vm /= k[:, None, None]
-    x0 = _kp_sample_x0(rng, 2.0 * beta * k / 3.0)
-    # uniform direction on the sphere for (x1, x2, x3)
-    cth = 2.0 * rng.random(n) - 1.0
-    phi = 2.0 * np.pi * rng.random(n)
-    rad = np.sqrt(np.maximum(1.0 - x0 * x0, 0.0))
-    sth = np.sqrt(np.maximum(1.0 - cth * cth, 0.0))
-    x1, x2, x3 = rad * sth * np.cos(phi), rad * sth * np.sin(phi), rad * cth
-    X = np.empty((n, 2, 2), dtype=np.complex128)
-    X[:, 0, 0] = x0 + 1j * x3
-    X[:, 0, 1] = x2 + 1j * x1
-    X[:, 1, 0] = -x2 + 1j * x1
-    X[:, 1, 1] = x0 - 1j * x3
-    r = X @ _dag(Vm)
-    R = np.zeros((n, 3, 3), dtype=np.complex128)
-    R[:, 0, 0] = R[:, 1, 1] = R[:, 2, 2] = 1.0
-    R[:, i, i], R[:, i, j], R[:, j, i], R[:, j, j] = r[:, 0, 0], r[:, 0, 1], r[:, 1, 0], r[:, 1, 1]
-    return R
+def _generators():
+    global _gen
+    if _gen is None:
+        if not os.path.exists(_GEN_LIB):
+            build_generators()
+        lib = ctypes.CDLL(_GEN_LIB)
+        lib.heatbath_su3.restype = ctypes.c_int
+        lib.heatbath_su3.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_uint64]
+        _gen = lib
+    return _gen
 
 
 def heatbath_gauge(dims, beta=6.0, sweeps=200, seed=0):
-    """Wilson-action gauge field after ``sweeps`` Cabibbo-Marinari heatbath sweeps.
+    """Wilson-action gauge field after ``sweeps`` Cabibbo-Marinari heatbath sweeps (cold start).
 
-    Cold start (all links 1).  One sweep updates, for mu = 0..3 and each site
-    parity, every U_mu(n) of that parity by the three SU(2) subgroups in turn
-    (links of one direction and parity share no staple).  Reunitarised after
-    every sweep.
+    Three SU(2) subgroups per link, each by Kennedy-Pendleton; mu = 0..3, even
+    then odd sites per sweep; reunitarised after every sweep; random numbers
+    from one SplitMix64 stream seeded with ``seed``.  See gen/heatbath.c.
     """
-    rng = np.random.default_rng(seed)
-    U = unit_gauge(dims)
     lat = _shape(dims)
-    t, z, y, x = np.meshgrid(*[np.arange(L) for L in lat], indexing="ij")
-    parity = (t + z + y + x) % 2
-    masks = [parity == p for p in (0, 1)]
-    for _ in range(sweeps):
-        for mu in range(4):
-            for p in (0, 1):
-                m = masks[p]
-                A = staple_sum(U, mu)[m]
-                Um = U[mu][m]
-                W = Um @ A
-                for (i, j) in _SUBGROUPS:
-                    R = _su2_heatbath(rng, W, i, j, beta)
-                    Um = R @ Um
-                    W = R @ W
-                U[mu][m] = Um
-        U = reunitarize(U)
+    U = np.empty((4,) + lat + (3, 3), dtype=np.complex128)
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    _generators().heatbath_su3(U.ctypes.data, d, float(beta), int(sweeps), int(seed))
     return U
 
 

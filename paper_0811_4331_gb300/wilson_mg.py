@@ -42,6 +42,7 @@ class mg_params(ctypes.Structure):
         ("coarse_prec", ctypes.c_int),
         ("reliable_delta", ctypes.c_double),
         ("seed", ctypes.c_uint64),
+        ("use_graphs", ctypes.c_int),
     ]
 
 
@@ -90,6 +91,9 @@ def _load():
         "mg_get_prolongator": (I, [VP, I, VP]),
         "mg_get_coarse_op": (I, [VP, I, VP]),
         "mg_footprint": (ctypes.c_size_t, [P(I), P(mg_params), I]),
+        "mg_profile": (I, [VP, ctypes.c_uint]),
+        "mg_launch_count": (ctypes.c_ulonglong, []),
+        "mg_profile_read": (I, [VP, I, I, P(ctypes.c_longlong), P(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -103,7 +107,12 @@ LIB = _load()
 # every entry point declared in include/wilson_mg.h
 EXPORTS = ["mg_last_error", "mg_default_params", "mg_setup", "mg_destroy", "mg_solve", "dslash_apply",
            "coarse_apply", "restrict_apply", "prolong_apply", "mr_apply", "vcycle_apply", "mg_field_to_internal",
-           "mg_field_from_internal", "mg_level_info", "mg_get_prolongator", "mg_get_coarse_op", "mg_footprint"]
+           "mg_field_from_internal", "mg_level_info", "mg_get_prolongator", "mg_get_coarse_op", "mg_footprint",
+           "mg_profile", "mg_profile_read", "mg_launch_count"]
+
+(MG_K_DSLASH, MG_K_COARSE, MG_K_RESTRICT, MG_K_PROLONG, MG_K_VECTOR, MG_K_COARSEST, MG_K_SETUP, MG_K_GALERKIN,
+ MG_K_INVERSE) = range(9)
+KERNEL_CLASS_NAMES = ["dslash", "coarse", "restrict", "prolong", "vector", "coarsest", "setup", "galerkin", "inverse"]
 
 
 def mg_last_error():
@@ -283,6 +292,22 @@ def mg_get_coarse_op(h, level):
 def mg_footprint(dims, params, nrhs):
     d = (ctypes.c_int * 4)(*[int(x) for x in dims])
     return int(LIB.mg_footprint(d, ctypes.byref(params), int(nrhs)))
+
+
+def mg_launch_count():
+    return int(LIB.mg_launch_count())
+
+
+def mg_profile(h, mask):
+    """Enable the per-launch event profiler of h (h None: default for handles created later)."""
+    _check(LIB.mg_profile(h.ptr if h is not None else None, int(mask)))
+
+
+def mg_profile_read(h, kclass, prec):
+    n = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    _check(LIB.mg_profile_read(h.ptr, kclass, prec, ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
 
 
 def internal_empty(h, level, prec, nrhs=1, device="cuda"):

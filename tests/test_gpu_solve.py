@@ -142,3 +142,21 @@ def test_bad_arguments():
     p = wm.mg_default_params(n_levels=2, block=[(2, 2, 2, 2)], nv=[97])
     with pytest.raises(wm.MgError):
         wm.mg_setup(U, dims, 0.1, p)
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_graph_replay_equals_eager_launches(mixed):
+    """The V-cycle captured as a CUDA graph gives bit-identical iterates to eager launches."""
+    wm = require_gpu()
+    dims, U, b, starts = _small_workload()
+    xs, its = [], []
+    for graphs in (1, 0):
+        p = wm.mg_default_params(n_levels=2, block=[(2, 2, 2, 2)], nv=[8], setup_sweeps=[10], mixed=mixed,
+                                 use_graphs=graphs)
+        h = wm.mg_setup(U, dims, 0.1, p, starts=starts)
+        x = np.zeros_like(b)
+        _, st = wm.mg_solve(h, b, x, 1e-10)
+        xs.append(x)
+        its.append(st[0]["iters"])
+    assert its[0] == its[1]
+    assert np.array_equal(xs[0], xs[1])

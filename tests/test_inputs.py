@@ -56,3 +56,22 @@ def test_heatbath_beta6_plaquette():
     assert 0.585 < inputs.plaquette(U) < 0.605
     M = U.reshape(-1, 3, 3)
     assert np.max(np.abs(np.linalg.det(M) - 1)) < 1e-13
+
+
+def _digests():
+    out = []
+    for line in open(os.path.join(GOLDEN, "heatbath_sha256.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        out.append((tuple(int(x) for x in f[:4]), float(f[4]), int(f[5]), int(f[6]), f[7]))
+    return out
+
+
+@pytest.mark.parametrize("case", _digests(), ids=lambda c: "x".join(map(str, c[0])))
+def test_heatbath_bit_reproducible(case):
+    """The heatbath field is identical bit for bit to the stored digest (any machine)."""
+    import hashlib
+    dims, beta, sweeps, seed, digest = case
+    U = inputs.heatbath_gauge(dims, beta, sweeps, seed)
+    assert hashlib.sha256(U.tobytes()).hexdigest() == digest
