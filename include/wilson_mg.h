@@ -197,6 +197,31 @@ int mg_get_prolongator(mg_handle* h, int level, double* out);
  * site itself, d = 1 + 2 mu the hop to n + mu, d = 2 + 2 mu to n - mu. */
 int mg_get_coarse_op(mg_handle* h, int level, double* out);
 
+/* Same as mr_apply (for nrhs = 1), but allocates nothing, for callers that
+ * cannot allocate device memory when they call it: a server that fixed its
+ * device footprint at start-up, or a thread that must not enter the driver's
+ * allocation path while other streams run.  mr_apply takes its scratch (the
+ * work vector A r and the reduction partial sums, ticket counter and result
+ * slot) from buffers the handle allocates on demand; this entry point takes
+ * it from one fixed array of 16 MiB compiled into the library, which every
+ * GPU that loads the library holds until the process exits.  The paper has
+ * no counterpart; it is a deployment variant of the Sec. 3 smoother.
+ *   - The level's scratch (one vector of the level in `prec`, plus
+ *     3 doubles per thread block of the operator kernel, plus 512 bytes)
+ *     must fit in 16 MiB, else MG_EINVAL and a message naming the sizes
+ *     (an FP64 level-0 vector alone is 192 bytes per site).
+ *   - The first call on a device looks up the array's device address once
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind; the call zeroes the ticket counter it needs before using it.
+ *     Calls whose work overlaps on the GPU (other streams, other threads)
+ *     race on the array: serialise them.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine.
+ * Arguments, layouts and the result are those of mr_apply. */
+int mr_apply_noalloc(mg_handle* h, int level, int prec, const void* b, void* x, void* r, int steps,
+                     void* stream);
+
 /* Kernel classes of the profiler. */
 typedef enum {
   MG_K_DSLASH = 0,   /* level-0 Wilson stencil */

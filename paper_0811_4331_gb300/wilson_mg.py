@@ -84,6 +84,7 @@ def _load():
         "restrict_apply": (I, [VP, I, I, VP, VP, I, VP]),
         "prolong_apply": (I, [VP, I, I, VP, VP, I, VP]),
         "mr_apply": (I, [VP, I, I, VP, VP, VP, I, VP]),
+        "mr_apply_noalloc": (I, [VP, I, I, VP, VP, VP, I, VP]),
         "vcycle_apply": (I, [VP, VP, VP, VP]),
         "mg_field_to_internal": (I, [VP, I, I, VP, I, VP, I, VP]),
         "mg_field_from_internal": (I, [VP, I, I, VP, VP, I, I, VP]),
@@ -108,7 +109,7 @@ LIB = _load()
 EXPORTS = ["mg_last_error", "mg_default_params", "mg_setup", "mg_destroy", "mg_solve", "dslash_apply",
            "coarse_apply", "restrict_apply", "prolong_apply", "mr_apply", "vcycle_apply", "mg_field_to_internal",
            "mg_field_from_internal", "mg_level_info", "mg_get_prolongator", "mg_get_coarse_op", "mg_footprint",
-           "mg_profile", "mg_profile_read", "mg_launch_count"]
+           "mg_profile", "mg_profile_read", "mg_launch_count", "mr_apply_noalloc"]
 
 (MG_K_DSLASH, MG_K_COARSE, MG_K_RESTRICT, MG_K_PROLONG, MG_K_VECTOR, MG_K_COARSEST, MG_K_SETUP, MG_K_GALERKIN,
  MG_K_INVERSE) = range(9)
@@ -249,6 +250,11 @@ def prolong_apply(h, level, prec, inp, out, nrhs=1, stream=None):
 
 def mr_apply(h, level, prec, b, x, r, steps, stream=None):
     _check(LIB.mr_apply(h.ptr, level, prec, _ptr(b)[0], _ptr(x)[0], _ptr(r)[0], steps, _stream(stream)))
+
+
+def mr_apply_noalloc(h, level, prec, b, x, r, steps, stream=None):
+    """mr_apply without device allocation (fixed in-library scratch, see the header)."""
+    _check(LIB.mr_apply_noalloc(h.ptr, level, prec, _ptr(b)[0], _ptr(x)[0], _ptr(r)[0], steps, _stream(stream)))
 
 
 def vcycle_apply(h, r, e, stream=None):
