@@ -8,10 +8,13 @@ field from tests/golden/mcrit.json), two-level adaptive MG with 4^4
 aggregates and Nv = 20 null vectors, one Gaussian right-hand side, outer
 flexible GCR(50) to a true FP64 relative residual of 1e-10.
 
-One step = the whole hot path for the four masses: mg_setup (null-vector
-relaxation, block Gram-Schmidt, Galerkin coarse operator, coarsest inverse)
-and mg_solve, in the chosen mixed-precision form (FP16 fine smoother,
-FP32 Krylov, FP64 reliable updates / Gram-Schmidt / coarsest solve).  The
+One step = the whole hot path for the four masses: one mg_setup at the
+lightest mass (null-vector relaxation, block Gram-Schmidt, Galerkin coarse
+operator, coarsest inverse), mg_retarget to each other mass (the null space is
+mass independent since D(m) = D(0) + m 1; coarse operators shifted, coarsest
+inverse rebuilt) and one mg_solve per mass, in the chosen mixed-precision form
+(FP16 fine smoother, FP32 Krylov, FP64 reliable updates / Gram-Schmidt /
+coarsest refinement).  The
 plain-FP64 form of the same step is timed beside it.  `value` is seconds
 per step (lower is better) with the gauge field and sources resident on the
 device; `e2e` is the same step through the C ABI with host buffers.
@@ -48,7 +51,7 @@ TOL = 1e-10
 RHS_SEED = 1
 BW_DIMS = (32, 32, 32, 64)
 WORKLOAD = "8^3x16 beta=6.0 heatbath (200 sweeps, seed 0), 2-level MG 4^4 blocks Nv=20 (300 MR setup sweeps), " \
-           "mass sweep m_crit+{0.1,0.03,0.01,0.003}, 1 Gaussian RHS, tol 1e-10"
+           "mass sweep m_crit+{0.1,0.03,0.01,0.003} (setup once, retarget per mass), 1 Gaussian RHS, tol 1e-10"
 
 
 def mcrit():
@@ -136,19 +139,23 @@ def native(args, rank, world, U, b):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
     def step(mixed, host=False, stats_out=None):
+        """One mass sweep: null-vector setup once at the lightest mass, every other mass
+        through mg_retarget (same eigenvectors: D(m) = D(0) + m 1), one solve per mass."""
         p = params(wm, mixed)
+        base = wm.mg_setup(U if host else Ud, DIMS, masses[-1], p, stream=stream)
         for m in masses:
+            h = base if m == masses[-1] else wm.mg_retarget(base, m, stream=stream)
             if host:
-                h = wm.mg_setup(U, DIMS, m, p, stream=stream)
                 x = np.zeros_like(b)
                 _, st = wm.mg_solve(h, b, x, TOL, stream=stream)
             else:
-                h = wm.mg_setup(Ud, DIMS, m, p, stream=stream)
                 x = torch.zeros_like(bd)
                 _, st = wm.mg_solve(h, bd, x, TOL, stream=stream)
             if stats_out is not None:
                 stats_out.append((m, st[0], x if host else x.cpu().numpy()))
-            del h
+            if h is not base:
+                wm.mg_destroy(h)
+        wm.mg_destroy(base)
 
     def timed(mixed, K, W, host=False):
         for _ in range(W):
@@ -208,7 +215,7 @@ def native(args, rank, world, U, b):
     # end to end through the C ABI with host buffers
     t_e2e = timed(1, max(1, min(args.steps, 3)), 1, host=True)
     V = int(np.prod(DIMS))
-    h2d = len(masses) * (U.nbytes + 2 * b.nbytes)
+    h2d = U.nbytes + len(masses) * 2 * b.nbytes
     d2h = len(masses) * b.nbytes
     out["e2e"] = {"value": float(np.median(t_e2e)), "unit": "s per 4-mass sweep", "h2d_bytes_per_step": h2d,
                   "d2h_bytes_per_step": d2h}
@@ -232,19 +239,27 @@ def profiled_step(wm, torch, Ud, bd, masses, stream):
     prec_names = ["f64", "f32", "f16", "bf16"]
     p = params(wm, 1)
     tot = {}
+
+    def collect(h):
+        for k, nm in enumerate(wm.KERNEL_CLASS_NAMES):
+            for prec in range(4):
+                n, ms = wm.mg_profile_read(h, k, prec)
+                if n:
+                    a = tot.get((nm, prec), [0, 0.0])
+                    tot[(nm, prec)] = [a[0] + n, a[1] + ms]
+
     wm.mg_profile(None, (1 << len(wm.KERNEL_CLASS_NAMES)) - 1)
     try:
+        base = wm.mg_setup(Ud, DIMS, masses[-1], p, stream=stream)
         for m in masses:
-            h = wm.mg_setup(Ud, DIMS, m, p, stream=stream)
+            h = base if m == masses[-1] else wm.mg_retarget(base, m, stream=stream)
             x = torch.zeros_like(bd)
             wm.mg_solve(h, bd, x, TOL, stream=stream)
-            for k, nm in enumerate(wm.KERNEL_CLASS_NAMES):
-                for prec in range(4):
-                    n, ms = wm.mg_profile_read(h, k, prec)
-                    if n:
-                        a = tot.get((nm, prec), [0, 0.0])
-                        tot[(nm, prec)] = [a[0] + n, a[1] + ms]
-            del h
+            if h is not base:
+                collect(h)
+                wm.mg_destroy(h)
+        collect(base)
+        wm.mg_destroy(base)
     finally:
         wm.mg_profile(None, 0)
     all_ms = sum(v[1] for v in tot.values())
@@ -340,8 +355,8 @@ def dslash_bandwidth(wm, torch, stream):
 RELAX_SAMPLE, ITER_SAMPLE = 10, 3
 ORACLE_SAMPLE = ("FP64 numpy oracle, single thread, on the same inputs: %d of the %d setup MR sweeps (all %d "
                  "candidates), then block QR + Galerkin P^+DP + dense LU in full, then %d GCR iterations; "
-                 "value = 4 x (relaxation x %d/%d + QR/Galerkin/LU) + sum over the 4 masses of (oracle "
-                 "iteration count from tests/golden/c2_reference.json) x (time per iteration)"
+                 "value = relaxation x %d/%d + QR/Galerkin/LU + 3 x LU (the other masses) + sum over the 4 "
+                 "masses of (oracle iteration count from tests/golden/c2_reference.json) x (time per iteration)"
                  % (RELAX_SAMPLE, SETUP_SWEEPS, NV, ITER_SAMPLE, SETUP_SWEEPS, RELAX_SAMPLE))
 
 
@@ -369,6 +384,7 @@ def oracle_sample(U, b, m):
     blk = mg.Blocking(lat, BLOCK, 12)
     P = mg.block_orthonormalize(cands, blk)
     Ac = mg.coarse_stencil(dirac.wilson_stencil(U, m), P, blk)
+    tl = time.perf_counter()
     lu = scipy.linalg.lu_factor(mg.dense_from_stencil(Ac))
     t2 = time.perf_counter()
     fine = mg.Level(apply, lat, 12)
@@ -384,9 +400,10 @@ def oracle_sample(U, b, m):
     t4 = time.perf_counter()
     relax = (t1 - t0) * SETUP_SWEEPS / RELAX_SAMPLE
     rest = t2 - t1
+    lu_s = t2 - tl
     per_iter = (t4 - t3) / ITER_SAMPLE
-    total = len(DMASSES) * (relax + rest) + sum(oracle_iters()) * per_iter
-    return total, {"relax_sample_s": round(t1 - t0, 3), "qr_galerkin_lu_s": round(rest, 3),
+    total = relax + rest + (len(DMASSES) - 1) * lu_s + sum(oracle_iters()) * per_iter
+    return total, {"relax_sample_s": round(t1 - t0, 3), "qr_galerkin_lu_s": round(rest, 3), "lu_s": round(lu_s, 3),
                    "per_iter_s": round(per_iter, 4), "sampled_s": round(t4 - t0 - (t3 - t2), 3)}
 
 
@@ -443,6 +460,107 @@ def reference_arm(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+# ---------------------------------------------------------------------------- multi-RHS workload
+C3_DIMS = (16, 16, 16, 32)
+C3_MCRIT = -0.8049  # Sec. 5: m_crit of the paper's beta = 6.0, 16^3 x 32 ensemble (our field is a stand-in)
+
+
+def c3_workload(args):
+    """16^3 x 32 beta = 6.0: 12 point sources (one per spin x colour) + 12 Gaussian sources in one
+    mixed-precision three-level solve, against 24 single-source plain FP64 solves (same hierarchy shape)."""
+    import torch
+    from paper_0811_4331_gb300 import wilson_mg as wm
+    stream = torch.cuda.current_stream()
+    U = inputs.heatbath_gauge(C3_DIMS, BETA, HB_SWEEPS, HB_SEED)
+    Ud = torch.from_numpy(U).cuda()
+    srcs = [inputs.point_source(C3_DIMS, s, c) for s in range(4) for c in range(3)]
+    srcs += [inputs.gaussian_spinor(C3_DIMS, 100 + r) for r in range(12)]
+    B = torch.from_numpy(np.stack(srcs)).cuda()
+    mass = C3_MCRIT + args.c3_dm
+    out = {"workload": "16^3x32 beta=6.0 heatbath (200 sweeps, seed 0), 3-level MG 4^4 then 2^4 blocks, Nv=24/24, "
+                       "m = -0.8049 + %g, 12 point + 12 Gaussian sources, tol 1e-10" % args.c3_dm}
+    res = {}
+    for mixed in (1, 0):
+        p = wm.mg_default_params(n_levels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 24],
+                                 setup_sweeps=[300, 100], mixed=mixed, seed=7)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = wm.mg_setup(Ud, C3_DIMS, mass, p, stream=stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        X = torch.zeros_like(B)
+        if mixed:
+            _, st = wm.mg_solve(h, B, X, TOL, stream=stream)
+            its = [s["iters"] for s in st]
+            rel = [s["true_rel_residual"] for s in st]
+        else:
+            its, rel = [], []
+            for r in range(B.shape[0]):
+                xr = torch.zeros_like(B[r])
+                _, st = wm.mg_solve(h, B[r].contiguous(), xr, TOL, stream=stream)
+                X[r] = xr
+                its.append(st[0]["iters"])
+                rel.append(st[0]["true_rel_residual"])
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        res["mixed_multi_rhs" if mixed else "fp64_single_rhs"] = {
+            "setup_s": round(t1 - t0, 4), "solve_s": round(t2 - t1, 4), "iters": its,
+            "max_true_rel_residual": max(rel)}
+        del h
+    out.update(res)
+    out["speedup_solve"] = round(res["fp64_single_rhs"]["solve_s"] / res["mixed_multi_rhs"]["solve_s"], 3)
+    return out
+
+
+# ---------------------------------------------------------------------------- serving workload
+def serve_workload(args):
+    """Poisson stream of solve requests over three beta = 6.0 fields (8^4, 12^4, 16^3 x 32): masses
+    uniform in [m_crit + 0.005, m_crit + 0.1], 1-12 Gaussian right-hand sides each, hierarchies cached per
+    field (setup at the lightest mass, retargeted per request), HBM-budget admission, 4 workers."""
+    import torch
+    from paper_0811_4331_gb300 import serve
+    from paper_0811_4331_gb300 import wilson_mg as wm
+    with open(os.path.join(ROOT, "tests", "golden", "mcrit.json")) as f:
+        mc = json.load(f)
+    crit = {(8, 8, 8, 8): mc["8x8x8x8_beta6.0_sweeps200_seed0"]["m_crit"],
+            (12, 12, 12, 12): mc.get("12x12x12x12_beta6.0_sweeps200_seed0", {}).get("m_crit", C3_MCRIT),
+            (16, 16, 16, 32): C3_MCRIT}
+    two = wm.mg_default_params(n_levels=2, block=[(4, 4, 4, 4)], nv=[20], setup_sweeps=[300], mixed=1, seed=7)
+    three = wm.mg_default_params(n_levels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 24],
+                                 setup_sweeps=[300, 100], mixed=1, seed=7)
+    fields = {}
+    for dims, p in (((8, 8, 8, 8), two), ((12, 12, 12, 12), two), ((16, 16, 16, 32), three)):
+        U = inputs.heatbath_gauge(dims, BETA, HB_SWEEPS, HB_SEED)
+        fields["x".join(map(str, dims))] = (U, dims, crit[dims] + 0.005, p)
+    names = sorted(fields)
+    budget = int(0.5 * torch.cuda.get_device_properties(0).total_memory)
+    rng = np.random.default_rng(4)
+    out = {"workload": "serving: Poisson arrivals, fields 8^4 / 12^4 / 16^3x32 (beta=6.0 heatbath), masses "
+                       "U[m_crit+0.005, m_crit+0.1], 1-12 Gaussian RHS, tol 1e-10, 4 workers, half of HBM as budget",
+           "rates": []}
+    srv = serve.SolveServer(fields, None, budget, workers=4)
+    for name in names:  # warm the per-field hierarchies (setup once per field)
+        srv.base(name)
+    n_per_rate = args.serve_requests // len(args.serve_rates)
+    for rate in args.serve_rates:
+        reqs = []
+        for i in range(n_per_rate):
+            f = names[int(rng.integers(0, len(names)))]
+            dims = fields[f][1]
+            nrhs = int(rng.integers(1, 13))
+            g = np.random.default_rng(int(rng.integers(1 << 30)))
+            shp = (nrhs,) + (dims[3], dims[2], dims[1], dims[0], 4, 3)
+            b = g.standard_normal(shp) + 1j * g.standard_normal(shp)
+            m = crit[dims] + float(rng.uniform(0.005, 0.1))
+            reqs.append(serve.Request(i, f, m, b, TOL, 0.0))
+        st = serve.run_stream(srv, reqs, serve.poisson_arrivals(rate, len(reqs), int(rng.integers(1 << 30))))
+        st["rate_per_s"] = rate
+        st["max_inflight"] = srv.max_inflight
+        out["rates"].append(st)
+    srv.close()
+    return out
+
+
 # ---------------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -455,6 +573,11 @@ def main():
     ap.add_argument("--no-dslash-hbm", action="store_true")
     ap.add_argument("--only-timed", action="store_true", help="time the mixed step only (for profiler runs)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--workload", choices=["c2", "c3", "serve"], default="c2",
+                    help="c2: the mass-sweep step (default bench line); c3: 24-source batched solve; serve: stream")
+    ap.add_argument("--c3-dm", type=float, default=0.02)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[10.0, 20.0, 40.0, 80.0])
     args = ap.parse_args()
     if args.oracle_sample:
         oracle_sample_main(args.oracle_sample)
@@ -467,6 +590,12 @@ def main():
             print(json.dumps(out))
         return
     import torch
+    if args.workload == "c3":
+        print(json.dumps(c3_workload(args)))
+        return
+    if args.workload == "serve":
+        print(json.dumps(serve_workload(args)))
+        return
     if world > 1:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl")

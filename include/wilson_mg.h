@@ -85,6 +85,11 @@ typedef struct {
   double reliable_delta;              /* mixed: inner FP32 GCR reduces ||r|| by this factor before an FP64 update */
   uint64_t seed;                      /* on-device start vectors: level l uses stream seed + l */
   int use_graphs;                     /* 1: replay the V-cycle as a captured CUDA graph; 0: launch eagerly */
+  int coarse_mma;                     /* mixed: 1 = coarse stencils of levels 1..L-2 on tensor cores (BF16
+                                         operator in MMA fragment order, FP32 accumulation) */
+  int coarse_solver;                  /* the coarse_cycles applications of the next level's V-cycle:
+                                         0 = as steps of flexible GCR preconditioned by it (default),
+                                         1 = as stationary sweeps e += V(r - A e) */
 } mg_params;
 
 /* Per right-hand side solve statistics. */
@@ -129,6 +134,16 @@ int mg_default_params(mg_params* p);
 int mg_setup(mg_handle** h, const double* gauge, int gauge_on_device, const int dims[4],
              double mass, const mg_params* p, const double* const* starts, void* stream);
 
+/* A new handle for mass `mass` that reuses the null vectors of `src`.
+ * D(m) = D(0) + m 1 has the same eigenvectors at every mass (Sec. 1), so the
+ * near-null space found by the setup of `src` serves any mass; and since
+ * P^+ P = 1 on every level (Eq. 2.3), A_l(m) = A_l(m_src) + (m - m_src) 1 for
+ * every Galerkin operator A_l = P^+ A_{l-1} P (Sec. 2).  The new handle owns
+ * device copies of the links, prolongators and coarse stencils of `src`
+ * (shifted), and its own coarsest inverse, rebuilt for `mass`.  `src` is
+ * not modified and stays valid.  Errors as mg_setup. */
+int mg_retarget(const mg_handle* src, double mass, mg_handle** h, void* stream);
+
 /* Free every device buffer of `h` (NULL is allowed). */
 int mg_destroy(mg_handle* h);
 
@@ -152,7 +167,9 @@ int dslash_apply(mg_handle* h, int prec, const void* in, void* out, int nrhs, vo
 
 /* out = A_level in for the coarse stencil operator of `level` >= 1
  * (A_l = P^+ A_{l-1} P, Sec. 2), internal layout, device memory.
- * Precisions: MG_F64 and MG_F32 (storage of operator and vectors).
+ * Precisions: the vector storage; the operator is held in the same
+ * precision, except that with coarse_mma an FP32 call runs on tensor cores
+ * with the operator in BF16 (FP32 accumulation).
  * Errors: MG_EINVAL (no such level / precision). */
 int coarse_apply(mg_handle* h, int level, int prec, const void* in, void* out, int nrhs,
                  void* stream);

@@ -31,8 +31,10 @@ modified Gram-Schmidt applied twice, in candidate order; the chirality split
 of a level with ncomp components per site puts components [0, ncomp/2) in
 chirality + and [ncomp/2, ncomp) in chirality -; the same smoother and alpha
 step are used on every level; the coarsest level is solved exactly by dense
-LU; the 4 coarse applications are 4 stationary V-cycle sweeps e_c += V(r_c -
-A_c e_c) starting from e_c = 0; inner products are <a|b> = sum conj(a) b.
+LU; the 4 coarse applications are 4 steps of flexible GCR on the coarse
+equation preconditioned by the next level's V-cycle, from e_c = 0 (4
+stationary sweeps e_c += V(r_c - A_c e_c) are the alternative reading,
+``coarse_solver="stationary"``); inner products are <a|b> = sum conj(a) b.
 
 Field arrays have shape (Lt, Lz, Ly, Lx, ncomp); a block size is given as
 (bx, by, bz, bt), matching the x-fastest site order.
@@ -290,13 +292,41 @@ def coarsest_solve(level, r):
     return scipy.linalg.lu_solve(level.lu, r.reshape(-1)).reshape(r.shape)
 
 
-def vcycle(hier, l, r, nu_pre=2, nu_post=2, omega=0.8, coarse_cycles=(4,)):
+def gcr_fixed(apply, b, precond, iters):
+    """``iters`` steps of flexible GCR on A x = b from x = 0 (modified Gram-Schmidt, no
+    restart, no stopping test): the Krylov-accelerated form of applying a preconditioner
+    ``iters`` times."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    Z, W = [], []
+    for _ in range(iters):
+        z = precond(r)
+        w = apply(z)
+        for j in range(len(W)):
+            beta = inner(W[j], w)
+            w = w - beta * W[j]
+            z = z - beta * Z[j]
+        nw = np.sqrt(norm2(w))
+        if nw == 0.0:
+            break
+        w = w / nw
+        z = z / nw
+        a = inner(w, r)
+        x = x + a * z
+        r = r - a * w
+        Z.append(z)
+        W.append(w)
+    return x
+
+
+def vcycle(hier, l, r, nu_pre=2, nu_post=2, omega=0.8, coarse_cycles=(4,), coarse_solver="gcr"):
     """One modified V(nu_pre, nu_post) cycle on level l applied to residual r.
 
     Pre-smooth from e = 0, restrict, solve the coarse equation (exactly on the
-    coarsest level, else by ``coarse_cycles[l]`` stationary sweeps of the next
-    level's V-cycle), prolong to x_c, add alpha x_c with
-    alpha = <A x_c|r0>/<A x_c|A x_c> (Eq. 3.5), post-smooth.
+    coarsest level, else by ``coarse_cycles[l]`` applications of the next
+    level's V-cycle: as flexible GCR steps preconditioned by it, the default,
+    or as stationary sweeps e_c += V(r_c - A_c e_c)), prolong to x_c, add
+    alpha x_c with alpha = <A x_c|r0>/<A x_c|A x_c> (Eq. 3.5), post-smooth.
     """
     lev = hier[l]
     if l == len(hier) - 1:
@@ -307,10 +337,16 @@ def vcycle(hier, l, r, nu_pre=2, nu_post=2, omega=0.8, coarse_cycles=(4,)):
         ec = coarsest_solve(hier[l + 1], rc)
     else:
         ncyc = coarse_cycles[l] if l < len(coarse_cycles) else 1
-        ec = vcycle(hier, l + 1, rc, nu_pre, nu_post, omega, coarse_cycles)
-        for _ in range(ncyc - 1):
-            ec = ec + vcycle(hier, l + 1, rc - hier[l + 1].apply(ec), nu_pre, nu_post,
-                             omega, coarse_cycles)
+
+        def inner_cycle(v):
+            return vcycle(hier, l + 1, v, nu_pre, nu_post, omega, coarse_cycles, coarse_solver)
+
+        if coarse_solver == "gcr":
+            ec = gcr_fixed(hier[l + 1].apply, rc, inner_cycle, ncyc)
+        else:
+            ec = inner_cycle(rc)
+            for _ in range(ncyc - 1):
+                ec = ec + inner_cycle(rc - hier[l + 1].apply(ec))
     xc = prolong(lev.P, lev.blk, ec)
     Axc = lev.apply(xc)
     alpha = minimal_residual_coefficient(Axc, res)
@@ -365,11 +401,11 @@ def fgcr(apply, b, precond=None, tol=1e-10, restart=50, max_restarts=100):
 
 
 def mg_solve(hier, b, tol=1e-10, restart=50, nu_pre=2, nu_post=2, omega=0.8,
-             coarse_cycles=(4,)):
+             coarse_cycles=(4,), coarse_solver="gcr"):
     """MG-GCR: flexible GCR(50) preconditioned by one modified V-cycle (Sec. 5)."""
     fine = hier[0]
 
     def precond(r):
-        return vcycle(hier, 0, r, nu_pre, nu_post, omega, coarse_cycles)
+        return vcycle(hier, 0, r, nu_pre, nu_post, omega, coarse_cycles, coarse_solver)
 
     return fgcr(fine.apply, b, precond, tol, restart)

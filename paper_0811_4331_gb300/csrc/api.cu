@@ -65,9 +65,12 @@ inline size_t slot_gcr_rn() { return slot_gcr_wr() + 4 * kMaxRhs; }
 inline size_t slot_gcr_bn() { return slot_gcr_rn() + 4 * kMaxRhs; }
 inline size_t slot_misc() { return slot_gcr_bn() + 4 * kMaxRhs; }
 inline size_t slot_beta() { return slot_misc() + 4 * kMaxRhs; }
-inline size_t slot_total() { return slot_beta() + (size_t)2 * kMaxBasis * kMaxRhs; }
+// inner GCR of the coarse correction of level l: dots, residual norms, betas (8 per rhs)
+inline size_t slot_inner(int l) { return slot_beta() + (size_t)2 * kMaxBasis * kMaxRhs + (size_t)l * 24 * kMaxRhs; }
+inline size_t slot_total() { return slot_inner(MG_MAX_LEVELS); }
+const int kInnerBasis = 8;
 
-enum { WV_E, WV_RES, WV_P, WV_XC, WV_AXC, WV_RC, WV_EC, WV_T, WV_DT, WV_IN, WV_A, WV_B, WV_COUNT };
+enum { WV_E, WV_RES, WV_P, WV_XC, WV_AXC, WV_RC, WV_EC, WV_T, WV_DT, WV_IN, WV_A, WV_B, WV_KW, WV_KZ, WV_COUNT };
 
 int prec_of(const mg_handle* h, int l) {
   if (!h->p.mixed) return MG_F64;
@@ -97,14 +100,14 @@ size_t bytes_of(int prec) { return prec == MG_F64 ? 16 : (prec == MG_F32 ? 8 : 4
 
 int check_prec(int prec) { return (prec >= 0 && prec <= 3) ? MG_OK : MG_EINVAL; }
 
-void* work(mg_handle* h, int l, int prec, int idx, int nrhs) {
+void* work(mg_handle* h, int l, int prec, int idx, int nrhs, int count = 1) {
   if ((int)h->work.size() <= l) h->work.resize(l + 1);
   auto& byprec = h->work[l];
   if (byprec.empty()) byprec.resize(4);
   auto& vecs = byprec[prec];
   if ((int)vecs.size() <= idx) vecs.resize(idx + 1);
   if (!vecs[idx]) vecs[idx].reset(new DevBuf());
-  const size_t need = h->lev[l]->n() * (size_t)nrhs * bytes_of(prec);
+  const size_t need = h->lev[l]->n() * (size_t)nrhs * bytes_of(prec) * (size_t)count;
   if (need > vecs[idx]->bytes || !vecs[idx]->p) {
     if (h->capturing) return nullptr;  // never allocate inside a capture
     ++h->buf_gen;
@@ -189,6 +192,16 @@ int op_apply(mg_handle* h, int l, int prec, const void* in, void* out, const voi
     d.red = h->red.at(slot, 4);
     Prof pf(h, MG_K_DSLASH, prec);
     LK(launch_wilson(d, h->st));
+  } else if (a.cop_mma.p && prec == MG_F32 && nrhs <= 64) {
+    // tensor cores: out = a_ A in + c_ y, then the dots in a separate deterministic pass
+    {
+      Prof pf(h, MG_K_COARSE, MG_BF16);
+      LK(launch_coarse_mma(prec, a.cop_mma.p, in, out, y, a.L, a.ncomp, nrhs, a_, c_, h->st));
+    }
+    if (z) {
+      Prof pf(h, MG_K_VECTOR, prec);
+      LK(launch_dot(prec, a.n(), nrhs, out, z, h->red.at(slot, 4), h->st));
+    }
   } else {
     if (!a.cop[prec].p) {
       set_error("coarse operator not stored in this precision");
@@ -261,7 +274,7 @@ int mr_steps(mg_handle* h, int l, int prec, const void* b, void* x, bool x_zero,
 const int kTrueResidualEvery = 25;
 
 // Number of FP64 iterative-refinement steps of the mixed-precision coarsest solve.
-const int kCoarsestRefine = 2;
+const int kCoarsestRefine = 1;
 
 // Exact solve on the coarsest level.  Plain: e = A^-1 r with the FP64
 // inverse.  Mixed: the inverse is FP32; the solve runs in FP64 as
@@ -297,6 +310,42 @@ int coarsest_solve(mg_handle* h, int l, int prec, const void* r, void* e, int nr
 }
 
 
+int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs);
+
+// e = `iters` steps of flexible GCR on A_l e = b from e = 0, preconditioned by
+// the V-cycle of level l (classical Gram-Schmidt applied twice; every scalar
+// stays on the device, so the whole solve is one graph-capturable sequence).
+int coarse_gcr(mg_handle* h, int l, int prec, const void* b, void* e, int iters, int nrhs) {
+  Level& a = *h->lev[l];
+  const size_t n = a.n();
+  const size_t vb = n * nrhs * bytes_of(prec);
+  void* r = work(h, l, prec, WV_T, nrhs);
+  char* W = (char*)work(h, l, prec, WV_KW, nrhs, kInnerBasis);
+  char* Z = (char*)work(h, l, prec, WV_KZ, nrhs, kInnerBasis);
+  if (!r || !W || !Z || iters > kInnerBasis) return MG_ENOMEM;
+  const size_t swr = slot_inner(l), srn = swr + 4 * kMaxRhs, sbeta = srn + 4 * kMaxRhs;
+  CK(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemsetAsync(e, 0, vb, h->st));
+  for (int k = 0; k < iters; ++k) {
+    void* zk = Z + (size_t)k * vb;
+    void* wk = W + (size_t)k * vb;
+    RET(vcycle(h, l, r, zk, nrhs));
+    RET(op_apply(h, l, prec, zk, wk, nullptr, 1.0, 0.0, nullptr, 0, nrhs));
+    Prof pf(h, MG_K_VECTOR, prec);
+    if (k == 0) {
+      LK(launch_dot(prec, n, nrhs, wk, r, h->red.at(swr, 4), h->st));
+    } else {
+      for (int pass = 0; pass < 2; ++pass) {
+        LK(launch_multidot(prec, n, nrhs, k, kInnerBasis, W, n * nrhs, wk, h->red.at(sbeta, 0), h->st));
+        LK(launch_multiaxpy(prec, n, nrhs, k, kInnerBasis, h->red.slot(sbeta), W, Z, n * nrhs, wk, zk, r,
+                            h->red.at(swr, 4), h->st));
+      }
+    }
+    LK(launch_gcr_update(prec, prec, n, nrhs, h->red.slot(swr), 4, wk, zk, e, r, h->red.at(srn + 2, 4), h->st));
+  }
+  return MG_OK;
+}
+
 // e = V_l(r): one modified V(nu_pre, nu_post) cycle on level l.
 int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
   const int L = (int)h->lev.size();
@@ -324,15 +373,19 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
   if (l + 1 == L - 1) {
     RET(coarsest_solve(h, l + 1, pc, rc, ec, nrhs));
   } else {
-    RET(vcycle(h, l + 1, rc, ec, nrhs));
-    void* t = work(h, l + 1, pc, WV_T, nrhs);
-    void* dt = work(h, l + 1, pc, WV_DT, nrhs);
-    if (!t || !dt) return MG_ENOMEM;
-    for (int c = 1; c < a.cycles; ++c) {
-      RET(op_apply(h, l + 1, pc, ec, t, rc, -1.0, 1.0, nullptr, 0, nrhs));
-      RET(vcycle(h, l + 1, t, dt, nrhs));
-      Prof pf(h, MG_K_VECTOR, pc);
-      LK(launch_convert(pc, pc, h->lev[l + 1]->n(), nrhs, dt, ec, 1.0, nullptr, 0, 0.0, 1, h->st));
+    if (h->p.coarse_solver == 0 && (pc == MG_F64 || pc == MG_F32)) {
+      RET(coarse_gcr(h, l + 1, pc, rc, ec, a.cycles, nrhs));
+    } else {
+      RET(vcycle(h, l + 1, rc, ec, nrhs));
+      void* t = work(h, l + 1, pc, WV_T, nrhs);
+      void* dt = work(h, l + 1, pc, WV_DT, nrhs);
+      if (!t || !dt) return MG_ENOMEM;
+      for (int c = 1; c < a.cycles; ++c) {
+        RET(op_apply(h, l + 1, pc, ec, t, rc, -1.0, 1.0, nullptr, 0, nrhs));
+        RET(vcycle(h, l + 1, t, dt, nrhs));
+        Prof pf(h, MG_K_VECTOR, pc);
+        LK(launch_convert(pc, pc, h->lev[l + 1]->n(), nrhs, dt, ec, 1.0, nullptr, 0, 0.0, 1, h->st));
+      }
     }
   }
   {
@@ -455,6 +508,40 @@ int mg_destroy(mg_handle* h) {
   return MG_OK;
 }
 
+// Dense inverse of the coarsest level (FP64, or FP32 refined in FP64 in the mixed form).
+static int build_coarsest(mg_handle* h) {
+  const int Lv = (int)h->lev.size();
+  if (Lv < 2) return MG_OK;
+  cudaStream_t st = h->st;
+  Level& c = *h->lev[Lv - 1];
+  const size_t N = c.n();
+  if (N > 8192) {
+    set_error("coarsest level has " + std::to_string(N) + " unknowns; the dense solve takes at most 8192");
+    return MG_EINVAL;
+  }
+  c.inv_prec = h->p.mixed ? MG_F32 : MG_F64;
+  const size_t eb = bytes_of(c.inv_prec);
+  DevBuf aug, col, errflag;
+  if (!aug.ensure(N * 2 * N * eb) || !col.ensure(dense_inverse_scratch_bytes(c.inv_prec, (int)N)) ||
+      !c.inv.ensure(N * N * eb) || !errflag.ensure(sizeof(int)))
+    return MG_ENOMEM;
+  CK(cudaMemsetAsync(errflag.p, 0, sizeof(int), st));
+  {
+    Prof pf(h, MG_K_INVERSE, c.inv_prec);
+    LK(dense_inverse(c.inv_prec, c.cop[MG_F64].as<double2>(), c.L, c.ncomp, aug.p, col.p, errflag.as<int>(), c.inv.p,
+                     st));
+  }
+  count_launches(N + 2);  // stencil-to-dense, init, one per pivot, finish (one counted by LK)
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (herr) {
+    set_error("coarsest operator is singular (zero pivot)");
+    return MG_EINVAL;
+  }
+  return MG_OK;
+}
+
 static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, const double* const* starts) {
   const mg_params& p = h->p;
   cudaStream_t st = h->st;
@@ -565,7 +652,8 @@ static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, co
       Prof pf(h, MG_K_SETUP, MG_F64);
       LK(launch_block_gs(g, cand.as<double2>(), a.P[MG_F64].as<double2>(), errflag.as<int>(), st));
     }
-    // Galerkin coarse operator, FP64, columns in batches of at most 1 GB of fields
+    // Galerkin coarse operator (FP64 arithmetic for the plain hierarchy, FP32
+    // for the mixed one; stored in FP64), columns in batches of at most 1 GB
     h->lev.emplace_back(new Level());
     Level& c = *h->lev[l + 1];
     for (int m = 0; m < 4; ++m) c.L[m] = a.Lc[m];
@@ -573,22 +661,29 @@ static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, co
     c.ncomp = 2 * a.nv;
     const int nc = c.ncomp;
     if (!c.cop[MG_F64].ensure((size_t)9 * nc * nc * c.V * 16)) return MG_ENOMEM;
-    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(nc, ((size_t)1 << 30) / vb));
+    const int gp = p.mixed ? MG_F32 : MG_F64;
+    const size_t np = (size_t)a.Vc * 2 * a.nv * a.nhalf * a.bsites;
+    if (gp != MG_F64 && !a.P[gp].p) {
+      if (!a.P[gp].ensure(np * bytes_of(gp))) return MG_ENOMEM;
+      LK(launch_convert(MG_F64, gp, np, 1, a.P[MG_F64].p, a.P[gp].p, 1.0, nullptr, 0, 0.0, 0, st));
+    }
+    const size_t vbg = a.n() * bytes_of(gp);
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(nc, ((size_t)1 << 30) / vbg));
     DevBuf cols;
-    if (!cols.ensure(vb * chunk)) return MG_ENOMEM;
+    if (!cols.ensure(vbg * chunk)) return MG_ENOMEM;
     for (int j0 = 0; j0 < nc; j0 += chunk) {
       const int ncols = std::min(chunk, nc - j0);
       {
-        Prof pf(h, MG_K_SETUP, MG_F64);
-        LK(launch_p_column(g, a.P[MG_F64].as<double2>(), j0, ncols, cols.as<double2>(), st));
+        Prof pf(h, MG_K_SETUP, gp);
+        LK(launch_p_column(gp, g, a.P[gp].p, j0, ncols, cols.p, st));
       }
-      Prof pf(h, MG_K_GALERKIN, MG_F64);
+      Prof pf(h, MG_K_GALERKIN, gp);
       if (l == 0)
-        LK(launch_galerkin_wilson(g, a.links[MG_F64].as<double2>(), h->mass, cols.as<double2>(),
-                                  a.P[MG_F64].as<double2>(), j0, ncols, c.cop[MG_F64].as<double2>(), st));
+        LK(launch_galerkin_wilson(gp, g, a.links[gp].p, h->mass, cols.p, a.P[gp].p, j0, ncols,
+                                  c.cop[MG_F64].as<double2>(), st));
       else
-        LK(launch_galerkin_stencil(g, a.cop[MG_F64].as<double2>(), cols.as<double2>(), a.P[MG_F64].as<double2>(),
-                                   j0, ncols, c.cop[MG_F64].as<double2>(), st));
+        LK(launch_galerkin_stencil(gp, g, a.cop[gp].p, cols.p, a.P[gp].p, j0, ncols, c.cop[MG_F64].as<double2>(),
+                                   st));
     }
     int herr = 0;
     CK(cudaMemcpyAsync(&herr, errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -600,8 +695,7 @@ static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, co
     // precision copies: this level's P for the cycle; the next level's
     // operator for its cycle and (mixed) its FP32 relaxation
     const int pr = prec_of(h, l);
-    if (pr != MG_F64) {
-      const size_t np = (size_t)a.Vc * 2 * a.nv * a.nhalf * a.bsites;
+    if (pr != MG_F64 && !a.P[pr].p) {
       if (!a.P[pr].ensure(np * bytes_of(pr))) return MG_ENOMEM;
       LK(launch_convert(MG_F64, pr, np, 1, a.P[MG_F64].p, a.P[pr].p, 1.0, nullptr, 0, 0.0, 0, st));
     }
@@ -613,35 +707,13 @@ static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, co
         if (!c.cop[q].ensure(ncop * bytes_of(q))) return MG_ENOMEM;
         LK(launch_convert(MG_F64, q, ncop, 1, c.cop[MG_F64].p, c.cop[q].p, 1.0, nullptr, 0, 0.0, 0, st));
       }
+      if (p.coarse_mma) {
+        if (!c.cop_mma.ensure(mma_pack_bytes(nc, c.V))) return MG_ENOMEM;
+        LK(launch_mma_pack(c.cop[MG_F64].as<double2>(), nc, c.V, c.cop_mma.p, st));
+      }
     }
   }
-  // ---- coarsest level: dense inverse (FP64, or FP32 refined in FP64 in the mixed form)
-  if (Lv >= 2) {
-    Level& c = *h->lev[Lv - 1];
-    const size_t N = c.n();
-    if (N > 8192) {
-      set_error("coarsest level has " + std::to_string(N) + " unknowns; the dense solve takes at most 8192");
-      return MG_EINVAL;
-    }
-    c.inv_prec = p.mixed ? MG_F32 : MG_F64;
-    const size_t eb = bytes_of(c.inv_prec);
-    DevBuf aug, col;
-    if (!aug.ensure(N * 2 * N * eb) || !col.ensure(dense_inverse_scratch_bytes(c.inv_prec, (int)N)) ||
-        !c.inv.ensure(N * N * eb))
-      return MG_ENOMEM;
-    CK(cudaMemsetAsync(errflag.p, 0, sizeof(int), st));
-    Prof pf(h, MG_K_INVERSE, c.inv_prec);
-    LK(dense_inverse(c.inv_prec, c.cop[MG_F64].as<double2>(), c.L, c.ncomp, aug.p, col.p, errflag.as<int>(), c.inv.p,
-                     st));
-    count_launches(N + 2);  // stencil-to-dense, init, one per pivot, finish (one counted by LK)
-    int herr = 0;
-    CK(cudaMemcpyAsync(&herr, errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (herr) {
-      set_error("coarsest operator is singular (zero pivot)");
-      return MG_EINVAL;
-    }
-  }
+  RET(build_coarsest(h));
   CK(cudaStreamSynchronize(st));
   return MG_OK;
 }
@@ -683,6 +755,84 @@ int mg_setup(mg_handle** hout, const double* gauge, int gauge_on_device, const i
     return MG_ENOMEM;
   }
   int rc = setup_impl(h, gauge, gauge_on_device, starts);
+  if (rc != MG_OK) {
+    mg_destroy(h);
+    return rc;
+  }
+  *hout = h;
+  return MG_OK;
+}
+
+static int retarget_impl(const mg_handle* src, mg_handle* h) {
+  cudaStream_t st = h->st;
+  const double delta = h->mass - src->mass;
+  for (size_t l = 0; l < src->lev.size(); ++l) {
+    const Level& a = *src->lev[l];
+    h->lev.emplace_back(new Level());
+    Level& b = *h->lev[l];
+    for (int m = 0; m < 4; ++m) {
+      b.L[m] = a.L[m];
+      b.blk[m] = a.blk[m];
+      b.Lc[m] = a.Lc[m];
+    }
+    b.V = a.V;
+    b.ncomp = a.ncomp;
+    b.nv = a.nv;
+    b.bsites = a.bsites;
+    b.nhalf = a.nhalf;
+    b.Vc = a.Vc;
+    b.sweeps = a.sweeps;
+    b.cycles = a.cycles;
+    for (int pr = 0; pr < 4; ++pr) {
+      const DevBuf* from[3] = {&a.links[pr], &a.cop[pr], &a.P[pr]};
+      DevBuf* to[3] = {&b.links[pr], &b.cop[pr], &b.P[pr]};
+      for (int q = 0; q < 3; ++q) {
+        if (!from[q]->p) continue;
+        if (!to[q]->ensure(from[q]->bytes)) return MG_ENOMEM;
+        CK(cudaMemcpyAsync(to[q]->p, from[q]->p, from[q]->bytes, cudaMemcpyDeviceToDevice, st));
+      }
+    }
+    // A_l(m) = A_l(m0) + (m - m0) 1 on every coarse level (P^+ P = 1)
+    if (l >= 1 && delta != 0.0) {
+      LK(launch_diag_shift(b.cop[MG_F64].as<double2>(), b.ncomp, b.V, delta, st));
+      const size_t ncop = (size_t)9 * b.ncomp * b.ncomp * b.V;
+      for (int pr = 1; pr < 4; ++pr)
+        if (b.cop[pr].p) LK(launch_convert(MG_F64, pr, ncop, 1, b.cop[MG_F64].p, b.cop[pr].p, 1.0, nullptr, 0, 0.0, 0, st));
+    }
+    if (a.cop_mma.p) {
+      if (!b.cop_mma.ensure(a.cop_mma.bytes)) return MG_ENOMEM;
+      LK(launch_mma_pack(b.cop[MG_F64].as<double2>(), b.ncomp, b.V, b.cop_mma.p, st));
+    }
+  }
+  RET(ensure_reducer(h, 1));
+  RET(build_coarsest(h));
+  CK(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+int mg_retarget(const mg_handle* src, double mass, mg_handle** hout, void* stream) {
+  if (!hout) return MG_EINVAL;
+  *hout = nullptr;
+  if (!src) {
+    set_error("mg_retarget: null handle");
+    return MG_EINVAL;
+  }
+  mg_handle* h = new mg_handle();
+  h->p = src->p;
+  h->mass = mass;
+  for (int m = 0; m < 4; ++m) h->dims[m] = src->dims[m];
+  h->st = (cudaStream_t)stream;
+  h->use_graphs = src->use_graphs;
+  h->prof_mask = __atomic_load_n(&g_default_prof_mask, __ATOMIC_RELAXED);
+  if (cudaMallocHost((void**)&h->host_slots, slot_total() * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    set_error("pinned host allocation failed");
+    return MG_ENOMEM;
+  }
+  // the source's work must be complete before its buffers are copied
+  if (src->st && src->st != h->st) cudaStreamSynchronize(src->st);
+  int rc = retarget_impl(src, h);
   if (rc != MG_OK) {
     mg_destroy(h);
     return rc;
@@ -826,8 +976,8 @@ int mg_get_prolongator(mg_handle* h, int level, double* out) {
   if (!f.ensure(a.n() * 16) || !tot.ensure(a.n() * 16) || !ext.ensure(a.n() * 16)) return MG_ENOMEM;
   const Agg g = agg_of(a);
   for (int k = 0; k < a.nv; ++k) {
-    LK(launch_p_column(g, a.P[MG_F64].as<double2>(), k, 1, tot.as<double2>(), st));
-    LK(launch_p_column(g, a.P[MG_F64].as<double2>(), a.nv + k, 1, f.as<double2>(), st));
+    LK(launch_p_column(MG_F64, g, a.P[MG_F64].p, k, 1, tot.p, st));
+    LK(launch_p_column(MG_F64, g, a.P[MG_F64].p, a.nv + k, 1, f.p, st));
     LK(launch_convert(MG_F64, MG_F64, a.n(), 1, f.p, tot.p, 1.0, nullptr, 0, 0.0, 1, st));
     LK(launch_int_to_ext(MG_F64, a.ncomp, a.V, 1, tot.p, ext.p, st));
     CK(cudaMemcpyAsync(out + (size_t)k * a.n() * 2, ext.p, a.n() * 16, cudaMemcpyDeviceToHost, st));
@@ -944,7 +1094,8 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
   }
   // Krylov buffers in precision pin: basis W, Z [restart][nrhs][n], x, r
   const size_t vbytes = n * nrhs * bi;
-  if (!h->gW.ensure(vbytes * restart) || !h->gZ.ensure(vbytes * restart) || !h->gx.ensure(vbytes) ||
+  const size_t slots = (size_t)((restart + 7) / 8) * 8;  // the multi-dot reads whole chunks of 8
+  if (!h->gW.ensure(vbytes * slots) || !h->gZ.ensure(vbytes * restart) || !h->gx.ensure(vbytes) ||
       !h->gr.ensure(vbytes))
     return MG_ENOMEM;
   double* hs = h->host_slots;

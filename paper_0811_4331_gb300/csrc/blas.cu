@@ -22,6 +22,13 @@ int vec_blocks(size_t n) {
 
 static inline bool launched() { return cudaGetLastError() == cudaSuccess; }
 
+// Blocks of the dot kernels: at least 8 elements per thread, at most one block per SM.
+int red_blocks(size_t n) {
+  size_t b = (n + 8 * kVecThreads - 1) / (8 * kVecThreads);
+  if (b > 152) b = 152;
+  return (int)(b < 1 ? 1 : b);
+}
+
 // ------------------------------------------------------------------ MR update
 template <typename S>
 __global__ void __launch_bounds__(kVecThreads) mr_update_kernel(const MrUpdate m) {
@@ -42,7 +49,7 @@ __global__ void __launch_bounds__(kVecThreads) mr_update_kernel(const MrUpdate m
   S* ro = (S*)m.r_out + off;
   const S* ri = (const S*)m.r_in + off;
   const S* p = (const S*)m.p + off;
-  double red[1] = {0.0};
+  R acc = (R)0;  // per-thread partial in the arithmetic type; FP64 only across threads
   for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < m.n; i += (size_t)gridDim.x * kVecThreads) {
     cx<R> x = xi ? ldc<R>(xi, i) : zero<R>();
     x = cfma(alpha, ldc<R>(u, i), x);
@@ -50,9 +57,10 @@ __global__ void __launch_bounds__(kVecThreads) mr_update_kernel(const MrUpdate m
     r = r - alpha * ldc<R>(p, i);
     stc(xo, i, x);
     stc(ro, i, r);
-    red[0] += (double)norm2(as_stored<S>(r));
+    acc += norm2(as_stored<S>(r));
   }
-  if (m.red.result) grid_reduce<1, kVecThreads>(red, m.red, rhs);
+  R red[1] = {acc};
+  if (m.red.result) grid_reduce<1, kVecThreads, R>(red, m.red, rhs);
 }
 
 int launch_mr_update(const MrUpdate& m, cudaStream_t st) {
@@ -74,20 +82,20 @@ __global__ void __launch_bounds__(kVecThreads) dot_kernel(size_t n, const S* a, 
   const int rhs = blockIdx.y;
   a += (size_t)rhs * n;
   b += (size_t)rhs * n;
-  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  R acc[4] = {(R)0, (R)0, (R)0, (R)0};
   for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
     cx<R> x = ldc<R>(a, i), y = ldc<R>(b, i);
     cx<R> d = cmul_conj(x, y);
-    red[0] += (double)d.re;
-    red[1] += (double)d.im;
-    red[2] += (double)norm2(x);
-    red[3] += (double)norm2(y);
+    acc[0] += d.re;
+    acc[1] += d.im;
+    acc[2] += norm2(x);
+    acc[3] += norm2(y);
   }
-  grid_reduce<4, kVecThreads>(red, ra, rhs);
+  grid_reduce<4, kVecThreads, R>(acc, ra, rhs);
 }
 
 int launch_dot(int prec, size_t n, int nrhs, const void* a, const void* b, RedArgs red, cudaStream_t st) {
-  dim3 grid(vec_blocks(n), nrhs);
+  dim3 grid(red_blocks(n), nrhs);
   switch (prec) {
     case 0: dot_kernel<double2><<<grid, kVecThreads, 0, st>>>(n, (const double2*)a, (const double2*)b, red); break;
     case 1: dot_kernel<float2><<<grid, kVecThreads, 0, st>>>(n, (const float2*)a, (const float2*)b, red); break;
@@ -105,6 +113,10 @@ int launch_dot(int prec, size_t n, int nrhs, const void* a, const void* b, RedAr
 // One block row computes CH dots <W_j|w> for j in [chunk * CH, chunk * CH + CH).
 constexpr int kChunk = 8;
 
+// The basis holds a multiple of kChunk vectors, so every block reads all
+// kChunk vectors of its chunk without a bound test (the dots beyond k are
+// computed from whatever the unused slots hold and are never read), and the
+// eight loads of an element issue back to back.
 template <typename S>
 __global__ void __launch_bounds__(kVecThreads)
     multidot_kernel(size_t n, int k, int kmax, const S* W, size_t jstride, const S* w, RedArgs ra) {
@@ -112,19 +124,23 @@ __global__ void __launch_bounds__(kVecThreads)
   const int chunk = blockIdx.y, rhs = blockIdx.z;
   const int j0 = chunk * kChunk;
   const S* wr = w + (size_t)rhs * n;
-  double red[2 * kChunk];
+  const S* Wc = W + (size_t)j0 * jstride + (size_t)rhs * n;
+  cx<R> acc[kChunk];
 #pragma unroll
-  for (int q = 0; q < 2 * kChunk; ++q) red[q] = 0.0;
+  for (int q = 0; q < kChunk; ++q) acc[q] = zero<R>();
   for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
     const cx<R> x = ldc<R>(wr, i);
+    cx<R> v[kChunk];
 #pragma unroll
-    for (int q = 0; q < kChunk; ++q) {
-      if (j0 + q < k) {
-        cx<R> d = cmul_conj(ldc<R>(W + (size_t)(j0 + q) * jstride + (size_t)rhs * n, i), x);
-        red[2 * q] += (double)d.re;
-        red[2 * q + 1] += (double)d.im;
-      }
-    }
+    for (int q = 0; q < kChunk; ++q) v[q] = ldc<R>(Wc + (size_t)q * jstride, i);
+#pragma unroll
+    for (int q = 0; q < kChunk; ++q) acc[q] = cfma_conj(v[q], x, acc[q]);
+  }
+  R red[2 * kChunk];
+#pragma unroll
+  for (int q = 0; q < kChunk; ++q) {
+    red[2 * q] = acc[q].re;
+    red[2 * q + 1] = acc[q].im;
   }
   // lane = rhs * nchunks + chunk; the result is laid out so that beta_j of
   // rhs r sits at result[(r * kmax + j) * 2]: stride between lanes is 2 CH
@@ -132,14 +148,14 @@ __global__ void __launch_bounds__(kVecThreads)
   RedArgs r2 = ra;
   r2.result = ra.result + (size_t)rhs * kmax * 2 + (size_t)chunk * 2 * kChunk - (size_t)(rhs * gridDim.y + chunk) * 2 * kChunk;
   r2.stride = 2 * kChunk;
-  grid_reduce<2 * kChunk, kVecThreads>(red, r2, rhs * gridDim.y + chunk);
+  grid_reduce<2 * kChunk, kVecThreads, R>(red, r2, rhs * gridDim.y + chunk);
 }
 
 int launch_multidot(int prec, size_t n, int nrhs, int k, int kmax, const void* W, size_t jstride, const void* w,
                     RedArgs red, cudaStream_t st) {
   if (k <= 0) return 0;
   if (kmax % kChunk) return -1;
-  dim3 grid(vec_blocks(n), (k + kChunk - 1) / kChunk, nrhs);
+  dim3 grid(red_blocks(n), (k + kChunk - 1) / kChunk, nrhs);
   switch (prec) {
     case 0:
       multidot_kernel<double2><<<grid, kVecThreads, 0, st>>>(n, k, kmax, (const double2*)W, jstride, (const double2*)w, red);
@@ -163,7 +179,7 @@ __global__ void __launch_bounds__(kVecThreads)
   const double* bt = beta + (size_t)rhs * kmax * 2;
   for (int j = threadIdx.x; j < k; j += kVecThreads) sb[j] = mk<R>((R)bt[2 * j], (R)bt[2 * j + 1]);
   __syncthreads();
-  double red[3] = {0.0, 0.0, 0.0};
+  R acc[3] = {(R)0, (R)0, (R)0};
   for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
     cx<R> wv = ldc<R>(w + off, i), zv = ldc<R>(z + off, i);
     // four basis vectors per round: eight independent loads in flight
@@ -190,11 +206,11 @@ __global__ void __launch_bounds__(kVecThreads)
     stc(z + off, i, zv);
     const cx<R> ws = as_stored<S>(wv);
     const cx<R> d = cmul_conj(ws, ldc<R>(r + off, i));
-    red[0] += (double)d.re;
-    red[1] += (double)d.im;
-    red[2] += (double)norm2(ws);
+    acc[0] += d.re;
+    acc[1] += d.im;
+    acc[2] += norm2(ws);
   }
-  if (ra.result) grid_reduce<3, kVecThreads>(red, ra, rhs);
+  if (ra.result) grid_reduce<3, kVecThreads, R>(acc, ra, rhs);
 }
 
 int launch_multiaxpy(int prec, size_t n, int nrhs, int k, int kmax, const double* beta, const void* W,
@@ -232,7 +248,7 @@ __global__ void __launch_bounds__(kVecThreads)
   const cx<R> a = mk<R>((R)ar, (R)ai);
   const cx<RX> ax = mk<RX>((RX)ar, (RX)ai);
   const size_t off = (size_t)rhs * n;
-  double red[1] = {0.0};
+  R acc = (R)0;
   for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
     const cx<R> wv = as_stored<S>(s * ldc<R>(w + off, i));
     const cx<R> zv = as_stored<S>(s * ldc<R>(z + off, i));
@@ -243,9 +259,10 @@ __global__ void __launch_bounds__(kVecThreads)
     stc(x + off, i, xv);
     cx<R> rv = ldc<R>(r + off, i) - a * wv;
     stc(r + off, i, rv);
-    red[0] += (double)norm2(as_stored<S>(rv));
+    acc += norm2(as_stored<S>(rv));
   }
-  grid_reduce<1, kVecThreads>(red, ra, rhs);
+  R red[1] = {acc};
+  grid_reduce<1, kVecThreads, R>(red, ra, rhs);
 }
 
 int launch_gcr_update(int prec, int xprec, size_t n, int nrhs, const double* dots, int dstride, void* w, void* z,

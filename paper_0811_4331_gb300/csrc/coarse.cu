@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(NT) coarse_apply_kernel(const CoarseArgs<S> A)
   const int o = t / G, q = t % G;  // output index o = i V + B
   const int rhs = blockIdx.y;
   const size_t voff = (size_t)rhs * n * V;
-  double red[3] = {0.0, 0.0, 0.0};
+  R red[3] = {(R)0, (R)0, (R)0};
   const bool live = o < n * V;
   cx<R> acc = zero<R>();
   int i = 0, B = 0;
@@ -81,12 +81,12 @@ __global__ void __launch_bounds__(NT) coarse_apply_kernel(const CoarseArgs<S> A)
     if (A.z) {
       const cx<R> vs = as_stored<S>(v);
       const cx<R> dd = cmul_conj(vs, ldc<R>(A.z, oo));
-      red[0] = (double)dd.re;
-      red[1] = (double)dd.im;
-      red[2] = (double)norm2(vs);
+      red[0] = dd.re;
+      red[1] = dd.im;
+      red[2] = norm2(vs);
     }
   }
-  if (A.z) grid_reduce<3, NT>(red, A.red, rhs);
+  if (A.z) grid_reduce<3, NT, R>(red, A.red, rhs);
 }
 
 // Lanes per output: enough threads for ~64K in flight, at most 32.
@@ -154,12 +154,14 @@ __device__ __forceinline__ int agg_site(const Agg& g, int B, int s) {
 }
 
 // r_c[(chi nv + k)][B] = sum_{c, s} conj(P[B][chi][k][c][s]) r[(chi nhalf + c)][site(B, s)]
+// One CTA per (aggregate, group of NT/32 rows): small coarse grids still fill the GPU.
 template <typename SI, typename SP, typename SO, int NT>
 __global__ void __launch_bounds__(NT) restrict_kernel(const Agg g, const SP* P, const SI* in, SO* out) {
   typedef typename Store<SP>::R R;
   extern __shared__ unsigned char smem_raw[];
   cx<R>* sm = (cx<R>*)smem_raw;  // [ncomp][bsites]
-  const int B = blockIdx.x, rhs = blockIdx.y;
+  const int ngroups = (2 * g.nv + NT / 32 - 1) / (NT / 32);
+  const int B = blockIdx.x / ngroups, grp = blockIdx.x % ngroups, rhs = blockIdx.y;
   const int bs = g.bsites, nh = g.nhalf;
   const SI* vin = in + (size_t)rhs * g.ncomp * g.V;
   for (int e = threadIdx.x; e < g.ncomp * bs; e += NT) {
@@ -169,7 +171,9 @@ __global__ void __launch_bounds__(NT) restrict_kernel(const Agg g, const SP* P, 
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int len = nh * bs;
-  for (int row = warp; row < 2 * g.nv; row += NT / 32) {
+  {
+    const int row = grp * (NT / 32) + warp;
+    if (row >= 2 * g.nv) return;
     const int chi = row / g.nv;
     const SP* pr = P + ((size_t)B * 2 * g.nv + row) * len;
     const cx<R>* v = sm + (size_t)chi * len;
@@ -185,17 +189,21 @@ __global__ void __launch_bounds__(NT) restrict_kernel(const Agg g, const SP* P, 
 }
 
 // x[(chi nhalf + c)][site(B, s)] = sum_k P[B][chi][k][c][s] x_c[(chi nv + k)][B]
+// One CTA per (aggregate, group of NT outputs).
 template <typename SI, typename SP, typename SO, int NT>
 __global__ void __launch_bounds__(NT) prolong_kernel(const Agg g, const SP* P, const SI* in, SO* out) {
   typedef typename Store<SP>::R R;
   extern __shared__ unsigned char smem_raw[];
   cx<R>* xc = (cx<R>*)smem_raw;  // [2 nv]
-  const int B = blockIdx.x, rhs = blockIdx.y;
+  const int ngroups = (g.ncomp * g.bsites + NT - 1) / NT;
+  const int B = blockIdx.x / ngroups, grp = blockIdx.x % ngroups, rhs = blockIdx.y;
   const int bs = g.bsites, nh = g.nhalf, nv = g.nv;
   for (int q = threadIdx.x; q < 2 * nv; q += NT) xc[q] = ldc<R>(in, ((size_t)rhs * 2 * nv + q) * g.Vc + B);
   __syncthreads();
   const size_t len = (size_t)nh * bs;
-  for (int e = threadIdx.x; e < g.ncomp * bs; e += NT) {
+  {
+    const int e = grp * NT + threadIdx.x;
+    if (e >= g.ncomp * bs) return;
     const int c = e / bs, s = e - c * bs;
     const int chi = c / nh, cl = c - chi * nh;
     const SP* pc = P + ((size_t)B * 2 + chi) * nv * len + (size_t)cl * bs + s;
@@ -213,7 +221,9 @@ static int restrict_t(const Agg& g, const void* P, const void* in, void* out, in
   if (sm > 200 * 1024) return -1;
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(restrict_kernel<SI, SP, SO, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  restrict_kernel<SI, SP, SO, NT><<<dim3(g.Vc, nrhs), NT, sm, st>>>(g, (const SP*)P, (const SI*)in, (SO*)out);
+  const int ngroups = (2 * g.nv + NT / 32 - 1) / (NT / 32);
+  restrict_kernel<SI, SP, SO, NT>
+      <<<dim3(g.Vc * ngroups, nrhs), NT, sm, st>>>(g, (const SP*)P, (const SI*)in, (SO*)out);
   return launched() ? 0 : -1;
 }
 
@@ -222,7 +232,9 @@ static int prolong_t(const Agg& g, const void* P, const void* in, void* out, int
   typedef typename Store<SP>::R R;
   constexpr int NT = 256;
   const size_t sm = (size_t)2 * g.nv * sizeof(cx<R>);
-  prolong_kernel<SI, SP, SO, NT><<<dim3(g.Vc, nrhs), NT, sm, st>>>(g, (const SP*)P, (const SI*)in, (SO*)out);
+  const int ngroups = (g.ncomp * g.bsites + NT - 1) / NT;
+  prolong_kernel<SI, SP, SO, NT>
+      <<<dim3(g.Vc * ngroups, nrhs), NT, sm, st>>>(g, (const SP*)P, (const SI*)in, (SO*)out);
   return launched() ? 0 : -1;
 }
 
@@ -247,6 +259,23 @@ int launch_prolong(int pin, int pP, int pout, const Agg& g, const void* P, const
     return prolong_t<float2, __nv_bfloat162, __nv_bfloat162>(g, P, in, out, nrhs, st);
   if (pin == 2 && pP == 2 && pout == 2) return prolong_t<__half2, __half2, __half2>(g, P, in, out, nrhs, st);
   return -1;
+}
+
+// C[0][i][i][B] += delta for every row i and coarse site B.
+__global__ void diag_shift_kernel(double2* C, int n, int V, double delta) {
+  const size_t tot = (size_t)n * V;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / V, B = e % V;
+    C[(i * n + i) * V + B].x += delta;
+  }
+}
+
+int launch_diag_shift(double2* C, int n, int V, double delta, cudaStream_t st) {
+  const size_t tot = (size_t)n * V;
+  size_t b = (tot + 255) / 256;
+  if (b > 4096) b = 4096;
+  diag_shift_kernel<<<(unsigned)(b < 1 ? 1 : b), 256, 0, st>>>(C, n, V, delta);
+  return launched() ? 0 : -1;
 }
 
 // ------------------------------------------------------------------ coarsest: dense inverse
@@ -312,58 +341,39 @@ __global__ void gj_init_kernel(const T* aug, int N, T* col0, unsigned long long*
   if ((threadIdx.x & 31) == 0 && best) atomicMax(keys, best);
 }
 
+// grid = (ceil((2N - k) / 256), N): block row = matrix row i, columns k .. 2N-1.
 template <typename T>
 __global__ void gj_step_kernel(T* aug, int N, int k, const T* colk, T* colnext, int* used,
                                unsigned long long* keys, int* err) {
   typedef typename Store<T>::R R;
-  __shared__ unsigned long long wbest[32];
   if (*err) return;
-  const size_t ld = 2 * (size_t)N;
+  const int i = blockIdx.y;
+  const int j = k + blockIdx.x * blockDim.x + threadIdx.x;
+  const int ld = 2 * N;
   const int p = pivot_row(keys[k]);
   if (p < 0 || p >= N) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *err = 1;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *err = 1;
     return;
   }
   const cx<R> piv = ldc<R>(colk, p);
   if (!(norm2(piv) > (R)0)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *err = 1;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *err = 1;
     return;
   }
-  const R den = norm2(piv);
-  const cx<R> pinv = mk<R>(piv.re / den, -piv.im / den);
-  const size_t width = ld - (size_t)k;  // columns k .. 2N-1 (columns < k of row p are zero)
-  const size_t tot = (size_t)N * width;
-  unsigned long long best = 0;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / width);
-    const size_t j = (size_t)k + e % width;
-    const size_t o = (size_t)i * ld + j;
-    cx<R> v = ldc<R>(aug, o);
-    if (i != p) {
-      const cx<R> f = ldc<R>(colk, i) * pinv;
-      v = (j == (size_t)k) ? zero<R>() : v - f * ldc<R>(aug, (size_t)p * ld + j);
-      stc(aug, o, v);
-    }
-    if (j == (size_t)k + 1 && (int)j < N) {
-      stc(colnext, i, v);
-      if (i != p && !used[i]) {
-        const unsigned long long key = pivot_key((float)norm2(v), i);
-        best = key > best ? key : best;
-      }
-    }
+  if (j >= ld) return;
+  const size_t o = (size_t)i * ld + j;
+  cx<R> v = ldc<R>(aug, o);
+  if (i != p) {
+    const R den = norm2(piv);
+    const cx<R> f = ldc<R>(colk, i) * mk<R>(piv.re / den, -piv.im / den);
+    v = (j == k) ? zero<R>() : v - f * ldc<R>(aug, (size_t)p * ld + j);
+    stc(aug, o, v);
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long other = __shfl_down_sync(0xffffffffu, best, o);
-    best = other > best ? other : best;
+  if (j == k + 1 && j < N) {
+    stc(colnext, i, v);
+    if (i != p && !used[i]) atomicMax(keys + k + 1, pivot_key((float)norm2(v), i));
   }
-  if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = best;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long b = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = wbest[w] > b ? wbest[w] : b;
-    if (b && k + 1 < N) atomicMax(keys + k + 1, b);
-    if (blockIdx.x == 0) used[p] = 1;
-  }
+  if (i == p && j == k) used[p] = 1;
 }
 
 // inv[k][c] = aug[p_k][N + c] / aug[p_k][k]
@@ -403,8 +413,8 @@ static int dense_inverse_t(const double2* C, const int L[4], int n, T* aug, T* c
   for (int k = 0; k < N; ++k) {
     const T* colk = cols + (size_t)(k & 1) * N;
     T* colnext = cols + (size_t)((k + 1) & 1) * N;
-    gj_step_kernel<T><<<grid_for((size_t)N * (2 * N - k), 2048), 256, 0, st>>>(aug, N, k, colk, colnext, used, keys,
-                                                                              err);
+    const dim3 grid((unsigned)((2 * N - k + 255) / 256), (unsigned)N);
+    gj_step_kernel<T><<<grid, 256, 0, st>>>(aug, N, k, colk, colnext, used, keys, err);
   }
   gj_finish_kernel<T><<<grid_for((size_t)N * N, 8192), 256, 0, st>>>(aug, N, keys, inv);
   return launched() ? 0 : -1;

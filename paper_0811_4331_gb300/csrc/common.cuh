@@ -204,12 +204,12 @@ struct RedArgs {
   int stride;         // doubles between lanes in result
 };
 
-template <int NV, int NT>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* NV * NT/32 */) {
+template <int NV, int NT, typename T>
+__device__ __forceinline__ void block_sum(T (&v)[NV], T* smem /* NV * NT/32 */) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    double s = v[k];
+    T s = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) smem[k * (NT / 32) + warp] = s;
@@ -218,7 +218,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* NV * 
   if (warp == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double s = lane < NT / 32 ? smem[k * (NT / 32) + lane] : 0.0;
+      T s = lane < NT / 32 ? smem[k * (NT / 32) + lane] : (T)0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
       v[k] = s;  // valid in thread 0
@@ -229,17 +229,20 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* NV * 
 
 // Finish a grid reduction for lane `ln` whose blocks are blockIdx.x in
 // [0, gridDim.x).  Call from every thread of every block with the thread's
-// partial values; NT = blockDim.x (a multiple of 32, <= 1024).
-template <int NV, int NT>
-__device__ void grid_reduce(double (&v)[NV], const RedArgs& ra, int ln) {
-  __shared__ double smem[NV * (NT / 32)];
+// partial values of type T; NT = blockDim.x (a multiple of 32, <= 1024).
+// The tree inside a block runs in T (FP32 for the FP32 / 16-bit kernels:
+// FP64 arithmetic is scarce on this part); the sum over blocks runs in FP64.
+template <int NV, int NT, typename T>
+__device__ __forceinline__ void grid_reduce(T (&v)[NV], const RedArgs& ra, int ln) {
+  __shared__ T smem_t[NV * (NT / 32)];
+  __shared__ double smem_d[NV * (NT / 32)];
   __shared__ bool last;
-  block_sum<NV, NT>(v, smem);
+  block_sum<NV, NT, T>(v, smem_t);
   const int nb = gridDim.x;
   if (threadIdx.x == 0) {
     double* dst = ra.partials + ((size_t)ln * nb + blockIdx.x) * NV;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) dst[k] = v[k];
+    for (int k = 0; k < NV; ++k) dst[k] = (double)v[k];
     __threadfence();
     unsigned t = atomicAdd(ra.tickets + ln, 1u);
     last = (t == (unsigned)nb - 1);
@@ -255,7 +258,7 @@ __device__ void grid_reduce(double (&v)[NV], const RedArgs& ra, int ln) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) w[k] += __ldcg(src + k);
   }
-  block_sum<NV, NT>(w, smem);
+  block_sum<NV, NT, double>(w, smem_d);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) ra.result[(size_t)ln * ra.stride + k] = w[k];

@@ -62,6 +62,7 @@ struct Level {
   // operator of this level, per storage precision (index = precision code)
   DevBuf links[4];  // level 0: [4][NL][V]
   DevBuf cop[4];    // level >= 1: stencil [9][ncomp][ncomp][V]
+  DevBuf cop_mma;   // level >= 1 (coarse_mma): BF16 stencil in MMA fragment order
   // prolongator to level l+1, per precision: [Vc][2][nv][nhalf][bsites]
   DevBuf P[4];
   // coarsest level: dense inverse [N][N], N = ncomp V, FP64 (plain) or FP32

@@ -32,6 +32,7 @@ int launch_pack_links(int prec, const void* ext, void* out, int V, cudaStream_t 
 // Every vector kernel works on nrhs vectors of n complex elements each,
 // right-hand side r at offset r * n.  Grid sizes are a pure function of n.
 int vec_blocks(size_t n);
+int red_blocks(size_t n);
 const int kVecThreads = 256;
 const int kMaxVecBlocks = 1216;  // 152 SMs x 8
 
@@ -62,7 +63,7 @@ int launch_dot(int prec, size_t n, int nrhs, const void* a, const void* b, RedAr
 // Classical Gram-Schmidt pieces for flexible GCR.
 // Basis vector j of rhs r at base + j * jstride + r * n (elements).
 // multidot: beta_j = <W_j|w> for j < k -> result[(r * kmax + j) * 2 + {0,1}] (red.stride
-// ignored; result holds kmax complex per rhs).
+// ignored; result holds kmax complex per rhs).  W must hold ceil(k / 8) * 8 vectors.
 int launch_multidot(int prec, size_t n, int nrhs, int k, int kmax, const void* W, size_t jstride,
                     const void* w, RedArgs red, cudaStream_t st);
 // w -= sum_j beta_j W_j, z -= sum_j beta_j Z_j (beta from multidot result);
@@ -107,6 +108,13 @@ struct CoarseCall {
 int launch_coarse_apply(const CoarseCall& k, cudaStream_t st);
 int coarse_blocks(int ncomp, int V);
 
+// Tensor-core coarse stencil (BF16 mma.sync, FP32 accumulation) for R <= 64
+// right-hand sides of storage prec (1 = FP32, 3 = BF16): out = a A in + c y2.
+size_t mma_pack_bytes(int n, int V);
+int launch_mma_pack(const double2* C, int n, int V, void* out, cudaStream_t st);
+int launch_coarse_mma(int prec, const void* Cf, const void* in, void* out, const void* y2, const int L[4], int n, int R,
+                      double a, double c, cudaStream_t st);
+
 // Aggregation of level l (fine side) into level l+1 (coarse side).
 struct Agg {
   int L[4];
@@ -124,6 +132,9 @@ int launch_restrict(int pin, int pP, int pout, const Agg& g, const void* P, cons
 int launch_prolong(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
                    cudaStream_t st);
 
+// C_0(B) += delta 1 on a coarse stencil [9][n][n][V] (FP64).
+int launch_diag_shift(double2* C, int n, int V, double delta, cudaStream_t st);
+
 // Coarsest level: dense inverse (Gauss-Jordan, partial pivoting) of an FP64
 // stencil operator in precision prec (0 or 1); aug is [N][2N] of precision
 // prec, scratch holds dense_inverse_scratch_bytes(prec, N), inv is [N][N];
@@ -138,11 +149,12 @@ int launch_dense_matvec(int pm, int pin, int pout, int N, const void* inv, const
 // Setup: blockwise Gram-Schmidt (err = 2 on rank loss), prolongator
 // columns as fields, Galerkin coarse stencil column j.
 int launch_block_gs(const Agg& g, const double2* cand, double2* P, int* err, cudaStream_t st);
-// Columns j0 .. j0 + ncols - 1 at v + (j - j0) * ncomp * V.
-int launch_p_column(const Agg& g, const double2* P, int j0, int ncols, double2* v, cudaStream_t st);
-int launch_galerkin_wilson(const Agg& g, const double2* links64, double mass, const double2* vj, const double2* P,
+// Columns j0 .. j0 + ncols - 1 at v + (j - j0) * ncomp * V, precision prec (0 or 1) of P and v.
+int launch_p_column(int prec, const Agg& g, const void* P, int j0, int ncols, void* v, cudaStream_t st);
+// Galerkin columns in the arithmetic of `prec` (0: FP64 inputs, 1: FP32 inputs); output always FP64 storage.
+int launch_galerkin_wilson(int prec, const Agg& g, const void* links, double mass, const void* vj, const void* P,
                            int j0, int ncols, double2* Cout, cudaStream_t st);
-int launch_galerkin_stencil(const Agg& g, const double2* Cfine, const double2* vj, const double2* P, int j0,
+int launch_galerkin_stencil(int prec, const Agg& g, const void* Cfine, const void* vj, const void* P, int j0,
                             int ncols, double2* Cout, cudaStream_t st);
 
 }  // namespace wmg

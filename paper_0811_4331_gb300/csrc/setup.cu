@@ -31,7 +31,7 @@ __device__ __forceinline__ int agg_site2(const Agg& g, int B, int s) {
 template <int NT>
 __device__ __forceinline__ cx<double> block_csum(cx<double> v, double* sm) {
   double a[2] = {v.re, v.im};
-  block_sum<2, NT>(a, sm);
+  block_sum<2, NT, double>(a, sm);
   __shared__ double out[2];
   if (threadIdx.x == 0) {
     out[0] = a[0];
@@ -97,15 +97,17 @@ int launch_block_gs(const Agg& g, const double2* cand, double2* P, int* err, cud
 
 // Column j of P (j = chi' nv + k') as a level-l field [ncomp][V]: the k'-th
 // orthonormal vector on its chirality chi' half, zero on the other half.
-__global__ void p_column_kernel(const Agg g, const double2* P, int j0, double2* vbase) {
+template <typename TP>
+__global__ void p_column_kernel(const Agg g, const TP* P, int j0, TP* vbase) {
   const size_t tot = (size_t)g.ncomp * g.V;
   const int j = j0 + blockIdx.y;
-  double2* v = vbase + (size_t)blockIdx.y * tot;
+  TP* v = vbase + (size_t)blockIdx.y * tot;
   const int chi = j / g.nv, k = j - chi * g.nv;
   const int len = g.nhalf * g.bsites;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(e / g.V), site = (int)(e % g.V);
-    double2 val = make_double2(0.0, 0.0);
+    TP val;
+    stc(&val, 0, zero<double>());
     if (c / g.nhalf == chi) {
       int cf[4], cb[4], cl[4];
       site_coords(site, g.L, cf);
@@ -121,40 +123,49 @@ __global__ void p_column_kernel(const Agg g, const double2* P, int j0, double2* 
   }
 }
 
-int launch_p_column(const Agg& g, const double2* P, int j0, int ncols, double2* v, cudaStream_t st) {
+int launch_p_column(int prec, const Agg& g, const void* P, int j0, int ncols, void* v, cudaStream_t st) {
   size_t tot = (size_t)g.ncomp * g.V;
   size_t b = (tot + 255) / 256;
   if (b > 8192) b = 8192;
-  p_column_kernel<<<dim3((unsigned)b, ncols), 256, 0, st>>>(g, P, j0, v);
+  if (prec == 0)
+    p_column_kernel<double2><<<dim3((unsigned)b, ncols), 256, 0, st>>>(g, (const double2*)P, j0, (double2*)v);
+  else if (prec == 1)
+    p_column_kernel<float2><<<dim3((unsigned)b, ncols), 256, 0, st>>>(g, (const float2*)P, j0, (float2*)v);
+  else
+    return -1;
   return launched() ? 0 : -1;
 }
 
 // ------------------------------------------------------------------ Galerkin build
-// h = A_d(n) v(n + e_d) on every site of aggregate B into sm_h[c][s].
+// h = A_d(n) v(n + e_d) on every site of aggregate B into sm_h[c][s], in the
+// arithmetic of the field's storage (FP64 for the plain hierarchy, FP32 for
+// the mixed one).
+template <typename TV, typename TL, int NL>
 struct WilsonHopOp {
-  const double2* U;  // FP64 links, 18 reals: [4][9][V]
+  typedef typename Store<TV>::R R;
+  const TL* U;  // links [4][NL][V]
   double mass;
-  __device__ void apply(const Agg& g, int B, int d, const double2* v, cx<double>* h, int nt) const {
+  __device__ void apply(const Agg& g, int B, int d, const TV* v, cx<R>* h, int nt) const {
     for (int s = threadIdx.x; s < g.bsites; s += nt) {
       const int n = agg_site2(g, B, s);
-      cx<double> acc[4][3];
+      cx<R> acc[4][3];
 #pragma unroll
       for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) acc[sp][a] = zero<double>();
+        for (int a = 0; a < 3; ++a) acc[sp][a] = zero<R>();
       if (d == 0) {
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-          for (int a = 0; a < 3; ++a) acc[sp][a] = (4.0 + mass) * ldc<double>(v, (size_t)(sp * 3 + a) * g.V + n);
+          for (int a = 0; a < 3; ++a) acc[sp][a] = (R)(4.0 + mass) * ldc<R>(v, (size_t)(sp * 3 + a) * g.V + n);
       } else {
         int c[4];
         site_coords(n, g.L, c);
         const int nb = neighbor(c, g.L, d);
         const int mu = (d - 1) >> 1;
         const bool fwd = d & 1;
-        Link<double> u;
-        load_link<double, double2, 9>(u, U, mu, g.V, fwd ? n : nb);
+        Link<R> u;
+        load_link<R, TL, NL>(u, U, mu, g.V, fwd ? n : nb);
         switch (d) {
           case 1: hop<0, true>(acc, v, g.V, nb, u); break;
           case 2: hop<0, false>(acc, v, g.V, nb, u); break;
@@ -168,7 +179,7 @@ struct WilsonHopOp {
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-          for (int a = 0; a < 3; ++a) acc[sp][a] = -0.5 * acc[sp][a];
+          for (int a = 0; a < 3; ++a) acc[sp][a] = (R)(-0.5) * acc[sp][a];
       }
 #pragma unroll
       for (int sp = 0; sp < 4; ++sp)
@@ -178,9 +189,11 @@ struct WilsonHopOp {
   }
 };
 
+template <typename TV>
 struct StencilHopOp {
-  const double2* C;  // [9][n][n][V] of the level being coarsened
-  __device__ void apply(const Agg& g, int B, int d, const double2* v, cx<double>* h, int nt) const {
+  typedef typename Store<TV>::R R;
+  const TV* C;  // [9][n][n][V] of the level being coarsened
+  __device__ void apply(const Agg& g, int B, int d, const TV* v, cx<R>* h, int nt) const {
     const int n = g.ncomp;
     for (int e = threadIdx.x; e < n * g.bsites; e += nt) {
       const int i = e / g.bsites, s = e - i * g.bsites;
@@ -188,9 +201,9 @@ struct StencilHopOp {
       int c[4];
       site_coords(site, g.L, c);
       const int nb = neighbor(c, g.L, d);
-      cx<double> acc = zero<double>();
-      const double2* row = C + ((size_t)(d * n + i) * n) * g.V + site;
-      for (int j = 0; j < n; ++j) acc = cfma(ldc<double>(row, (size_t)j * g.V), ldc<double>(v, (size_t)j * g.V + nb), acc);
+      cx<R> acc = zero<R>();
+      const TV* row = C + ((size_t)(d * n + i) * n) * g.V + site;
+      for (int j = 0; j < n; ++j) acc = cfma(ldc<R>(row, (size_t)j * g.V), ldc<R>(v, (size_t)j * g.V + nb), acc);
       h[e] = acc;
     }
   }
@@ -205,31 +218,32 @@ __device__ __forceinline__ bool crosses(const Agg& g, int s, int d) {
   return (d & 1) ? (cl[mu] == g.blk[mu] - 1) : (cl[mu] == 0);
 }
 
-template <typename Op, int NT>
-__global__ void __launch_bounds__(NT) galerkin_kernel(const Agg g, Op op, const double2* vbase, const double2* P,
-                                                      int j0, double2* Cout) {
-  const int j = j0 + blockIdx.y;
-  const double2* vj = vbase + (size_t)blockIdx.y * g.ncomp * g.V;
+template <typename Op, typename TP, int NT>
+__global__ void __launch_bounds__(NT) galerkin_kernel(const Agg g, Op op, const TP* vbase, const TP* P, int j0,
+                                                      double2* Cout) {
+  typedef typename Store<TP>::R R;
   extern __shared__ unsigned char smem_raw[];
-  cx<double>* h = (cx<double>*)smem_raw;                     // [ncomp][bsites]
-  cx<double>* acc0 = h + (size_t)g.ncomp * g.bsites;         // [2 nv]
+  cx<R>* h = (cx<R>*)smem_raw;                        // [ncomp][bsites]
+  cx<R>* acc0 = h + (size_t)g.ncomp * g.bsites;       // [2 nv]
+  const int j = j0 + blockIdx.y;
+  const TP* vj = vbase + (size_t)blockIdx.y * g.ncomp * g.V;
   const int B = blockIdx.x;
   const int nc = 2 * g.nv;  // coarse components
   const int len = g.nhalf * g.bsites;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < nc; i += NT) acc0[i] = zero<double>();
+  for (int i = threadIdx.x; i < nc; i += NT) acc0[i] = zero<R>();
   __syncthreads();
   for (int d = 0; d < 9; ++d) {
     op.apply(g, B, d, vj, h, NT);
     __syncthreads();
     for (int row = warp; row < nc; row += NT / 32) {
       const int chi = row / g.nv;
-      const double2* pr = P + ((size_t)B * 2 * g.nv + row) * len;
-      const cx<double>* hv = h + (size_t)chi * len;
-      cx<double> in = zero<double>(), out = zero<double>();
+      const TP* pr = P + ((size_t)B * 2 * g.nv + row) * len;
+      const cx<R>* hv = h + (size_t)chi * len;
+      cx<R> in = zero<R>(), out = zero<R>();
       for (int e = lane; e < len; e += 32) {
         const int s = e % g.bsites;
-        const cx<double> t = cmul_conj(ldc<double>(pr, e), hv[e]);
+        const cx<R> t = cmul_conj(ldc<R>(pr, e), hv[e]);
         if (crosses(g, s, d))
           out = out + t;
         else
@@ -249,34 +263,54 @@ __global__ void __launch_bounds__(NT) galerkin_kernel(const Agg g, Op op, const 
     }
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < nc; i += NT) Cout[((size_t)(0 * nc + i) * nc + j) * g.Vc + B] = make_double2(acc0[i].re, acc0[i].im);
+  for (int i = threadIdx.x; i < nc; i += NT)
+    Cout[((size_t)(0 * nc + i) * nc + j) * g.Vc + B] = make_double2(acc0[i].re, acc0[i].im);
 }
 
-template <typename Op>
-static int galerkin_t(const Agg& g, const Op& op, const double2* vj, const double2* P, int j0, int ncols,
-                      double2* Cout, cudaStream_t st) {
+template <typename Op, typename TP>
+static int galerkin_t(const Agg& g, const Op& op, const void* vj, const void* P, int j0, int ncols, double2* Cout,
+                      cudaStream_t st) {
+  typedef typename Store<TP>::R R;
   constexpr int NT = 256;
-  const size_t sm = ((size_t)g.ncomp * g.bsites + 2 * g.nv) * sizeof(cx<double>);
+  const size_t sm = ((size_t)g.ncomp * g.bsites + 2 * g.nv) * sizeof(cx<R>);
   if (sm > 200 * 1024) return -1;
   if (sm > 48 * 1024)
-    cudaFuncSetAttribute(galerkin_kernel<Op, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  galerkin_kernel<Op, NT><<<dim3(g.Vc, ncols), NT, sm, st>>>(g, op, vj, P, j0, Cout);
+    cudaFuncSetAttribute(galerkin_kernel<Op, TP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  galerkin_kernel<Op, TP, NT><<<dim3(g.Vc, ncols), NT, sm, st>>>(g, op, (const TP*)vj, (const TP*)P, j0, Cout);
   return launched() ? 0 : -1;
 }
 
-int launch_galerkin_wilson(const Agg& g, const double2* links64, double mass, const double2* vj, const double2* P,
+// prec 0: FP64 links (18 reals), P and fields; prec 1: FP32 links (12 reals), P and fields.
+int launch_galerkin_wilson(int prec, const Agg& g, const void* links, double mass, const void* vj, const void* P,
                            int j0, int ncols, double2* Cout, cudaStream_t st) {
-  WilsonHopOp op;
-  op.U = links64;
-  op.mass = mass;
-  return galerkin_t(g, op, vj, P, j0, ncols, Cout, st);
+  if (prec == 0) {
+    WilsonHopOp<double2, double2, 9> op;
+    op.U = (const double2*)links;
+    op.mass = mass;
+    return galerkin_t<decltype(op), double2>(g, op, vj, P, j0, ncols, Cout, st);
+  }
+  if (prec == 1) {
+    WilsonHopOp<float2, float2, 6> op;
+    op.U = (const float2*)links;
+    op.mass = mass;
+    return galerkin_t<decltype(op), float2>(g, op, vj, P, j0, ncols, Cout, st);
+  }
+  return -1;
 }
 
-int launch_galerkin_stencil(const Agg& g, const double2* Cfine, const double2* vj, const double2* P, int j0,
+int launch_galerkin_stencil(int prec, const Agg& g, const void* Cfine, const void* vj, const void* P, int j0,
                             int ncols, double2* Cout, cudaStream_t st) {
-  StencilHopOp op;
-  op.C = Cfine;
-  return galerkin_t(g, op, vj, P, j0, ncols, Cout, st);
+  if (prec == 0) {
+    StencilHopOp<double2> op;
+    op.C = (const double2*)Cfine;
+    return galerkin_t<decltype(op), double2>(g, op, vj, P, j0, ncols, Cout, st);
+  }
+  if (prec == 1) {
+    StencilHopOp<float2> op;
+    op.C = (const float2*)Cfine;
+    return galerkin_t<decltype(op), float2>(g, op, vj, P, j0, ncols, Cout, st);
+  }
+  return -1;
 }
 
 }  // namespace wmg

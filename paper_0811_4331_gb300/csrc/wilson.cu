@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(NT) wilson_kernel(const WilsonArgs<S, G, NL> A
   const int s = blockIdx.x * NT + threadIdx.x;
   const int rhs = blockIdx.y;
   const S* in = A.in + rhs * A.vstride;
-  double red[3] = {0.0, 0.0, 0.0};
+  R acc3[3] = {(R)0, (R)0, (R)0};  // per-thread partial dots in the arithmetic type
   if (s < V) {
     int c[4], stride[4];
     {
@@ -103,13 +103,13 @@ __global__ void __launch_bounds__(NT) wilson_kernel(const WilsonArgs<S, G, NL> A
           cx<R> vs = as_stored<S>(v);
           cx<R> zz = ldc<R>(z, i);
           cx<R> d = cmul_conj(vs, zz);
-          red[0] += (double)d.re;
-          red[1] += (double)d.im;
-          red[2] += (double)norm2(vs);
+          acc3[0] += d.re;
+          acc3[1] += d.im;
+          acc3[2] += norm2(vs);
         }
       }
   }
-  if (A.z) grid_reduce<3, NT>(red, A.red, rhs);
+  if (A.z) grid_reduce<3, NT, R>(acc3, A.red, rhs);
 }
 
 template <typename S, typename G, int NL>

@@ -43,6 +43,8 @@ class mg_params(ctypes.Structure):
         ("reliable_delta", ctypes.c_double),
         ("seed", ctypes.c_uint64),
         ("use_graphs", ctypes.c_int),
+        ("coarse_mma", ctypes.c_int),
+        ("coarse_solver", ctypes.c_int),
     ]
 
 
@@ -78,6 +80,7 @@ def _load():
         "mg_default_params": (I, [P(mg_params)]),
         "mg_setup": (I, [P(VP), VP, I, P(I), D, P(mg_params), VP, VP]),
         "mg_destroy": (I, [VP]),
+        "mg_retarget": (I, [VP, D, P(VP), VP]),
         "mg_solve": (I, [VP, VP, VP, I, I, D, P(mg_stats), VP]),
         "dslash_apply": (I, [VP, I, VP, VP, I, VP]),
         "coarse_apply": (I, [VP, I, I, VP, VP, I, VP]),
@@ -106,7 +109,7 @@ def _load():
 LIB = _load()
 
 # every entry point declared in include/wilson_mg.h
-EXPORTS = ["mg_last_error", "mg_default_params", "mg_setup", "mg_destroy", "mg_solve", "dslash_apply",
+EXPORTS = ["mg_last_error", "mg_default_params", "mg_setup", "mg_retarget", "mg_destroy", "mg_solve", "dslash_apply",
            "coarse_apply", "restrict_apply", "prolong_apply", "mr_apply", "vcycle_apply", "mg_field_to_internal",
            "mg_field_from_internal", "mg_level_info", "mg_get_prolongator", "mg_get_coarse_op", "mg_footprint",
            "mg_profile", "mg_profile_read", "mg_launch_count", "mr_apply_noalloc"]
@@ -208,6 +211,13 @@ def mg_setup(gauge, dims, mass, params, starts=None, stream=None):
     h = ctypes.c_void_p()
     _check(LIB.mg_setup(ctypes.byref(h), gp, gdev, d, float(mass), ctypes.byref(params), sp, _stream(stream)))
     return Handle(h, dims)
+
+
+def mg_retarget(src, mass, stream=None):
+    """New handle for `mass` sharing the null vectors of `src` (coarse operators shifted)."""
+    h = ctypes.c_void_p()
+    _check(LIB.mg_retarget(src.ptr, float(mass), ctypes.byref(h), _stream(stream)))
+    return Handle(h, src.dims)
 
 
 def mg_destroy(h):

@@ -217,3 +217,22 @@ def test_three_level_mg_solve():
     b = inputs.gaussian_spinor(dims, 4).reshape(lat + (12,))
     x, info = mg.mg_solve(h, b, tol=1e-10)
     assert info["true_rel_residual"] <= 1e-10
+
+
+def test_gcr_fixed_is_minimal_residual_krylov():
+    """n steps of GCR with the identity preconditioner solve an n x n system (Krylov space exhausted);
+    one step with the exact inverse as preconditioner solves at once."""
+    rng = np.random.default_rng(2)
+    n = 12
+    A = np.eye(n) * 3 + rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x = mg.gcr_fixed(lambda v: A @ v, b, lambda r: r.copy(), n)
+    assert np.linalg.norm(A @ x - b) < 1e-10 * np.linalg.norm(b)
+    x1 = mg.gcr_fixed(lambda v: A @ v, b, lambda r: np.linalg.solve(A, r), 1)
+    assert np.linalg.norm(A @ x1 - b) < 1e-12 * np.linalg.norm(b)
+    # residual after k steps is the minimum over the k-dimensional Krylov space
+    for k in (2, 5):
+        xk = mg.gcr_fixed(lambda v: A @ v, b, lambda r: r.copy(), k)
+        K = np.stack([np.linalg.matrix_power(A, j) @ b for j in range(k)], axis=1)
+        c = np.linalg.lstsq(A @ K, b, rcond=None)[0]
+        assert abs(np.linalg.norm(A @ xk - b) - np.linalg.norm(A @ (K @ c) - b)) < 1e-9 * np.linalg.norm(b)
