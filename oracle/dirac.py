@@ -9,7 +9,7 @@ parameter r = 1 this is, for a spinor psi(n) with 4 spin x 3 colour components,
                - 1/2 sum_mu [ (1 - gamma_mu) U_mu(n)        psi(n + mu)
                             + (1 + gamma_mu) U_mu(n - mu)^+ psi(n - mu) ].
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
   * gamma basis: the chiral basis
         gamma_k = [[0, -i sigma_k], [i sigma_k, 0]]  (k = 1, 2, 3  <->  x, y, z)
         gamma_4 = [[0, 1], [1, 0]]                  (t)

@@ -21,10 +21,13 @@ Every function follows a passage of the paper (Clark et al., Lattice 2008):
                              4 applications of the next level's V-cycle
                              between restriction and prolongation on the fine
                              grid.
+* ``refine_setup``        -- the adaptive step of Sec. 2 beyond relaxation: the
+                             current multigrid cycle applied to A x = 0 from
+                             each candidate gives the next candidates.
 * ``fgcr``                -- GCR(50) as the outer Krylov method (Sec. 5),
                              flexible because the preconditioner varies.
 
-Readings where the paper is silent (listed in the design doc): one relaxation =
+Readings where the paper is silent: one relaxation =
 one MR step; candidates start from independent Gaussian vectors, get l MR
 steps on A x = 0 with omega = 0.8 and are normalised to unit norm; the QR is
 modified Gram-Schmidt applied twice, in candidate order; the chirality split
@@ -34,7 +37,11 @@ step are used on every level; the coarsest level is solved exactly by dense
 LU; the 4 coarse applications are 4 steps of flexible GCR on the coarse
 equation preconditioned by the next level's V-cycle, from e_c = 0 (4
 stationary sweeps e_c += V(r_c - A_c e_c) are the alternative reading,
-``coarse_solver="stationary"``); inner products are <a|b> = sum conj(a) b.
+``coarse_solver="stationary"``); an adaptive pass starts from the current
+candidates (read back from P), takes a fixed number of steps
+x <- x + M(-A x) and refines the levels finest first, each with the cycle
+that the levels below it give at that point; inner products are
+<a|b> = sum conj(a) b.
 
 Field arrays have shape (Lt, Lz, Ly, Lx, ncomp); a block size is given as
 (bx, by, bz, bt), matching the x-fastest site order.
@@ -284,6 +291,48 @@ def mg_setup(U, mass, levels, starts, omega=0.8):
         hier.append(nxt)
     last = hier[-1]
     last.lu = scipy.linalg.lu_factor(dense_from_stencil(last.stencil))
+    return hier
+
+
+def candidates_from_prolongator(P, blk):
+    """Candidates whose block QR reproduces P: vector k is column k of P on the
+    chirality-0 components and column Nv + k on the chirality-1 components."""
+    nv = P.shape[-1] // 2
+    h = blk.half
+    return [np.concatenate([P[..., :h, k], P[..., h:, nv + k]], axis=-1) for k in range(nv)]
+
+
+def rebuild_below(hier, l):
+    """Galerkin operators of levels l+1 .. from the current P's (Sec. 2), coarsest LU last."""
+    for j in range(l, len(hier) - 1):
+        Ac = coarse_stencil(hier[j].stencil, hier[j].P, hier[j].blk)
+        hier[j + 1].stencil = Ac
+        hier[j + 1].apply = (lambda A: (lambda y: dirac.stencil_apply(A, y)))(Ac)
+    last = hier[-1]
+    last.lu = scipy.linalg.lu_factor(dense_from_stencil(last.stencil))
+
+
+def refine_setup(hier, passes, cycles, nu_pre=2, nu_post=2, omega=0.8, coarse_cycles=(4,),
+                 coarse_solver="gcr"):
+    """Adaptive passes over a relaxation-built hierarchy (Sec. 2: the current
+    multigrid solver applied to A x = 0 yields the next candidates).
+
+    In each pass, level by level from the finest: every candidate x of the
+    level (read back from P) takes ``cycles`` steps x <- x + M(-A x), M the
+    current V-cycle of that level; the results, unit-normalised, give P by
+    block QR (Eq. 2.3) and the operators below are rebuilt before the next
+    level is refined.
+    """
+    for _ in range(passes):
+        for l in range(len(hier) - 1):
+            cur = hier[l]
+            cands = []
+            for x in candidates_from_prolongator(cur.P, cur.blk):
+                for _ in range(cycles):
+                    x = x + vcycle(hier, l, -cur.apply(x), nu_pre, nu_post, omega, coarse_cycles, coarse_solver)
+                cands.append(x / np.sqrt(norm2(x)))
+            cur.P = block_orthonormalize(cands, cur.blk)
+            rebuild_below(hier, l)
     return hier
 
 

@@ -236,3 +236,66 @@ def test_gcr_fixed_is_minimal_residual_krylov():
         K = np.stack([np.linalg.matrix_power(A, j) @ b for j in range(k)], axis=1)
         c = np.linalg.lstsq(A @ K, b, rcond=None)[0]
         assert abs(np.linalg.norm(A @ xk - b) - np.linalg.norm(A @ (K @ c) - b)) < 1e-9 * np.linalg.norm(b)
+
+
+def test_candidates_read_back_from_P_reproduce_P():
+    """Block QR of the candidates read back from P returns P itself (Eq. 2.3: the
+    columns of each aggregate are already orthonormal, so Gram-Schmidt keeps them)."""
+    dims = (4, 4, 4, 4)
+    U = inputs.random_gauge(dims, 5)
+    lat = _lat(dims)
+    starts = [inputs.null_vector_starts(lat, 12, 6, 9)]
+    h = mg.mg_setup(U, 0.1, [dict(block=(2, 2, 2, 2), nv=6, sweeps=4)], starts)
+    cands = mg.candidates_from_prolongator(h[0].P, h[0].blk)
+    assert len(cands) == 6 and cands[0].shape == lat + (12,)
+    P2 = mg.block_orthonormalize(cands, h[0].blk)
+    assert np.max(np.abs(P2 - h[0].P)) < 1e-12
+
+
+def test_cycle_annihilates_the_coarse_space_without_smoothing():
+    """With no smoothing and an exact coarse solve, M A x = x for x = P y: the
+    correction P A_c^-1 P^+ A P y = P y and alpha = 1 (Eq. 3.5), so the
+    adaptive step x + M(-A x) returns 0 (a sign error returns 2 x)."""
+    dims = (4, 4, 4, 4)
+    U = inputs.random_gauge(dims, 6)
+    lat = _lat(dims)
+    starts = [inputs.null_vector_starts(lat, 12, 6, 10)]
+    h = mg.mg_setup(U, 0.05, [dict(block=(2, 2, 2, 2), nv=6, sweeps=4)], starts)
+    rng = np.random.default_rng(3)
+    y = rng.standard_normal(h[1].lattice + (12,)) + 1j * rng.standard_normal(h[1].lattice + (12,))
+    x = mg.prolong(h[0].P, h[0].blk, y)
+    x1 = x + mg.vcycle(h, 0, -h[0].apply(x), nu_pre=0, nu_post=0)
+    assert np.linalg.norm(x1) < 1e-10 * np.linalg.norm(x)
+
+
+def test_refine_setup_keeps_the_invariants_and_helps():
+    """After an adaptive pass on a 3-level hierarchy: P^+ P = 1 and the chirality
+    zeros on every level (Eq. 2.3), both coarse stencils equal the brute-force
+    Galerkin products of the new P's, and MG-GCR needs no more iterations than
+    before the pass."""
+    dims = (4, 4, 4, 4)
+    U = inputs.heatbath_gauge(dims, 6.0, 30, 5)
+    lat = _lat(dims)
+    starts = [inputs.null_vector_starts(lat, 12, 6, 11),
+              inputs.null_vector_starts((2, 2, 2, 2), 12, 4, 12)]
+    spec = [dict(block=(2, 2, 2, 2), nv=6, sweeps=3), dict(block=(2, 2, 1, 1), nv=4, sweeps=3)]
+    h = mg.mg_setup(U, -0.6, spec, starts)
+    b = inputs.gaussian_spinor(dims, 1).reshape(lat + (12,))
+    _, before = mg.mg_solve(h, b, tol=1e-10)
+    P_old = h[0].P.copy()
+    mg.refine_setup(h, 1, 2)
+    assert np.max(np.abs(h[0].P - P_old)) > 1e-3  # the pass changed the prolongator
+    for l in range(2):
+        P, blk = h[l].P, h[l].blk
+        nv = P.shape[-1] // 2
+        G = np.einsum("...ci,...cj->...ij", np.conj(P), P)
+        Gb = blk.block_sum(G)
+        assert np.max(np.abs(Gb - np.eye(2 * nv))) < 1e-12
+        assert np.all(P[..., :blk.half, nv:] == 0) and np.all(P[..., blk.half:, :nv] == 0)
+        D = dirac.dense_matrix(h[l].apply, h[l].lattice + (h[l].ncomp,))
+        Pm = dirac.dense_matrix(lambda y: mg.prolong(P, blk, y), h[l + 1].lattice + (2 * nv,))
+        Dc = dirac.dense_matrix(h[l + 1].apply, h[l + 1].lattice + (2 * nv,))
+        assert np.max(np.abs(Dc - Pm.conj().T @ D @ Pm)) < 1e-11 * np.max(np.abs(D))
+    x, after = mg.mg_solve(h, b, tol=1e-10)
+    assert after["true_rel_residual"] <= 1e-10
+    assert after["iters"] <= before["iters"]
