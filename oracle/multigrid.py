@@ -21,9 +21,10 @@ Every function follows a passage of the paper (Clark et al., Lattice 2008):
                              4 applications of the next level's V-cycle
                              between restriction and prolongation on the fine
                              grid.
-* ``refine_setup``        -- the adaptive step of Sec. 2 beyond relaxation: the
-                             current multigrid cycle applied to A x = 0 from
-                             each candidate gives the next candidates.
+* ``build_levels``        -- the adaptive steps of Sec. 2 beyond relaxation:
+                             the current solver (MG-preconditioned GCR)
+                             applied to A x = 0 from a random start gives the
+                             next prototype, appended to V^k, P rebuilt.
 * ``fgcr``                -- GCR(50) as the outer Krylov method (Sec. 5),
                              flexible because the preconditioner varies.
 
@@ -37,11 +38,11 @@ step are used on every level; the coarsest level is solved exactly by dense
 LU; the 4 coarse applications are 4 steps of flexible GCR on the coarse
 equation preconditioned by the next level's V-cycle, from e_c = 0 (4
 stationary sweeps e_c += V(r_c - A_c e_c) are the alternative reading,
-``coarse_solver="stationary"``); an adaptive pass starts from the current
-candidates (read back from P), takes a fixed number of steps
-x <- x + M(-A x) and refines the levels finest first, each with the cycle
-that the levels below it give at that point; inner products are
-<a|b> = sum conj(a) b.
+``coarse_solver="stationary"``); an adaptive step runs a fixed number of
+iterations of flexible GCR preconditioned by the level's V-cycle (restarted
+every 8) from a random start and appends a batch of such vectors at once
+(each batch made with the solver of the V^k before it); the levels below are
+rebuilt from scratch after each step; inner products are <a|b> = sum conj(a) b.
 
 Field arrays have shape (Lt, Lz, Ly, Lx, ncomp); a block size is given as
 (bx, by, bz, bt), matching the x-fastest site order.
@@ -261,13 +262,15 @@ class Level:
         self.lu = None
 
 
-def mg_setup(U, mass, levels, starts, omega=0.8):
+def mg_setup(U, mass, levels, starts, omega=0.8, nu_pre=2, nu_post=2, coarse_cycles=(4,), coarse_solver="gcr"):
     """Build the multigrid hierarchy (Sec. 2 adaptive steps, Sec. 3, Sec. 5).
 
     ``levels`` lists, for every level that gets a coarser one below it, a dict
-    with ``block`` (bx, by, bz, bt), ``nv`` and ``sweeps``.  ``starts[l]`` are
-    the random initial candidates of level l (arrays shaped like that level's
-    fields).  The coarsest level gets a dense LU factorisation.
+    with ``block`` (bx, by, bz, bt), ``nv`` and ``sweeps``, and optionally
+    ``adapt_nv``, ``adapt_steps`` and ``adapt_cycles`` (see ``build_levels``).
+    ``starts[l]`` are the Nv random start vectors of level l (arrays shaped
+    like that level's fields).  The coarsest level gets a dense LU
+    factorisation.  The cycle options are those the adaptive steps run.
     """
     lat = U.shape[1:5]
     fine = Level(None, lat, 12)
@@ -278,62 +281,92 @@ def mg_setup(U, mass, levels, starts, omega=0.8):
 
     fine.apply = apply_fine
     hier = [fine]
-    for l, spec in enumerate(levels):
-        cur = hier[-1]
-        cands = relax_null_vectors(cur.apply, starts[l], spec["sweeps"], omega)
-        blk = Blocking(cur.lattice, spec["block"], cur.ncomp)
-        cur.blk = blk
-        cur.P = block_orthonormalize(cands, blk)
-        Ac = coarse_stencil(cur.stencil, cur.P, blk)
-        nxt = Level(None, blk.coarse, 2 * spec["nv"])
-        nxt.stencil = Ac
-        nxt.apply = (lambda A: (lambda y: dirac.stencil_apply(A, y)))(Ac)
-        hier.append(nxt)
-    last = hier[-1]
-    last.lu = scipy.linalg.lu_factor(dense_from_stencil(last.stencil))
+    cycle = dict(nu_pre=nu_pre, nu_post=nu_post, omega=omega, coarse_cycles=coarse_cycles,
+                 coarse_solver=coarse_solver)
+    build_levels(hier, 0, levels, starts, omega, cycle)
     return hier
 
 
-def candidates_from_prolongator(P, blk):
-    """Candidates whose block QR reproduces P: vector k is column k of P on the
-    chirality-0 components and column Nv + k on the chirality-1 components."""
-    nv = P.shape[-1] // 2
-    h = blk.half
-    return [np.concatenate([P[..., :h, k], P[..., h:, nv + k]], axis=-1) for k in range(nv)]
+def coarsen(hier, l, cands, spec):
+    """P of level l from the candidates (Eq. 2.3) and A_{l+1} = P^+ A_l P (Sec. 2);
+    replaces every level below l."""
+    cur = hier[l]
+    del hier[l + 1:]
+    blk = Blocking(cur.lattice, spec["block"], cur.ncomp)
+    cur.blk = blk
+    cur.P = block_orthonormalize(cands, blk)
+    Ac = coarse_stencil(cur.stencil, cur.P, blk)
+    nxt = Level(None, blk.coarse, 2 * len(cands))
+    nxt.stencil = Ac
+    nxt.apply = (lambda A: (lambda y: dirac.stencil_apply(A, y)))(Ac)
+    hier.append(nxt)
 
 
-def rebuild_below(hier, l):
-    """Galerkin operators of levels l+1 .. from the current P's (Sec. 2), coarsest LU last."""
-    for j in range(l, len(hier) - 1):
-        Ac = coarse_stencil(hier[j].stencil, hier[j].P, hier[j].blk)
-        hier[j + 1].stencil = Ac
-        hier[j + 1].apply = (lambda A: (lambda y: dirac.stencil_apply(A, y)))(Ac)
-    last = hier[-1]
-    last.lu = scipy.linalg.lu_factor(dense_from_stencil(last.stencil))
+def adaptive_prototype(hier, l, x, iters, cycle, restart=8):
+    """The current solver of level l -- flexible GCR preconditioned by the level's
+    multigrid cycle (Sec. 5) -- applied to A x = 0 from x for ``iters``
+    iterations, restarted every ``restart`` (Sec. 2: its iterate is the next
+    prototype of the algebraically smooth error)."""
+    A = hier[l].apply
+
+    def precond(v):
+        return vcycle(hier, l, v, **cycle)
+
+    done = 0
+    while done < iters:
+        k = min(restart, iters - done)
+        x = x + gcr_fixed(A, -A(x), precond, k)
+        done += k
+    return x
 
 
-def refine_setup(hier, passes, cycles, nu_pre=2, nu_post=2, omega=0.8, coarse_cycles=(4,),
-                 coarse_solver="gcr"):
-    """Adaptive passes over a relaxation-built hierarchy (Sec. 2: the current
-    multigrid solver applied to A x = 0 yields the next candidates).
+def build_levels(hier, l, levels, starts, omega, cycle):
+    """Levels l+1 .. coarsest below the operator of level l (Sec. 2).
 
-    In each pass, level by level from the finest: every candidate x of the
-    level (read back from P) takes ``cycles`` steps x <- x + M(-A x), M the
-    current V-cycle of that level; the results, unit-normalised, give P by
-    block QR (Eq. 2.3) and the operators below are rebuilt before the next
-    level is refined.
+    V^k of level l starts with the first Nv - adapt_nv candidates from
+    relaxation (``relax_null_vectors``).  It is then augmented in
+    ``adapt_steps`` batches -- batch s holds adapt_nv // steps vectors, one
+    more for s < adapt_nv % steps -- each vector the result of ``adapt_cycles``
+    iterations of the current solver on A x = 0 from its random start
+    (``adaptive_prototype``), unit-normalised (Sec. 2: the current solver
+    applied to A x = 0 gives the next prototype).  After every change of V^k the prolongator is
+    rebuilt and the levels below are built again by this same procedure.
+    ``starts[l]`` are always shaped for the final hierarchy; a level built
+    while the level above has k < Nv candidates takes, of each start, the
+    first k components of each chirality half.
     """
-    for _ in range(passes):
-        for l in range(len(hier) - 1):
-            cur = hier[l]
-            cands = []
-            for x in candidates_from_prolongator(cur.P, cur.blk):
-                for _ in range(cycles):
-                    x = x + vcycle(hier, l, -cur.apply(x), nu_pre, nu_post, omega, coarse_cycles, coarse_solver)
-                cands.append(x / np.sqrt(norm2(x)))
-            cur.P = block_orthonormalize(cands, cur.blk)
-            rebuild_below(hier, l)
-    return hier
+    if l == len(levels):
+        hier[l].lu = scipy.linalg.lu_factor(dense_from_stencil(hier[l].stencil))
+        return
+    spec = levels[l]
+    cur = hier[l]
+    nv = spec["nv"]
+    steps = spec.get("adapt_steps", 0)
+    na = spec.get("adapt_nv", 0) if steps > 0 else 0
+    if not 0 <= na < nv:
+        raise ValueError("adapt_nv must be in [0, nv)")
+    steps = min(steps, na)
+    k0 = nv - na
+    st = starts[l]
+    if st[0].shape[-1] > cur.ncomp:
+        # while the level above is still short of its Nv candidates this level
+        # has fewer components: its starts are the full-size ones restricted to
+        # the components that exist (the first k of each chirality half)
+        k, kf = cur.ncomp // 2, st[0].shape[-1] // 2
+        comps = list(range(k)) + list(range(kf, kf + k))
+        st = [v[..., comps] for v in st]
+    cands = relax_null_vectors(cur.apply, st[:k0], spec["sweeps"], omega)
+    coarsen(hier, l, cands, spec)
+    build_levels(hier, l + 1, levels, starts, omega, cycle)
+    nxt = k0
+    for s in range(steps):
+        q = na // steps + (1 if s < na % steps else 0)
+        for x in st[nxt:nxt + q]:
+            x = adaptive_prototype(hier, l, x, spec.get("adapt_cycles", 16), cycle)
+            cands.append(x / np.sqrt(norm2(x)))
+        nxt += q
+        coarsen(hier, l, cands, spec)
+        build_levels(hier, l + 1, levels, starts, omega, cycle)
 
 
 def coarsest_solve(level, r):

@@ -238,20 +238,6 @@ def test_gcr_fixed_is_minimal_residual_krylov():
         assert abs(np.linalg.norm(A @ xk - b) - np.linalg.norm(A @ (K @ c) - b)) < 1e-9 * np.linalg.norm(b)
 
 
-def test_candidates_read_back_from_P_reproduce_P():
-    """Block QR of the candidates read back from P returns P itself (Eq. 2.3: the
-    columns of each aggregate are already orthonormal, so Gram-Schmidt keeps them)."""
-    dims = (4, 4, 4, 4)
-    U = inputs.random_gauge(dims, 5)
-    lat = _lat(dims)
-    starts = [inputs.null_vector_starts(lat, 12, 6, 9)]
-    h = mg.mg_setup(U, 0.1, [dict(block=(2, 2, 2, 2), nv=6, sweeps=4)], starts)
-    cands = mg.candidates_from_prolongator(h[0].P, h[0].blk)
-    assert len(cands) == 6 and cands[0].shape == lat + (12,)
-    P2 = mg.block_orthonormalize(cands, h[0].blk)
-    assert np.max(np.abs(P2 - h[0].P)) < 1e-12
-
-
 def test_cycle_annihilates_the_coarse_space_without_smoothing():
     """With no smoothing and an exact coarse solve, M A x = x for x = P y: the
     correction P A_c^-1 P^+ A P y = P y and alpha = 1 (Eq. 3.5), so the
@@ -268,34 +254,68 @@ def test_cycle_annihilates_the_coarse_space_without_smoothing():
     assert np.linalg.norm(x1) < 1e-10 * np.linalg.norm(x)
 
 
-def test_refine_setup_keeps_the_invariants_and_helps():
-    """After an adaptive pass on a 3-level hierarchy: P^+ P = 1 and the chirality
-    zeros on every level (Eq. 2.3), both coarse stencils equal the brute-force
-    Galerkin products of the new P's, and MG-GCR needs no more iterations than
-    before the pass."""
+def test_adaptive_setup_keeps_the_invariants_and_helps():
+    """Adaptive steps on both levels of a 3-level hierarchy (Sec. 2: V^k grown by
+    prototypes from the current cycle on A x = 0): P^+ P = 1 and the chirality
+    zeros on every level (Eq. 2.3); both coarse stencils equal the brute-force
+    Galerkin products of the final P's; the first Nv - adapt_nv columns of each
+    chirality are those of the relaxation-only P with that many vectors (the
+    adaptive vectors are appended, Gram-Schmidt runs in order); MG-GCR needs no
+    more iterations than with Nv relaxation vectors."""
     dims = (4, 4, 4, 4)
     U = inputs.heatbath_gauge(dims, 6.0, 30, 5)
     lat = _lat(dims)
     starts = [inputs.null_vector_starts(lat, 12, 6, 11),
               inputs.null_vector_starts((2, 2, 2, 2), 12, 4, 12)]
     spec = [dict(block=(2, 2, 2, 2), nv=6, sweeps=3), dict(block=(2, 2, 1, 1), nv=4, sweeps=3)]
-    h = mg.mg_setup(U, -0.6, spec, starts)
+    aspec = [dict(sp, adapt_nv=3, adapt_steps=2, adapt_cycles=4) for sp in spec]
     b = inputs.gaussian_spinor(dims, 1).reshape(lat + (12,))
-    _, before = mg.mg_solve(h, b, tol=1e-10)
-    P_old = h[0].P.copy()
-    mg.refine_setup(h, 1, 2)
-    assert np.max(np.abs(h[0].P - P_old)) > 1e-3  # the pass changed the prolongator
+    h0 = mg.mg_setup(U, -0.6, spec, starts)
+    _, before = mg.mg_solve(h0, b, tol=1e-10)
+    h = mg.mg_setup(U, -0.6, aspec, starts)
     for l in range(2):
         P, blk = h[l].P, h[l].blk
         nv = P.shape[-1] // 2
-        G = np.einsum("...ci,...cj->...ij", np.conj(P), P)
-        Gb = blk.block_sum(G)
-        assert np.max(np.abs(Gb - np.eye(2 * nv))) < 1e-12
+        G = blk.block_sum(np.einsum("...ci,...cj->...ij", np.conj(P), P))
+        assert np.max(np.abs(G - np.eye(2 * nv))) < 1e-12
         assert np.all(P[..., :blk.half, nv:] == 0) and np.all(P[..., blk.half:, :nv] == 0)
         D = dirac.dense_matrix(h[l].apply, h[l].lattice + (h[l].ncomp,))
         Pm = dirac.dense_matrix(lambda y: mg.prolong(P, blk, y), h[l + 1].lattice + (2 * nv,))
         Dc = dirac.dense_matrix(h[l + 1].apply, h[l + 1].lattice + (2 * nv,))
         assert np.max(np.abs(Dc - Pm.conj().T @ D @ Pm)) < 1e-11 * np.max(np.abs(D))
+    # the relaxation part of V^k on level 0 is the prefix of the final P
+    hr = mg.mg_setup(U, -0.6, [dict(spec[0], nv=3)], [starts[0][:3]])
+    assert np.max(np.abs(h[0].P[..., [0, 1, 2, 6, 7, 8]] - hr[0].P)) < 1e-12
+    assert np.max(np.abs(h[0].P - h0[0].P)) > 1e-2  # the adaptive vectors changed the rest
     x, after = mg.mg_solve(h, b, tol=1e-10)
     assert after["true_rel_residual"] <= 1e-10
-    assert after["iters"] <= before["iters"]
+    assert after["iters"] <= before["iters"], (after["iters"], before["iters"])
+
+
+def test_adaptive_prototype_is_a_minimal_residual_solve_of_the_null_equation():
+    """The prototype of an adaptive step is the current solver (flexible GCR with the
+    V-cycle, Sec. 5) applied to A x = 0 (Sec. 2): ||A x|| never grows with the
+    iteration count, across the restart at 8 too (a sign error in the right-hand
+    side -A x doubles x instead); and with an exact preconditioner (P square
+    unitary, so the V-cycle is A^-1) one iteration returns x = 0."""
+    dims = (4, 4, 4, 4)
+    U = inputs.heatbath_gauge(dims, 6.0, 30, 5)
+    lat = _lat(dims)
+    h = mg.mg_setup(U, -0.6, [dict(block=(2, 2, 2, 2), nv=6, sweeps=3)],
+                    [inputs.null_vector_starts(lat, 12, 6, 11)])
+    x0 = inputs.null_vector_starts(lat, 12, 1, 40)[0]
+    cyc = dict(nu_pre=2, nu_post=2, omega=0.8, coarse_cycles=(4,), coarse_solver="gcr")
+    res = [np.sqrt(mg.norm2(h[0].apply(x0)))]
+    for k in range(1, 11):
+        res.append(np.sqrt(mg.norm2(h[0].apply(mg.adaptive_prototype(h, 0, x0, k, cyc)))))
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(res, res[1:])), res
+    assert res[-1] < 0.5 * res[0]
+    # exact preconditioner: 2^4 lattice, one 2^4 block, Nv = 6|b| = 96
+    d2 = (2, 2, 2, 2)
+    U2 = inputs.random_gauge(d2, 1)
+    l2 = _lat(d2)
+    h2 = mg.mg_setup(U2, 0.1, [dict(block=(2, 2, 2, 2), nv=96, sweeps=0)],
+                     [inputs.null_vector_starts(l2, 12, 96, 3)])
+    y0 = inputs.null_vector_starts(l2, 12, 1, 41)[0]
+    y1 = mg.adaptive_prototype(h2, 0, y0, 1, dict(cyc, nu_pre=0, nu_post=0))
+    assert np.sqrt(mg.norm2(y1)) < 1e-10 * np.sqrt(mg.norm2(y0))
