@@ -90,6 +90,14 @@ typedef struct {
   int coarse_solver;                  /* the coarse_cycles applications of the next level's V-cycle:
                                          0 = as steps of flexible GCR preconditioned by it (default),
                                          1 = as stationary sweeps e += V(r - A e) */
+  int adapt_steps;                    /* adaptive steps of Sec. 2 per level: the first nv - adapt_nv[l]
+                                         candidates come from relaxation; each step appends a batch of the
+                                         rest, made by the current solver (flexible GCR preconditioned by the
+                                         level's multigrid cycle, restarted every 8 iterations) applied to
+                                         A x = 0 from random starts, and rebuilds P and the levels below
+                                         (default 0: relaxation only) */
+  int adapt_cycles;                   /* solver iterations per adaptive candidate (default 16) */
+  int adapt_nv[MG_MAX_LEVELS - 1];    /* candidates of level l made by the adaptive steps, < nv[l] */
 } mg_params;
 
 /* Per right-hand side solve statistics. */
@@ -154,7 +162,7 @@ int mg_destroy(mg_handle* h);
  *           on_device != 0, else host memory.  x is the initial guess on
  *           entry (zero it for none) and the solution on return.
  *   stats : NULL or an array of nrhs mg_stats.
- * Every returned x is judged by its true FP64 residual, recomputed at exit.
+ * Every returned x is checked against its true FP64 residual, recomputed at exit.
  * Errors: MG_EINVAL, MG_ENOCONV (x and stats still filled), MG_EBREAKDOWN,
  * MG_ENAN, MG_ECUDA. */
 int mg_solve(mg_handle* h, const double* b, double* x, int nrhs, int on_device, double tol,

@@ -70,7 +70,7 @@ inline size_t slot_inner(int l) { return slot_beta() + (size_t)2 * kMaxBasis * k
 inline size_t slot_total() { return slot_inner(MG_MAX_LEVELS); }
 const int kInnerBasis = 8;
 
-enum { WV_E, WV_RES, WV_P, WV_XC, WV_AXC, WV_RC, WV_EC, WV_T, WV_DT, WV_IN, WV_A, WV_B, WV_KW, WV_KZ, WV_COUNT };
+enum { WV_E, WV_RES, WV_P, WV_XC, WV_AXC, WV_RC, WV_EC, WV_T, WV_DT, WV_IN, WV_A, WV_B, WV_KW, WV_KZ, WV_PR, WV_PE, WV_COUNT };
 
 int prec_of(const mg_handle* h, int l) {
   if (!h->p.mixed) return MG_F64;
@@ -315,21 +315,35 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs);
 // e = `iters` steps of flexible GCR on A_l e = b from e = 0, preconditioned by
 // the V-cycle of level l (classical Gram-Schmidt applied twice; every scalar
 // stays on the device, so the whole solve is one graph-capturable sequence).
+// The Krylov vectors are FP64 or FP32 (`prec`); where the level's cycle runs
+// in another (16-bit) storage, each residual goes to it scaled to unit norm
+// per right-hand side and the cycle's output comes back unscaled.
 int coarse_gcr(mg_handle* h, int l, int prec, const void* b, void* e, int iters, int nrhs) {
   Level& a = *h->lev[l];
   const size_t n = a.n();
   const size_t vb = n * nrhs * bytes_of(prec);
+  const int pl = prec_of(h, l);
   void* r = work(h, l, prec, WV_T, nrhs);
   char* W = (char*)work(h, l, prec, WV_KW, nrhs, kInnerBasis);
   char* Z = (char*)work(h, l, prec, WV_KZ, nrhs, kInnerBasis);
-  if (!r || !W || !Z || iters > kInnerBasis) return MG_ENOMEM;
+  void* rl = pl == prec ? nullptr : work(h, l, pl, WV_PR, nrhs);
+  void* el = pl == prec ? nullptr : work(h, l, pl, WV_PE, nrhs);
+  if (!r || !W || !Z || iters > kInnerBasis || (pl != prec && (!rl || !el))) return MG_ENOMEM;
   const size_t swr = slot_inner(l), srn = swr + 4 * kMaxRhs, sbeta = srn + 4 * kMaxRhs;
   CK(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, h->st));
   CK(cudaMemsetAsync(e, 0, vb, h->st));
+  if (pl != prec) LK(launch_dot(prec, n, nrhs, r, r, h->red.at(srn, 4), h->st));  // ||r||^2 at srn + 2
+  const double sig = sqrt((double)n) / 8.0;
   for (int k = 0; k < iters; ++k) {
     void* zk = Z + (size_t)k * vb;
     void* wk = W + (size_t)k * vb;
-    RET(vcycle(h, l, r, zk, nrhs));
+    if (pl == prec) {
+      RET(vcycle(h, l, r, zk, nrhs));
+    } else {
+      LK(launch_convert(prec, pl, n, nrhs, r, rl, sig, h->red.slot(srn + 2), 4, -0.5, 0, h->st));
+      RET(vcycle(h, l, rl, el, nrhs));
+      LK(launch_convert(pl, prec, n, nrhs, el, zk, 1.0 / sig, h->red.slot(srn + 2), 4, 0.5, 0, h->st));
+    }
     RET(op_apply(h, l, prec, zk, wk, nullptr, 1.0, 0.0, nullptr, 0, nrhs));
     Prof pf(h, MG_K_VECTOR, prec);
     if (k == 0) {
@@ -494,6 +508,7 @@ int mg_default_params(mg_params* p) {
   p->reliable_delta = 1e-4;
   p->seed = 0;
   p->use_graphs = 1;
+  p->adapt_cycles = 16;
   return MG_OK;
 }
 
@@ -542,6 +557,255 @@ static int build_coarsest(mg_handle* h) {
   return MG_OK;
 }
 
+// ------------------------------------------------------------------ setup pieces
+// Geometry of the aggregation of level l into level l+1.
+static int init_level(mg_handle* h, int l) {
+  const mg_params& p = h->p;
+  Level& a = *h->lev[l];
+  a.nv = p.nv[l];
+  a.sweeps = p.setup_sweeps[l];
+  a.cycles = p.coarse_cycles[l] < 1 ? 1 : p.coarse_cycles[l];
+  a.nhalf = a.ncomp / 2;
+  a.bsites = 1;
+  a.Vc = 1;
+  for (int m = 0; m < 4; ++m) {
+    a.blk[m] = p.block[l][m];
+    if (a.blk[m] < 1 || a.L[m] % a.blk[m]) {
+      set_error("level " + std::to_string(l) + ": extent not divisible by the block size");
+      return MG_EINVAL;
+    }
+    a.Lc[m] = a.L[m] / a.blk[m];
+    a.bsites *= a.blk[m];
+    a.Vc *= a.Lc[m];
+  }
+  if (a.nv < 1 || a.nv > a.nhalf * a.bsites) {
+    set_error("level " + std::to_string(l) + ": nv must be in [1, ncomp/2 * block sites]");
+    return MG_EINVAL;
+  }
+  return ensure_reducer(h, a.nv);
+}
+
+// The Nv random start vectors of level l, FP64 [nv][ncomp][V]: the caller's
+// (host, external layout) or the counter-based Gaussian generator's.  Both
+// are defined on the final hierarchy, where level l >= 1 has 2 nv[l-1]
+// components; while the level above still has k < nv[l-1] candidates, the
+// starts are restricted to the first k components of each chirality half.
+static int make_starts(mg_handle* h, int l, const double* start, DevBuf& S) {
+  cudaStream_t st = h->st;
+  Level& a = *h->lev[l];
+  const int nfull = l == 0 ? 12 : 2 * h->p.nv[l - 1];
+  const size_t vbf = (size_t)nfull * a.V * 16, vb = a.n() * 16;
+  DevBuf full;
+  if (!full.ensure(vbf * a.nv) || !S.ensure(vb * a.nv)) return MG_ENOMEM;
+  if (start) {
+    DevBuf ext;
+    if (!ext.ensure(vbf * a.nv)) return MG_ENOMEM;
+    CK(cudaMemcpyAsync(ext.p, start, vbf * a.nv, cudaMemcpyHostToDevice, st));
+    LK(launch_ext_to_int(MG_F64, nfull, a.V, a.nv, ext.p, full.p, st));
+  } else {
+    Prof pf(h, MG_K_SETUP, MG_F64);
+    LK(launch_gaussian_starts(h->p.seed + (uint64_t)l, a.nv, nfull, a.V, full.p, st));
+  }
+  if (nfull == a.ncomp) {
+    CK(cudaMemcpyAsync(S.p, full.p, vb * a.nv, cudaMemcpyDeviceToDevice, st));
+  } else {
+    const size_t half = (size_t)(a.ncomp / 2) * a.V * 16, fhalf = (size_t)(nfull / 2) * a.V * 16;
+    CK(cudaMemcpy2DAsync(S.p, vb, full.p, vbf, half, a.nv, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpy2DAsync((char*)S.p + half, vb, (char*)full.p + fhalf, vbf, half, a.nv, cudaMemcpyDeviceToDevice,
+                         st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+// Sec. 2 adaptive steps 1-2: `sweeps` MR steps on A x = 0 from the k FP64
+// vectors at x64 (all of them right-hand sides of one launch), then unit
+// normalisation, in place.
+static int relax_candidates(mg_handle* h, int l, void* x64, int k) {
+  const mg_params& p = h->p;
+  cudaStream_t st = h->st;
+  Level& a = *h->lev[l];
+  const int rp = p.mixed ? MG_F32 : MG_F64;  // the mixed form relaxes in FP32
+  DevBuf candr, rr, pp;
+  void* x = x64;
+  const size_t vr = a.n() * bytes_of(rp);
+  if (rp != MG_F64) {
+    if (!candr.ensure(vr * k)) return MG_ENOMEM;
+    LK(launch_convert(MG_F64, rp, a.n(), k, x64, candr.p, 1.0, nullptr, 0, 0.0, 0, st));
+    x = candr.p;
+  }
+  if (!rr.ensure(vr * k) || !pp.ensure(vr * k)) return MG_ENOMEM;
+  RET(ensure_reducer(h, k));
+  const size_t sl = slot_level(l);
+  if (a.sweeps > 0) {
+    RET(op_apply(h, l, rp, x, rr.p, nullptr, -1.0, 0.0, nullptr, 0, k));
+    for (int s = 0; s < a.sweeps; ++s) {
+      // FP32 relaxation: the recursively updated residual drifts from -A x
+      // once it has shrunk by a few orders, so it is recomputed every
+      // kTrueResidualEvery steps (FP64 follows the plain recursion).
+      if (rp != MG_F64 && s > 0 && s % kTrueResidualEvery == 0)
+        RET(op_apply(h, l, rp, x, rr.p, nullptr, -1.0, 0.0, nullptr, 0, k));
+      RET(op_apply(h, l, rp, rr.p, pp.p, nullptr, 1.0, 0.0, rr.p, sl, k));
+      RET(mr_update(h, l, rp, x, x, rr.p, rr.p, rr.p, pp.p, sl, p.omega, k));
+    }
+  }
+  LK(launch_dot(rp, a.n(), k, x, x, h->red.at(slot_misc(), 4), st));
+  LK(launch_convert(rp, MG_F64, a.n(), k, x, x64, 1.0, h->red.slot(slot_misc() + 2), 4, -0.5, 0, st));
+  CK(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+// A_{l+1} = P_l^+ A_l P_l (Sec. 2) from the current P_l and A_l: FP64
+// arithmetic for the plain hierarchy, FP32 for the mixed one, stored in FP64;
+// then the precision copies of A_{l+1} the cycle and the relaxation use.
+static int galerkin(mg_handle* h, int l) {
+  const mg_params& p = h->p;
+  cudaStream_t st = h->st;
+  const int Lv = p.n_levels;
+  Level& a = *h->lev[l];
+  Level& c = *h->lev[l + 1];
+  const int nc = c.ncomp;
+  const Agg g = agg_of(a);
+  if (!c.cop[MG_F64].ensure((size_t)9 * nc * nc * c.V * 16)) return MG_ENOMEM;
+  const int gp = p.mixed ? MG_F32 : MG_F64;
+  const size_t vbg = a.n() * bytes_of(gp);
+  const int chunk = (int)std::max<size_t>(1, std::min<size_t>(nc, ((size_t)1 << 30) / vbg));
+  DevBuf cols;
+  if (!cols.ensure(vbg * chunk)) return MG_ENOMEM;
+  for (int j0 = 0; j0 < nc; j0 += chunk) {
+    const int ncols = std::min(chunk, nc - j0);
+    {
+      Prof pf(h, MG_K_SETUP, gp);
+      LK(launch_p_column(gp, g, a.P[gp].p, j0, ncols, cols.p, st));
+    }
+    Prof pf(h, MG_K_GALERKIN, gp);
+    if (l == 0)
+      LK(launch_galerkin_wilson(gp, g, a.links[gp].p, h->mass, cols.p, a.P[gp].p, j0, ncols,
+                                c.cop[MG_F64].as<double2>(), st));
+    else
+      LK(launch_galerkin_stencil(gp, g, a.cop[gp].p, cols.p, a.P[gp].p, j0, ncols, c.cop[MG_F64].as<double2>(),
+                                 st));
+  }
+  if (p.mixed && l + 2 < Lv) {
+    const size_t ncop = (size_t)9 * nc * nc * c.V;
+    const int want[2] = {MG_F32, p.coarse_prec};
+    for (int q : want) {
+      if (!c.cop[q].ensure(ncop * bytes_of(q))) return MG_ENOMEM;
+      LK(launch_convert(MG_F64, q, ncop, 1, c.cop[MG_F64].p, c.cop[q].p, 1.0, nullptr, 0, 0.0, 0, st));
+    }
+    if (p.coarse_mma) {
+      if (!c.cop_mma.ensure(mma_pack_bytes(nc, c.V))) return MG_ENOMEM;
+      LK(launch_mma_pack(c.cop[MG_F64].as<double2>(), nc, c.V, c.cop_mma.p, st));
+    }
+  }
+  return MG_OK;
+}
+
+// P_l from FP64 candidates (Sec. 2 step 3, Eq. 2.3: blockwise Gram-Schmidt,
+// chirality kept), its precision copies, then A_{l+1} (level l+1 is created
+// on first use).
+static int build_level(mg_handle* h, int l, DevBuf& cand) {
+  const mg_params& p = h->p;
+  cudaStream_t st = h->st;
+  Level& a = *h->lev[l];
+  const Agg g = agg_of(a);
+  const size_t np = (size_t)a.Vc * 2 * a.nv * a.nhalf * a.bsites;
+  DevBuf errflag;
+  if (!errflag.ensure(sizeof(int)) || !a.P[MG_F64].ensure(np * 16)) return MG_ENOMEM;
+  CK(cudaMemsetAsync(errflag.p, 0, sizeof(int), st));
+  {
+    Prof pf(h, MG_K_SETUP, MG_F64);
+    LK(launch_block_gs(g, cand.as<double2>(), a.P[MG_F64].as<double2>(), errflag.as<int>(), st));
+  }
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (herr == 2) {
+    set_error("block Gram-Schmidt lost rank on level " + std::to_string(l));
+    return MG_ERANK;
+  }
+  const int copies[2] = {p.mixed ? MG_F32 : MG_F64, prec_of(h, l)};
+  for (int pr : copies) {
+    if (pr == MG_F64) continue;
+    if (!a.P[pr].ensure(np * bytes_of(pr))) return MG_ENOMEM;
+    LK(launch_convert(MG_F64, pr, np, 1, a.P[MG_F64].p, a.P[pr].p, 1.0, nullptr, 0, 0.0, 0, st));
+  }
+  if ((int)h->lev.size() == l + 1) h->lev.emplace_back(new Level());
+  Level& c = *h->lev[l + 1];  // its size follows the current number of candidates
+  for (int m = 0; m < 4; ++m) c.L[m] = a.Lc[m];
+  c.V = a.Vc;
+  c.ncomp = 2 * a.nv;
+  return galerkin(h, l);
+}
+
+// One adaptive step of Sec. 2 for the q FP64 vectors at x64 (random starts):
+// `iters` iterations of the current solver -- flexible GCR preconditioned by
+// the multigrid cycle of level l, restarted every kInnerBasis iterations --
+// on A x = 0 from x, all q as right-hand sides of one batched solve, then unit
+// normalisation, in place.  x stays FP64; each restart solves A e = -A x with
+// FP64 or FP32 Krylov vectors (the mixed form) from the residual scaled to
+// unit norm per right-hand side, and adds e to x.
+static int adapt_candidates(mg_handle* h, int l, void* x64, int q, int iters) {
+  cudaStream_t st = h->st;
+  Level& a = *h->lev[l];
+  const size_t n = a.n();
+  const int pg = prec_of(h, l) == MG_F64 ? MG_F64 : MG_F32;
+  DevBuf R, Rg, Eg;
+  if (!R.ensure(n * 16 * q) || !Rg.ensure(n * bytes_of(pg) * q) || !Eg.ensure(n * bytes_of(pg) * q))
+    return MG_ENOMEM;
+  RET(ensure_reducer(h, q));
+  const double sig = sqrt((double)n) / 8.0;
+  for (int done = 0; done < iters; done += kInnerBasis) {
+    const int k = std::min(kInnerBasis, iters - done);
+    RET(op_apply(h, l, MG_F64, x64, R.p, nullptr, -1.0, 0.0, nullptr, 0, q));
+    LK(launch_dot(MG_F64, n, q, R.p, R.p, h->red.at(slot_misc(), 4), st));
+    LK(launch_convert(MG_F64, pg, n, q, R.p, Rg.p, sig, h->red.slot(slot_misc() + 2), 4, -0.5, 0, st));
+    RET(coarse_gcr(h, l, pg, Rg.p, Eg.p, k, q));
+    LK(launch_convert(pg, MG_F64, n, q, Eg.p, x64, 1.0 / sig, h->red.slot(slot_misc() + 2), 4, 0.5, 1, st));
+  }
+  LK(launch_dot(MG_F64, n, q, x64, x64, h->red.at(slot_misc(), 4), st));
+  LK(launch_convert(MG_F64, MG_F64, n, q, x64, x64, 1.0, h->red.slot(slot_misc() + 2), 4, -0.5, 0, st));
+  CK(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+// Levels l .. coarsest from the operator of level l (Sec. 2): V^k of level l
+// starts as the first Nv - adapt_nv[l] relaxed candidates; each of the
+// adapt_steps adaptive steps appends a batch of candidates made by the
+// current solver (whose cycle needs the levels below, rebuilt by the same
+// procedure after every change of P_l).  Batch s holds
+// adapt_nv / steps candidates, one more for s < adapt_nv % steps.
+static int build_from(mg_handle* h, int l, const double* const* starts) {
+  const mg_params& p = h->p;
+  if (l + 1 >= p.n_levels) return build_coarsest(h);
+  RET(init_level(h, l));
+  Level& a = *h->lev[l];
+  const int nv = a.nv;
+  int na = p.adapt_steps > 0 ? p.adapt_nv[l] : 0;
+  if (na < 0 || na >= nv) {
+    set_error("level " + std::to_string(l) + ": adapt_nv must be in [0, nv)");
+    return MG_EINVAL;
+  }
+  const int steps = std::min(p.adapt_steps, na);
+  const int k0 = nv - na;
+  const size_t vb = a.n() * 16;
+  DevBuf cand;
+  RET(make_starts(h, l, starts ? starts[l] : nullptr, cand));
+  RET(relax_candidates(h, l, cand.p, k0));
+  a.nv = k0;
+  RET(build_level(h, l, cand));
+  RET(build_from(h, l + 1, starts));
+  for (int s = 0; s < steps; ++s) {
+    const int q = na / steps + (s < na % steps ? 1 : 0);
+    Level& al = *h->lev[l];
+    RET(adapt_candidates(h, l, (char*)cand.p + vb * al.nv, q, p.adapt_cycles < 1 ? 1 : p.adapt_cycles));
+    al.nv += q;
+    RET(build_level(h, l, cand));
+    RET(build_from(h, l + 1, starts));
+  }
+  return MG_OK;
+}
+
 static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, const double* const* starts) {
   const mg_params& p = h->p;
   cudaStream_t st = h->st;
@@ -574,146 +838,9 @@ static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, co
     CK(cudaStreamSynchronize(st));
   }
   RET(ensure_reducer(h, 1));
-  DevBuf errflag;
-  if (!errflag.ensure(sizeof(int))) return MG_ENOMEM;
-  CK(cudaMemsetAsync(errflag.p, 0, sizeof(int), st));
-  // ---- coarser levels
-  for (int l = 0; l + 1 < Lv; ++l) {
-    Level& a = *h->lev[l];
-    a.nv = p.nv[l];
-    a.sweeps = p.setup_sweeps[l];
-    a.cycles = p.coarse_cycles[l] < 1 ? 1 : p.coarse_cycles[l];
-    a.nhalf = a.ncomp / 2;
-    a.bsites = 1;
-    a.Vc = 1;
-    for (int m = 0; m < 4; ++m) {
-      a.blk[m] = p.block[l][m];
-      if (a.blk[m] < 1 || a.L[m] % a.blk[m]) {
-        set_error("level " + std::to_string(l) + ": extent not divisible by the block size");
-        return MG_EINVAL;
-      }
-      a.Lc[m] = a.L[m] / a.blk[m];
-      a.bsites *= a.blk[m];
-      a.Vc *= a.Lc[m];
-    }
-    if (a.nv < 1 || a.nv > a.nhalf * a.bsites) {
-      set_error("level " + std::to_string(l) + ": nv must be in [1, ncomp/2 * block sites]");
-      return MG_EINVAL;
-    }
-    RET(ensure_reducer(h, a.nv));
-    // candidates, FP64 internal [nv][ncomp][V]; relaxed in FP32 in the mixed form
-    const int rp = p.mixed ? MG_F32 : MG_F64;
-    DevBuf cand, candr, rr, pp;
-    const size_t vb = a.n() * 16;
-    if (!cand.ensure(vb * a.nv)) return MG_ENOMEM;
-    if (starts && starts[l]) {
-      DevBuf ext;
-      if (!ext.ensure(vb * a.nv)) return MG_ENOMEM;
-      CK(cudaMemcpyAsync(ext.p, starts[l], vb * a.nv, cudaMemcpyHostToDevice, st));
-      LK(launch_ext_to_int(MG_F64, a.ncomp, a.V, a.nv, ext.p, cand.p, st));
-      CK(cudaStreamSynchronize(st));
-    } else {
-      Prof pf(h, MG_K_SETUP, MG_F64);
-      LK(launch_gaussian_starts(p.seed + (uint64_t)l, a.nv, a.ncomp, a.V, cand.p, st));
-    }
-    void* x = cand.p;
-    const size_t vr = a.n() * bytes_of(rp);
-    if (rp != MG_F64) {
-      if (!candr.ensure(vr * a.nv)) return MG_ENOMEM;
-      LK(launch_convert(MG_F64, rp, a.n(), a.nv, cand.p, candr.p, 1.0, nullptr, 0, 0.0, 0, st));
-      x = candr.p;
-    }
-    if (!rr.ensure(vr * a.nv) || !pp.ensure(vr * a.nv)) return MG_ENOMEM;
-    // relax A x = 0 (Sec. 2 steps 1-2): r = -A x, then MR steps, all candidates at once
-    const size_t sl = slot_level(l);
-    if (a.sweeps > 0) {
-      RET(op_apply(h, l, rp, x, rr.p, nullptr, -1.0, 0.0, nullptr, 0, a.nv));
-      for (int s = 0; s < a.sweeps; ++s) {
-        // FP32 relaxation: the recursively updated residual drifts from -A x
-        // once it has shrunk by a few orders, so it is recomputed every
-        // kTrueResidualEvery steps (FP64 follows the plain recursion).
-        if (rp != MG_F64 && s > 0 && s % kTrueResidualEvery == 0)
-          RET(op_apply(h, l, rp, x, rr.p, nullptr, -1.0, 0.0, nullptr, 0, a.nv));
-        RET(op_apply(h, l, rp, rr.p, pp.p, nullptr, 1.0, 0.0, rr.p, sl, a.nv));
-        RET(mr_update(h, l, rp, x, x, rr.p, rr.p, rr.p, pp.p, sl, p.omega, a.nv));
-      }
-    }
-    // unit-normalise every candidate
-    LK(launch_dot(rp, a.n(), a.nv, x, x, h->red.at(slot_misc(), 4), st));
-    LK(launch_convert(rp, MG_F64, a.n(), a.nv, x, cand.p, 1.0, h->red.slot(slot_misc() + 2), 4, -0.5, 0, st));
-    CK(cudaStreamSynchronize(st));
-    candr.release();
-    pp.release();
-    rr.release();
-    // blockwise Gram-Schmidt into P (Eq. 2.3), FP64
-    const Agg g = agg_of(a);
-    if (!a.P[MG_F64].ensure((size_t)a.Vc * 2 * a.nv * a.nhalf * a.bsites * 16)) return MG_ENOMEM;
-    {
-      Prof pf(h, MG_K_SETUP, MG_F64);
-      LK(launch_block_gs(g, cand.as<double2>(), a.P[MG_F64].as<double2>(), errflag.as<int>(), st));
-    }
-    // Galerkin coarse operator (FP64 arithmetic for the plain hierarchy, FP32
-    // for the mixed one; stored in FP64), columns in batches of at most 1 GB
-    h->lev.emplace_back(new Level());
-    Level& c = *h->lev[l + 1];
-    for (int m = 0; m < 4; ++m) c.L[m] = a.Lc[m];
-    c.V = a.Vc;
-    c.ncomp = 2 * a.nv;
-    const int nc = c.ncomp;
-    if (!c.cop[MG_F64].ensure((size_t)9 * nc * nc * c.V * 16)) return MG_ENOMEM;
-    const int gp = p.mixed ? MG_F32 : MG_F64;
-    const size_t np = (size_t)a.Vc * 2 * a.nv * a.nhalf * a.bsites;
-    if (gp != MG_F64 && !a.P[gp].p) {
-      if (!a.P[gp].ensure(np * bytes_of(gp))) return MG_ENOMEM;
-      LK(launch_convert(MG_F64, gp, np, 1, a.P[MG_F64].p, a.P[gp].p, 1.0, nullptr, 0, 0.0, 0, st));
-    }
-    const size_t vbg = a.n() * bytes_of(gp);
-    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(nc, ((size_t)1 << 30) / vbg));
-    DevBuf cols;
-    if (!cols.ensure(vbg * chunk)) return MG_ENOMEM;
-    for (int j0 = 0; j0 < nc; j0 += chunk) {
-      const int ncols = std::min(chunk, nc - j0);
-      {
-        Prof pf(h, MG_K_SETUP, gp);
-        LK(launch_p_column(gp, g, a.P[gp].p, j0, ncols, cols.p, st));
-      }
-      Prof pf(h, MG_K_GALERKIN, gp);
-      if (l == 0)
-        LK(launch_galerkin_wilson(gp, g, a.links[gp].p, h->mass, cols.p, a.P[gp].p, j0, ncols,
-                                  c.cop[MG_F64].as<double2>(), st));
-      else
-        LK(launch_galerkin_stencil(gp, g, a.cop[gp].p, cols.p, a.P[gp].p, j0, ncols, c.cop[MG_F64].as<double2>(),
-                                   st));
-    }
-    int herr = 0;
-    CK(cudaMemcpyAsync(&herr, errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (herr == 2) {
-      set_error("block Gram-Schmidt lost rank on level " + std::to_string(l));
-      return MG_ERANK;
-    }
-    // precision copies: this level's P for the cycle; the next level's
-    // operator for its cycle and (mixed) its FP32 relaxation
-    const int pr = prec_of(h, l);
-    if (pr != MG_F64 && !a.P[pr].p) {
-      if (!a.P[pr].ensure(np * bytes_of(pr))) return MG_ENOMEM;
-      LK(launch_convert(MG_F64, pr, np, 1, a.P[MG_F64].p, a.P[pr].p, 1.0, nullptr, 0, 0.0, 0, st));
-    }
-    if (p.mixed && l + 2 < Lv) {
-      const size_t ncop = (size_t)9 * nc * nc * c.V;
-      const int want[2] = {MG_F32, p.coarse_prec};
-      for (int q : want) {
-        if (c.cop[q].p) continue;
-        if (!c.cop[q].ensure(ncop * bytes_of(q))) return MG_ENOMEM;
-        LK(launch_convert(MG_F64, q, ncop, 1, c.cop[MG_F64].p, c.cop[q].p, 1.0, nullptr, 0, 0.0, 0, st));
-      }
-      if (p.coarse_mma) {
-        if (!c.cop_mma.ensure(mma_pack_bytes(nc, c.V))) return MG_ENOMEM;
-        LK(launch_mma_pack(c.cop[MG_F64].as<double2>(), nc, c.V, c.cop_mma.p, st));
-      }
-    }
-  }
-  RET(build_coarsest(h));
+  // ---- coarser levels (Sec. 2): candidates, P, the Galerkin operators, the
+  // coarsest inverse
+  RET(build_from(h, 0, starts));
   CK(cudaStreamSynchronize(st));
   return MG_OK;
 }

@@ -45,6 +45,9 @@ class mg_params(ctypes.Structure):
         ("use_graphs", ctypes.c_int),
         ("coarse_mma", ctypes.c_int),
         ("coarse_solver", ctypes.c_int),
+        ("adapt_steps", ctypes.c_int),
+        ("adapt_cycles", ctypes.c_int),
+        ("adapt_nv", ctypes.c_int * 3),
     ]
 
 
@@ -161,7 +164,7 @@ def mg_default_params(**kw):
             for l, b in enumerate(v):
                 for m in range(4):
                     p.block[l][m] = int(b[m])
-        elif k in ("nv", "setup_sweeps", "coarse_cycles"):
+        elif k in ("nv", "setup_sweeps", "coarse_cycles", "adapt_nv"):
             arr = getattr(p, k)
             for l, x in enumerate(v):
                 arr[l] = int(x)

@@ -24,7 +24,7 @@ def _oracle_vectors(P, nv, nhalf):
     return np.moveaxis(v, -1, 0)
 
 
-def _setup_both(wm, dims, mass, levels, seed=0, device_starts=False, pseed=7):
+def _setup_both(wm, dims, mass, levels, seed=0, device_starts=False, pseed=7, adapt=(0, 3)):
     U = inputs.random_gauge(dims, seed)
     lat = lattice(dims)
     starts, shapes = [], [(lat, 12)]
@@ -35,10 +35,12 @@ def _setup_both(wm, dims, mass, levels, seed=0, device_starts=False, pseed=7):
         shapes.append((blk.coarse, 2 * spec["nv"]))
     p = wm.mg_default_params(n_levels=len(levels) + 1, block=[s["block"] for s in levels],
                              nv=[s["nv"] for s in levels], setup_sweeps=[s["sweeps"] for s in levels],
-                             seed=pseed)
+                             seed=pseed, adapt_steps=adapt[0], adapt_cycles=adapt[1],
+                             adapt_nv=[s.get("adapt_nv", 0) for s in levels])
     h = wm.mg_setup(U, dims, mass, p, starts=None if device_starts else
                     [np.stack(s).reshape(len(s), -1, s[0].shape[-1]) for s in starts])
-    hier = mg.mg_setup(U, mass, levels, starts)
+    levels_o = [dict(sp, adapt_steps=adapt[0], adapt_cycles=adapt[1]) for sp in levels]
+    hier = mg.mg_setup(U, mass, levels_o, starts, coarse_cycles=(p.coarse_cycles[0],))
     return h, hier, U
 
 
@@ -62,6 +64,51 @@ def test_prolongator_and_coarse_operator(dims, levels):
         Ac = wm.mg_get_coarse_op(h, l + 1)
         want_c = hier[l + 1].stencil.reshape(Ac.shape)
         assert np.max(np.abs(Ac - want_c)) < 1e-10 * np.max(np.abs(want_c)), l
+
+
+# (dims, levels, solver iterations per prototype).  The second level of the 3-level
+# case has 160 unknowns: more iterations there would solve A x = 0 to rounding
+# level, leaving a prototype made of rounding noise on either side.
+ADAPT_CASES = [
+    ((4, 4, 4, 4), [dict(block=(2, 2, 2, 2), nv=8, sweeps=6, adapt_nv=5)], 10),   # batches of 3 and 2; a restart
+    ((4, 4, 4, 4), [dict(block=(2, 2, 2, 2), nv=5, sweeps=4, adapt_nv=2),        # three levels, both adaptive
+                    dict(block=(2, 2, 1, 1), nv=4, sweeps=4, adapt_nv=2)], 3),
+]
+
+
+@pytest.mark.parametrize("device_starts", [False, True])
+@pytest.mark.parametrize("dims,levels,iters", ADAPT_CASES)
+def test_adaptive_setup_matches_oracle(dims, levels, iters, device_starts):
+    """Adaptive steps (Sec. 2: V^k augmented by prototypes from the current solver
+    applied to A x = 0), two steps per level: P and the coarse operators of every
+    level match the oracle's.  The prototypes pass through whole V-cycles, so the
+    tolerance is the V-cycle's (1e-9) amplified by the block QR's conditioning: 1e-8."""
+    wm = require_gpu()
+    h, hier, U = _setup_both(wm, dims, 0.1, levels, adapt=(2, iters), device_starts=device_starts)
+    for l, spec in enumerate(levels):
+        got = wm.mg_get_prolongator(h, l)
+        nhalf = hier[l].ncomp // 2
+        want = _oracle_vectors(hier[l].P, spec["nv"], nhalf).reshape(got.shape)
+        assert np.max(np.abs(got - want)) < 1e-8, (l, np.max(np.abs(got - want)))
+        Ac = wm.mg_get_coarse_op(h, l + 1)
+        want_c = hier[l + 1].stencil.reshape(Ac.shape)
+        assert np.max(np.abs(Ac - want_c)) < 1e-8 * np.max(np.abs(want_c)), l
+
+
+def test_adaptive_setup_mixed_solves():
+    """The mixed hierarchy (FP32 relaxation, FP32 GCR with the 16-bit V-cycle making the prototypes)
+    with half of its Nv = 12 vectors from two adaptive steps gives a solve to the
+    1e-10 true FP64 residual."""
+    wm = require_gpu()
+    dims = (8, 8, 8, 8)
+    U = inputs.random_gauge(dims, 2)
+    b = inputs.gaussian_spinor(dims, 3)
+    p = wm.mg_default_params(mixed=1, nv=[12], setup_sweeps=[10], adapt_steps=2, adapt_nv=[6])
+    h = wm.mg_setup(U, dims, -0.2, p)
+    x = np.zeros_like(b)
+    wm.mg_solve(h, b, x, 1e-10)
+    r = b.reshape(lattice(dims) + (4, 3)) - dirac.wilson_dirac(U, x.reshape(lattice(dims) + (4, 3)), -0.2)
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b) * 1.01
 
 
 def test_device_start_vectors_follow_the_counter_definition():

@@ -1,4 +1,4 @@
-"""GPU MG-GCR solves, judged by the true FP64 residual (recomputed by the oracle) and
+"""GPU MG-GCR solves, checked against the true FP64 residual (recomputed by the oracle) and
 against the unique solution x = D^-1 b (dense LU where the lattice is small).
 
 The solution of D x = b is unique (Sec. 1: Re(lambda) > 0 at these masses), so
