@@ -81,7 +81,7 @@ typedef struct {
   int max_iter;                       /* outer GCR iteration cap (all restarts) */
   int mixed;                          /* 0 = plain FP64 everywhere; 1 = mixed precision */
   int fine_prec;                      /* mixed: storage of level-0 smoother work (MG_F16/MG_BF16/MG_F32) */
-  int coarse_prec;                    /* mixed: storage of levels 1..L-2 (MG_F32/MG_F16/MG_BF16) */
+  int coarse_prec;                    /* mixed: storage of levels 1..L-1 (MG_F32, or fine_prec itself) */
   double reliable_delta;              /* mixed: inner FP32 GCR reduces ||r|| by this factor before an FP64 update */
   uint64_t seed;                      /* on-device start vectors: level l uses stream seed + l */
   int use_graphs;                     /* 1: replay the V-cycle as a captured CUDA graph; 0: launch eagerly */

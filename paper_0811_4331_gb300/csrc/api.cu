@@ -67,14 +67,15 @@ inline size_t slot_misc() { return slot_gcr_bn() + 4 * kMaxRhs; }
 inline size_t slot_beta() { return slot_misc() + 4 * kMaxRhs; }
 // inner GCR of the coarse correction of level l: dots, residual norms, betas (8 per rhs)
 inline size_t slot_inner(int l) { return slot_beta() + (size_t)2 * kMaxBasis * kMaxRhs + (size_t)l * 24 * kMaxRhs; }
-inline size_t slot_total() { return slot_inner(MG_MAX_LEVELS); }
+inline size_t slot_gcr_pre() { return slot_inner(MG_MAX_LEVELS); }  // <w|r>, ||w||^2 before Gram-Schmidt
+inline size_t slot_total() { return slot_gcr_pre() + 4 * kMaxRhs; }
 const int kInnerBasis = 8;
 
 enum { WV_E, WV_RES, WV_P, WV_XC, WV_AXC, WV_RC, WV_EC, WV_T, WV_DT, WV_IN, WV_A, WV_B, WV_KW, WV_KZ, WV_PR, WV_PE, WV_COUNT };
 
 int prec_of(const mg_handle* h, int l) {
   if (!h->p.mixed) return MG_F64;
-  const int L = (int)h->lev.size();
+  const int L = h->p.n_levels;  // not lev.size(): during setup the levels below l may not exist yet
   if (l == 0) return h->p.fine_prec;
   if (l == L - 1) return MG_F32;  // coarsest vectors; the inverse stays FP64
   return h->p.coarse_prec;
@@ -283,7 +284,7 @@ int coarsest_solve(mg_handle* h, int l, int prec, const void* r, void* e, int nr
   Level& a = *h->lev[l];
   if (a.inv_prec == MG_F64 && prec == MG_F64) {
     Prof pf(h, MG_K_COARSEST, prec);
-    LK(launch_dense_matvec(0, 0, 0, a.N(), a.inv.p, r, e, nrhs, 0, h->st));
+    LK(launch_dense_matvec(0, 0, 0, a.N(), a.inv.p, r, e, nrhs, 0, h->st, a.mm_scratch.p));
     return MG_OK;
   }
   void* r64 = work(h, l, MG_F64, WV_A, nrhs);
@@ -297,12 +298,12 @@ int coarsest_solve(mg_handle* h, int l, int prec, const void* r, void* e, int nr
   }
   {
     Prof pf(h, MG_K_COARSEST, MG_F32);
-    LK(launch_dense_matvec(a.inv_prec, 0, 0, a.N(), a.inv.p, r64, e64, nrhs, 0, h->st));
+    LK(launch_dense_matvec(a.inv_prec, 0, 0, a.N(), a.inv.p, r64, e64, nrhs, 0, h->st, a.mm_scratch.p));
   }
   for (int it = 0; it < kCoarsestRefine; ++it) {
     RET(op_apply(h, l, MG_F64, e64, t64, r64, -1.0, 1.0, nullptr, 0, nrhs));
     Prof pf(h, MG_K_COARSEST, MG_F32);
-    LK(launch_dense_matvec(a.inv_prec, 0, 0, a.N(), a.inv.p, t64, e64, nrhs, 1, h->st));
+    LK(launch_dense_matvec(a.inv_prec, 0, 0, a.N(), a.inv.p, t64, e64, nrhs, 1, h->st, a.mm_scratch.p));
   }
   Prof pf(h, MG_K_VECTOR, prec);
   LK(launch_convert(MG_F64, prec, n, nrhs, e64, e, 1.0, nullptr, 0, 0.0, 0, h->st));
@@ -375,6 +376,10 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
   if (!res || !xc || !axc || !rc || !ec) {
     set_error("out of device memory for V-cycle work vectors");
     return MG_ENOMEM;
+  }
+  if (!a.P[prec].p) {
+    set_error("prolongator of level " + std::to_string(l) + " not stored in the cycle's precision");
+    return MG_EINVAL;
   }
   // pre-smoothing from e = 0
   RET(mr_steps(h, l, prec, r, e, true, res, h->p.nu_pre, nrhs));
@@ -538,8 +543,11 @@ static int build_coarsest(mg_handle* h) {
   const size_t eb = bytes_of(c.inv_prec);
   DevBuf aug, col, errflag;
   if (!aug.ensure(N * 2 * N * eb) || !col.ensure(dense_inverse_scratch_bytes(c.inv_prec, (int)N)) ||
-      !c.inv.ensure(N * N * eb) || !errflag.ensure(sizeof(int)))
+      !c.inv.ensure(N * N * eb) || !errflag.ensure(sizeof(int)) ||
+      !c.mm_scratch.ensure(dense_matvec_scratch_bytes((int)N)))
     return MG_ENOMEM;
+  // the product's tickets sit after the partial tiles, at an offset that depends on N
+  CK(cudaMemsetAsync(c.mm_scratch.p, 0, dense_matvec_scratch_bytes((int)N), st));
   CK(cudaMemsetAsync(errflag.p, 0, sizeof(int), st));
   {
     Prof pf(h, MG_K_INVERSE, c.inv_prec);
@@ -866,6 +874,10 @@ int mg_setup(mg_handle** hout, const double* gauge, int gauge_on_device, const i
   if (p->mixed && (check_prec(p->fine_prec) || p->fine_prec == MG_F64 || check_prec(p->coarse_prec) ||
                    p->coarse_prec == MG_F64)) {
     set_error("mixed precision needs fine_prec and coarse_prec in {F32, F16, BF16}");
+    return MG_EINVAL;
+  }
+  if (p->mixed && p->coarse_prec != MG_F32 && p->coarse_prec != p->fine_prec) {
+    set_error("mixed precision needs coarse_prec == F32 or coarse_prec == fine_prec (the transfer kernels' pairs)");
     return MG_EINVAL;
   }
   mg_handle* h = new mg_handle();
@@ -1222,9 +1234,12 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
   // Krylov buffers in precision pin: basis W, Z [restart][nrhs][n], x, r
   const size_t vbytes = n * nrhs * bi;
   const size_t slots = (size_t)((restart + 7) / 8) * 8;  // the multi-dot reads whole chunks of 8
-  if (!h->gW.ensure(vbytes * slots) || !h->gZ.ensure(vbytes * restart) || !h->gx.ensure(vbytes) ||
-      !h->gr.ensure(vbytes))
+  const size_t hbytes = (size_t)nrhs * kMaxBasis * kMaxBasis * 16, abytes = (size_t)nrhs * kMaxBasis * 16;
+  if (!h->gW.ensure(vbytes * slots) || !h->gZ.ensure(vbytes * restart) || !h->gr.ensure(vbytes) ||
+      !h->gH.ensure(hbytes) || !h->galpha.ensure(abytes) || !h->gy.ensure(abytes))
     return MG_ENOMEM;
+  double2* H = h->gH.as<double2>();
+  double2* alpha = h->galpha.as<double2>();
   double* hs = h->host_slots;
   std::vector<double> bn(nrhs), rn(nrhs);
   LK(launch_dot(MG_F64, n, nrhs, h->gb64.p, h->gb64.p, h->red.at(slot_gcr_bn(), 4), st));
@@ -1262,9 +1277,9 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
       status = MG_ENOCONV;
       break;
     }
-    // start of a cycle: Krylov residual r = r64 (converted), x = 0
+    // start of a cycle: Krylov residual r = r64 (converted), H = 0
     LK(launch_convert(MG_F64, pin, n, nrhs, h->gr64.p, h->gr.p, 1.0, nullptr, 0, 0.0, 0, st));
-    CK(cudaMemsetAsync(h->gx.p, 0, vbytes, st));
+    CK(cudaMemsetAsync(H, 0, hbytes, st));
     LK(launch_dot(pin, n, nrhs, h->gr.p, h->gr.p, h->red.at(slot_gcr_rn(), 4), st));
     std::vector<double> r0 = rn;
     int k = 0;
@@ -1297,27 +1312,30 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
       } else {
         CK(cudaMemcpyAsync(zk, h->gr.p, vbytes, cudaMemcpyDeviceToDevice, st));
       }
-      // w = D z
-      RET(op_apply(h, 0, pin, zk, wk, nullptr, 1.0, 0.0, nullptr, 0, nrhs));
+      // w = D z, with <w|r> and ||w||^2 fused
+      RET(op_apply(h, 0, pin, zk, wk, nullptr, 1.0, 0.0, h->gr.p, slot_gcr_pre(), nrhs));
       ++fine;
       if (pin == MG_F64) ++fine64;
-      // classical Gram-Schmidt, twice, against the previous w's
-      if (k == 0) {
-        Prof pf2(h, MG_K_VECTOR, pin);
-        LK(launch_dot(pin, n, nrhs, wk, h->gr.p, h->red.at(slot_gcr_wr(), 4), st));
-      } else {
+      // classical Gram-Schmidt of w against the previous w's (z stays as the
+      // cycle made it): one pass, and a second one for the right-hand sides
+      // whose ||w|| the first pass cut below 1/sqrt(2)
+      const double* dots = h->red.slot(slot_gcr_pre());
+      if (k > 0) {
         Prof pf2(h, MG_K_VECTOR, pin);
         for (int pass = 0; pass < 2; ++pass) {
-          LK(launch_multidot(pin, n, nrhs, k, kMaxBasis, h->gW.p, n * nrhs, wk, h->red.at(slot_beta(), 0), st));
-          RedArgs r2 = h->red.at(slot_gcr_wr(), 4);
-          LK(launch_multiaxpy(pin, n, nrhs, k, kMaxBasis, h->red.slot(slot_beta()), h->gW.p, h->gZ.p, n * nrhs, wk,
-                              zk, h->gr.p, r2, st));
+          const double* pre = pass ? h->red.slot(slot_gcr_pre() + 2) : nullptr;
+          const double* post = pass ? h->red.slot(slot_gcr_wr() + 2) : nullptr;
+          LK(launch_multidot(pin, n, nrhs, k, kMaxBasis, h->gW.p, n * nrhs, wk, h->red.at(slot_beta(), 0), st, pre,
+                             post, 4));
+          LK(launch_gs_update(pin, n, nrhs, k, kMaxBasis, h->red.slot(slot_beta()), h->gW.p, n * nrhs, wk, h->gr.p,
+                              h->red.at(slot_gcr_wr(), 4), H, k, pre, post, 4, st));
         }
+        dots = h->red.slot(slot_gcr_wr());
       }
       {
         Prof pf2(h, MG_K_VECTOR, pin);
-        LK(launch_gcr_update(pin, pin, n, nrhs, h->red.slot(slot_gcr_wr()), 4, wk, zk, h->gx.p, h->gr.p,
-                             h->red.at(slot_gcr_rn() + 2, 4), st));
+        LK(launch_gcr_step(pin, n, nrhs, dots, 4, wk, h->gr.p, h->red.at(slot_gcr_rn() + 2, 4), H, alpha, k,
+                           kMaxBasis, st));
       }
       RET(read_slots(h, slot_gcr_rn(), 4 * nrhs));
       ++k;
@@ -1335,8 +1353,12 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
       }
       if (inner_done || k == restart || total_iters >= h->p.max_iter) break;
     }
-    // x64 += x (the cycle's correction), then the true residual in FP64
-    LK(launch_convert(pin, MG_F64, n, nrhs, h->gx.p, h->gx64.p, 1.0, nullptr, 0, 0.0, 1, st));
+    // x64 += Z H^-1 alpha (the cycle's correction), then the true residual in FP64
+    {
+      Prof pf2(h, MG_K_VECTOR, pin);
+      LK(launch_back_substitute(nrhs, k, kMaxBasis, H, alpha, h->gy.as<double2>(), st));
+      LK(launch_zcombine(pin, MG_F64, n, nrhs, k, kMaxBasis, h->gy.as<double2>(), h->gZ.p, n * nrhs, h->gx64.p, st));
+    }
     RET(true_residual());
     if (k == restart) ++restarts;
     ++reliable;

@@ -117,11 +117,26 @@ constexpr int kChunk = 8;
 // kChunk vectors of its chunk without a bound test (the dots beyond k are
 // computed from whatever the unused slots hold and are never read), and the
 // eight loads of an element issue back to back.
+// Second Gram-Schmidt pass on demand: with `pre` and `post` (the squared norm
+// of w before and after the first pass, `cstride` doubles between right-hand
+// sides) a pass runs for a right-hand side only where the first one removed
+// more than half of ||w||^2 -- the reorthogonalisation test of Daniel,
+// Gragg, Kaufman and Stewart (Math. Comp. 30, 1976) with eta = 1/sqrt(2).
+// Every block of a right-hand side takes the same decision before it touches
+// a reduction, so a skipped right-hand side leaves its tickets and slots as
+// they were.
+__device__ __forceinline__ bool gs_pass_skipped(const double* pre, const double* post, int cstride, int rhs) {
+  if (!pre) return false;
+  return !(post[(size_t)rhs * cstride] < 0.5 * pre[(size_t)rhs * cstride]);
+}
+
 template <typename S>
 __global__ void __launch_bounds__(kVecThreads)
-    multidot_kernel(size_t n, int k, int kmax, const S* W, size_t jstride, const S* w, RedArgs ra) {
+    multidot_kernel(size_t n, int k, int kmax, const S* W, size_t jstride, const S* w, RedArgs ra,
+                    const double* pre, const double* post, int cstride) {
   typedef typename Store<S>::R R;
   const int chunk = blockIdx.y, rhs = blockIdx.z;
+  if (gs_pass_skipped(pre, post, cstride, rhs)) return;
   const int j0 = chunk * kChunk;
   const S* wr = w + (size_t)rhs * n;
   const S* Wc = W + (size_t)j0 * jstride + (size_t)rhs * n;
@@ -152,16 +167,18 @@ __global__ void __launch_bounds__(kVecThreads)
 }
 
 int launch_multidot(int prec, size_t n, int nrhs, int k, int kmax, const void* W, size_t jstride, const void* w,
-                    RedArgs red, cudaStream_t st) {
+                    RedArgs red, cudaStream_t st, const double* pre, const double* post, int cstride) {
   if (k <= 0) return 0;
   if (kmax % kChunk) return -1;
   dim3 grid(red_blocks(n), (k + kChunk - 1) / kChunk, nrhs);
   switch (prec) {
     case 0:
-      multidot_kernel<double2><<<grid, kVecThreads, 0, st>>>(n, k, kmax, (const double2*)W, jstride, (const double2*)w, red);
+      multidot_kernel<double2><<<grid, kVecThreads, 0, st>>>(n, k, kmax, (const double2*)W, jstride, (const double2*)w,
+                                                             red, pre, post, cstride);
       break;
     case 1:
-      multidot_kernel<float2><<<grid, kVecThreads, 0, st>>>(n, k, kmax, (const float2*)W, jstride, (const float2*)w, red);
+      multidot_kernel<float2><<<grid, kVecThreads, 0, st>>>(n, k, kmax, (const float2*)W, jstride, (const float2*)w,
+                                                            red, pre, post, cstride);
       break;
     default: return -1;
   }
@@ -277,6 +294,198 @@ int launch_gcr_update(int prec, int xprec, size_t n, int nrhs, const double* dot
   else if (prec == 1 && xprec == 0)
     gcr_update_kernel<float2, double2><<<grid, kVecThreads, 0, st>>>(n, dots, dstride, (float2*)w, (float2*)z,
                                                                       (double2*)x, (float2*)r, red);
+  else
+    return -1;
+  return launched() ? 0 : -1;
+}
+
+// ------------------------------------------------------------------ GCR with a deferred solution update
+// The outer flexible GCR keeps the preconditioned vectors z_j as they come
+// out of the cycle and orthonormalises only w = A z against the previous
+// w's: A Z = W H with H upper triangular (the Gram-Schmidt coefficients above
+// the diagonal, the norms on it).  The residual update r -= alpha_k w_k needs
+// only W; at the end of a cycle x += Z y with H y = alpha.  One Gram-Schmidt
+// pass (plus a second one on demand) then reads each basis vector once per
+// iteration instead of W and Z twice.
+
+// w -= sum_j beta_j W_j, fused <w|r> and ||w||^2 (3 values per right-hand
+// side); the coefficients are added to column hk of H.
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads)
+    gs_update_kernel(size_t n, int k, int kmax, const double* beta, const S* W, size_t jstride, S* w, const S* r,
+                     RedArgs ra, double2* H, int hk, const double* pre, const double* post, int cstride) {
+  typedef typename Store<S>::R R;
+  __shared__ cx<R> sb[64];
+  const int rhs = blockIdx.y;
+  if (gs_pass_skipped(pre, post, cstride, rhs)) return;
+  const size_t off = (size_t)rhs * n;
+  const double* bt = beta + (size_t)rhs * kmax * 2;
+  for (int j = threadIdx.x; j < k; j += kVecThreads) sb[j] = mk<R>((R)bt[2 * j], (R)bt[2 * j + 1]);
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < k; j += kVecThreads) {
+      double2& hj = H[((size_t)rhs * kmax + j) * kmax + hk];
+      hj.x += bt[2 * j];
+      hj.y += bt[2 * j + 1];
+    }
+  __syncthreads();
+  R acc[3] = {(R)0, (R)0, (R)0};
+  for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
+    cx<R> wv = ldc<R>(w + off, i);
+    int j = 0;
+    for (; j + 8 <= k; j += 8) {  // eight independent loads in flight
+      cx<R> a[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[q] = ldc<R>(W + (size_t)(j + q) * jstride + off, i);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) wv = wv - sb[j + q] * a[q];
+    }
+    for (; j < k; ++j) wv = wv - sb[j] * ldc<R>(W + (size_t)j * jstride + off, i);
+    stc(w + off, i, wv);
+    const cx<R> ws = as_stored<S>(wv);
+    const cx<R> d = cmul_conj(ws, ldc<R>(r + off, i));
+    acc[0] += d.re;
+    acc[1] += d.im;
+    acc[2] += norm2(ws);
+  }
+  grid_reduce<3, kVecThreads, R>(acc, ra, rhs);
+}
+
+int launch_gs_update(int prec, size_t n, int nrhs, int k, int kmax, const double* beta, const void* W, size_t jstride,
+                     void* w, const void* r, RedArgs red, double2* H, int hk, const double* pre, const double* post,
+                     int cstride, cudaStream_t st) {
+  if (k <= 0 || k > 64) return k <= 0 ? 0 : -1;
+  dim3 grid(vec_blocks(n), nrhs);
+  switch (prec) {
+    case 0:
+      gs_update_kernel<double2><<<grid, kVecThreads, 0, st>>>(n, k, kmax, beta, (const double2*)W, jstride,
+                                                              (double2*)w, (const double2*)r, red, H, hk, pre, post,
+                                                              cstride);
+      break;
+    case 1:
+      gs_update_kernel<float2><<<grid, kVecThreads, 0, st>>>(n, k, kmax, beta, (const float2*)W, jstride, (float2*)w,
+                                                             (const float2*)r, red, H, hk, pre, post, cstride);
+      break;
+    default: return -1;
+  }
+  return launched() ? 0 : -1;
+}
+
+// w_k = w / ||w||, alpha_k = <w_k|r>, r -= alpha_k w_k, fused ||r||^2; H[k][k]
+// = ||w|| and alpha_k are kept for the end of the cycle.  dots = (<w|r>, ||w||^2)
+// of the orthogonalised w.
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads)
+    gcr_step_kernel(size_t n, const double* dots, int dstride, S* w, S* r, RedArgs ra, double2* H, double2* alpha,
+                    int k, int kmax) {
+  typedef typename Store<S>::R R;
+  const int rhs = blockIdx.y;
+  const double* d = dots + (size_t)rhs * dstride;
+  const double nw2 = d[2];
+  double inv = 0.0, ar = 0.0, ai = 0.0;
+  if (nw2 > 0.0 && isfinite(nw2)) {
+    inv = 1.0 / sqrt(nw2);
+    ar = d[0] * inv;
+    ai = d[1] * inv;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    H[((size_t)rhs * kmax + k) * kmax + k] = make_double2(nw2 > 0.0 ? sqrt(nw2) : 0.0, 0.0);
+    alpha[(size_t)rhs * kmax + k] = make_double2(ar, ai);
+  }
+  const R s = (R)inv;
+  const cx<R> a = mk<R>((R)ar, (R)ai);
+  const size_t off = (size_t)rhs * n;
+  R acc = (R)0;
+  for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
+    const cx<R> wv = as_stored<S>(s * ldc<R>(w + off, i));
+    stc(w + off, i, wv);
+    const cx<R> rv = ldc<R>(r + off, i) - a * wv;
+    stc(r + off, i, rv);
+    acc += norm2(as_stored<S>(rv));
+  }
+  R red[1] = {acc};
+  grid_reduce<1, kVecThreads, R>(red, ra, rhs);
+}
+
+int launch_gcr_step(int prec, size_t n, int nrhs, const double* dots, int dstride, void* w, void* r, RedArgs red,
+                    double2* H, double2* alpha, int k, int kmax, cudaStream_t st) {
+  dim3 grid(vec_blocks(n), nrhs);
+  if (prec == 0)
+    gcr_step_kernel<double2><<<grid, kVecThreads, 0, st>>>(n, dots, dstride, (double2*)w, (double2*)r, red, H, alpha,
+                                                           k, kmax);
+  else if (prec == 1)
+    gcr_step_kernel<float2><<<grid, kVecThreads, 0, st>>>(n, dots, dstride, (float2*)w, (float2*)r, red, H, alpha, k,
+                                                          kmax);
+  else
+    return -1;
+  return launched() ? 0 : -1;
+}
+
+// y = H^-1 alpha for the k x k upper-triangular H of each right-hand side
+// (back substitution in FP64, one thread per right-hand side: k <= 64).
+__global__ void back_substitute_kernel(int k, int kmax, const double2* H, const double2* alpha, double2* y) {
+  const int rhs = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  const double2* Hr = H + (size_t)rhs * kmax * kmax;
+  const double2* ar = alpha + (size_t)rhs * kmax;
+  double2* yr = y + (size_t)rhs * kmax;
+  for (int i = k - 1; i >= 0; --i) {
+    double sr = ar[i].x, si = ar[i].y;
+    for (int j = i + 1; j < k; ++j) {
+      const double2 h = Hr[(size_t)i * kmax + j], v = yr[j];
+      sr -= h.x * v.x - h.y * v.y;
+      si -= h.x * v.y + h.y * v.x;
+    }
+    const double dd = Hr[(size_t)i * kmax + i].x;
+    yr[i] = dd > 0.0 ? make_double2(sr / dd, si / dd) : make_double2(0.0, 0.0);
+  }
+}
+
+int launch_back_substitute(int nrhs, int k, int kmax, const double2* H, const double2* alpha, double2* y,
+                           cudaStream_t st) {
+  if (k <= 0) return 0;
+  back_substitute_kernel<<<nrhs, 32, 0, st>>>(k, kmax, H, alpha, y);
+  return launched() ? 0 : -1;
+}
+
+// x += sum_j y_j Z_j (Z in the Krylov precision, x FP64 or the same).
+template <typename SZ, typename SX>
+__global__ void __launch_bounds__(kVecThreads)
+    zcombine_kernel(size_t n, int k, int kmax, const double2* y, const SZ* Z, size_t jstride, SX* x) {
+  typedef typename Store<SX>::R RX;
+  __shared__ cx<RX> sy[64];
+  const int rhs = blockIdx.y;
+  const size_t off = (size_t)rhs * n;
+  for (int j = threadIdx.x; j < k; j += kVecThreads) {
+    const double2 v = y[(size_t)rhs * kmax + j];
+    sy[j] = mk<RX>((RX)v.x, (RX)v.y);
+  }
+  __syncthreads();
+  for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
+    cx<RX> xv = ldc<RX>(x + off, i);
+    int j = 0;
+    for (; j + 8 <= k; j += 8) {
+      cx<RX> a[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[q] = ldc<RX>(Z + (size_t)(j + q) * jstride + off, i);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) xv = cfma(sy[j + q], a[q], xv);
+    }
+    for (; j < k; ++j) xv = cfma(sy[j], ldc<RX>(Z + (size_t)j * jstride + off, i), xv);
+    stc(x + off, i, xv);
+  }
+}
+
+int launch_zcombine(int zprec, int xprec, size_t n, int nrhs, int k, int kmax, const double2* y, const void* Z,
+                    size_t jstride, void* x, cudaStream_t st) {
+  if (k <= 0) return 0;
+  if (k > 64) return -1;
+  dim3 grid(vec_blocks(n), nrhs);
+  if (zprec == 0 && xprec == 0)
+    zcombine_kernel<double2, double2><<<grid, kVecThreads, 0, st>>>(n, k, kmax, y, (const double2*)Z, jstride,
+                                                                    (double2*)x);
+  else if (zprec == 1 && xprec == 0)
+    zcombine_kernel<float2, double2><<<grid, kVecThreads, 0, st>>>(n, k, kmax, y, (const float2*)Z, jstride,
+                                                                   (double2*)x);
   else
     return -1;
   return launched() ? 0 : -1;

@@ -241,23 +241,32 @@ static int prolong_t(const Agg& g, const void* P, const void* in, void* out, int
 // Supported (vector-in, P, vector-out) precision triples.
 int launch_restrict(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
                     cudaStream_t st) {
+  // several right-hand sides with 16-bit vectors and P: tensor cores, P read once
+  if ((pin == 2 || pin == 3) && pP == pin && (pout == 1 || pout == pin) && transfer_mma_ok(g, nrhs))
+    return launch_restrict_mma(pin, pP, pout, g, P, in, out, nrhs, st);
   if (pin == 0 && pP == 0 && pout == 0) return restrict_t<double2, double2, double2>(g, P, in, out, nrhs, st);
   if (pin == 1 && pP == 1 && pout == 1) return restrict_t<float2, float2, float2>(g, P, in, out, nrhs, st);
   if (pin == 2 && pP == 2 && pout == 1) return restrict_t<__half2, __half2, float2>(g, P, in, out, nrhs, st);
   if (pin == 3 && pP == 3 && pout == 1)
     return restrict_t<__nv_bfloat162, __nv_bfloat162, float2>(g, P, in, out, nrhs, st);
   if (pin == 2 && pP == 2 && pout == 2) return restrict_t<__half2, __half2, __half2>(g, P, in, out, nrhs, st);
+  if (pin == 3 && pP == 3 && pout == 3)
+    return restrict_t<__nv_bfloat162, __nv_bfloat162, __nv_bfloat162>(g, P, in, out, nrhs, st);
   return -1;
 }
 
 int launch_prolong(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
                    cudaStream_t st) {
+  if ((pP == 2 || pP == 3) && pout == pP && (pin == 1 || pin == pP) && transfer_mma_ok(g, nrhs))
+    return launch_prolong_mma(pin, pP, pout, g, P, in, out, nrhs, st);
   if (pin == 0 && pP == 0 && pout == 0) return prolong_t<double2, double2, double2>(g, P, in, out, nrhs, st);
   if (pin == 1 && pP == 1 && pout == 1) return prolong_t<float2, float2, float2>(g, P, in, out, nrhs, st);
   if (pin == 1 && pP == 2 && pout == 2) return prolong_t<float2, __half2, __half2>(g, P, in, out, nrhs, st);
   if (pin == 1 && pP == 3 && pout == 3)
     return prolong_t<float2, __nv_bfloat162, __nv_bfloat162>(g, P, in, out, nrhs, st);
   if (pin == 2 && pP == 2 && pout == 2) return prolong_t<__half2, __half2, __half2>(g, P, in, out, nrhs, st);
+  if (pin == 3 && pP == 3 && pout == 3)
+    return prolong_t<__nv_bfloat162, __nv_bfloat162, __nv_bfloat162>(g, P, in, out, nrhs, st);
   return -1;
 }
 
@@ -469,8 +478,118 @@ __global__ void dense_matvec_kernel(int N, const TM* inv, const SI* x, SO* y, in
   }
 }
 
+// Y = inv X (+ Y if acc) for 4 <= nrhs <= 64: a dense product, tiled so that
+// each element of the inverse is read once per launch instead of once per
+// right-hand side.  CTA (tile, ks) owns 16 rows, every right-hand side and the
+// ks-th of KS contiguous K ranges; a K step stages 16 x 32 of the inverse and
+// 32 x nrhs of X in shared memory; thread t accumulates row t % 16 for the
+// right-hand sides t / 16 + 16 q.  The K ranges keep the dependent chain of
+// each CTA short enough to fill the GPU (the coarsest matrix has ~1500 rows).
+// Each CTA parks its partial tile; the last CTA of a row tile to finish (an
+// atomic ticket, reset by it) adds the KS partials in ks order and writes Y,
+// so the sum is deterministic.  Arithmetic in the matrix's precision.
+constexpr int kMmRows = 16, kMmK = 32, kMmThreads = 256;
+
+template <typename TM, typename SI, typename SO>
+__global__ void __launch_bounds__(kMmThreads)
+    dense_matmul_kernel(int N, const TM* inv, const SI* x, SO* y, int R, int acc, int kper,
+                        cx<typename Store<TM>::R>* part, unsigned* tickets) {
+  typedef typename Store<TM>::R Rt;
+  __shared__ cx<Rt> As[kMmRows][kMmK + 1];
+  __shared__ cx<Rt> Bs[kMmK][64];
+  __shared__ unsigned last;
+  const int row0 = blockIdx.x * kMmRows, ks = blockIdx.y, KS = gridDim.y;
+  const int kbeg = ks * kper, kend = min(N, kbeg + kper);
+  const int tr = threadIdx.x % kMmRows, tg = threadIdx.x / kMmRows;  // row in tile, rhs group (0..15)
+  constexpr int kPer = 4;                                             // 64 rhs / 16 groups
+  cx<Rt> accv[kPer];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) accv[q] = zero<Rt>();
+  for (int k0 = kbeg; k0 < kend; k0 += kMmK) {
+    for (int e = threadIdx.x; e < kMmRows * kMmK; e += kMmThreads) {
+      const int r = e / kMmK, c = e % kMmK;
+      const int gr = row0 + r, gc = k0 + c;
+      As[r][c] = (gr < N && gc < kend) ? ldc<Rt>(inv, (size_t)gr * N + gc) : zero<Rt>();
+    }
+    for (int e = threadIdx.x; e < kMmK * R; e += kMmThreads) {
+      const int r = e / kMmK, c = e % kMmK;
+      Bs[c][r] = (k0 + c < kend) ? ldc<Rt>(x, (size_t)r * N + k0 + c) : zero<Rt>();
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kMmK; ++kk) {
+      const cx<Rt> a = As[tr][kk];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int r = tg + 16 * q;
+        if (r < R) accv[q] = cfma(a, Bs[kk][r], accv[q]);
+      }
+    }
+    __syncthreads();
+  }
+  const int grow = row0 + tr;
+  // park this K range's tile: part[ks][r][row]
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int r = tg + 16 * q;
+    if (r < R && grow < N) part[((size_t)ks * R + r) * N + grow] = accv[q];
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&tickets[blockIdx.x], 1u) == (unsigned)(KS - 1));
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (grow < N) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int r = tg + 16 * q;
+      if (r >= R) break;
+      const volatile Rt* pv = (const volatile Rt*)part;  // other CTAs' tiles, past the ticket
+      cx<Rt> sum = zero<Rt>();
+      for (int j = 0; j < KS; ++j) {
+        const size_t idx = ((size_t)j * R + r) * N + grow;
+        sum = sum + mk<Rt>(pv[2 * idx], pv[2 * idx + 1]);
+      }
+      const size_t o = (size_t)r * N + grow;
+      cx<double> v = mk<double>((double)sum.re, (double)sum.im);
+      if (acc) v = v + ldc<double>(y, o);
+      stc(y, o, v);
+    }
+  }
+  if (threadIdx.x == 0) tickets[blockIdx.x] = 0u;
+}
+
+// Scratch of the tiled product: partial tiles (up to 8 K ranges x 64 rhs x N
+// complex FP64) and one ticket per 16-row tile.
+size_t dense_matvec_scratch_bytes(int N) {
+  return (size_t)8 * 64 * N * 16 + (size_t)((N + kMmRows - 1) / kMmRows) * sizeof(unsigned) + 256;
+}
+
 int launch_dense_matvec(int pm, int pin, int pout, int N, const void* inv, const void* x, void* y, int nrhs, int acc,
-                        cudaStream_t st) {
+                        cudaStream_t st, void* scratch) {
+  if (scratch && nrhs >= 4 && nrhs <= 64) {
+    const int tiles = (N + kMmRows - 1) / kMmRows;
+    int KS = (2 * 152 + tiles - 1) / tiles;  // about two CTAs per SM
+    KS = KS < 1 ? 1 : (KS > 8 ? 8 : KS);
+    int kper = (N + KS - 1) / KS;
+    kper = (kper + kMmK - 1) / kMmK * kMmK;
+    KS = (N + kper - 1) / kper;
+    const dim3 g(tiles, KS);
+    unsigned* tickets = (unsigned*)((char*)scratch + (size_t)8 * 64 * N * 16);
+    if (pm == 0 && pin == 0 && pout == 0)
+      dense_matmul_kernel<double2, double2, double2><<<g, kMmThreads, 0, st>>>(
+          N, (const double2*)inv, (const double2*)x, (double2*)y, nrhs, acc, kper, (cx<double>*)scratch, tickets);
+    else if (pm == 1 && pin == 0 && pout == 0)
+      dense_matmul_kernel<float2, double2, double2><<<g, kMmThreads, 0, st>>>(
+          N, (const float2*)inv, (const double2*)x, (double2*)y, nrhs, acc, kper, (cx<float>*)scratch, tickets);
+    else if (pm == 1 && pin == 1 && pout == 1)
+      dense_matmul_kernel<float2, float2, float2><<<g, kMmThreads, 0, st>>>(
+          N, (const float2*)inv, (const float2*)x, (float2*)y, nrhs, acc, kper, (cx<float>*)scratch, tickets);
+    else
+      return -1;
+    return launched() ? 0 : -1;
+  }
   dim3 grid((N * 32 + 255) / 256, nrhs);
   if (pm == 0 && pin == 0 && pout == 0)
     dense_matvec_kernel<double2, double2, double2>

@@ -68,6 +68,7 @@ struct Level {
   // coarsest level: dense inverse [N][N], N = ncomp V, FP64 (plain) or FP32
   // (mixed: applied with FP64 iterative refinement)
   DevBuf inv;
+  DevBuf mm_scratch;  // partial tiles and tickets of the many-right-hand-side inverse product
   int inv_prec = 0;
   int N() const { return ncomp * V; }
   size_t n() const { return (size_t)ncomp * V; }
@@ -112,8 +113,8 @@ struct mg_handle {
   std::vector<std::vector<std::vector<std::unique_ptr<wmg::DevBuf>>>> work;
   int work_nrhs = 0;
   // outer solver buffers
-  wmg::DevBuf gx, gr, gw, gz, gW, gZ, gb64, gx64, gr64, gtmp;
-  int basis_cap = 0;  // vectors held by gW / gZ per rhs
+  wmg::DevBuf gr, gW, gZ, gb64, gx64, gr64, gtmp;
+  wmg::DevBuf gH, galpha, gy;  // outer GCR: H (A Z = W H), alpha, y = H^-1 alpha per right-hand side
   wmg::DevBuf err_flag;  // device int set by setup kernels on failure
   // profiler: event pairs per (class, precision)
   unsigned prof_mask = 0;

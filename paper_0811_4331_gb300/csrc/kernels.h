@@ -65,7 +65,24 @@ int launch_dot(int prec, size_t n, int nrhs, const void* a, const void* b, RedAr
 // multidot: beta_j = <W_j|w> for j < k -> result[(r * kmax + j) * 2 + {0,1}] (red.stride
 // ignored; result holds kmax complex per rhs).  W must hold ceil(k / 8) * 8 vectors.
 int launch_multidot(int prec, size_t n, int nrhs, int k, int kmax, const void* W, size_t jstride,
-                    const void* w, RedArgs red, cudaStream_t st);
+                    const void* w, RedArgs red, cudaStream_t st, const double* pre = nullptr,
+                    const double* post = nullptr, int cstride = 0);
+// Outer GCR with a deferred solution update (A Z = W H, x += Z H^-1 alpha at
+// the end of a cycle).  gs_update: w -= sum_j beta_j W_j with fused <w|r>,
+// ||w||^2 and H[:, hk] += beta; pre/post/cstride as for the multi-dot (a
+// second pass runs only where the first removed more than half of ||w||^2).
+int launch_gs_update(int prec, size_t n, int nrhs, int k, int kmax, const double* beta, const void* W, size_t jstride,
+                     void* w, const void* r, RedArgs red, double2* H, int hk, const double* pre, const double* post,
+                     int cstride, cudaStream_t st);
+// w /= ||w||, alpha_k = <w|r>, r -= alpha_k w with fused ||r||^2; stores H[k][k], alpha_k.
+int launch_gcr_step(int prec, size_t n, int nrhs, const double* dots, int dstride, void* w, void* r, RedArgs red,
+                    double2* H, double2* alpha, int k, int kmax, cudaStream_t st);
+// y = H^-1 alpha (upper triangular, per right-hand side).
+int launch_back_substitute(int nrhs, int k, int kmax, const double2* H, const double2* alpha, double2* y,
+                           cudaStream_t st);
+// x += sum_j y_j Z_j.
+int launch_zcombine(int zprec, int xprec, size_t n, int nrhs, int k, int kmax, const double2* y, const void* Z,
+                    size_t jstride, void* x, cudaStream_t st);
 // w -= sum_j beta_j W_j, z -= sum_j beta_j Z_j (beta from multidot result);
 // then reduce ||w||^2 and <w|r> per rhs into red2 (3 values: re, im, |w|^2).
 int launch_multiaxpy(int prec, size_t n, int nrhs, int k, int kmax, const double* beta, const void* W,
@@ -131,6 +148,13 @@ int launch_restrict(int pin, int pP, int pout, const Agg& g, const void* P, cons
                     cudaStream_t st);
 int launch_prolong(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
                    cudaStream_t st);
+// Tensor-core transfers for 2..64 right-hand sides with 16-bit P (nv <= 64,
+// nv / 16 rounded up in {1, 2, 4}); launch_restrict / launch_prolong pick them.
+bool transfer_mma_ok(const Agg& g, int nrhs);
+int launch_restrict_mma(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
+                        cudaStream_t st);
+int launch_prolong_mma(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
+                       cudaStream_t st);
 
 // C_0(B) += delta 1 on a coarse stencil [9][n][n][V] (FP64).
 int launch_diag_shift(double2* C, int n, int V, double delta, cudaStream_t st);
@@ -143,8 +167,12 @@ int dense_inverse(int prec, const double2* C, const int L[4], int n, void* aug, 
                   cudaStream_t st);
 size_t dense_inverse_scratch_bytes(int prec, int N);
 // y = inv x (+ y if acc); (matrix, in, out) precisions (0,0,0), (1,0,0), (1,1,1).
+// With scratch (dense_matvec_scratch_bytes(N), tickets zeroed once) 4..64
+// right-hand sides run as one tiled product; otherwise one warp per row and
+// right-hand side.
 int launch_dense_matvec(int pm, int pin, int pout, int N, const void* inv, const void* x, void* y, int nrhs,
-                        int acc, cudaStream_t st);
+                        int acc, cudaStream_t st, void* scratch);
+size_t dense_matvec_scratch_bytes(int N);
 
 // Setup: blockwise Gram-Schmidt (err = 2 on rank loss), prolongator
 // columns as fields, Galerkin coarse stencil column j.

@@ -83,17 +83,20 @@ def test_unpreconditioned_gcr(lu_small):
     assert rel_err(x, xl) < 1e-8
 
 
-@pytest.mark.parametrize("mixed", [0, 1])
-def test_three_level_solve_and_multi_rhs(mixed):
+@pytest.mark.parametrize("mixed,extra", [(0, {}), (1, {}), (1, dict(coarse_mma=1)), (1, dict(coarse_prec=2)),
+                                         (1, dict(fine_prec=3, coarse_prec=3))])
+def test_three_level_solve_and_multi_rhs(mixed, extra):
+    """Five right-hand sides (the coarsest inverse is applied as one tiled product), every
+    storage scheme of the coarse levels: FP64, FP32 (CUDA cores / BF16 tensor cores), FP16, BF16."""
     wm = require_gpu()
     dims = (8, 8, 8, 8)
     mass = -0.2
     U = inputs.random_gauge(dims, 4)
-    nrhs = 3
+    nrhs = 5
     b = np.stack([inputs.gaussian_spinor(dims, 20 + r) for r in range(nrhs)])
     b[1] = inputs.point_source(dims, 2, 1)
     p = wm.mg_default_params(n_levels=3, block=[(2, 2, 2, 2), (2, 2, 2, 2)], nv=[8, 6], setup_sweeps=[8, 8],
-                             mixed=mixed)
+                             mixed=mixed, **extra)
     h = wm.mg_setup(U, dims, mass, p)
     x = np.zeros_like(b)
     _, st = wm.mg_solve(h, b, x, 1e-10)
