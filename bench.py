@@ -231,13 +231,9 @@ def native(args, rank, world, U, b):
     return out
 
 
-def profiled_step(wm, torch, Ud, bd, masses, stream):
-    """One extra step (setup + solve) with the per-launch event profiler on every kernel class.
-
-    Returns the roofline of the dominant kernel and the device-time share of every class.
-    """
-    prec_names = ["f64", "f32", "f16", "bf16"]
-    p = params(wm, 1)
+def class_profile(wm, handles_run, peaks):
+    """Run `handles_run(collect)` with the per-launch event profiler on every kernel class;
+    return {(class, prec): [launches, ms, algorithmic bytes]}."""
     tot = {}
 
     def collect(h):
@@ -245,11 +241,65 @@ def profiled_step(wm, torch, Ud, bd, masses, stream):
             for prec in range(4):
                 n, ms = wm.mg_profile_read(h, k, prec)
                 if n:
-                    a = tot.get((nm, prec), [0, 0.0])
-                    tot[(nm, prec)] = [a[0] + n, a[1] + ms]
+                    nb = wm.mg_profile_bytes(h, k, prec)
+                    a = tot.get((nm, prec), [0, 0.0, 0.0])
+                    tot[(nm, prec)] = [a[0] + n, a[1] + ms, a[2] + nb]
 
     wm.mg_profile(None, (1 << len(wm.KERNEL_CLASS_NAMES)) - 1)
     try:
+        handles_run(collect)
+    finally:
+        wm.mg_profile(None, 0)
+    return tot
+
+
+PREC_NAMES = ["f64", "f32", "f16", "bf16"]
+
+
+def shares_and_roofline(tot, peaks, galerkin_flops=None, inverse_n=None):
+    """Device-time share of every class and the roofline of the dominant one: achieved =
+    algorithmic bytes (each operand once per launch) / summed CUDA-event time of its launches."""
+    all_ms = sum(v[1] for v in tot.values())
+    hbm = peaks.get("hbm_gbs")
+    shares = {}
+    for k, v in sorted(tot.items(), key=lambda kv: -kv[1][1]):
+        e = {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / all_ms, 4)}
+        if v[2] > 0:
+            e["algorithmic_GB"] = round(v[2] / 1e9, 4)
+            e["achieved_GBs"] = round(v[2] / (v[1] / 1e3) / 1e9, 1)
+        shares["%s/%s" % (k[0], PREC_NAMES[k[1]])] = e
+    (top, tprec), (n, ms, nb) = max(tot.items(), key=lambda kv: kv[1][1])
+    avg_s = ms / 1e3 / max(n, 1)
+    roof = {"kernel": "%s/%s" % (top, PREC_NAMES[tprec]), "launches": n, "avg_us": round(avg_s * 1e6, 3),
+            "traffic": None}
+    if nb > 0:
+        ach = nb / n / avg_s / 1e9
+        roof.update(bound="hbm", achieved=round(ach, 1), peak=hbm, unit="GB/s", frac=round(ach / hbm, 4),
+                    algorithmic="%.4g B per launch (mean over %d launches; each operand once per launch)" % (nb / n, n))
+    elif top == "galerkin" and galerkin_flops:
+        ach = galerkin_flops / avg_s / 1e12
+        roof.update(bound="alu", achieved=round(ach, 3), peak=1.196, unit="TFLOP/s (FP64)",
+                    frac=round(ach / 1.196, 4), algorithmic="%.3g FP64 flop per launch" % galerkin_flops)
+    elif top == "inverse" and inverse_n:
+        fl = 8.0 * inverse_n ** 3
+        pk = 74.6 if tprec == 1 else 1.196
+        ach = fl / avg_s / 1e12
+        roof.update(bound="alu", achieved=round(ach, 3), peak=pk, unit="TFLOP/s", frac=round(ach / pk, 4),
+                    algorithmic="Gauss-Jordan, 8 N^3 flop, N = %d" % inverse_n)
+    else:
+        roof.update(bound="latency", achieved=None, peak=None, unit=None, frac=None)
+    return roof, shares
+
+
+def profiled_step(wm, torch, Ud, bd, masses, stream):
+    """One extra step (setup + solve per mass) with the per-launch event profiler on every kernel class.
+
+    Returns the roofline of the dominant class and the device-time share of every class.
+    """
+    p = params(wm, 1)
+    peaks = measured_peaks()
+
+    def run(collect):
         base = wm.mg_setup(Ud, DIMS, masses[-1], p, stream=stream)
         for m in masses:
             h = base if m == masses[-1] else wm.mg_retarget(base, m, stream=stream)
@@ -260,42 +310,12 @@ def profiled_step(wm, torch, Ud, bd, masses, stream):
                 wm.mg_destroy(h)
         collect(base)
         wm.mg_destroy(base)
-    finally:
-        wm.mg_profile(None, 0)
-    all_ms = sum(v[1] for v in tot.values())
-    shares = {"%s/%s" % (k[0], prec_names[k[1]]): {"launches": v[0], "ms": round(v[1], 4),
-                                                    "share": round(v[1] / all_ms, 4)}
-              for k, v in sorted(tot.items(), key=lambda kv: -kv[1][1])}
+
+    tot = class_profile(wm, run, peaks)
     V = int(np.prod(DIMS))
-    peaks = measured_peaks()
-    (top, tprec), (n, ms) = max(tot.items(), key=lambda kv: kv[1][1])
-    avg_s = ms / 1e3 / max(n, 1)
-    roof = {"kernel": "%s/%s" % (top, prec_names[tprec]), "launches": n, "avg_us": round(avg_s * 1e6, 3),
-            "traffic": None}
-    if top == "dslash":
-        bps = {0: 960, 1: 384, 2: 192, 3: 192}[tprec]
-        ach = bps * V / avg_s / 1e9
-        roof.update(bound="hbm", achieved=round(ach, 1), peak=peaks.get("hbm_gbs"), unit="GB/s",
-                    frac=round(ach / peaks.get("hbm_gbs"), 4),
-                    algorithmic="%d B/site x %d sites per launch" % (bps, V))
-    elif top == "galerkin":
-        # per (coarse site, column): 9 directions x (hop on |b| sites, ~170 flop/site,
-        # + 2Nv x 6|b| complex MACs of the projection)
-        bs = int(np.prod(BLOCK))
-        fl = 9 * (bs * 170 + 2 * NV * 6 * bs * 8) * (V // bs) * 2 * NV
-        ach = fl / avg_s / 1e12
-        roof.update(bound="alu", achieved=round(ach, 3), peak=1.196, unit="TFLOP/s (FP64)",
-                    frac=round(ach / 1.196, 4), algorithmic="%.3g FP64 flop per launch" % fl)
-    elif top == "inverse":
-        N = 2 * NV * (V // int(np.prod(BLOCK)))
-        fl = 8.0 * N ** 3
-        ach = fl / avg_s / 1e12
-        roof.update(bound="alu", achieved=round(ach, 3), peak=74.6 if tprec == 1 else 1.196,
-                    unit="TFLOP/s", frac=round(ach / (74.6 if tprec == 1 else 1.196), 4),
-                    algorithmic="Gauss-Jordan, 8 N^3 flop, N = %d" % N)
-    else:
-        roof.update(bound="latency", achieved=None, peak=None, unit=None, frac=None)
-    return roof, shares
+    bs = int(np.prod(BLOCK))
+    gal = 9 * (bs * 170 + 2 * NV * 6 * bs * 8) * (V // bs) * 2 * NV
+    return shares_and_roofline(tot, peaks, galerkin_flops=gal, inverse_n=2 * NV * (V // bs))
 
 
 def measured_peaks():
@@ -481,8 +501,9 @@ def c3_workload(args):
                        "m = -0.8049 + %g, 12 point + 12 Gaussian sources, tol 1e-10" % args.c3_dm}
     res = {}
     for mixed in (1, 0):
+        # the mixed form applies the level-1 stencil to all right-hand sides on tensor cores
         p = wm.mg_default_params(n_levels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 24],
-                                 setup_sweeps=[300, 100], mixed=mixed, seed=7)
+                                 setup_sweeps=[300, 100], mixed=mixed, seed=7, coarse_mma=mixed)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = wm.mg_setup(Ud, C3_DIMS, mass, p, stream=stream)
@@ -509,6 +530,19 @@ def c3_workload(args):
         del h
     out.update(res)
     out["speedup_solve"] = round(res["fp64_single_rhs"]["solve_s"] / res["mixed_multi_rhs"]["solve_s"], 3)
+    # class shares and the dominant class's roofline of the mixed multi-RHS solve (one profiled run)
+    p = wm.mg_default_params(n_levels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 24],
+                             setup_sweeps=[300, 100], mixed=1, seed=7, coarse_mma=1)
+
+    def run(collect):
+        h = wm.mg_setup(Ud, C3_DIMS, mass, p, stream=stream)
+        X = torch.zeros_like(B)
+        wm.mg_solve(h, B, X, TOL, stream=stream)
+        collect(h)
+        wm.mg_destroy(h)
+
+    tot = class_profile(wm, run, measured_peaks())
+    out["roofline"], out["kernel_shares"] = shares_and_roofline(tot, measured_peaks())
     return out
 
 
@@ -522,21 +556,28 @@ def serve_workload(args):
     from paper_0811_4331_gb300 import wilson_mg as wm
     with open(os.path.join(ROOT, "tests", "golden", "mcrit.json")) as f:
         mc = json.load(f)
-    crit = {(8, 8, 8, 8): mc["8x8x8x8_beta6.0_sweeps200_seed0"]["m_crit"],
-            (12, 12, 12, 12): mc.get("12x12x12x12_beta6.0_sweeps200_seed0", {}).get("m_crit", C3_MCRIT),
-            (16, 16, 16, 32): C3_MCRIT}
+    # m_crit of each field from the oracle where it has been computed; otherwise the paper's
+    # 16^3 x 32 value (Sec. 5) with the lightest masses kept 0.03 above it (the stand-in field's own
+    # critical mass is not known to better than that)
+    def crit_of(dims):
+        key = "%dx%dx%dx%d_beta6.0_sweeps200_seed0" % dims
+        return (mc[key]["m_crit"], 0.005) if key in mc else (C3_MCRIT, 0.03)
+
+    crit = {d: crit_of(d) for d in ((8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32))}
     two = wm.mg_default_params(n_levels=2, block=[(4, 4, 4, 4)], nv=[20], setup_sweeps=[300], mixed=1, seed=7)
     three = wm.mg_default_params(n_levels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 24],
-                                 setup_sweeps=[300, 100], mixed=1, seed=7)
+                                 setup_sweeps=[300, 100], mixed=1, seed=7, coarse_mma=1)
     fields = {}
     for dims, p in (((8, 8, 8, 8), two), ((12, 12, 12, 12), two), ((16, 16, 16, 32), three)):
         U = inputs.heatbath_gauge(dims, BETA, HB_SWEEPS, HB_SEED)
-        fields["x".join(map(str, dims))] = (U, dims, crit[dims] + 0.005, p)
+        fields["x".join(map(str, dims))] = (U, dims, crit[dims][0] + crit[dims][1], p)
     names = sorted(fields)
     budget = int(0.5 * torch.cuda.get_device_properties(0).total_memory)
     rng = np.random.default_rng(4)
     out = {"workload": "serving: Poisson arrivals, fields 8^4 / 12^4 / 16^3x32 (beta=6.0 heatbath), masses "
-                       "U[m_crit+0.005, m_crit+0.1], 1-12 Gaussian RHS, tol 1e-10, 4 workers, half of HBM as budget",
+                       "U[m_crit+0.005, m_crit+0.1] (oracle m_crit; else the paper's -0.8049 and U[+0.03, +0.1]), "
+                       "1-12 Gaussian RHS, tol 1e-10, 4 workers, half of HBM as budget",
+           "m_crit": {"x".join(map(str, d)): v[0] for d, v in crit.items()},
            "rates": []}
     srv = serve.SolveServer(fields, None, budget, workers=4)
     for name in names:  # warm the per-field hierarchies (setup once per field)
@@ -551,7 +592,7 @@ def serve_workload(args):
             g = np.random.default_rng(int(rng.integers(1 << 30)))
             shp = (nrhs,) + (dims[3], dims[2], dims[1], dims[0], 4, 3)
             b = g.standard_normal(shp) + 1j * g.standard_normal(shp)
-            m = crit[dims] + float(rng.uniform(0.005, 0.1))
+            m = crit[dims][0] + float(rng.uniform(crit[dims][1], 0.1))
             reqs.append(serve.Request(i, f, m, b, TOL, 0.0))
         st = serve.run_stream(srv, reqs, serve.poisson_arrivals(rate, len(reqs), int(rng.integers(1 << 30))))
         st["rate_per_s"] = rate

@@ -258,7 +258,8 @@ typedef enum {
   MG_K_SETUP = 6,    /* start vectors, block Gram-Schmidt, prolongator columns, copies */
   MG_K_GALERKIN = 7, /* Galerkin build of the coarse stencil */
   MG_K_INVERSE = 8,  /* dense coarsest inverse (the whole elimination as one interval) */
-  MG_K_CLASSES = 9
+  MG_K_GRAM = 9,     /* Gram-Schmidt of the outer GCR (multi-dot + update, both passes as one interval) */
+  MG_K_CLASSES = 10
 } mg_kernel_class;
 
 /* Enable (mask != 0, bit c = class c) or disable the per-launch profiler
@@ -273,6 +274,13 @@ int mg_profile(mg_handle* h, unsigned mask);
  * time (milliseconds) of class `kclass` with storage precision `prec`
  * since the last mg_profile call. */
 int mg_profile_read(mg_handle* h, int kclass, int prec, long long* launches, double* ms);
+
+/* The algorithmic bytes of the same launches: every operand of a profiled
+ * scope counted once (a stencil's matrix or links once per launch, each
+ * right-hand side's vectors once), so bytes / time is the bandwidth that the
+ * scope achieved against its compulsory traffic.  Classes without a count
+ * (setup, Galerkin, inverse) report 0. */
+int mg_profile_bytes(mg_handle* h, int kclass, int prec, double* bytes);
 
 /* Number of kernels this library has launched since it was loaded, over
  * all handles and threads (a monotonic counter). */

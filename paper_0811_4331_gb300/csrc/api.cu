@@ -141,13 +141,16 @@ int ensure_reducer(mg_handle* h, int nrhs) {
 
 // Per-launch event profiler (mg_profile): brackets each launch of a selected
 // kernel class with a pair of events on the handle's stream.
+// Event pair around the launches of one scope, with the scope's algorithmic
+// bytes (each operand read or written once; 0 where not counted).
 struct Prof {
   mg_handle* h;
   bool on;
   size_t idx = 0;
   int key;
-  Prof(mg_handle* hh, int cls, int prec)
-      : h(hh), on(((hh->prof_mask >> cls) & 1u) && !hh->capturing), key(cls * 4 + prec) {
+  double bytes;
+  Prof(mg_handle* hh, int cls, int prec, double nbytes = 0.0)
+      : h(hh), on(((hh->prof_mask >> cls) & 1u) && !hh->capturing), key(cls * 4 + prec), bytes(nbytes) {
     if (!on) return;
     while (h->prof_used + 2 > h->prof_pool.size()) {
       cudaEvent_t e;
@@ -165,7 +168,7 @@ struct Prof {
   ~Prof() {
     if (!on) return;
     cudaEventRecord(h->prof_pool[idx + 1], h->st);
-    h->prof_marks.push_back(std::make_pair(key, idx));
+    h->prof_marks.push_back({key, idx, bytes});
   }
 };
 
@@ -191,16 +194,20 @@ int op_apply(mg_handle* h, int l, int prec, const void* in, void* out, const voi
     d.c = c_;
     d.nrhs = nrhs;
     d.red = h->red.at(slot, 4);
-    Prof pf(h, MG_K_DSLASH, prec);
+    // spinor in and out per right-hand side, y and z where they are other vectors, links once
+    const double sb = 12.0 * a.V * bytes_of(prec);
+    const double lb = 4.0 * a.V * (prec == MG_F64 ? 9 : 6) * bytes_of(prec);
+    Prof pf(h, MG_K_DSLASH, prec, nrhs * sb * (2 + (y && y != in) + (z && z != in && z != y)) + lb);
     LK(launch_wilson(d, h->st));
   } else if (a.cop_mma.p && prec == MG_F32 && nrhs <= 64) {
     // tensor cores: out = a_ A in + c_ y, then the dots in a separate deterministic pass
+    const double vb = (double)a.n() * bytes_of(prec);
     {
-      Prof pf(h, MG_K_COARSE, MG_BF16);
+      Prof pf(h, MG_K_COARSE, MG_BF16, (double)mma_pack_bytes(a.ncomp, a.V) + nrhs * vb * (2 + (y != nullptr)));
       LK(launch_coarse_mma(prec, a.cop_mma.p, in, out, y, a.L, a.ncomp, nrhs, a_, c_, h->st));
     }
     if (z) {
-      Prof pf(h, MG_K_VECTOR, prec);
+      Prof pf(h, MG_K_VECTOR, prec, nrhs * vb * (z == out ? 1 : 2));
       LK(launch_dot(prec, a.n(), nrhs, out, z, h->red.at(slot, 4), h->st));
     }
   } else {
@@ -221,7 +228,9 @@ int op_apply(mg_handle* h, int l, int prec, const void* in, void* out, const voi
     k.c = c_;
     k.nrhs = nrhs;
     k.red = h->red.at(slot, 4);
-    Prof pf(h, MG_K_COARSE, prec);
+    const double vb = (double)a.n() * bytes_of(prec);
+    Prof pf(h, MG_K_COARSE, prec,
+            9.0 * a.ncomp * a.ncomp * a.V * bytes_of(prec) + nrhs * vb * (2 + (y && y != in) + (z && z != in && z != y)));
     LK(launch_coarse_apply(k, h->st));
   }
   return MG_OK;
@@ -244,7 +253,8 @@ int mr_update(mg_handle* h, int l, int prec, void* x_out, const void* x_in, cons
   m.omega = omega;
   m.red = h->red.at(0, 0);
   m.red.result = nullptr;
-  Prof pf(h, MG_K_VECTOR, prec);
+  const int streams = 4 + (x_in != nullptr) + (r_in != r_out && r_in != u && r_in != p);  // u, p, r_in, x_out, r_out
+  Prof pf(h, MG_K_VECTOR, prec, (double)streams * nrhs * m.n * bytes_of(prec));
   LK(launch_mr_update(m, h->st));
   return MG_OK;
 }
@@ -282,8 +292,9 @@ const int kCoarsestRefine = 1;
 // e = X r, then kCoarsestRefine times e += X (r - A e) with the FP64 stencil.
 int coarsest_solve(mg_handle* h, int l, int prec, const void* r, void* e, int nrhs) {
   Level& a = *h->lev[l];
+  const double mvb = (double)a.N() * a.N() * bytes_of(a.inv_prec) + 2.0 * nrhs * a.N() * 16;  // inverse once, x and y
   if (a.inv_prec == MG_F64 && prec == MG_F64) {
-    Prof pf(h, MG_K_COARSEST, prec);
+    Prof pf(h, MG_K_COARSEST, prec, mvb);
     LK(launch_dense_matvec(0, 0, 0, a.N(), a.inv.p, r, e, nrhs, 0, h->st, a.mm_scratch.p));
     return MG_OK;
   }
@@ -297,12 +308,12 @@ int coarsest_solve(mg_handle* h, int l, int prec, const void* r, void* e, int nr
     LK(launch_convert(prec, MG_F64, n, nrhs, r, r64, 1.0, nullptr, 0, 0.0, 0, h->st));
   }
   {
-    Prof pf(h, MG_K_COARSEST, MG_F32);
+    Prof pf(h, MG_K_COARSEST, MG_F32, mvb);
     LK(launch_dense_matvec(a.inv_prec, 0, 0, a.N(), a.inv.p, r64, e64, nrhs, 0, h->st, a.mm_scratch.p));
   }
   for (int it = 0; it < kCoarsestRefine; ++it) {
     RET(op_apply(h, l, MG_F64, e64, t64, r64, -1.0, 1.0, nullptr, 0, nrhs));
-    Prof pf(h, MG_K_COARSEST, MG_F32);
+    Prof pf(h, MG_K_COARSEST, MG_F32, mvb + (double)nrhs * a.N() * 16);
     LK(launch_dense_matvec(a.inv_prec, 0, 0, a.N(), a.inv.p, t64, e64, nrhs, 1, h->st, a.mm_scratch.p));
   }
   Prof pf(h, MG_K_VECTOR, prec);
@@ -385,8 +396,10 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
   RET(mr_steps(h, l, prec, r, e, true, res, h->p.nu_pre, nrhs));
   // restrict, coarse solve, prolong
   const Agg g = agg_of(a);
+  const double pbytes = (double)a.Vc * 2 * a.nv * a.nhalf * a.bsites * bytes_of(prec);  // P once
+  const double fbytes = (double)a.n() * bytes_of(prec) * nrhs, cbytes = (double)h->lev[l + 1]->n() * bytes_of(pc) * nrhs;
   {
-    Prof pf(h, MG_K_RESTRICT, prec);
+    Prof pf(h, MG_K_RESTRICT, prec, pbytes + fbytes + cbytes);
     LK(launch_restrict(prec, prec, pc, g, a.P[prec].p, res, rc, nrhs, h->st));
   }
   if (l + 1 == L - 1) {
@@ -408,7 +421,7 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
     }
   }
   {
-    Prof pf(h, MG_K_PROLONG, prec);
+    Prof pf(h, MG_K_PROLONG, prec, pbytes + fbytes + cbytes);
     LK(launch_prolong(pc, prec, prec, g, a.P[prec].p, ec, xc, nrhs, h->st));
   }
   // alpha = <A x_c|r0> / <A x_c|A x_c>  (Eq. 3.5);  e += alpha x_c, r0 -= alpha A x_c
@@ -1159,16 +1172,25 @@ int mg_profile(mg_handle* h, unsigned mask) {
   return MG_OK;
 }
 
+int mg_profile_bytes(mg_handle* h, int kclass, int prec, double* bytes) {
+  if (!h || !bytes || kclass < 0 || kclass >= MG_K_CLASSES || check_prec(prec)) return MG_EINVAL;
+  double tot = 0.0;
+  for (auto& m : h->prof_marks)
+    if (m.key == kclass * 4 + prec) tot += m.bytes;
+  *bytes = tot;
+  return MG_OK;
+}
+
 int mg_profile_read(mg_handle* h, int kclass, int prec, long long* launches, double* ms) {
   if (!h || kclass < 0 || kclass >= MG_K_CLASSES || check_prec(prec)) return MG_EINVAL;
   CK(cudaStreamSynchronize(h->st));
   long long n = 0;
   double tot = 0.0;
   for (auto& m : h->prof_marks) {
-    if (m.first != kclass * 4 + prec) continue;
-    CK(cudaEventSynchronize(h->prof_pool[m.second + 1]));
+    if (m.key != kclass * 4 + prec) continue;
+    CK(cudaEventSynchronize(h->prof_pool[m.idx + 1]));
     float t = 0.0f;
-    CK(cudaEventElapsedTime(&t, h->prof_pool[m.second], h->prof_pool[m.second + 1]));
+    CK(cudaEventElapsedTime(&t, h->prof_pool[m.idx], h->prof_pool[m.idx + 1]));
     tot += t;
     ++n;
   }
@@ -1300,12 +1322,13 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
           if (!rin || !eout) return MG_ENOMEM;
           // scale the residual to RMS 1/8 per component for 16-bit storage
           const double sig = sqrt((double)n) / 8.0;
+          const double cvb = (double)n * nrhs * (bytes_of(pin) + bytes_of(pf));
           {
-            Prof pf2(h, MG_K_VECTOR, pin);
+            Prof pf2(h, MG_K_VECTOR, pin, cvb);
             LK(launch_convert(pin, pf, n, nrhs, h->gr.p, rin, sig, h->red.slot(slot_gcr_rn() + 2), 4, -0.5, 0, st));
           }
           RET(vcycle_graph(h, rin, eout, nrhs));
-          Prof pf2(h, MG_K_VECTOR, pin);
+          Prof pf2(h, MG_K_VECTOR, pin, cvb);
           LK(launch_convert(pf, pin, n, nrhs, eout, zk, 1.0 / sig, h->red.slot(slot_gcr_rn() + 2), 4, 0.5, 0, st));
         }
         fine += per_cycle;
@@ -1321,7 +1344,8 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
       // whose ||w|| the first pass cut below 1/sqrt(2)
       const double* dots = h->red.slot(slot_gcr_pre());
       if (k > 0) {
-        Prof pf2(h, MG_K_VECTOR, pin);
+        // one pass: the multi-dot reads W_0..W_k-1 and w, the update reads them and r and writes w
+        Prof pf2(h, MG_K_GRAM, pin, (2.0 * k + 4.0) * (double)vbytes);
         for (int pass = 0; pass < 2; ++pass) {
           const double* pre = pass ? h->red.slot(slot_gcr_pre() + 2) : nullptr;
           const double* post = pass ? h->red.slot(slot_gcr_wr() + 2) : nullptr;
@@ -1333,7 +1357,7 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
         dots = h->red.slot(slot_gcr_wr());
       }
       {
-        Prof pf2(h, MG_K_VECTOR, pin);
+        Prof pf2(h, MG_K_VECTOR, pin, 4.0 * (double)vbytes);
         LK(launch_gcr_step(pin, n, nrhs, dots, 4, wk, h->gr.p, h->red.at(slot_gcr_rn() + 2, 4), H, alpha, k,
                            kMaxBasis, st));
       }
@@ -1355,7 +1379,7 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
     }
     // x64 += Z H^-1 alpha (the cycle's correction), then the true residual in FP64
     {
-      Prof pf2(h, MG_K_VECTOR, pin);
+      Prof pf2(h, MG_K_VECTOR, pin, (double)k * vbytes + 2.0 * n * nrhs * 16);
       LK(launch_back_substitute(nrhs, k, kMaxBasis, H, alpha, h->gy.as<double2>(), st));
       LK(launch_zcombine(pin, MG_F64, n, nrhs, k, kMaxBasis, h->gy.as<double2>(), h->gZ.p, n * nrhs, h->gx64.p, st));
     }

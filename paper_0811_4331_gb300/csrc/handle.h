@@ -120,7 +120,12 @@ struct mg_handle {
   unsigned prof_mask = 0;
   std::vector<cudaEvent_t> prof_pool;
   size_t prof_used = 0;
-  std::vector<std::pair<int, size_t>> prof_marks;  // (class * 4 + prec, index of start event)
+  struct ProfMark {
+    int key;       // class * 4 + prec
+    size_t idx;    // index of the start event
+    double bytes;  // algorithmic bytes of the interval (0: not counted)
+  };
+  std::vector<ProfMark> prof_marks;
   // CUDA graphs of the V-cycle, keyed by (nrhs, input, output, buffer generation)
   struct CycleGraph {
     int nrhs;

@@ -101,6 +101,7 @@ def _load():
         "mg_profile": (I, [VP, ctypes.c_uint]),
         "mg_launch_count": (ctypes.c_ulonglong, []),
         "mg_profile_read": (I, [VP, I, I, P(ctypes.c_longlong), P(D)]),
+        "mg_profile_bytes": (I, [VP, I, I, P(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -115,11 +116,12 @@ LIB = _load()
 EXPORTS = ["mg_last_error", "mg_default_params", "mg_setup", "mg_retarget", "mg_destroy", "mg_solve", "dslash_apply",
            "coarse_apply", "restrict_apply", "prolong_apply", "mr_apply", "vcycle_apply", "mg_field_to_internal",
            "mg_field_from_internal", "mg_level_info", "mg_get_prolongator", "mg_get_coarse_op", "mg_footprint",
-           "mg_profile", "mg_profile_read", "mg_launch_count", "mr_apply_noalloc"]
+           "mg_profile", "mg_profile_read", "mg_profile_bytes", "mg_launch_count", "mr_apply_noalloc"]
 
 (MG_K_DSLASH, MG_K_COARSE, MG_K_RESTRICT, MG_K_PROLONG, MG_K_VECTOR, MG_K_COARSEST, MG_K_SETUP, MG_K_GALERKIN,
- MG_K_INVERSE) = range(9)
-KERNEL_CLASS_NAMES = ["dslash", "coarse", "restrict", "prolong", "vector", "coarsest", "setup", "galerkin", "inverse"]
+ MG_K_INVERSE, MG_K_GRAM) = range(10)
+KERNEL_CLASS_NAMES = ["dslash", "coarse", "restrict", "prolong", "vector", "coarsest", "setup", "galerkin", "inverse",
+                      "gram"]
 
 
 def mg_last_error():
@@ -327,6 +329,12 @@ def mg_profile_read(h, kclass, prec):
     ms = ctypes.c_double()
     _check(LIB.mg_profile_read(h.ptr, kclass, prec, ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+def mg_profile_bytes(h, kclass, prec):
+    b = ctypes.c_double()
+    _check(LIB.mg_profile_bytes(h.ptr, kclass, prec, ctypes.byref(b)))
+    return b.value
 
 
 def internal_empty(h, level, prec, nrhs=1, device="cuda"):
