@@ -152,6 +152,12 @@ int mg_setup(mg_handle** h, const double* gauge, int gauge_on_device, const int 
  * not modified and stays valid.  Errors as mg_setup. */
 int mg_retarget(const mg_handle* src, double mass, mg_handle** h, void* stream);
 
+/* mg_retarget for `count` (1..64) masses at once: h[z] gets masses[z].  The
+ * coarsest inverses of all of them are built by one batched elimination
+ * (every pivot step of every matrix in one launch).  On error no handle is
+ * returned (h[z] = NULL). */
+int mg_retarget_batch(const mg_handle* src, const double* masses, int count, mg_handle** h, void* stream);
+
 /* Free every device buffer of `h` (NULL is allowed). */
 int mg_destroy(mg_handle* h);
 
@@ -167,6 +173,22 @@ int mg_destroy(mg_handle* h);
  * MG_ENAN, MG_ECUDA. */
 int mg_solve(mg_handle* h, const double* b, double* x, int nrhs, int on_device, double tol,
              mg_stats* stats, void* stream);
+
+/* Unpreconditioned Krylov solvers on level 0 alone: the methods the paper
+ * measures multigrid against (Secs. 4-5).
+ *   method : MG_KRYLOV_BICGSTAB -- BiCGstab (van der Vorst 1992) on D x = b;
+ *            MG_KRYLOV_CGNR     -- CG on D^+ D x = D^+ b, D^+ = gamma5 D gamma5.
+ *   FP64 throughout on the handle's FP64 links (any handle: the hierarchy is
+ *   not used); one right-hand side after the other; b, x, nrhs, on_device,
+ *   tol, stats as mg_solve (stats.iters = iterations, stats.fine_dslash =
+ *   operator applications); a recursive residual below tol is confirmed by
+ *   the true residual, else the method restarts from it.
+ * Errors: MG_EINVAL, MG_ENOCONV after max_iter iterations (x and stats
+ * filled), MG_ENAN, MG_ECUDA. */
+#define MG_KRYLOV_BICGSTAB 0
+#define MG_KRYLOV_CGNR 1
+int krylov_solve(mg_handle* h, int method, const double* b, double* x, int nrhs, int on_device, double tol,
+                 int max_iter, mg_stats* stats, void* stream);
 
 /* out = D in on level 0 (Sec. 1 operator above) for nrhs internal-layout
  * spinors of precision `prec` (device memory; in and out must not overlap).
@@ -281,6 +303,25 @@ int mg_profile_read(mg_handle* h, int kclass, int prec, long long* launches, dou
  * scope achieved against its compulsory traffic.  Classes without a count
  * (setup, Galerkin, inverse) report 0. */
 int mg_profile_bytes(mg_handle* h, int kclass, int prec, double* bytes);
+
+/* Launch-shape tuner (no counterpart in the paper).  Kernels with several
+ * launch shapes -- the dslash without fused dots (threads per CTA), the
+ * tensor-core coarse stencil and the tensor-core restriction / prolongation
+ * (right-hand sides per CTA) -- are timed once per (kernel, precision, sizes,
+ * right-hand sides) on first use outside graph capture, writing scratch
+ * outputs only, and the fastest shape is kept for the process.  All shapes
+ * of a kernel give bit-identical results, so the tuner changes speed only.
+ * mode: 0 = off (default shapes), 1 = on (the default), 2 = forget every
+ * choice and turn on, 3 / 4 = force the last / first shape of every kernel
+ * (for testing that all shapes agree).  Returns the previous mode, or -1 for
+ * a bad mode. */
+int mg_tune(int mode);
+
+/* Text report of the tuner's choices, one line per key:
+ * "<kernel>|<precision>|<sizes...>|<rhs> <chosen shape> <us of shape 0> ...".
+ * Writes at most cap - 1 characters and a NUL into buf (if buf != NULL and
+ * cap > 0); returns the length of the whole report. */
+int mg_tune_report(char* buf, int cap);
 
 /* Number of kernels this library has launched since it was loaded, over
  * all handles and threads (a monotonic counter). */

@@ -10,6 +10,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -172,6 +174,75 @@ struct Prof {
   }
 };
 
+// ------------------------------------------------------------------ launch-shape tuner
+// Process-wide choice of the fastest launch shape for each (kernel, precision,
+// sizes, right-hand sides).  The candidate shapes of every tuned kernel give
+// bit-identical results (they only regroup right-hand sides or sites over
+// CTAs), so tuning changes speed, never numbers.  On the first launch of a
+// key outside graph capture each shape runs once to warm up and kTuneReps
+// times between two events on the handle's stream, writing scratch outputs
+// only; a shape whose launch fails is skipped.  Mode 0 turns tuning off
+// (default shapes), 1 tunes, and 3 / 4 force the last / first shape of every
+// key (to check that all shapes agree).
+struct TuneEntry {
+  int variant;
+  std::vector<float> us;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneEntry> g_tune;
+int g_tune_mode = 1;
+const int kTuneReps = 3;
+
+template <class F>
+int tuned(mg_handle* h, const std::string& key, int nvar, F&& run) {
+  if (nvar <= 1 || g_tune_mode == 0) return -1;
+  if (g_tune_mode == 3) return nvar - 1;
+  if (g_tune_mode == 4) return 0;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key);
+  if (it != g_tune.end()) return it->second.variant;
+  if (h->capturing) return -1;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1;
+  }
+  std::vector<float> us(nvar, -1.0f);
+  int best = -1;
+  float bt = 0.0f;
+  for (int v = 0; v < nvar; ++v) {
+    if (run(v) != 0) {
+      cudaGetLastError();
+      continue;
+    }
+    bool ok = cudaEventRecord(e0, h->st) == cudaSuccess;
+    for (int r = 0; r < kTuneReps && ok; ++r) ok = run(v) == 0;
+    ok = ok && cudaEventRecord(e1, h->st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = 0.0f;
+    if (!ok || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    us[v] = ms * 1000.0f / kTuneReps;
+    if (best < 0 || us[v] < bt) {
+      best = v;
+      bt = us[v];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g_tune[key] = {best, us};
+  count_launches((unsigned long long)nvar * (kTuneReps + 1));
+  return best;
+}
+
+std::string tkey(const char* kernel, std::initializer_list<long long> v) {
+  std::string k = kernel;
+  for (long long x : v) k += "|" + std::to_string(x);
+  return k;
+}
+
 // out = a_ * (A_l in) + c_ * y; optional dots <out|z>, ||out||^2 into slot.
 int op_apply(mg_handle* h, int l, int prec, const void* in, void* out, const void* y, double a_, double c_,
              const void* z, size_t slot, int nrhs) {
@@ -197,14 +268,30 @@ int op_apply(mg_handle* h, int l, int prec, const void* in, void* out, const voi
     // spinor in and out per right-hand side, y and z where they are other vectors, links once
     const double sb = 12.0 * a.V * bytes_of(prec);
     const double lb = 4.0 * a.V * (prec == MG_F64 ? 9 : 6) * bytes_of(prec);
+    {
+      DevBuf scratch;
+      d.variant = tuned(h, tkey("dslash", {prec, a.L[0], a.L[1], a.L[2], a.L[3], nrhs, y != nullptr, z != nullptr}),
+                        wilson_variants(prec, z != nullptr, nrhs), [&](int v) {
+                          if (!scratch.p && !scratch.ensure((size_t)a.n() * nrhs * bytes_of(prec))) return -1;
+                          DslashCall t = d;
+                          t.out = scratch.p;
+                          t.variant = v;
+                          return launch_wilson(t, h->st);
+                        });
+    }
     Prof pf(h, MG_K_DSLASH, prec, nrhs * sb * (2 + (y && y != in) + (z && z != in && z != y)) + lb);
     LK(launch_wilson(d, h->st));
   } else if (a.cop_mma.p && prec == MG_F32 && nrhs <= 64) {
     // tensor cores: out = a_ A in + c_ y, then the dots in a separate deterministic pass
     const double vb = (double)a.n() * bytes_of(prec);
     {
+      DevBuf scratch;
+      const int var = tuned(h, tkey("coarse_mma", {prec, a.ncomp, a.V, nrhs}), coarse_mma_variants(nrhs), [&](int v) {
+        if (!scratch.p && !scratch.ensure((size_t)vb * nrhs)) return -1;
+        return launch_coarse_mma(prec, a.cop_mma.p, in, scratch.p, y, a.L, a.ncomp, nrhs, a_, c_, h->st, v);
+      });
       Prof pf(h, MG_K_COARSE, MG_BF16, (double)mma_pack_bytes(a.ncomp, a.V) + nrhs * vb * (2 + (y != nullptr)));
-      LK(launch_coarse_mma(prec, a.cop_mma.p, in, out, y, a.L, a.ncomp, nrhs, a_, c_, h->st));
+      LK(launch_coarse_mma(prec, a.cop_mma.p, in, out, y, a.L, a.ncomp, nrhs, a_, c_, h->st, var));
     }
     if (z) {
       Prof pf(h, MG_K_VECTOR, prec, nrhs * vb * (z == out ? 1 : 2));
@@ -398,9 +485,25 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
   const Agg g = agg_of(a);
   const double pbytes = (double)a.Vc * 2 * a.nv * a.nhalf * a.bsites * bytes_of(prec);  // P once
   const double fbytes = (double)a.n() * bytes_of(prec) * nrhs, cbytes = (double)h->lev[l + 1]->n() * bytes_of(pc) * nrhs;
+  const bool xmma = (prec == MG_F16 || prec == MG_BF16) && transfer_mma_ok(g, nrhs);
+  int rvar = -1, pvar = -1;
+  if (xmma) {
+    DevBuf scratch;
+    const size_t need = (size_t)std::max(fbytes, cbytes);
+    rvar = tuned(h, tkey("restrict_mma", {prec, pc, a.nv, a.bsites, a.Vc, nrhs}), transfer_mma_variants(nrhs),
+                 [&](int v) {
+                   if (!scratch.p && !scratch.ensure(need)) return -1;
+                   return launch_restrict(prec, prec, pc, g, a.P[prec].p, res, scratch.p, nrhs, h->st, v);
+                 });
+    pvar = tuned(h, tkey("prolong_mma", {prec, pc, a.nv, a.bsites, a.Vc, nrhs}), transfer_mma_variants(nrhs),
+                 [&](int v) {
+                   if (!scratch.p && !scratch.ensure(need)) return -1;
+                   return launch_prolong(pc, prec, prec, g, a.P[prec].p, rc, scratch.p, nrhs, h->st, v);
+                 });
+  }
   {
     Prof pf(h, MG_K_RESTRICT, prec, pbytes + fbytes + cbytes);
-    LK(launch_restrict(prec, prec, pc, g, a.P[prec].p, res, rc, nrhs, h->st));
+    LK(launch_restrict(prec, prec, pc, g, a.P[prec].p, res, rc, nrhs, h->st, rvar));
   }
   if (l + 1 == L - 1) {
     RET(coarsest_solve(h, l + 1, pc, rc, ec, nrhs));
@@ -422,7 +525,7 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
   }
   {
     Prof pf(h, MG_K_PROLONG, prec, pbytes + fbytes + cbytes);
-    LK(launch_prolong(pc, prec, prec, g, a.P[prec].p, ec, xc, nrhs, h->st));
+    LK(launch_prolong(pc, prec, prec, g, a.P[prec].p, ec, xc, nrhs, h->st, pvar));
   }
   // alpha = <A x_c|r0> / <A x_c|A x_c>  (Eq. 3.5);  e += alpha x_c, r0 -= alpha A x_c
   const size_t sl = slot_level(l);
@@ -542,41 +645,56 @@ int mg_destroy(mg_handle* h) {
 }
 
 // Dense inverse of the coarsest level (FP64, or FP32 refined in FP64 in the mixed form).
-static int build_coarsest(mg_handle* h) {
-  const int Lv = (int)h->lev.size();
+// Dense inverse of the coarsest operator of each handle (Sec. 4: exact
+// coarsest solve), FP64 (plain) or FP32 (mixed).  Handles of one batch share
+// the coarsest geometry (retargets of one hierarchy) and every elimination
+// launch.
+static int build_coarsest_many(mg_handle* const* hs, int count) {
+  mg_handle* h0 = hs[0];
+  const int Lv = (int)h0->lev.size();
   if (Lv < 2) return MG_OK;
-  cudaStream_t st = h->st;
-  Level& c = *h->lev[Lv - 1];
-  const size_t N = c.n();
+  cudaStream_t st = h0->st;
+  const Level& c0 = *h0->lev[Lv - 1];
+  const size_t N = c0.n();
   if (N > 8192) {
     set_error("coarsest level has " + std::to_string(N) + " unknowns; the dense solve takes at most 8192");
     return MG_EINVAL;
   }
-  c.inv_prec = h->p.mixed ? MG_F32 : MG_F64;
-  const size_t eb = bytes_of(c.inv_prec);
+  const int prec = h0->p.mixed ? MG_F32 : MG_F64;
+  const size_t eb = bytes_of(prec);
   DevBuf aug, col, errflag;
-  if (!aug.ensure(N * 2 * N * eb) || !col.ensure(dense_inverse_scratch_bytes(c.inv_prec, (int)N)) ||
-      !c.inv.ensure(N * N * eb) || !errflag.ensure(sizeof(int)) ||
-      !c.mm_scratch.ensure(dense_matvec_scratch_bytes((int)N)))
+  if (!aug.ensure(N * 2 * N * eb * count) || !col.ensure(dense_inverse_scratch_bytes(prec, (int)N) * count) ||
+      !errflag.ensure(sizeof(int) * count))
     return MG_ENOMEM;
-  // the product's tickets sit after the partial tiles, at an offset that depends on N
-  CK(cudaMemsetAsync(c.mm_scratch.p, 0, dense_matvec_scratch_bytes((int)N), st));
-  CK(cudaMemsetAsync(errflag.p, 0, sizeof(int), st));
+  std::vector<const double2*> C(count);
+  std::vector<void*> inv(count);
+  for (int z = 0; z < count; ++z) {
+    Level& c = *hs[z]->lev[Lv - 1];
+    c.inv_prec = prec;
+    if (!c.inv.ensure(N * N * eb) || !c.mm_scratch.ensure(dense_matvec_scratch_bytes((int)N))) return MG_ENOMEM;
+    // the product's tickets sit after the partial tiles, at an offset that depends on N
+    CK(cudaMemsetAsync(c.mm_scratch.p, 0, dense_matvec_scratch_bytes((int)N), st));
+    C[z] = c.cop[MG_F64].as<double2>();
+    inv[z] = c.inv.p;
+  }
+  CK(cudaMemsetAsync(errflag.p, 0, sizeof(int) * count, st));
   {
-    Prof pf(h, MG_K_INVERSE, c.inv_prec);
-    LK(dense_inverse(c.inv_prec, c.cop[MG_F64].as<double2>(), c.L, c.ncomp, aug.p, col.p, errflag.as<int>(), c.inv.p,
-                     st));
+    Prof pf(h0, MG_K_INVERSE, prec);
+    LK(dense_inverse_batch(prec, C.data(), c0.L, c0.ncomp, count, aug.p, col.p, errflag.as<int>(), inv.data(), st));
   }
-  count_launches(N + 2);  // stencil-to-dense, init, one per pivot, finish (one counted by LK)
-  int herr = 0;
-  CK(cudaMemcpyAsync(&herr, errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  count_launches(N + 3 * (size_t)count - 1);  // per matrix: stencil-to-dense, init, finish; one per pivot
+  std::vector<int> herr(count, 0);
+  CK(cudaMemcpyAsync(herr.data(), errflag.p, sizeof(int) * count, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (herr) {
-    set_error("coarsest operator is singular (zero pivot)");
-    return MG_EINVAL;
-  }
+  for (int z = 0; z < count; ++z)
+    if (herr[z]) {
+      set_error("coarsest operator is singular (zero pivot)");
+      return MG_EINVAL;
+    }
   return MG_OK;
 }
+
+static int build_coarsest(mg_handle* h) { return build_coarsest_many(&h, 1); }
 
 // ------------------------------------------------------------------ setup pieces
 // Geometry of the aggregation of level l into level l+1.
@@ -915,7 +1033,7 @@ int mg_setup(mg_handle** hout, const double* gauge, int gauge_on_device, const i
   return MG_OK;
 }
 
-static int retarget_impl(const mg_handle* src, mg_handle* h) {
+static int retarget_impl(const mg_handle* src, mg_handle* h, bool coarsest = true) {
   cudaStream_t st = h->st;
   const double delta = h->mass - src->mass;
   for (size_t l = 0; l < src->lev.size(); ++l) {
@@ -957,7 +1075,7 @@ static int retarget_impl(const mg_handle* src, mg_handle* h) {
     }
   }
   RET(ensure_reducer(h, 1));
-  RET(build_coarsest(h));
+  if (coarsest) RET(build_coarsest(h));
   CK(cudaStreamSynchronize(st));
   return MG_OK;
 }
@@ -990,6 +1108,45 @@ int mg_retarget(const mg_handle* src, double mass, mg_handle** hout, void* strea
     return rc;
   }
   *hout = h;
+  return MG_OK;
+}
+
+int mg_retarget_batch(const mg_handle* src, const double* masses, int count, mg_handle** hout, void* stream) {
+  if (!hout || !masses || count < 1 || count > 64) {
+    set_error("mg_retarget_batch: bad argument");
+    return MG_EINVAL;
+  }
+  for (int z = 0; z < count; ++z) hout[z] = nullptr;
+  if (!src) {
+    set_error("mg_retarget_batch: null handle");
+    return MG_EINVAL;
+  }
+  std::vector<mg_handle*> hs;
+  auto fail = [&](int rc) {
+    for (mg_handle* x : hs) mg_destroy(x);
+    return rc;
+  };
+  if (src->st && src->st != (cudaStream_t)stream) cudaStreamSynchronize(src->st);
+  for (int z = 0; z < count; ++z) {
+    mg_handle* h = new mg_handle();
+    h->p = src->p;
+    h->mass = masses[z];
+    for (int m = 0; m < 4; ++m) h->dims[m] = src->dims[m];
+    h->st = (cudaStream_t)stream;
+    h->use_graphs = src->use_graphs;
+    h->prof_mask = __atomic_load_n(&g_default_prof_mask, __ATOMIC_RELAXED);
+    hs.push_back(h);
+    if (cudaMallocHost((void**)&h->host_slots, slot_total() * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("pinned host allocation failed");
+      return fail(MG_ENOMEM);
+    }
+    const int rc = retarget_impl(src, h, false);
+    if (rc != MG_OK) return fail(rc);
+  }
+  const int rc = build_coarsest_many(hs.data(), count);
+  if (rc != MG_OK) return fail(rc);
+  for (int z = 0; z < count; ++z) hout[z] = hs[z];
   return MG_OK;
 }
 
@@ -1159,6 +1316,35 @@ int mg_get_coarse_op(mg_handle* h, int level, double* out) {
 }
 
 unsigned long long mg_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+int mg_tune(int mode) {
+  if (mode < 0 || mode > 4) return -1;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const int prev = g_tune_mode;
+  if (mode == 2) {
+    g_tune.clear();
+    g_tune_mode = 1;
+  } else {
+    g_tune_mode = mode;
+  }
+  return prev;
+}
+
+int mg_tune_report(char* buf, int cap) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::string r;
+  for (auto& kv : g_tune) {
+    r += kv.first + " " + std::to_string(kv.second.variant);
+    for (float u : kv.second.us) r += " " + std::to_string(u);
+    r += "\n";
+  }
+  if (buf && cap > 0) {
+    const size_t n = std::min(r.size(), (size_t)cap - 1);
+    memcpy(buf, r.data(), n);
+    buf[n] = 0;
+  }
+  return (int)r.size();
+}
 
 int mg_profile(mg_handle* h, unsigned mask) {
   if (!h) {
@@ -1424,6 +1610,241 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
 }
 
 }  // namespace
+
+// ====================================================================== Krylov baselines
+namespace {
+
+// D^+ v = gamma5 D gamma5 v (gamma5-Hermiticity, Sec. 1) on level 0, FP64:
+// components 6..11 (spins 2 and 3) change sign before and after the stencil.
+int dslash_dag(mg_handle* h, const void* in, void* out, void* tmp) {
+  Level& f = *h->lev[0];
+  const size_t half = (size_t)6 * f.V;
+  CK(cudaMemcpyAsync(tmp, in, half * 16, cudaMemcpyDeviceToDevice, h->st));
+  LK(launch_convert(MG_F64, MG_F64, half, 1, (const char*)in + half * 16, (char*)tmp + half * 16, -1.0, nullptr, 0,
+                    0.0, 0, h->st));
+  RET(op_apply(h, 0, MG_F64, tmp, out, nullptr, 1.0, 0.0, nullptr, 0, 1));
+  LK(launch_convert(MG_F64, MG_F64, half, 1, (char*)out + half * 16, (char*)out + half * 16, -1.0, nullptr, 0, 0.0,
+                    0, h->st));
+  return MG_OK;
+}
+
+struct Cx {
+  double re, im;
+};
+inline Cx cdiv(Cx a, Cx b) {
+  const double d = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+inline Cx cmul(Cx a, Cx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+
+// out = c0 x0 + c1 x1 + c2 x2, with <w|out>, ||out||^2 into slot (w optional)
+int lincomb(mg_handle* h, double2* out, std::initializer_list<std::pair<const void*, Cx>> terms, const void* w,
+            size_t slot) {
+  LinComb L;
+  L.out = out;
+  L.w = (const double2*)w;
+  int t = 0;
+  for (auto& tc : terms) {
+    L.x[t] = (const double2*)tc.first;
+    L.c[t] = make_double2(tc.second.re, tc.second.im);
+    ++t;
+  }
+  for (; t < 3; ++t) {
+    L.x[t] = nullptr;
+    L.c[t] = make_double2(0.0, 0.0);
+  }
+  const size_t n = h->lev[0]->n();
+  Prof pf(h, MG_K_VECTOR, MG_F64, (double)n * 16 * (terms.size() + 1 + (w != nullptr)));
+  LK(launch_lincomb(n, L, h->red.at(slot, 4), h->st));
+  return MG_OK;
+}
+
+// <a|b>, ||a||^2, ||b||^2 of two FP64 level-0 vectors, read back
+int dot3(mg_handle* h, const void* a, const void* b, Cx* ab, double* aa, double* bb) {
+  const size_t n = h->lev[0]->n();
+  {
+    Prof pf(h, MG_K_VECTOR, MG_F64, (double)n * 16 * (a == b ? 1 : 2));
+    LK(launch_dot(MG_F64, n, 1, a, b, h->red.at(slot_misc(), 4), h->st));
+  }
+  RET(read_slots(h, slot_misc(), 4));
+  const double* s = h->host_slots;
+  if (ab) *ab = {s[0], s[1]};
+  if (aa) *aa = s[2];
+  if (bb) *bb = s[3];
+  return MG_OK;
+}
+
+int krylov_one(mg_handle* h, int method, double2* b, double2* x, double tol, int max_iter, mg_stats* st) {
+  const size_t n = h->lev[0]->n(), vb = n * 16;
+  DevBuf buf;
+  if (!buf.ensure(vb * 6)) return MG_ENOMEM;
+  double2* r = buf.as<double2>();
+  double2* v1 = r + n;  // BiCGstab: rhat | CGNR: z
+  double2* v2 = r + 2 * n;  // p
+  double2* v3 = r + 3 * n;  // v | q
+  double2* v4 = r + 4 * n;  // s | D^+ scratch
+  double2* v5 = r + 5 * n;  // t
+  long long mv = 0;
+  int iters = 0;
+  double bb = 0.0, rr = 0.0;
+  RET(dot3(h, b, b, nullptr, &bb, nullptr));
+  const double bn = sqrt(bb);
+  if (!(bn > 0.0)) {
+    set_error("krylov_solve: zero right-hand side");
+    return MG_EINVAL;
+  }
+  int status = MG_ENOCONV;
+  const size_t sl = slot_misc() + 4;
+  while (iters < max_iter) {
+    RET(op_apply(h, 0, MG_F64, x, r, b, -1.0, 1.0, nullptr, 0, 1));  // r = b - D x
+    ++mv;
+    RET(dot3(h, r, r, nullptr, &rr, nullptr));
+    if (!isfinite(rr)) {
+      set_error("krylov_solve: residual is not finite");
+      return MG_ENAN;
+    }
+    if (sqrt(rr) <= tol * bn) {
+      status = MG_OK;
+      break;
+    }
+    if (method == MG_KRYLOV_BICGSTAB) {
+      CK(cudaMemcpyAsync(v1, r, vb, cudaMemcpyDeviceToDevice, h->st));  // shadow residual
+      CK(cudaMemsetAsync(v2, 0, vb, h->st));
+      CK(cudaMemsetAsync(v3, 0, vb, h->st));
+      Cx rho = {1, 0}, alpha = {1, 0}, omega = {1, 0}, rho_new = {rr, 0};
+      while (iters < max_iter) {
+        const Cx beta = cmul(cdiv(rho_new, rho), cdiv(alpha, omega));
+        const Cx bo = cmul(beta, omega);
+        RET(lincomb(h, v2, {{r, {1, 0}}, {v2, beta}, {v3, {-bo.re, -bo.im}}}, nullptr, sl));  // p
+        RET(op_apply(h, 0, MG_F64, v2, v3, nullptr, 1.0, 0.0, nullptr, 0, 1));              // v = D p
+        ++mv;
+        Cx rv;
+        RET(dot3(h, v1, v3, &rv, nullptr, nullptr));
+        alpha = cdiv(rho_new, rv);
+        RET(lincomb(h, v4, {{r, {1, 0}}, {v3, {-alpha.re, -alpha.im}}}, v1, sl));  // s = r - alpha v
+        RET(read_slots(h, sl, 4));
+        ++iters;
+        if (sqrt(h->host_slots[2]) <= tol * bn) {  // converged on the half step
+          RET(lincomb(h, x, {{x, {1, 0}}, {v2, alpha}}, nullptr, sl));
+          break;
+        }
+        RET(op_apply(h, 0, MG_F64, v4, v5, nullptr, 1.0, 0.0, nullptr, 0, 1));  // t = D s
+        ++mv;
+        Cx ts;
+        double tt = 0.0;
+        RET(dot3(h, v5, v4, &ts, &tt, nullptr));
+        omega = {ts.re / tt, ts.im / tt};
+        RET(lincomb(h, x, {{x, {1, 0}}, {v2, alpha}, {v4, omega}}, nullptr, sl));          // x += alpha p + omega s
+        RET(lincomb(h, r, {{v4, {1, 0}}, {v5, {-omega.re, -omega.im}}}, v1, sl));          // r = s - omega t
+        RET(read_slots(h, sl, 4));
+        rho = rho_new;
+        rho_new = {h->host_slots[0], h->host_slots[1]};
+        const double rn = sqrt(h->host_slots[2]);
+        if (!isfinite(rn)) {
+          set_error("krylov_solve: residual is not finite");
+          return MG_ENAN;
+        }
+        if (rn <= tol * bn) break;
+      }
+    } else {
+      RET(dslash_dag(h, r, v1, v4));  // z = D^+ r
+      ++mv;
+      CK(cudaMemcpyAsync(v2, v1, vb, cudaMemcpyDeviceToDevice, h->st));
+      double zz = 0.0;
+      RET(dot3(h, v1, v1, nullptr, &zz, nullptr));
+      while (iters < max_iter) {
+        RET(op_apply(h, 0, MG_F64, v2, v3, nullptr, 1.0, 0.0, nullptr, 0, 1));  // q = D p
+        ++mv;
+        double qq = 0.0;
+        RET(dot3(h, v3, v3, nullptr, &qq, nullptr));
+        const double a = zz / qq;
+        RET(lincomb(h, x, {{x, {1, 0}}, {v2, {a, 0}}}, nullptr, sl));
+        RET(lincomb(h, r, {{r, {1, 0}}, {v3, {-a, 0}}}, r, sl));
+        RET(read_slots(h, sl, 4));
+        ++iters;
+        const double rn = sqrt(h->host_slots[2]);
+        if (!isfinite(rn)) {
+          set_error("krylov_solve: residual is not finite");
+          return MG_ENAN;
+        }
+        if (rn <= tol * bn) break;
+        RET(dslash_dag(h, r, v1, v4));
+        ++mv;
+        double zn = 0.0;
+        RET(dot3(h, v1, v1, nullptr, &zn, nullptr));
+        RET(lincomb(h, v2, {{v1, {1, 0}}, {v2, {zn / zz, 0}}}, nullptr, sl));
+        zz = zn;
+      }
+    }
+  }
+  if (status != MG_OK) {  // the true residual at exit
+    RET(op_apply(h, 0, MG_F64, x, r, b, -1.0, 1.0, nullptr, 0, 1));
+    ++mv;
+    RET(dot3(h, r, r, nullptr, &rr, nullptr));
+    if (sqrt(rr) <= tol * bn) status = MG_OK;
+  }
+  if (st) {
+    st->iters = iters;
+    st->restarts = 0;
+    st->reliable_updates = 0;
+    st->fine_dslash = mv;
+    st->fine_dslash_f64 = mv;
+    st->true_rel_residual = sqrt(rr) / bn;
+  }
+  return status;
+}
+
+}  // namespace
+
+extern "C" int krylov_solve(mg_handle* h, int method, const double* b_ext, double* x_ext, int nrhs, int on_device,
+                            double tol, int max_iter, mg_stats* stats, void* stream) {
+  if (!h || !b_ext || !x_ext || nrhs < 1 || !(tol > 0.0) || max_iter < 1 ||
+      (method != MG_KRYLOV_BICGSTAB && method != MG_KRYLOV_CGNR) || !h->lev[0]->links[MG_F64].p) {
+    set_error("krylov_solve: bad argument");
+    return MG_EINVAL;
+  }
+  cudaStream_t keep = h->st;
+  h->st = (cudaStream_t)stream;
+  Level& f = *h->lev[0];
+  const size_t n = f.n(), vb = n * 16;
+  int rc = MG_OK;
+  DevBuf bx, stage;
+  if (!bx.ensure(vb * 2 * nrhs) || (!on_device && !stage.ensure(vb * 2 * nrhs))) {
+    h->st = keep;
+    return MG_ENOMEM;
+  }
+  auto body = [&]() -> int {
+    RET(ensure_reducer(h, 1));
+    const void* bs = b_ext;
+    const void* xs = x_ext;
+    if (!on_device) {
+      CK(cudaMemcpyAsync(stage.p, b_ext, vb * nrhs, cudaMemcpyHostToDevice, h->st));
+      CK(cudaMemcpyAsync((char*)stage.p + vb * nrhs, x_ext, vb * nrhs, cudaMemcpyHostToDevice, h->st));
+      bs = stage.p;
+      xs = (char*)stage.p + vb * nrhs;
+    }
+    double2* B = bx.as<double2>();
+    double2* X = B + n * nrhs;
+    LK(launch_ext_to_int(MG_F64, 12, f.V, nrhs, bs, B, h->st));
+    LK(launch_ext_to_int(MG_F64, 12, f.V, nrhs, xs, X, h->st));
+    int worst = MG_OK;
+    for (int r = 0; r < nrhs; ++r) {
+      auto t0 = std::chrono::steady_clock::now();
+      const int s = krylov_one(h, method, B + n * r, X + n * r, tol, max_iter, stats ? stats + r : nullptr);
+      if (s != MG_OK && s != MG_ENOCONV) return s;
+      if (s == MG_ENOCONV) worst = s;
+      if (stats) stats[r].solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    void* dst = on_device ? (void*)x_ext : stage.p;
+    LK(launch_int_to_ext(MG_F64, 12, f.V, nrhs, X, dst, h->st));
+    if (!on_device) CK(cudaMemcpyAsync(x_ext, stage.p, vb * nrhs, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return worst;
+  };
+  rc = body();
+  h->st = keep;
+  return rc;
+}
 
 extern "C" int mg_solve(mg_handle* h, const double* b, double* x, int nrhs, int on_device, double tol,
                         mg_stats* stats, void* stream) {

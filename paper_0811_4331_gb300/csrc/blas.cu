@@ -63,13 +63,77 @@ __global__ void __launch_bounds__(kVecThreads) mr_update_kernel(const MrUpdate m
   if (m.red.result) grid_reduce<1, kVecThreads, R>(red, m.red, rhs);
 }
 
+// 16-bit storage: a thread moves two complex numbers per access (8-byte
+// loads and stores instead of 4-byte ones; the per-element work is the same).
+template <typename S>
+struct __align__(8) Pair16 {
+  S a, b;
+};
+
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads) mr_update2_kernel(const MrUpdate m) {
+  typedef Pair16<S> P2;
+  const int rhs = blockIdx.y;
+  const double* d = m.dots + (size_t)rhs * m.dstride;
+  const double den = d[2];
+  double ar = 0.0, ai = 0.0;
+  if (den > 0.0 && isfinite(den)) {
+    ar = m.omega * d[0] / den;
+    ai = m.omega * d[1] / den;
+  }
+  const cx<float> alpha = mk<float>((float)ar, (float)ai);
+  const size_t off = (size_t)rhs * m.n / 2;
+  P2* xo = (P2*)m.x_out + off;
+  const P2* xi = m.x_in ? (const P2*)m.x_in + off : nullptr;
+  const P2* u = (const P2*)m.u + off;
+  P2* ro = (P2*)m.r_out + off;
+  const P2* ri = (const P2*)m.r_in + off;
+  const P2* p = (const P2*)m.p + off;
+  const unsigned n2 = (unsigned)(m.n / 2);
+  float acc = 0.f;
+  for (unsigned i = blockIdx.x * kVecThreads + threadIdx.x; i < n2; i += gridDim.x * kVecThreads) {
+    const P2 uu = u[i], rr = ri[i], pp = p[i];
+    P2 xx;
+    if (xi) xx = xi[i];
+    cx<float> x0 = xi ? ldc<float>(&xx.a, 0) : zero<float>(), x1 = xi ? ldc<float>(&xx.b, 0) : zero<float>();
+    x0 = cfma(alpha, ldc<float>(&uu.a, 0), x0);
+    x1 = cfma(alpha, ldc<float>(&uu.b, 0), x1);
+    const cx<float> r0 = ldc<float>(&rr.a, 0) - alpha * ldc<float>(&pp.a, 0);
+    const cx<float> r1 = ldc<float>(&rr.b, 0) - alpha * ldc<float>(&pp.b, 0);
+    P2 xw, rw;
+    stc(&xw.a, 0, x0);
+    stc(&xw.b, 0, x1);
+    stc(&rw.a, 0, r0);
+    stc(&rw.b, 0, r1);
+    xo[i] = xw;
+    ro[i] = rw;
+    acc += norm2(as_stored<S>(r0)) + norm2(as_stored<S>(r1));
+  }
+  float red[1] = {acc};
+  if (m.red.result) grid_reduce<1, kVecThreads, float>(red, m.red, rhs);
+}
+
 int launch_mr_update(const MrUpdate& m, cudaStream_t st) {
   dim3 grid(vec_blocks(m.n), m.nrhs);
+  auto al8 = [](const void* q) { return ((uintptr_t)q & 7u) == 0; };
+  const bool pairs = (m.prec == 2 || m.prec == 3) && m.n % 2 == 0 && m.n / 2 < (1u << 31) && al8(m.x_out) &&
+                     al8(m.x_in) && al8(m.u) && al8(m.r_out) && al8(m.r_in) && al8(m.p);
+  if (pairs) grid.x = vec_blocks(m.n / 2);
   switch (m.prec) {
     case 0: mr_update_kernel<double2><<<grid, kVecThreads, 0, st>>>(m); break;
     case 1: mr_update_kernel<float2><<<grid, kVecThreads, 0, st>>>(m); break;
-    case 2: mr_update_kernel<__half2><<<grid, kVecThreads, 0, st>>>(m); break;
-    case 3: mr_update_kernel<__nv_bfloat162><<<grid, kVecThreads, 0, st>>>(m); break;
+    case 2:
+      if (pairs)
+        mr_update2_kernel<__half2><<<grid, kVecThreads, 0, st>>>(m);
+      else
+        mr_update_kernel<__half2><<<grid, kVecThreads, 0, st>>>(m);
+      break;
+    case 3:
+      if (pairs)
+        mr_update2_kernel<__nv_bfloat162><<<grid, kVecThreads, 0, st>>>(m);
+      else
+        mr_update_kernel<__nv_bfloat162><<<grid, kVecThreads, 0, st>>>(m);
+      break;
     default: return -1;
   }
   return launched() ? 0 : -1;
@@ -488,6 +552,33 @@ int launch_zcombine(int zprec, int xprec, size_t n, int nrhs, int k, int kmax, c
                                                                    (double2*)x);
   else
     return -1;
+  return launched() ? 0 : -1;
+}
+
+// ------------------------------------------------------------------ Krylov baselines
+// out = c0 x0 + c1 x1 + c2 x2 (complex host coefficients, FP64; unused terms
+// have a null x; out may be one of the x), with <w|out> and ||out||^2
+// reduced when w is given (lane 0, 3 values).
+__global__ void __launch_bounds__(kVecThreads) lincomb_kernel(size_t n, LinComb L, RedArgs ra) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
+    cx<double> v = zero<double>();
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+      if (L.x[t]) v = cfma(mk<double>(L.c[t].x, L.c[t].y), ldc<double>(L.x[t], i), v);
+    stc(L.out, i, v);
+    if (L.w) {
+      const cx<double> d = cmul_conj(ldc<double>(L.w, i), v);
+      acc[0] += d.re;
+      acc[1] += d.im;
+      acc[2] += norm2(v);
+    }
+  }
+  if (L.w) grid_reduce<3, kVecThreads, double>(acc, ra, 0);
+}
+
+int launch_lincomb(size_t n, const LinComb& L, RedArgs red, cudaStream_t st) {
+  lincomb_kernel<<<red_blocks(n), kVecThreads, 0, st>>>(n, L, red);
   return launched() ? 0 : -1;
 }
 

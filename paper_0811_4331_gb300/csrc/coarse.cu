@@ -240,10 +240,10 @@ static int prolong_t(const Agg& g, const void* P, const void* in, void* out, int
 
 // Supported (vector-in, P, vector-out) precision triples.
 int launch_restrict(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
-                    cudaStream_t st) {
+                    cudaStream_t st, int variant) {
   // several right-hand sides with 16-bit vectors and P: tensor cores, P read once
   if ((pin == 2 || pin == 3) && pP == pin && (pout == 1 || pout == pin) && transfer_mma_ok(g, nrhs))
-    return launch_restrict_mma(pin, pP, pout, g, P, in, out, nrhs, st);
+    return launch_restrict_mma(pin, pP, pout, g, P, in, out, nrhs, st, variant);
   if (pin == 0 && pP == 0 && pout == 0) return restrict_t<double2, double2, double2>(g, P, in, out, nrhs, st);
   if (pin == 1 && pP == 1 && pout == 1) return restrict_t<float2, float2, float2>(g, P, in, out, nrhs, st);
   if (pin == 2 && pP == 2 && pout == 1) return restrict_t<__half2, __half2, float2>(g, P, in, out, nrhs, st);
@@ -256,9 +256,9 @@ int launch_restrict(int pin, int pP, int pout, const Agg& g, const void* P, cons
 }
 
 int launch_prolong(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
-                   cudaStream_t st) {
+                   cudaStream_t st, int variant) {
   if ((pP == 2 || pP == 3) && pout == pP && (pin == 1 || pin == pP) && transfer_mma_ok(g, nrhs))
-    return launch_prolong_mma(pin, pP, pout, g, P, in, out, nrhs, st);
+    return launch_prolong_mma(pin, pP, pout, g, P, in, out, nrhs, st, variant);
   if (pin == 0 && pP == 0 && pout == 0) return prolong_t<double2, double2, double2>(g, P, in, out, nrhs, st);
   if (pin == 1 && pP == 1 && pout == 1) return prolong_t<float2, float2, float2>(g, P, in, out, nrhs, st);
   if (pin == 1 && pP == 2 && pout == 2) return prolong_t<float2, __half2, __half2>(g, P, in, out, nrhs, st);
@@ -350,11 +350,21 @@ __global__ void gj_init_kernel(const T* aug, int N, T* col0, unsigned long long*
   if ((threadIdx.x & 31) == 0 && best) atomicMax(keys, best);
 }
 
-// grid = (ceil((2N - k) / 256), N): block row = matrix row i, columns k .. 2N-1.
+// grid = (ceil((2N - k) / 256), N, batch): block row = matrix row i, columns
+// k .. 2N-1, blockIdx.z = the matrix of a batch (independent eliminations
+// that share the launches).  Per matrix z: aug at aug0 + z N 2N, column
+// snapshots cols0 + z 2N (current (k & 1), next), pivot keys keys0 + z (N+1),
+// used-row flags used0 + z N, error flag err0 + z.
 template <typename T>
-__global__ void gj_step_kernel(T* aug, int N, int k, const T* colk, T* colnext, int* used,
-                               unsigned long long* keys, int* err) {
+__global__ void gj_step_kernel(T* aug0, int N, int k, T* cols0, int* used0, unsigned long long* keys0, int* err0) {
   typedef typename Store<T>::R R;
+  const int z = blockIdx.z;
+  T* aug = aug0 + (size_t)z * N * 2 * N;
+  const T* colk = cols0 + (size_t)z * 2 * N + (size_t)(k & 1) * N;
+  T* colnext = cols0 + (size_t)z * 2 * N + (size_t)((k + 1) & 1) * N;
+  int* used = used0 + (size_t)z * N;
+  unsigned long long* keys = keys0 + (size_t)z * (N + 1);
+  int* err = err0 + z;
   if (*err) return;
   const int i = blockIdx.y;
   const int j = k + blockIdx.x * blockDim.x + threadIdx.x;
@@ -410,37 +420,46 @@ static unsigned grid_for(size_t tot, size_t cap) {
 }
 
 template <typename T>
-static int dense_inverse_t(const double2* C, const int L[4], int n, T* aug, T* cols, int* err, T* inv,
-                           unsigned long long* keys, int* used, cudaStream_t st) {
+static int dense_inverse_t(const double2* const* C, const int L[4], int n, int batch, T* aug, char* sc, int* err,
+                           void* const* inv, cudaStream_t st) {
   const int V = L[0] * L[1] * L[2] * L[3];
   const int N = n * V;
-  stencil_to_dense_kernel<T><<<grid_for((size_t)N * 2 * N, 8192), 256, 0, st>>>(C, L[0], L[1], L[2], L[3], n, aug);
-  cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (N + 1), st);
-  cudaMemsetAsync(used, 0, sizeof(int) * N, st);
-  gj_init_kernel<T><<<grid_for(N, 1024), 256, 0, st>>>(aug, N, cols, keys);
+  const size_t nn2 = (size_t)N * 2 * N;
+  T* cols = (T*)sc;
+  unsigned long long* keys = (unsigned long long*)(sc + (size_t)batch * 2 * N * sizeof(T));
+  int* used = (int*)(keys + (size_t)batch * (N + 1));
+  cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (N + 1) * batch, st);
+  cudaMemsetAsync(used, 0, sizeof(int) * N * batch, st);
+  for (int z = 0; z < batch; ++z) {
+    stencil_to_dense_kernel<T><<<grid_for(nn2, 8192), 256, 0, st>>>(C[z], L[0], L[1], L[2], L[3], n, aug + z * nn2);
+    gj_init_kernel<T><<<grid_for(N, 1024), 256, 0, st>>>(aug + z * nn2, N, cols + (size_t)z * 2 * N,
+                                                         keys + (size_t)z * (N + 1));
+  }
   if (!launched()) return -1;
   for (int k = 0; k < N; ++k) {
-    const T* colk = cols + (size_t)(k & 1) * N;
-    T* colnext = cols + (size_t)((k + 1) & 1) * N;
-    const dim3 grid((unsigned)((2 * N - k + 255) / 256), (unsigned)N);
-    gj_step_kernel<T><<<grid, 256, 0, st>>>(aug, N, k, colk, colnext, used, keys, err);
+    const dim3 grid((unsigned)((2 * N - k + 255) / 256), (unsigned)N, (unsigned)batch);
+    gj_step_kernel<T><<<grid, 256, 0, st>>>(aug, N, k, cols, used, keys, err);
   }
-  gj_finish_kernel<T><<<grid_for((size_t)N * N, 8192), 256, 0, st>>>(aug, N, keys, inv);
+  for (int z = 0; z < batch; ++z)
+    gj_finish_kernel<T><<<grid_for((size_t)N * N, 8192), 256, 0, st>>>(aug + z * nn2, N, keys + (size_t)z * (N + 1),
+                                                                      (T*)inv[z]);
   return launched() ? 0 : -1;
+}
+
+int dense_inverse_batch(int prec, const double2* const* C, const int L[4], int n, int batch, void* aug, void* scratch,
+                        int* err, void* const* inv, cudaStream_t st) {
+  // scratch: per matrix two column snapshots [2][N] of the element type, then N + 1 pivot keys per
+  // matrix, then N used-row flags per matrix
+  if (batch < 1) return -1;
+  if (prec == 0) return dense_inverse_t<double2>(C, L, n, batch, (double2*)aug, (char*)scratch, err, inv, st);
+  if (prec == 1) return dense_inverse_t<float2>(C, L, n, batch, (float2*)aug, (char*)scratch, err, inv, st);
+  return -1;
 }
 
 int dense_inverse(int prec, const double2* C, const int L[4], int n, void* aug, void* scratch, int* err, void* inv,
                   cudaStream_t st) {
-  // scratch: two column snapshots [2][N] of the element type, N + 1 pivot keys, N used-row flags
-  const int N = n * L[0] * L[1] * L[2] * L[3];
-  const size_t eb = prec == 0 ? 16 : 8;
-  char* sc = (char*)scratch;
-  unsigned long long* keys = (unsigned long long*)(sc + 2 * (size_t)N * eb);
-  int* used = (int*)(keys + N + 1);
-  if (prec == 0)
-    return dense_inverse_t<double2>(C, L, n, (double2*)aug, (double2*)sc, err, (double2*)inv, keys, used, st);
-  if (prec == 1) return dense_inverse_t<float2>(C, L, n, (float2*)aug, (float2*)sc, err, (float2*)inv, keys, used, st);
-  return -1;
+  void* invs[1] = {inv};
+  return dense_inverse_batch(prec, &C, L, n, 1, aug, scratch, err, invs, st);
 }
 
 size_t dense_inverse_scratch_bytes(int prec, int N) {

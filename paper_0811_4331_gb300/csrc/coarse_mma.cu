@@ -99,6 +99,7 @@ __global__ void coarse_mma_kernel(const uint4* Cf, const S* in, S* out, const S*
   const int L[4] = {L0, L1, L2, L3};
   const int V = L0 * L1 * L2 * L3;
   const int B = blockIdx.x;
+  const int r0 = blockIdx.y * NT8 * 8;  // first right-hand side of this CTA (launch-shape split)
   const int Rpad = NT8 * 8;
   const int T = npad / 16;
   const int KW = 2 * npad;  // one neighbour's row of Ys: re then im
@@ -108,8 +109,8 @@ __global__ void coarse_mma_kernel(const uint4* Cf, const S* in, S* out, const S*
   for (int e = threadIdx.x; e < 9 * Rpad * npad; e += blockDim.x) {
     const int j = e % npad, r = (e / npad) % Rpad, d = e / (npad * Rpad);
     float re = 0.f, im = 0.f;
-    if (j < n && r < R) {
-      const cx<float> v = ldc<float>(in, ((size_t)r * n + j) * V + neighbor(cB, L, d));
+    if (j < n && r0 + r < R) {
+      const cx<float> v = ldc<float>(in, ((size_t)(r0 + r) * n + j) * V + neighbor(cB, L, d));
       re = v.re;
       im = v.im;
     }
@@ -154,7 +155,7 @@ __global__ void coarse_mma_kernel(const uint4* Cf, const S* in, S* out, const S*
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int i = t * 16 + gid + (k >= 2 ? 8 : 0);
-      const int r = q * 8 + 2 * tig + (k & 1);
+      const int r = r0 + q * 8 + 2 * tig + (k & 1);
       if (i < n && r < R) {
         const size_t o = ((size_t)r * n + i) * V + B;
         cx<float> v = mk<float>(a * accr[q][k], a * acci[q][k]);
@@ -164,19 +165,39 @@ __global__ void coarse_mma_kernel(const uint4* Cf, const S* in, S* out, const S*
     }
 }
 
+// Launch shapes: variant v splits the right-hand sides over CTAs in groups of
+// kMmaTiles[v] tiles of 8 (each output's arithmetic is the same in every shape).
+static const int kMmaTiles[] = {8, 4, 2, 1, 3, 6};
+constexpr int kMmaVariants = 6;
+
+int coarse_mma_variants(int R) {
+  const int NT8 = (R + 7) / 8;
+  int nv = 0;
+  for (int v = 0; v < kMmaVariants; ++v) nv += kMmaTiles[v] <= NT8 ? 1 : 0;
+  return nv;
+}
+
 int launch_coarse_mma(int prec, const void* Cf, const void* in, void* out, const void* y2, const int L[4], int n, int R,
-                      double a, double c, cudaStream_t st) {
+                      double a, double c, cudaStream_t st, int variant) {
   if (prec != 1 && prec != 3) return -1;
   const int npad = (n + 15) / 16 * 16, T = npad / 16;
   const int V = L[0] * L[1] * L[2] * L[3];
-  const int NT8 = (R + 7) / 8;
+  const int NT8all = (R + 7) / 8;
+  int NT8 = NT8all;  // default: one CTA per coarse site holds every right-hand side
+  if (variant >= 0) {
+    int seen = -1;
+    for (int v = 0; v < kMmaVariants; ++v)
+      if (kMmaTiles[v] <= NT8all && ++seen == variant) NT8 = kMmaTiles[v];
+  }
+  const int splits = (NT8all + NT8 - 1) / NT8;
   const size_t sm = (size_t)9 * NT8 * 8 * 2 * npad * sizeof(__nv_bfloat16);
   if (sm > 200 * 1024 || T > 32) return -1;
 #define WMG_MMA(S, K)                                                                                    \
   {                                                                                                      \
     auto kern = coarse_mma_kernel<S, K>;                                                                 \
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-    kern<<<V, 32 * T, sm, st>>>((const uint4*)Cf, (const S*)in, (S*)out, (const S*)y2, L[0], L[1], L[2], L[3], n, \
+    kern<<<dim3(V, splits), 32 * T, sm, st>>>((const uint4*)Cf, (const S*)in, (S*)out, (const S*)y2, L[0], L[1],    \
+                                              L[2], L[3], n,                                                       \
                                 npad, R, (float)a, (float)c);                                            \
   }
 #define WMG_MMA_R(S)                       \

@@ -23,8 +23,10 @@ struct DslashCall {
   double a, b, c;     // out = a in + b Hop(in) + c y
   int nrhs;
   RedArgs red;        // lane = right-hand side, 3 values
+  int variant = -1;   // launch shape (wilson_variants), -1 = default
 };
 int launch_wilson(const DslashCall& d, cudaStream_t st);
+int wilson_variants(int prec, bool dots, int nrhs);
 int wilson_blocks(int V);
 int launch_pack_links(int prec, const void* ext, void* out, int V, cudaStream_t st);
 
@@ -67,6 +69,15 @@ int launch_dot(int prec, size_t n, int nrhs, const void* a, const void* b, RedAr
 int launch_multidot(int prec, size_t n, int nrhs, int k, int kmax, const void* W, size_t jstride,
                     const void* w, RedArgs red, cudaStream_t st, const double* pre = nullptr,
                     const double* post = nullptr, int cstride = 0);
+// out = sum_t c[t] x[t] (FP64, complex host coefficients, null x[t] = unused
+// term); with w, <w|out> and ||out||^2 are reduced into red (lane 0).
+struct LinComb {
+  double2* out;
+  const double2* x[3];
+  double2 c[3];
+  const double2* w;
+};
+int launch_lincomb(size_t n, const LinComb& L, RedArgs red, cudaStream_t st);
 // Outer GCR with a deferred solution update (A Z = W H, x += Z H^-1 alpha at
 // the end of a cycle).  gs_update: w -= sum_j beta_j W_j with fused <w|r>,
 // ||w||^2 and H[:, hk] += beta; pre/post/cstride as for the multi-dot (a
@@ -129,8 +140,11 @@ int coarse_blocks(int ncomp, int V);
 // right-hand sides of storage prec (1 = FP32, 3 = BF16): out = a A in + c y2.
 size_t mma_pack_bytes(int n, int V);
 int launch_mma_pack(const double2* C, int n, int V, void* out, cudaStream_t st);
+// variant >= 0 picks one of coarse_mma_variants(R) launch shapes (right-hand
+// sides split over CTAs); every shape gives bit-identical results.
 int launch_coarse_mma(int prec, const void* Cf, const void* in, void* out, const void* y2, const int L[4], int n, int R,
-                      double a, double c, cudaStream_t st);
+                      double a, double c, cudaStream_t st, int variant = -1);
+int coarse_mma_variants(int R);
 
 // Aggregation of level l (fine side) into level l+1 (coarse side).
 struct Agg {
@@ -145,16 +159,18 @@ struct Agg {
   int Vc;
 };
 int launch_restrict(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
-                    cudaStream_t st);
+                    cudaStream_t st, int variant = -1);
 int launch_prolong(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
-                   cudaStream_t st);
+                   cudaStream_t st, int variant = -1);
 // Tensor-core transfers for 2..64 right-hand sides with 16-bit P (nv <= 64,
 // nv / 16 rounded up in {1, 2, 4}); launch_restrict / launch_prolong pick them.
 bool transfer_mma_ok(const Agg& g, int nrhs);
 int launch_restrict_mma(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
-                        cudaStream_t st);
+                        cudaStream_t st, int variant = -1);
 int launch_prolong_mma(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
-                       cudaStream_t st);
+                       cudaStream_t st, int variant = -1);
+// Launch shapes of the tensor-core transfers (right-hand sides split over CTAs; bit-identical results).
+int transfer_mma_variants(int nrhs);
 
 // C_0(B) += delta 1 on a coarse stencil [9][n][n][V] (FP64).
 int launch_diag_shift(double2* C, int n, int V, double delta, cudaStream_t st);
@@ -166,6 +182,12 @@ int launch_diag_shift(double2* C, int n, int V, double delta, cudaStream_t st);
 int dense_inverse(int prec, const double2* C, const int L[4], int n, void* aug, void* scratch, int* err, void* inv,
                   cudaStream_t st);
 size_t dense_inverse_scratch_bytes(int prec, int N);
+// The same for `batch` independent matrices (C[z] -> inv[z], host arrays of
+// device pointers) sharing every elimination launch; aug holds batch N x 2N
+// matrices, scratch batch x dense_inverse_scratch_bytes(prec, N), err batch
+// flags.
+int dense_inverse_batch(int prec, const double2* const* C, const int L[4], int n, int batch, void* aug, void* scratch,
+                        int* err, void* const* inv, cudaStream_t st);
 // y = inv x (+ y if acc); (matrix, in, out) precisions (0,0,0), (1,0,0), (1,1,1).
 // With scratch (dense_matvec_scratch_bytes(N), tickets zeroed once) 4..64
 // right-hand sides run as one tiled product; otherwise one warp per row and

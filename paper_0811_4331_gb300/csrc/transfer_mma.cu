@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(kTThreads)
   T* Vs = Ps + 2 * Mp * kTKs;    // [2][Rp][kTKs]
   int* sidx = (int*)(smem_raw + sidx_off);  // fine site of each aggregate-local site
   const int B = blockIdx.x, chi = blockIdx.y;
+  const int r0 = blockIdx.z * Rp;  // first right-hand side of this CTA (launch-shape split)
   const int len = g.nhalf * g.bsites;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
   const int mt = warp % MT, ks0 = warp / MT;
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(kTThreads)
 #pragma unroll 4
       for (int r = rr; r < Rp; r += kTThreads / kTK) {
         T re = zero16, im = zero16;
-        if (live && r < R) planes<T>(in[(size_t)r * rstride + base], re, im);
+        if (live && r0 + r < R) planes<T>(in[(size_t)(r0 + r) * rstride + base], re, im);
         Vs[(size_t)r * kTKs + el] = re;
         Vs[(size_t)(Rp + r) * kTKs + el] = im;
       }
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(kTThreads)
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int k = mt * 16 + gid + (e >= 2 ? 8 : 0);
-      const int r = q * 8 + 2 * tig + (e & 1);
+      const int r = r0 + q * 8 + 2 * tig + (e & 1);
       if (k < g.nv && r < R)
         stc(out, ((size_t)r * 2 * g.nv + chi * g.nv + k) * g.Vc + B, mk<float>(accr[q][e], acci[q][e]));
     }
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(kTThreads)
   T* Pt = Xs + 2 * Rp * Kps;     // [2][kTK][Kps]
   int* sidx = (int*)(smem_raw + sidx_off);
   const int B = blockIdx.x, chi = blockIdx.y;
+  const int r0 = blockIdx.z * Rp;  // first right-hand side of this CTA (launch-shape split)
   const int len = g.nhalf * g.bsites;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
   const T2* Pb = P + ((size_t)B * 2 + chi) * g.nv * len;
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(kTThreads)
   for (int t = threadIdx.x; t < Rp * Kp; t += kTThreads) {
     const int r = t / Kp, k = t % Kp;
     T re = MmaT<T>::from(0.f), im = re;
-    if (r < R && k < g.nv) planes<T>(in[((size_t)r * 2 * g.nv + chi * g.nv + k) * g.Vc + B], re, im);
+    if (r0 + r < R && k < g.nv) planes<T>(in[((size_t)(r0 + r) * 2 * g.nv + chi * g.nv + k) * g.Vc + B], re, im);
     Xs[(size_t)r * Kps + k] = re;
     Xs[(size_t)(Rp + r) * Kps + k] = im;
   }
@@ -268,7 +270,7 @@ __global__ void __launch_bounds__(kTThreads)
       for (int q = 0; q < NT8; ++q)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          const int r = q * 8 + 2 * tig + j;
+          const int r = r0 + q * 8 + 2 * tig + j;
           if (r < R) stc(out, (size_t)r * g.ncomp * g.V + o, mk<float>(accr[q][2 * h + j], acci[q][2 * h + j]));
         }
     }
@@ -298,12 +300,34 @@ bool transfer_mma_ok(const Agg& g, int nrhs) {
   return nrhs >= 2 && nrhs <= 64 && (MT == 1 || MT == 2 || MT == 4) && g.ncomp % 2 == 0 && g.bsites <= 8192;
 }
 
-template <typename T, typename SI, typename SO>
-static int restrict_mma_t(const Agg& g, const void* P, const void* in, void* out, int nrhs, cudaStream_t st) {
+// Launch shapes: variant v puts kXTiles[v] tiles of 8 right-hand sides in a CTA
+// (the admissible ones for nrhs, in this order); the default holds them all.
+static const int kXTiles[] = {8, 4, 2, 1, 3, 6};
+constexpr int kXVariants = 6;
+
+int transfer_mma_variants(int nrhs) {
   const int NT8 = (nrhs + 7) / 8;
+  int nv = 0;
+  for (int v = 0; v < kXVariants; ++v) nv += kXTiles[v] <= NT8 ? 1 : 0;
+  return nv;
+}
+
+static int tiles_of(int nrhs, int variant) {
+  const int all = (nrhs + 7) / 8;
+  if (variant < 0) return all;
+  int seen = -1;
+  for (int v = 0; v < kXVariants; ++v)
+    if (kXTiles[v] <= all && ++seen == variant) return kXTiles[v];
+  return all;
+}
+
+template <typename T, typename SI, typename SO>
+static int restrict_mma_t(const Agg& g, const void* P, const void* in, void* out, int nrhs, cudaStream_t st,
+                          int variant) {
+  const int NT8 = tiles_of(nrhs, variant);
   size_t so = 0;
   const size_t sm = restrict_smem(g, NT8, &so);
-  const dim3 grid(g.Vc, 2);
+  const dim3 grid(g.Vc, 2, ((nrhs + 7) / 8 + NT8 - 1) / NT8);
 #define WMG_RM(K)                                                                                              \
   {                                                                                                            \
     auto kern = restrict_mma_kernel<T, SI, SO, K>;                                                             \
@@ -326,11 +350,12 @@ static int restrict_mma_t(const Agg& g, const void* P, const void* in, void* out
 }
 
 template <typename T, typename SI, typename SO>
-static int prolong_mma_t(const Agg& g, const void* P, const void* in, void* out, int nrhs, cudaStream_t st) {
-  const int NT8 = (nrhs + 7) / 8;
+static int prolong_mma_t(const Agg& g, const void* P, const void* in, void* out, int nrhs, cudaStream_t st,
+                         int variant) {
+  const int NT8 = tiles_of(nrhs, variant);
   size_t so = 0;
   const size_t sm = prolong_smem(g, NT8, &so);
-  const dim3 grid(g.Vc, 2);
+  const dim3 grid(g.Vc, 2, ((nrhs + 7) / 8 + NT8 - 1) / NT8);
 #define WMG_PM(K)                                                                                              \
   {                                                                                                            \
     auto kern = prolong_mma_kernel<T, SI, SO, K>;                                                              \
@@ -354,24 +379,28 @@ static int prolong_mma_t(const Agg& g, const void* P, const void* in, void* out,
 
 // (vector-in, P, vector-out) precision triples with 16-bit P: 2 = FP16, 3 = BF16, 1 = FP32.
 int launch_restrict_mma(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
-                        cudaStream_t st) {
-  if (pin == 2 && pP == 2 && pout == 1) return restrict_mma_t<__half, __half2, float2>(g, P, in, out, nrhs, st);
+                        cudaStream_t st, int variant) {
+  if (pin == 2 && pP == 2 && pout == 1)
+    return restrict_mma_t<__half, __half2, float2>(g, P, in, out, nrhs, st, variant);
   if (pin == 3 && pP == 3 && pout == 1)
-    return restrict_mma_t<__nv_bfloat16, __nv_bfloat162, float2>(g, P, in, out, nrhs, st);
-  if (pin == 2 && pP == 2 && pout == 2) return restrict_mma_t<__half, __half2, __half2>(g, P, in, out, nrhs, st);
+    return restrict_mma_t<__nv_bfloat16, __nv_bfloat162, float2>(g, P, in, out, nrhs, st, variant);
+  if (pin == 2 && pP == 2 && pout == 2)
+    return restrict_mma_t<__half, __half2, __half2>(g, P, in, out, nrhs, st, variant);
   if (pin == 3 && pP == 3 && pout == 3)
-    return restrict_mma_t<__nv_bfloat16, __nv_bfloat162, __nv_bfloat162>(g, P, in, out, nrhs, st);
+    return restrict_mma_t<__nv_bfloat16, __nv_bfloat162, __nv_bfloat162>(g, P, in, out, nrhs, st, variant);
   return -1;
 }
 
 int launch_prolong_mma(int pin, int pP, int pout, const Agg& g, const void* P, const void* in, void* out, int nrhs,
-                       cudaStream_t st) {
-  if (pin == 1 && pP == 2 && pout == 2) return prolong_mma_t<__half, float2, __half2>(g, P, in, out, nrhs, st);
+                       cudaStream_t st, int variant) {
+  if (pin == 1 && pP == 2 && pout == 2)
+    return prolong_mma_t<__half, float2, __half2>(g, P, in, out, nrhs, st, variant);
   if (pin == 1 && pP == 3 && pout == 3)
-    return prolong_mma_t<__nv_bfloat16, float2, __nv_bfloat162>(g, P, in, out, nrhs, st);
-  if (pin == 2 && pP == 2 && pout == 2) return prolong_mma_t<__half, __half2, __half2>(g, P, in, out, nrhs, st);
+    return prolong_mma_t<__nv_bfloat16, float2, __nv_bfloat162>(g, P, in, out, nrhs, st, variant);
+  if (pin == 2 && pP == 2 && pout == 2)
+    return prolong_mma_t<__half, __half2, __half2>(g, P, in, out, nrhs, st, variant);
   if (pin == 3 && pP == 3 && pout == 3)
-    return prolong_mma_t<__nv_bfloat16, __nv_bfloat162, __nv_bfloat162>(g, P, in, out, nrhs, st);
+    return prolong_mma_t<__nv_bfloat16, __nv_bfloat162, __nv_bfloat162>(g, P, in, out, nrhs, st, variant);
   return -1;
 }
 

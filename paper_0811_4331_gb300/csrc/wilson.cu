@@ -40,27 +40,37 @@ struct WilsonArgs {
   RedArgs red;
 };
 
-template <int MU, typename R, typename S, typename G, int NL>
-__device__ __forceinline__ void hop_pair(cx<R> (&acc)[4][3], const WilsonArgs<S, G, NL>& A, const S* in,
+// The two hops of direction MU for NR right-hand sides: each link is loaded
+// (and its third row rebuilt) once and applied to every right-hand side.
+template <int MU, int NR, typename R, typename S, typename G, int NL>
+__device__ __forceinline__ void hop_pair(cx<R> (&acc)[NR][4][3], const WilsonArgs<S, G, NL>& A, const S* in,
                                          int s, const int (&c)[4], const int (&stride)[4]) {
   const int L = A.L[MU], st = stride[MU];
   const int fwd = (c[MU] == L - 1) ? s - (L - 1) * st : s + st;
   const int bwd = (c[MU] == 0) ? s + (L - 1) * st : s - st;
   Link<R> u;
   load_link<R, G, NL>(u, A.U, MU, A.V, s);
-  hop<MU, true>(acc, in, A.V, fwd, u);
+#pragma unroll
+  for (int r = 0; r < NR; ++r) hop<MU, true>(acc[r], in + r * A.vstride, A.V, fwd, u);
   load_link<R, G, NL>(u, A.U, MU, A.V, bwd);
-  hop<MU, false>(acc, in, A.V, bwd, u);
+#pragma unroll
+  for (int r = 0; r < NR; ++r) hop<MU, false>(acc[r], in + r * A.vstride, A.V, bwd, u);
 }
 
-template <typename S, typename G, int NL, int NT>
+// Thread = (site, NR consecutive right-hand sides).  Every right-hand side's
+// output and dot partials are computed with the same operations in the same
+// order for any NT and NR, and the dots of right-hand side r are reduced over
+// the same CTAs of NT sites, so a launch shape never changes a result bit.
+template <typename S, typename G, int NL, int NT, int NR>
 __global__ void __launch_bounds__(NT) wilson_kernel(const WilsonArgs<S, G, NL> A) {
   typedef typename Store<S>::R R;
   const int V = A.V;
   const int s = blockIdx.x * NT + threadIdx.x;
-  const int rhs = blockIdx.y;
-  const S* in = A.in + rhs * A.vstride;
-  R acc3[3] = {(R)0, (R)0, (R)0};  // per-thread partial dots in the arithmetic type
+  const int rhs0 = blockIdx.y * NR;
+  const S* in = A.in + rhs0 * A.vstride;
+  R acc3[NR][3];  // per-thread partial dots in the arithmetic type
+#pragma unroll
+  for (int r = 0; r < NR; ++r) acc3[r][0] = acc3[r][1] = acc3[r][2] = (R)0;
   if (s < V) {
     int c[4], stride[4];
     {
@@ -76,40 +86,74 @@ __global__ void __launch_bounds__(NT) wilson_kernel(const WilsonArgs<S, G, NL> A
       stride[2] = A.L[0] * A.L[1];
       stride[3] = stride[2] * A.L[2];
     }
-    cx<R> acc[4][3];
+    cx<R> acc[NR][4][3];
 #pragma unroll
-    for (int sp = 0; sp < 4; ++sp)
+    for (int r = 0; r < NR; ++r)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) acc[sp][a] = zero<R>();
-    hop_pair<0>(acc, A, in, s, c, stride);
-    hop_pair<1>(acc, A, in, s, c, stride);
-    hop_pair<2>(acc, A, in, s, c, stride);
-    hop_pair<3>(acc, A, in, s, c, stride);
+      for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[r][sp][a] = zero<R>();
+    hop_pair<0, NR>(acc, A, in, s, c, stride);
+    hop_pair<1, NR>(acc, A, in, s, c, stride);
+    hop_pair<2, NR>(acc, A, in, s, c, stride);
+    hop_pair<3, NR>(acc, A, in, s, c, stride);
     const R ca = (R)A.a, cb = (R)A.b, cc = (R)A.c;
-    S* out = A.out + rhs * A.vstride;
-    const S* y = A.y ? A.y + rhs * A.vstride : nullptr;
-    const S* z = A.z ? A.z + rhs * A.vstride : nullptr;
 #pragma unroll
-    for (int sp = 0; sp < 4; ++sp)
+    for (int r = 0; r < NR; ++r) {
+      const size_t ro = (size_t)(rhs0 + r) * A.vstride;
+      S* out = A.out + ro;
+      const S* inr = A.in + ro;
+      const S* y = A.y ? A.y + ro : nullptr;
+      const S* z = A.z ? A.z + ro : nullptr;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const size_t i = (size_t)(sp * 3 + a) * V + s;
-        cx<R> v = cb * acc[sp][a];
-        v = v + ca * ldc<R>(in, i);
-        if (y) v = v + cc * ldc<R>(y, i);
-        stc(out, i, v);
-        if (z) {
-          // reduce the value as stored, so dots see exactly the vector kept
-          cx<R> vs = as_stored<S>(v);
-          cx<R> zz = ldc<R>(z, i);
-          cx<R> d = cmul_conj(vs, zz);
-          acc3[0] += d.re;
-          acc3[1] += d.im;
-          acc3[2] += norm2(vs);
+      for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const size_t i = (size_t)(sp * 3 + a) * V + s;
+          cx<R> v = cb * acc[r][sp][a];
+          v = v + ca * ldc<R>(inr, i);
+          if (y) v = v + cc * ldc<R>(y, i);
+          stc(out, i, v);
+          if (z) {
+            // reduce the value as stored, so dots see exactly the vector kept
+            cx<R> vs = as_stored<S>(v);
+            cx<R> zz = ldc<R>(z, i);
+            cx<R> d = cmul_conj(vs, zz);
+            acc3[r][0] += d.re;
+            acc3[r][1] += d.im;
+            acc3[r][2] += norm2(vs);
+          }
         }
-      }
+    }
   }
-  if (A.z) grid_reduce<3, NT, R>(acc3, A.red, rhs);
+  if (A.z) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) grid_reduce<3, NT, R>(acc3[r], A.red, rhs0 + r);
+  }
+}
+
+template <typename S, typename G, int NL, int NT, int NR>
+static int launch_nt(const WilsonArgs<S, G, NL>& A, int nrhs, cudaStream_t st) {
+  dim3 grid((A.V + NT - 1) / NT, nrhs / NR);
+  wilson_kernel<S, G, NL, NT, NR><<<grid, NT, 0, st>>>(A);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Launch shapes (threads per CTA NT, right-hand sides per thread NR), in the
+// order a tuner sees them: with fused dots NT stays 128 (the reduction's
+// association depends on the CTA size), NR = 2 needs an even count; FP64 has
+// the one default shape (its stencil is bound by FP64 arithmetic).
+struct WShape {
+  int nt, nr;
+};
+static const WShape kShapesDots[] = {{128, 1}, {128, 2}};
+static const WShape kShapesFree[] = {{128, 1}, {64, 1}, {256, 1}, {128, 2}, {64, 2}, {256, 2}};
+
+int wilson_variants(int prec, bool dots, int nrhs) {
+  if (prec == 0) return 1;
+  const bool even = nrhs % 2 == 0;
+  if (dots) return even ? 2 : 1;
+  return even ? 6 : 3;
 }
 
 template <typename S, typename G, int NL>
@@ -127,10 +171,20 @@ static int launch_t(const DslashCall& d, cudaStream_t st) {
   A.c = d.c;
   A.vstride = (size_t)12 * A.V;
   A.red = d.red;
-  constexpr int NT = 128;
-  dim3 grid((A.V + NT - 1) / NT, d.nrhs);
-  wilson_kernel<S, G, NL, NT><<<grid, NT, 0, st>>>(A);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  if constexpr (NL == 9) {
+    return launch_nt<S, G, NL, 128, 1>(A, d.nrhs, st);
+  }
+  WShape sh = {128, 1};
+  if (d.variant >= 0 && d.variant < wilson_variants(1, d.z != nullptr, d.nrhs))
+    sh = d.z ? kShapesDots[d.variant] : kShapesFree[d.variant];
+  if (sh.nr == 2) {
+    if (sh.nt == 64) return launch_nt<S, G, NL, 64, 2>(A, d.nrhs, st);
+    if (sh.nt == 256) return launch_nt<S, G, NL, 256, 2>(A, d.nrhs, st);
+    return launch_nt<S, G, NL, 128, 2>(A, d.nrhs, st);
+  }
+  if (sh.nt == 64) return launch_nt<S, G, NL, 64, 1>(A, d.nrhs, st);
+  if (sh.nt == 256) return launch_nt<S, G, NL, 256, 1>(A, d.nrhs, st);
+  return launch_nt<S, G, NL, 128, 1>(A, d.nrhs, st);
 }
 
 int wilson_blocks(int V) { return (V + 127) / 128; }

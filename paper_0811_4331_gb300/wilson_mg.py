@@ -84,7 +84,9 @@ def _load():
         "mg_setup": (I, [P(VP), VP, I, P(I), D, P(mg_params), VP, VP]),
         "mg_destroy": (I, [VP]),
         "mg_retarget": (I, [VP, D, P(VP), VP]),
+        "mg_retarget_batch": (I, [VP, P(D), I, P(VP), VP]),
         "mg_solve": (I, [VP, VP, VP, I, I, D, P(mg_stats), VP]),
+        "krylov_solve": (I, [VP, I, VP, VP, I, I, D, I, P(mg_stats), VP]),
         "dslash_apply": (I, [VP, I, VP, VP, I, VP]),
         "coarse_apply": (I, [VP, I, I, VP, VP, I, VP]),
         "restrict_apply": (I, [VP, I, I, VP, VP, I, VP]),
@@ -102,6 +104,8 @@ def _load():
         "mg_launch_count": (ctypes.c_ulonglong, []),
         "mg_profile_read": (I, [VP, I, I, P(ctypes.c_longlong), P(D)]),
         "mg_profile_bytes": (I, [VP, I, I, P(D)]),
+        "mg_tune": (I, [I]),
+        "mg_tune_report": (I, [ctypes.c_char_p, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -116,7 +120,8 @@ LIB = _load()
 EXPORTS = ["mg_last_error", "mg_default_params", "mg_setup", "mg_retarget", "mg_destroy", "mg_solve", "dslash_apply",
            "coarse_apply", "restrict_apply", "prolong_apply", "mr_apply", "vcycle_apply", "mg_field_to_internal",
            "mg_field_from_internal", "mg_level_info", "mg_get_prolongator", "mg_get_coarse_op", "mg_footprint",
-           "mg_profile", "mg_profile_read", "mg_profile_bytes", "mg_launch_count", "mr_apply_noalloc"]
+           "mg_profile", "mg_profile_read", "mg_profile_bytes", "mg_launch_count", "mr_apply_noalloc", "mg_tune",
+           "mg_tune_report", "krylov_solve", "mg_retarget_batch"]
 
 (MG_K_DSLASH, MG_K_COARSE, MG_K_RESTRICT, MG_K_PROLONG, MG_K_VECTOR, MG_K_COARSEST, MG_K_SETUP, MG_K_GALERKIN,
  MG_K_INVERSE, MG_K_GRAM) = range(10)
@@ -225,6 +230,15 @@ def mg_retarget(src, mass, stream=None):
     return Handle(h, src.dims)
 
 
+def mg_retarget_batch(src, masses, stream=None):
+    """New handles for several masses at once (one batched elimination builds all coarsest inverses)."""
+    n = len(masses)
+    ms = (ctypes.c_double * n)(*[float(m) for m in masses])
+    hs = (ctypes.c_void_p * n)()
+    _check(LIB.mg_retarget_batch(src.ptr, ms, n, hs, _stream(stream)))
+    return [Handle(ctypes.c_void_p(hs[i]), src.dims) for i in range(n)]
+
+
 def mg_destroy(h):
     if h.ptr:
         _check(LIB.mg_destroy(h.ptr))
@@ -241,6 +255,26 @@ def mg_solve(h, b, x, tol, stream=None, raise_on_noconv=True):
     if bdev != xdev:
         raise ValueError("b and x must both be host arrays or both device tensors")
     status = LIB.mg_solve(h.ptr, bp, xp, nrhs, bdev, float(tol), st, _stream(stream))
+    stats = [s.as_dict() for s in st]
+    if status != MG_OK and (status != MG_ENOCONV or raise_on_noconv):
+        raise MgError(status, mg_last_error(), stats)
+    return status, stats
+
+
+MG_KRYLOV_BICGSTAB, MG_KRYLOV_CGNR = 0, 1
+
+
+def krylov_solve(h, method, b, x, tol, max_iter=100000, stream=None, raise_on_noconv=True):
+    """Unpreconditioned BiCGstab or CG-on-the-normal-equations solve (FP64) in place on x.
+    Returns (status, [stats dict per rhs])."""
+    shp = b.shape
+    nrhs = 1 if len(shp) == 6 else int(shp[0])
+    st = (mg_stats * nrhs)()
+    bp, bdev = _ptr(b)
+    xp, xdev = _ptr(x)
+    if bdev != xdev:
+        raise ValueError("b and x must both be host arrays or both device tensors")
+    status = LIB.krylov_solve(h.ptr, int(method), bp, xp, nrhs, bdev, float(tol), int(max_iter), st, _stream(stream))
     stats = [s.as_dict() for s in st]
     if status != MG_OK and (status != MG_ENOCONV or raise_on_noconv):
         raise MgError(status, mg_last_error(), stats)
@@ -329,6 +363,26 @@ def mg_profile_read(h, kclass, prec):
     ms = ctypes.c_double()
     _check(LIB.mg_profile_read(h.ptr, kclass, prec, ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+def mg_tune(mode):
+    """Launch-shape tuner mode (0 off, 1 on, 2 forget and on, 3 / 4 force last / first shape); returns the old mode."""
+    r = LIB.mg_tune(int(mode))
+    if r < 0:
+        raise MgError(MG_EINVAL, "mg_tune: bad mode", None)
+    return r
+
+
+def mg_tune_report():
+    """{key: (chosen shape, [microseconds per shape])} of the launch-shape tuner."""
+    n = LIB.mg_tune_report(None, 0)
+    buf = ctypes.create_string_buffer(n + 1)
+    LIB.mg_tune_report(buf, n + 1)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        f = line.split()
+        out[f[0]] = (int(f[1]), [float(x) for x in f[2:]])
+    return out
 
 
 def mg_profile_bytes(h, kclass, prec):
