@@ -662,9 +662,10 @@ static int build_coarsest_many(mg_handle* const* hs, int count) {
   }
   const int prec = h0->p.mixed ? MG_F32 : MG_F64;
   const size_t eb = bytes_of(prec);
-  DevBuf aug, col, errflag;
+  DevBuf aug, col, errflag, blk;
+  const size_t bb = gjb_scratch_bytes((int)N, eb, count);
   if (!aug.ensure(N * 2 * N * eb * count) || !col.ensure(dense_inverse_scratch_bytes(prec, (int)N) * count) ||
-      !errflag.ensure(sizeof(int) * count))
+      !errflag.ensure(sizeof(int) * count) || (bb && !blk.ensure(bb)))
     return MG_ENOMEM;
   std::vector<const double2*> C(count);
   std::vector<void*> inv(count);
@@ -680,9 +681,10 @@ static int build_coarsest_many(mg_handle* const* hs, int count) {
   CK(cudaMemsetAsync(errflag.p, 0, sizeof(int) * count, st));
   {
     Prof pf(h0, MG_K_INVERSE, prec);
-    LK(dense_inverse_batch(prec, C.data(), c0.L, c0.ncomp, count, aug.p, col.p, errflag.as<int>(), inv.data(), st));
+    LK(dense_inverse_batch(prec, C.data(), c0.L, c0.ncomp, count, aug.p, col.p, errflag.as<int>(), inv.data(),
+                           blk.p, st));
   }
-  count_launches(N + 3 * (size_t)count - 1);  // per matrix: stencil-to-dense, init, finish; one per pivot
+  count_launches(N + 3 * (size_t)count - 1);  // per matrix: stencil-to-dense, init, finish; one per pivot (or panel pair)
   std::vector<int> herr(count, 0);
   CK(cudaMemcpyAsync(herr.data(), errflag.p, sizeof(int) * count, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

@@ -220,7 +220,7 @@ static int restrict_t(const Agg& g, const void* P, const void* in, void* out, in
   const size_t sm = (size_t)g.ncomp * g.bsites * sizeof(cx<R>);
   if (sm > 200 * 1024) return -1;
   if (sm > 48 * 1024)
-    cudaFuncSetAttribute(restrict_kernel<SI, SP, SO, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_big_smem(restrict_kernel<SI, SP, SO, NT>);
   const int ngroups = (2 * g.nv + NT / 32 - 1) / (NT / 32);
   restrict_kernel<SI, SP, SO, NT>
       <<<dim3(g.Vc * ngroups, nrhs), NT, sm, st>>>(g, (const SP*)P, (const SI*)in, (SO*)out);
@@ -419,9 +419,155 @@ static unsigned grid_for(size_t tot, size_t cap) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
+// ------------------------------------------------------------------ blocked Gauss-Jordan
+// The same elimination (partial pivoting on the largest |a_ik|, rows kept in
+// place, every other row eliminated) grouped in panels of b columns.  For a
+// panel starting at column kb, the b steps act on the other columns as one
+// linear map C -> T C with T = prod_j (1 - l_j e_{p_j}^+); T = 1 - X E^+ for
+// E = [e_{p_0} .. e_{p_b-1}], so T C = C - E C_P + (T E) C_P, where C_P are
+// the b pivot rows of C before the panel.  One CTA per matrix runs the b
+// steps on the panel columns in shared memory and tracks T E by applying the
+// same steps to b extra columns (column j set to e_{p_j} just before step
+// j); a second kernel applies the rank-b update to the trailing columns (the
+// columns left of the panel are already zero off their pivot rows and do not
+// change).  The per-element arithmetic differs from the column-by-column
+// order only by rounding.
+
+// Panel kernel: one CTA per matrix z (blockIdx.x), nt threads.  Shared:
+// panel [N][b] and tracker [N][b] of element type T, multipliers [N],
+// used-row flags [N], reduction scratch.
+template <typename T>
+__global__ void gjb_panel_kernel(T* aug0, int N, int kb, int b, unsigned long long* keys0, int* used0, T* te0,
+                                 T* prow0, int* err0) {
+  typedef typename Store<T>::R R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int z = blockIdx.x;
+  T* aug = aug0 + (size_t)z * N * 2 * N;
+  unsigned long long* keys = keys0 + (size_t)z * (N + 1);
+  int* used = used0 + (size_t)z * N;
+  T* te = te0 + (size_t)z * N * b;
+  T* prow = prow0 + (size_t)z * b * 2 * N;
+  int* err = err0 + z;
+  cx<R>* Ps = (cx<R>*)smem_raw;           // [N][b]
+  cx<R>* Ts = Ps + (size_t)N * b;         // [N][b]
+  cx<R>* Ls = Ts + (size_t)N * b;         // [N]
+  unsigned long long* red = (unsigned long long*)(Ls + N);  // [32]
+  __shared__ int piv_s[16];
+  const int nt = blockDim.x, t = threadIdx.x;
+  const size_t ld = 2 * (size_t)N;
+  if (*err) return;
+  for (int e = t; e < N * b; e += nt) {
+    const int i = e / b, j = e - i * b;
+    Ps[e] = ldc<R>(aug, (size_t)i * ld + kb + j);
+    Ts[e] = zero<R>();
+  }
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
+    // pivot: the largest |a_ik|^2 over rows not yet used, ties to the lower row
+    unsigned long long best = 0;
+    for (int i = t; i < N; i += nt)
+      if (!used[i]) {
+        const unsigned long long key = pivot_key((float)norm2(Ps[(size_t)i * b + j]), i);
+        best = key > best ? key : best;
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_down_sync(0xffffffffu, best, o);
+      best = other > best ? other : best;
+    }
+    if ((t & 31) == 0) red[t >> 5] = best;
+    __syncthreads();
+    if (t < 32) {
+      best = t < nt / 32 ? red[t] : 0ull;
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_down_sync(0xffffffffu, best, o);
+        best = other > best ? other : best;
+      }
+      if (t == 0) {
+        const int p = best ? pivot_row(best) : -1;
+        const bool ok = p >= 0 && p < N && norm2(Ps[(size_t)p * b + j]) > (R)0;
+        piv_s[j] = ok ? p : -1;
+        if (ok) {
+          keys[kb + j] = best;
+          used[p] = 1;
+          Ts[(size_t)p * b + j] = mk<R>((R)1, (R)0);
+        } else {
+          *err = 1;
+        }
+      }
+    }
+    __syncthreads();
+    const int p = piv_s[j];
+    if (p < 0) return;
+    const cx<R> pv = Ps[(size_t)p * b + j];
+    const R den = norm2(pv);
+    const cx<R> pinv = mk<R>(pv.re / den, -pv.im / den);
+    for (int i = t; i < N; i += nt) Ls[i] = Ps[(size_t)i * b + j] * pinv;
+    __syncthreads();
+    // every other row: panel columns j.. and tracker columns ..j
+    for (int e = t; e < N * b; e += nt) {
+      const int i = e / b, jj = e - i * b;
+      if (i == p) continue;
+      const cx<R> l = Ls[i];
+      if (jj >= j) Ps[e] = (jj == j) ? zero<R>() : Ps[e] - l * Ps[(size_t)p * b + jj];
+      if (jj <= j) Ts[e] = Ts[e] - l * Ts[(size_t)p * b + jj];
+    }
+    __syncthreads();
+  }
+  // the panel back, T E for the trailing update, and the pivot rows of the trailing columns
+  for (int e = t; e < N * b; e += nt) {
+    const int i = e / b, j = e - i * b;
+    stc(aug, (size_t)i * ld + kb + j, Ps[e]);
+    stc(te, e, Ts[e]);
+  }
+  const int c0 = kb + b, nc = 2 * N - c0;
+  for (int e = t; e < b * nc; e += nt) {
+    const int j = e / nc, c = e - j * nc;
+    prow[(size_t)j * 2 * N + c0 + c] = aug[(size_t)piv_s[j] * ld + c0 + c];
+  }
+}
+
+// Trailing update of the columns right of the panel: for row i and column c,
+// a = (i a pivot row of the panel ? 0 : a) + sum_j TE[i][j] prow[j][c].
+// grid = (column tiles of 256, rows, batch).
+template <typename T>
+__global__ void gjb_update_kernel(T* aug0, int N, int kb, int b, const unsigned long long* keys0, const T* te0,
+                                  const T* prow0, const int* err0) {
+  typedef typename Store<T>::R R;
+  const int z = blockIdx.z;
+  if (err0[z]) return;
+  T* aug = aug0 + (size_t)z * N * 2 * N;
+  const unsigned long long* keys = keys0 + (size_t)z * (N + 1);
+  const T* te = te0 + (size_t)z * N * b;
+  const T* prow = prow0 + (size_t)z * b * 2 * N;
+  const int i = blockIdx.y;
+  const int c = kb + b + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= 2 * N) return;
+  bool pivot = false;
+  cx<R> acc = zero<R>();
+  for (int j = 0; j < b; ++j) {
+    pivot |= pivot_row(keys[kb + j]) == i;
+    acc = cfma(ldc<R>(te, (size_t)i * b + j), ldc<R>(prow, (size_t)j * 2 * N + c), acc);
+  }
+  const size_t o = (size_t)i * 2 * N + c;
+  stc(aug, o, pivot ? acc : ldc<R>(aug, o) + acc);
+}
+
+// Panel width for N rows of element size eb: the panel, its tracker and the
+// multipliers in one CTA's shared memory; 0 = too large, use single steps.
+static int gjb_width(int N, size_t eb) {
+  for (int b = 8; b >= 2; b /= 2)
+    if ((2 * (size_t)b + 1) * N * eb + 256 <= 200 * 1024) return b;
+  return 0;
+}
+
+size_t gjb_scratch_bytes(int N, size_t eb, int batch) {
+  const int b = gjb_width(N, eb);
+  return b ? (size_t)batch * ((size_t)N * b + (size_t)b * 2 * N) * eb + 256 : 0;
+}
+
 template <typename T>
 static int dense_inverse_t(const double2* const* C, const int L[4], int n, int batch, T* aug, char* sc, int* err,
-                           void* const* inv, cudaStream_t st) {
+                           void* const* inv, void* blk, cudaStream_t st) {
   const int V = L[0] * L[1] * L[2] * L[3];
   const int N = n * V;
   const size_t nn2 = (size_t)N * 2 * N;
@@ -436,9 +582,25 @@ static int dense_inverse_t(const double2* const* C, const int L[4], int n, int b
                                                          keys + (size_t)z * (N + 1));
   }
   if (!launched()) return -1;
-  for (int k = 0; k < N; ++k) {
-    const dim3 grid((unsigned)((2 * N - k + 255) / 256), (unsigned)N, (unsigned)batch);
-    gj_step_kernel<T><<<grid, 256, 0, st>>>(aug, N, k, cols, used, keys, err);
+  const int b = blk ? gjb_width(N, sizeof(T)) : 0;
+  if (b) {
+    T* te = (T*)blk;
+    T* prow = te + (size_t)batch * N * b;
+    const size_t sm = (2 * (size_t)b + 1) * N * sizeof(T) + 32 * sizeof(unsigned long long);
+    allow_big_smem(gjb_panel_kernel<T>);
+    for (int kb = 0; kb < N; kb += b) {
+      const int bw = N - kb < b ? N - kb : b;
+      gjb_panel_kernel<T><<<batch, 1024, sm, st>>>(aug, N, kb, bw, keys, used, te, prow, err);
+      if (kb + bw < 2 * N) {
+        const dim3 grid((unsigned)((2 * N - kb - bw + 255) / 256), (unsigned)N, (unsigned)batch);
+        gjb_update_kernel<T><<<grid, 256, 0, st>>>(aug, N, kb, bw, keys, te, prow, err);
+      }
+    }
+  } else {
+    for (int k = 0; k < N; ++k) {
+      const dim3 grid((unsigned)((2 * N - k + 255) / 256), (unsigned)N, (unsigned)batch);
+      gj_step_kernel<T><<<grid, 256, 0, st>>>(aug, N, k, cols, used, keys, err);
+    }
   }
   for (int z = 0; z < batch; ++z)
     gj_finish_kernel<T><<<grid_for((size_t)N * N, 8192), 256, 0, st>>>(aug + z * nn2, N, keys + (size_t)z * (N + 1),
@@ -447,19 +609,19 @@ static int dense_inverse_t(const double2* const* C, const int L[4], int n, int b
 }
 
 int dense_inverse_batch(int prec, const double2* const* C, const int L[4], int n, int batch, void* aug, void* scratch,
-                        int* err, void* const* inv, cudaStream_t st) {
+                        int* err, void* const* inv, void* blk, cudaStream_t st) {
   // scratch: per matrix two column snapshots [2][N] of the element type, then N + 1 pivot keys per
-  // matrix, then N used-row flags per matrix
+  // matrix, then N used-row flags per matrix; blk (optional): the blocked form's tracker and pivot rows
   if (batch < 1) return -1;
-  if (prec == 0) return dense_inverse_t<double2>(C, L, n, batch, (double2*)aug, (char*)scratch, err, inv, st);
-  if (prec == 1) return dense_inverse_t<float2>(C, L, n, batch, (float2*)aug, (char*)scratch, err, inv, st);
+  if (prec == 0) return dense_inverse_t<double2>(C, L, n, batch, (double2*)aug, (char*)scratch, err, inv, blk, st);
+  if (prec == 1) return dense_inverse_t<float2>(C, L, n, batch, (float2*)aug, (char*)scratch, err, inv, blk, st);
   return -1;
 }
 
 int dense_inverse(int prec, const double2* C, const int L[4], int n, void* aug, void* scratch, int* err, void* inv,
                   cudaStream_t st) {
   void* invs[1] = {inv};
-  return dense_inverse_batch(prec, &C, L, n, 1, aug, scratch, err, invs, st);
+  return dense_inverse_batch(prec, &C, L, n, 1, aug, scratch, err, invs, nullptr, st);
 }
 
 size_t dense_inverse_scratch_bytes(int prec, int N) {

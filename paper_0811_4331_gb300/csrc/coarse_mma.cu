@@ -195,7 +195,7 @@ int launch_coarse_mma(int prec, const void* Cf, const void* in, void* out, const
 #define WMG_MMA(S, K)                                                                                    \
   {                                                                                                      \
     auto kern = coarse_mma_kernel<S, K>;                                                                 \
-    if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+    if (sm > 48 * 1024) allow_big_smem(kern);                                                            \
     kern<<<dim3(V, splits), 32 * T, sm, st>>>((const uint4*)Cf, (const S*)in, (S*)out, (const S*)y2, L[0], L[1],    \
                                               L[2], L[3], n,                                                       \
                                 npad, R, (float)a, (float)c);                                            \

@@ -9,6 +9,36 @@
 
 namespace wmg {
 
+// Dynamic shared memory above 48 KB needs a per-kernel opt-in.  The attribute
+// is global to the kernel, so a value chosen per launch would race between
+// host threads launching the same kernel with different sizes; every caller
+// sets the device's maximum instead, the same value from any thread (the
+// amount a launch really uses still sets its occupancy).
+inline int smem_optin_bytes() {
+  static const int v = [] {
+    int d = 0, x = 48 * 1024;
+    if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&x, cudaDevAttrMaxSharedMemoryPerBlockOptin, d) !=
+                                                 cudaSuccess) {
+      cudaGetLastError();
+      x = 48 * 1024;
+    }
+    return x;
+  }();
+  return v;
+}
+template <typename K>
+inline void allow_big_smem(K kern) {
+  cudaFuncAttributes fa;
+  int bytes = smem_optin_bytes();
+  if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess)
+    bytes -= (int)fa.sharedSizeBytes;  // the opt-in limit covers static plus dynamic shared memory
+  else
+    cudaGetLastError();
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+    cudaGetLastError();
+}
+
+
 // ------------------------------------------------------------------ complex
 template <typename R>
 struct cx {

@@ -186,8 +186,11 @@ size_t dense_inverse_scratch_bytes(int prec, int N);
 // device pointers) sharing every elimination launch; aug holds batch N x 2N
 // matrices, scratch batch x dense_inverse_scratch_bytes(prec, N), err batch
 // flags.
+// With blk (gjb_scratch_bytes(N, element size, batch) bytes, 0 = not
+// available for this N) the elimination runs in panels (blocked form).
 int dense_inverse_batch(int prec, const double2* const* C, const int L[4], int n, int batch, void* aug, void* scratch,
-                        int* err, void* const* inv, cudaStream_t st);
+                        int* err, void* const* inv, void* blk, cudaStream_t st);
+size_t gjb_scratch_bytes(int N, size_t eb, int batch);
 // y = inv x (+ y if acc); (matrix, in, out) precisions (0,0,0), (1,0,0), (1,1,1).
 // With scratch (dense_matvec_scratch_bytes(N), tickets zeroed once) 4..64
 // right-hand sides run as one tiled product; otherwise one warp per row and

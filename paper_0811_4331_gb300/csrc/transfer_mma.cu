@@ -331,7 +331,7 @@ static int restrict_mma_t(const Agg& g, const void* P, const void* in, void* out
 #define WMG_RM(K)                                                                                              \
   {                                                                                                            \
     auto kern = restrict_mma_kernel<T, SI, SO, K>;                                                             \
-    if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);       \
+    if (sm > 48 * 1024) allow_big_smem(kern);                                                                  \
     kern<<<grid, kTThreads, sm, st>>>(g, (const typename MmaT<T>::T2*)P, (const SI*)in, (SO*)out, nrhs, (int)so); \
   }
   switch (NT8) {
@@ -359,7 +359,7 @@ static int prolong_mma_t(const Agg& g, const void* P, const void* in, void* out,
 #define WMG_PM(K)                                                                                              \
   {                                                                                                            \
     auto kern = prolong_mma_kernel<T, SI, SO, K>;                                                              \
-    if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);       \
+    if (sm > 48 * 1024) allow_big_smem(kern);                                                                  \
     kern<<<grid, kTThreads, sm, st>>>(g, (const typename MmaT<T>::T2*)P, (const SI*)in, (SO*)out, nrhs, (int)so); \
   }
   switch (NT8) {
