@@ -30,18 +30,33 @@ int red_blocks(size_t n) {
 }
 
 // ------------------------------------------------------------------ MR update
+// Per-right-hand-side scalars are formed once per CTA by its first thread (in
+// FP64, from the FP64 reduction slots) and shared: FP64 division and square
+// root run at a small fraction of the FP32 rate on this part, so no thread of
+// a vector kernel evaluates them for itself.
+template <typename R>
+__device__ __forceinline__ cx<R> mr_alpha(const MrUpdate& m, int rhs) {
+  __shared__ double sa[2];
+  if (threadIdx.x == 0) {
+    const double* d = m.dots + (size_t)rhs * m.dstride;
+    const double den = d[2];
+    double ar = 0.0, ai = 0.0;
+    if (den > 0.0 && isfinite(den)) {
+      ar = m.omega * d[0] / den;
+      ai = m.omega * d[1] / den;
+    }
+    sa[0] = ar;
+    sa[1] = ai;
+  }
+  __syncthreads();
+  return mk<R>((R)sa[0], (R)sa[1]);
+}
+
 template <typename S>
 __global__ void __launch_bounds__(kVecThreads) mr_update_kernel(const MrUpdate m) {
   typedef typename Store<S>::R R;
   const int rhs = blockIdx.y;
-  const double* d = m.dots + (size_t)rhs * m.dstride;
-  const double den = d[2];
-  double ar = 0.0, ai = 0.0;
-  if (den > 0.0 && isfinite(den)) {
-    ar = m.omega * d[0] / den;
-    ai = m.omega * d[1] / den;
-  }
-  const cx<R> alpha = mk<R>((R)ar, (R)ai);
+  const cx<R> alpha = mr_alpha<R>(m, rhs);
   const size_t off = (size_t)rhs * m.n;
   S* xo = (S*)m.x_out + off;
   const S* xi = m.x_in ? (const S*)m.x_in + off : nullptr;
@@ -74,14 +89,7 @@ template <typename S>
 __global__ void __launch_bounds__(kVecThreads) mr_update2_kernel(const MrUpdate m) {
   typedef Pair16<S> P2;
   const int rhs = blockIdx.y;
-  const double* d = m.dots + (size_t)rhs * m.dstride;
-  const double den = d[2];
-  double ar = 0.0, ai = 0.0;
-  if (den > 0.0 && isfinite(den)) {
-    ar = m.omega * d[0] / den;
-    ai = m.omega * d[1] / den;
-  }
-  const cx<float> alpha = mk<float>((float)ar, (float)ai);
+  const cx<float> alpha = mr_alpha<float>(m, rhs);
   const size_t off = (size_t)rhs * m.n / 2;
   P2* xo = (P2*)m.x_out + off;
   const P2* xi = m.x_in ? (const P2*)m.x_in + off : nullptr;
@@ -317,14 +325,22 @@ __global__ void __launch_bounds__(kVecThreads)
   typedef typename Store<S>::R R;
   typedef typename Store<SX>::R RX;
   const int rhs = blockIdx.y;
-  const double* d = dots + (size_t)rhs * dstride;
-  const double nw2 = d[2];
-  double inv = 0.0, ar = 0.0, ai = 0.0;
-  if (nw2 > 0.0 && isfinite(nw2)) {
-    inv = 1.0 / sqrt(nw2);
-    ar = d[0] * inv;
-    ai = d[1] * inv;
+  __shared__ double sc[3];
+  if (threadIdx.x == 0) {
+    const double* d = dots + (size_t)rhs * dstride;
+    const double nw2 = d[2];
+    double inv = 0.0, ar = 0.0, ai = 0.0;
+    if (nw2 > 0.0 && isfinite(nw2)) {
+      inv = 1.0 / sqrt(nw2);
+      ar = d[0] * inv;
+      ai = d[1] * inv;
+    }
+    sc[0] = inv;
+    sc[1] = ar;
+    sc[2] = ai;
   }
+  __syncthreads();
+  const double inv = sc[0], ar = sc[1], ai = sc[2];
   const R s = (R)inv;
   const cx<R> a = mk<R>((R)ar, (R)ai);
   const cx<RX> ax = mk<RX>((RX)ar, (RX)ai);
@@ -443,18 +459,26 @@ __global__ void __launch_bounds__(kVecThreads)
                     int k, int kmax) {
   typedef typename Store<S>::R R;
   const int rhs = blockIdx.y;
-  const double* d = dots + (size_t)rhs * dstride;
-  const double nw2 = d[2];
-  double inv = 0.0, ar = 0.0, ai = 0.0;
-  if (nw2 > 0.0 && isfinite(nw2)) {
-    inv = 1.0 / sqrt(nw2);
-    ar = d[0] * inv;
-    ai = d[1] * inv;
+  __shared__ double sc[3];
+  if (threadIdx.x == 0) {
+    const double* d = dots + (size_t)rhs * dstride;
+    const double nw2 = d[2];
+    double inv = 0.0, ar = 0.0, ai = 0.0;
+    if (nw2 > 0.0 && isfinite(nw2)) {
+      inv = 1.0 / sqrt(nw2);
+      ar = d[0] * inv;
+      ai = d[1] * inv;
+    }
+    sc[0] = inv;
+    sc[1] = ar;
+    sc[2] = ai;
+    if (blockIdx.x == 0) {
+      H[((size_t)rhs * kmax + k) * kmax + k] = make_double2(nw2 > 0.0 ? sqrt(nw2) : 0.0, 0.0);
+      alpha[(size_t)rhs * kmax + k] = make_double2(ar, ai);
+    }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    H[((size_t)rhs * kmax + k) * kmax + k] = make_double2(nw2 > 0.0 ? sqrt(nw2) : 0.0, 0.0);
-    alpha[(size_t)rhs * kmax + k] = make_double2(ar, ai);
-  }
+  __syncthreads();
+  const double inv = sc[0], ar = sc[1], ai = sc[2];
   const R s = (R)inv;
   const cx<R> a = mk<R>((R)ar, (R)ai);
   const size_t off = (size_t)rhs * n;
@@ -587,11 +611,17 @@ template <typename SI, typename SO>
 __global__ void __launch_bounds__(kVecThreads) convert_kernel(size_t n, const SI* in, SO* out, double s0,
                                                               const double* slot, int sstride, double sexp, int acc) {
   const int rhs = blockIdx.y;
-  double s = s0;
-  if (slot) {
-    const double v = slot[(size_t)rhs * sstride];
-    s *= (sexp == 0.5) ? sqrt(v) : (sexp == -0.5 ? (v > 0.0 ? 1.0 / sqrt(v) : 0.0) : pow(v, sexp));
+  __shared__ double ss;
+  if (threadIdx.x == 0) {
+    double s = s0;
+    if (slot) {
+      const double v = slot[(size_t)rhs * sstride];
+      s *= (sexp == 0.5) ? sqrt(v) : (sexp == -0.5 ? (v > 0.0 ? 1.0 / sqrt(v) : 0.0) : pow(v, sexp));
+    }
+    ss = s;
   }
+  __syncthreads();
+  const double s = ss;
   const size_t off = (size_t)rhs * n;
   for (size_t i = (size_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecThreads) {
     if (sizeof(typename Store<SI>::R) == 8 || sizeof(typename Store<SO>::R) == 8) {

@@ -528,28 +528,49 @@ __global__ void gjb_panel_kernel(T* aug0, int N, int kb, int b, unsigned long lo
 
 // Trailing update of the columns right of the panel: for row i and column c,
 // a = (i a pivot row of the panel ? 0 : a) + sum_j TE[i][j] prow[j][c].
-// grid = (column tiles of 256, rows, batch).
+// grid = (column tiles of 256, row groups of kGjbRows, batch): a thread keeps
+// its column's b pivot-row values in registers for kGjbRows rows, and the
+// group's TE rows and pivot flags sit in shared memory.
+constexpr int kGjbRows = 16;
+
 template <typename T>
-__global__ void gjb_update_kernel(T* aug0, int N, int kb, int b, const unsigned long long* keys0, const T* te0,
-                                  const T* prow0, const int* err0) {
+__global__ void __launch_bounds__(256) gjb_update_kernel(T* aug0, int N, int kb, int b,
+                                                         const unsigned long long* keys0, const T* te0,
+                                                         const T* prow0, const int* err0) {
   typedef typename Store<T>::R R;
+  __shared__ cx<R> tes[kGjbRows][8];
+  __shared__ int isp[kGjbRows];
   const int z = blockIdx.z;
   if (err0[z]) return;
   T* aug = aug0 + (size_t)z * N * 2 * N;
   const unsigned long long* keys = keys0 + (size_t)z * (N + 1);
   const T* te = te0 + (size_t)z * N * b;
   const T* prow = prow0 + (size_t)z * b * 2 * N;
-  const int i = blockIdx.y;
+  const int i0 = blockIdx.y * kGjbRows;
+  for (int e = threadIdx.x; e < kGjbRows * 8; e += blockDim.x) {  // all 8 slots: unused ones must be 0, not NaN
+    const int r = e / 8, j = e % 8;
+    tes[r][j] = (i0 + r < N && j < b) ? ldc<R>(te, (size_t)(i0 + r) * b + j) : zero<R>();
+  }
+  if (threadIdx.x < kGjbRows) {
+    int piv = 0;
+    for (int j = 0; j < b; ++j) piv |= pivot_row(keys[kb + j]) == i0 + (int)threadIdx.x;
+    isp[threadIdx.x] = piv;
+  }
+  __syncthreads();
   const int c = kb + b + blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= 2 * N) return;
-  bool pivot = false;
-  cx<R> acc = zero<R>();
-  for (int j = 0; j < b; ++j) {
-    pivot |= pivot_row(keys[kb + j]) == i;
-    acc = cfma(ldc<R>(te, (size_t)i * b + j), ldc<R>(prow, (size_t)j * 2 * N + c), acc);
+  cx<R> pr[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) pr[j] = j < b ? ldc<R>(prow, (size_t)j * 2 * N + c) : zero<R>();
+  const int rows = min(kGjbRows, N - i0);
+  for (int r = 0; r < rows; ++r) {
+    cx<R> acc = zero<R>();
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j < b) acc = cfma(tes[r][j], pr[j], acc);
+    const size_t o = (size_t)(i0 + r) * 2 * N + c;
+    stc(aug, o, isp[r] ? acc : ldc<R>(aug, o) + acc);
   }
-  const size_t o = (size_t)i * 2 * N + c;
-  stc(aug, o, pivot ? acc : ldc<R>(aug, o) + acc);
 }
 
 // Panel width for N rows of element size eb: the panel, its tracker and the
@@ -592,7 +613,8 @@ static int dense_inverse_t(const double2* const* C, const int L[4], int n, int b
       const int bw = N - kb < b ? N - kb : b;
       gjb_panel_kernel<T><<<batch, 1024, sm, st>>>(aug, N, kb, bw, keys, used, te, prow, err);
       if (kb + bw < 2 * N) {
-        const dim3 grid((unsigned)((2 * N - kb - bw + 255) / 256), (unsigned)N, (unsigned)batch);
+        const dim3 grid((unsigned)((2 * N - kb - bw + 255) / 256), (unsigned)((N + kGjbRows - 1) / kGjbRows),
+                        (unsigned)batch);
         gjb_update_kernel<T><<<grid, 256, 0, st>>>(aug, N, kb, bw, keys, te, prow, err);
       }
     }
