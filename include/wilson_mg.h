@@ -98,6 +98,10 @@ typedef struct {
                                          (default 0: relaxation only) */
   int adapt_cycles;                   /* solver iterations per adaptive candidate (default 16) */
   int adapt_nv[MG_MAX_LEVELS - 1];    /* candidates of level l made by the adaptive steps, < nv[l] */
+  int defer_coarsest;                 /* 1: mg_setup leaves the coarsest inverse to the first solve on this
+                                         handle (for a hierarchy that only feeds mg_retarget_batch, which
+                                         builds every retargeted inverse in shared launches); ignored with
+                                         adaptive steps, which need it during setup (default 0) */
 } mg_params;
 
 /* Per right-hand side solve statistics. */

@@ -696,7 +696,17 @@ static int build_coarsest_many(mg_handle* const* hs, int count) {
   return MG_OK;
 }
 
-static int build_coarsest(mg_handle* h) { return build_coarsest_many(&h, 1); }
+static int build_coarsest(mg_handle* h) {
+  RET(build_coarsest_many(&h, 1));
+  if (h->lev.size() >= 2) h->lev.back()->inv_pending = false;
+  return MG_OK;
+}
+
+// A deferred coarsest inverse is built before the first cycle that needs it.
+static int ensure_coarsest(mg_handle* h) {
+  if (h->lev.size() >= 2 && h->lev.back()->inv_pending) RET(build_coarsest(h));
+  return MG_OK;
+}
 
 // ------------------------------------------------------------------ setup pieces
 // Geometry of the aggregation of level l into level l+1.
@@ -918,7 +928,14 @@ static int adapt_candidates(mg_handle* h, int l, void* x64, int q, int iters) {
 // adapt_nv / steps candidates, one more for s < adapt_nv % steps.
 static int build_from(mg_handle* h, int l, const double* const* starts) {
   const mg_params& p = h->p;
-  if (l + 1 >= p.n_levels) return build_coarsest(h);
+  if (l + 1 >= p.n_levels) {
+    // deferred: only without adaptive steps, whose cycles need the coarsest solve during setup
+    if (p.defer_coarsest && p.adapt_steps == 0 && l > 0) {
+      h->lev[l]->inv_pending = true;
+      return MG_OK;
+    }
+    return build_coarsest(h);
+  }
   RET(init_level(h, l));
   Level& a = *h->lev[l];
   const int nv = a.nv;
@@ -1224,6 +1241,7 @@ int vcycle_apply(mg_handle* h, const void* r, void* e, void* stream) {
   cudaStream_t keep = h->st;
   h->st = (cudaStream_t)stream;
   int rc = ensure_reducer(h, 1);
+  if (rc == MG_OK) rc = ensure_coarsest(h);
   if (rc == MG_OK) rc = vcycle(h, 0, r, e, 1);
   h->st = keep;
   return rc;
@@ -1421,6 +1439,7 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
   const size_t bi = bytes_of(pin);
   const int restart = h->p.gcr_restart;
   RET(ensure_reducer(h, nrhs));
+  RET(ensure_coarsest(h));
   auto t0 = std::chrono::steady_clock::now();
   // FP64 x, b, r in the internal layout
   if (!h->gx64.ensure(n * nrhs * 16) || !h->gb64.ensure(n * nrhs * 16) || !h->gr64.ensure(n * nrhs * 16) ||

@@ -434,11 +434,10 @@ static unsigned grid_for(size_t tot, size_t cap) {
 // order only by rounding.
 
 // Panel kernel: one CTA per matrix z (blockIdx.x), nt threads.  Shared:
-// panel [N][b] and tracker [N][b] of element type T, multipliers [N],
-// used-row flags [N], reduction scratch.
-template <typename T>
-__global__ void gjb_panel_kernel(T* aug0, int N, int kb, int b, unsigned long long* keys0, int* used0, T* te0,
-                                 T* prow0, int* err0) {
+// panel [N][b] and tracker [N][b] of element type T.
+template <typename T, int B>
+__global__ void __launch_bounds__(1024) gjb_panel_kernel(T* aug0, int N, int kb, int b, unsigned long long* keys0,
+                                                         int* used0, T* te0, T* prow0, int* err0) {
   typedef typename Store<T>::R R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int z = blockIdx.x;
@@ -448,48 +447,49 @@ __global__ void gjb_panel_kernel(T* aug0, int N, int kb, int b, unsigned long lo
   T* te = te0 + (size_t)z * N * b;
   T* prow = prow0 + (size_t)z * b * 2 * N;
   int* err = err0 + z;
-  cx<R>* Ps = (cx<R>*)smem_raw;           // [N][b]
-  cx<R>* Ts = Ps + (size_t)N * b;         // [N][b]
-  cx<R>* Ls = Ts + (size_t)N * b;         // [N]
-  unsigned long long* red = (unsigned long long*)(Ls + N);  // [32]
-  __shared__ int piv_s[16];
-  const int nt = blockDim.x, t = threadIdx.x;
+  // column-major: thread i of a warp touches consecutive words.  Panel column
+  // j keeps its pre-step values (zeroed off the pivot row on write-back).
+  cx<R>* Ps = (cx<R>*)smem_raw;    // [b][N]
+  cx<R>* Ts = Ps + (size_t)B * N;  // [b][N]
+  __shared__ unsigned long long wkey[32];
+  __shared__ int piv_s[B];
+  const int nt = blockDim.x, t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const size_t ld = 2 * (size_t)N;
   if (*err) return;
-  for (int e = t; e < N * b; e += nt) {
-    const int i = e / b, j = e - i * b;
-    Ps[e] = ldc<R>(aug, (size_t)i * ld + kb + j);
-    Ts[e] = zero<R>();
-  }
-  __syncthreads();
-  for (int j = 0; j < b; ++j) {
-    // pivot: the largest |a_ik|^2 over rows not yet used, ties to the lower row
-    unsigned long long best = 0;
-    for (int i = t; i < N; i += nt)
-      if (!used[i]) {
-        const unsigned long long key = pivot_key((float)norm2(Ps[(size_t)i * b + j]), i);
-        best = key > best ? key : best;
-      }
+  auto warp_max = [&](unsigned long long v) {
     for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long other = __shfl_down_sync(0xffffffffu, best, o);
-      best = other > best ? other : best;
+      const unsigned long long other = __shfl_down_sync(0xffffffffu, v, o);
+      v = other > v ? other : v;
     }
-    if ((t & 31) == 0) red[t >> 5] = best;
-    __syncthreads();
-    if (t < 32) {
-      best = t < nt / 32 ? red[t] : 0ull;
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long other = __shfl_down_sync(0xffffffffu, best, o);
-        best = other > best ? other : best;
-      }
-      if (t == 0) {
-        const int p = best ? pivot_row(best) : -1;
-        const bool ok = p >= 0 && p < N && norm2(Ps[(size_t)p * b + j]) > (R)0;
+    return v;
+  };
+  unsigned long long best = 0;
+  for (int e = t; e < N * b; e += nt) {  // coalesced along the panel's row
+    const int i = e / b, j = e - i * b;
+    const cx<R> v = ldc<R>(aug, (size_t)i * ld + kb + j);
+    Ps[(size_t)j * N + i] = v;
+    Ts[(size_t)j * N + i] = zero<R>();
+    if (j == 0 && !used[i]) {
+      const unsigned long long key = pivot_key((float)norm2(v), i);
+      best = key > best ? key : best;
+    }
+  }
+  best = warp_max(best);
+  if (lane == 0) wkey[warp] = best;
+#pragma unroll 1
+  for (int j = 0; j < b; ++j) {
+    __syncthreads();  // the column's candidate keys and the previous step's updates are complete
+    if (warp == 0) {
+      unsigned long long v = lane < nt / 32 ? wkey[lane] : 0ull;
+      v = warp_max(v);
+      if (lane == 0) {
+        const int p = v ? pivot_row(v) : -1;
+        const bool ok = p >= 0 && p < N && norm2(Ps[(size_t)j * N + p]) > (R)0;
         piv_s[j] = ok ? p : -1;
         if (ok) {
-          keys[kb + j] = best;
+          keys[kb + j] = v;
           used[p] = 1;
-          Ts[(size_t)p * b + j] = mk<R>((R)1, (R)0);
+          Ts[(size_t)j * N + p] = mk<R>((R)1, (R)0);
         } else {
           *err = 1;
         }
@@ -498,26 +498,40 @@ __global__ void gjb_panel_kernel(T* aug0, int N, int kb, int b, unsigned long lo
     __syncthreads();
     const int p = piv_s[j];
     if (p < 0) return;
-    const cx<R> pv = Ps[(size_t)p * b + j];
+    const cx<R> pv = Ps[(size_t)j * N + p];
     const R den = norm2(pv);
     const cx<R> pinv = mk<R>(pv.re / den, -pv.im / den);
-    for (int i = t; i < N; i += nt) Ls[i] = Ps[(size_t)i * b + j] * pinv;
-    __syncthreads();
-    // every other row: panel columns j.. and tracker columns ..j
-    for (int e = t; e < N * b; e += nt) {
-      const int i = e / b, jj = e - i * b;
+    // every other row: panel columns right of j, tracker columns up to j; the
+    // updated column j+1 yields the next step's pivot candidates
+    best = 0;
+    for (int i = t; i < N; i += nt) {
       if (i == p) continue;
-      const cx<R> l = Ls[i];
-      if (jj >= j) Ps[e] = (jj == j) ? zero<R>() : Ps[e] - l * Ps[(size_t)p * b + jj];
-      if (jj <= j) Ts[e] = Ts[e] - l * Ts[(size_t)p * b + jj];
+      const cx<R> l = Ps[(size_t)j * N + i] * pinv;
+#pragma unroll
+      for (int jj = 0; jj < B; ++jj) {
+        if (jj >= b) break;
+        if (jj > j) {
+          const cx<R> v = Ps[(size_t)jj * N + i] - l * Ps[(size_t)jj * N + p];
+          Ps[(size_t)jj * N + i] = v;
+          if (jj == j + 1 && !used[i]) {
+            const unsigned long long key = pivot_key((float)norm2(v), i);
+            best = key > best ? key : best;
+          }
+        } else {
+          Ts[(size_t)jj * N + i] = Ts[(size_t)jj * N + i] - l * Ts[(size_t)jj * N + p];
+        }
+      }
     }
-    __syncthreads();
+    best = warp_max(best);
+    if (lane == 0) wkey[warp] = best;
   }
-  // the panel back, T E for the trailing update, and the pivot rows of the trailing columns
+  __syncthreads();
+  // the panel back (its columns zero off their pivot rows), T E for the
+  // trailing update, and the pivot rows of the trailing columns
   for (int e = t; e < N * b; e += nt) {
     const int i = e / b, j = e - i * b;
-    stc(aug, (size_t)i * ld + kb + j, Ps[e]);
-    stc(te, e, Ts[e]);
+    stc(aug, (size_t)i * ld + kb + j, i == piv_s[j] ? Ps[(size_t)j * N + i] : zero<R>());
+    stc(te, e, Ts[(size_t)j * N + i]);
   }
   const int c0 = kb + b, nc = 2 * N - c0;
   for (int e = t; e < b * nc; e += nt) {
@@ -563,21 +577,27 @@ __global__ void __launch_bounds__(256) gjb_update_kernel(T* aug0, int N, int kb,
 #pragma unroll
   for (int j = 0; j < 8; ++j) pr[j] = j < b ? ldc<R>(prow, (size_t)j * 2 * N + c) : zero<R>();
   const int rows = min(kGjbRows, N - i0);
-  for (int r = 0; r < rows; ++r) {
+  // all the group's loads first (independent, in flight together), then the stores
+  cx<R> av[kGjbRows];
+#pragma unroll
+  for (int r = 0; r < kGjbRows; ++r)
+    av[r] = r < rows ? ldc<R>(aug, (size_t)(i0 + r) * 2 * N + c) : zero<R>();
+#pragma unroll
+  for (int r = 0; r < kGjbRows; ++r) {
+    if (r >= rows) break;
     cx<R> acc = zero<R>();
 #pragma unroll
     for (int j = 0; j < 8; ++j)
       if (j < b) acc = cfma(tes[r][j], pr[j], acc);
-    const size_t o = (size_t)(i0 + r) * 2 * N + c;
-    stc(aug, o, isp[r] ? acc : ldc<R>(aug, o) + acc);
+    stc(aug, (size_t)(i0 + r) * 2 * N + c, isp[r] ? acc : av[r] + acc);
   }
 }
 
-// Panel width for N rows of element size eb: the panel, its tracker and the
-// multipliers in one CTA's shared memory; 0 = too large, use single steps.
+// Panel width for N rows of element size eb: the panel and its tracker in
+// one CTA's shared memory; 0 = too large, use single steps.
 static int gjb_width(int N, size_t eb) {
   for (int b = 8; b >= 2; b /= 2)
-    if ((2 * (size_t)b + 1) * N * eb + 256 <= 200 * 1024) return b;
+    if (2 * (size_t)b * N * eb <= 200 * 1024) return b;
   return 0;
 }
 
@@ -607,11 +627,12 @@ static int dense_inverse_t(const double2* const* C, const int L[4], int n, int b
   if (b) {
     T* te = (T*)blk;
     T* prow = te + (size_t)batch * N * b;
-    const size_t sm = (2 * (size_t)b + 1) * N * sizeof(T) + 32 * sizeof(unsigned long long);
-    allow_big_smem(gjb_panel_kernel<T>);
+    const size_t sm = 2 * (size_t)b * N * sizeof(T);
+    auto panel = b == 8 ? gjb_panel_kernel<T, 8> : (b == 4 ? gjb_panel_kernel<T, 4> : gjb_panel_kernel<T, 2>);
+    allow_big_smem(panel);
     for (int kb = 0; kb < N; kb += b) {
       const int bw = N - kb < b ? N - kb : b;
-      gjb_panel_kernel<T><<<batch, 1024, sm, st>>>(aug, N, kb, bw, keys, used, te, prow, err);
+      panel<<<batch, 1024, sm, st>>>(aug, N, kb, bw, keys, used, te, prow, err);
       if (kb + bw < 2 * N) {
         const dim3 grid((unsigned)((2 * N - kb - bw + 255) / 256), (unsigned)((N + kGjbRows - 1) / kGjbRows),
                         (unsigned)batch);
@@ -648,37 +669,6 @@ int dense_inverse(int prec, const double2* C, const int L[4], int n, void* aug, 
 
 size_t dense_inverse_scratch_bytes(int prec, int N) {
   return 2 * (size_t)N * (prec == 0 ? 16 : 8) + 8 * ((size_t)N + 1) + 4 * (size_t)N + 64;
-}
-
-// y = inv x (+ y if acc) for nrhs vectors; one warp per row.  Arithmetic in
-// the matrix's precision.
-template <typename TM, typename SI, typename SO>
-__global__ void dense_matvec_kernel(int N, const TM* inv, const SI* x, SO* y, int acc) {
-  typedef typename Store<TM>::R R;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int rhs = blockIdx.y;
-  if (warp >= N) return;
-  const TM* row = inv + (size_t)warp * N;
-  const SI* xr = x + (size_t)rhs * N;
-  cx<R> a = zero<R>(), b = zero<R>();
-  int j = lane;
-  for (; j + 32 < N; j += 64) {  // two independent chains
-    a = cfma(ldc<R>(row, j), ldc<R>(xr, j), a);
-    b = cfma(ldc<R>(row, j + 32), ldc<R>(xr, j + 32), b);
-  }
-  for (; j < N; j += 32) a = cfma(ldc<R>(row, j), ldc<R>(xr, j), a);
-  a = a + b;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a.re += __shfl_down_sync(0xffffffffu, a.re, o);
-    a.im += __shfl_down_sync(0xffffffffu, a.im, o);
-  }
-  if (lane == 0) {
-    const size_t o = (size_t)rhs * N + warp;
-    cx<double> v = mk<double>((double)a.re, (double)a.im);
-    if (acc) v = v + ldc<double>(y, o);
-    stc(y, o, v);
-  }
 }
 
 // Y = inv X (+ Y if acc) for 4 <= nrhs <= 64: a dense product, tiled so that
@@ -769,8 +759,64 @@ size_t dense_matvec_scratch_bytes(int N) {
   return (size_t)8 * 64 * N * 16 + (size_t)((N + kMmRows - 1) / kMmRows) * sizeof(unsigned) + 256;
 }
 
+// y = inv x (+ y if acc) for 1-3 right-hand sides: a CTA of kMvWarps warps per
+// row, warp w summing columns [w N / kMvWarps, (w+1) N / kMvWarps) with two
+// independent chains, the warps' sums added in warp order (deterministic).
+constexpr int kMvWarps = 4;
+
+template <typename TM, typename SI, typename SO>
+__global__ void __launch_bounds__(32 * kMvWarps) dense_matvec4_kernel(int N, const TM* inv, const SI* x, SO* y,
+                                                                      int acc) {
+  typedef typename Store<TM>::R R;
+  __shared__ cx<R> part[kMvWarps];
+  const int row = blockIdx.x, rhs = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = (int)((long)warp * N / kMvWarps), c1 = (int)((long)(warp + 1) * N / kMvWarps);
+  const TM* rp = inv + (size_t)row * N;
+  const SI* xr = x + (size_t)rhs * N;
+  cx<R> a = zero<R>(), b = zero<R>();
+  int j = c0 + lane;
+  for (; j + 32 < c1; j += 64) {
+    a = cfma(ldc<R>(rp, j), ldc<R>(xr, j), a);
+    b = cfma(ldc<R>(rp, j + 32), ldc<R>(xr, j + 32), b);
+  }
+  for (; j < c1; j += 32) a = cfma(ldc<R>(rp, j), ldc<R>(xr, j), a);
+  a = a + b;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a.re += __shfl_down_sync(0xffffffffu, a.re, o);
+    a.im += __shfl_down_sync(0xffffffffu, a.im, o);
+  }
+  if (lane == 0) part[warp] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cx<R> s = part[0];
+#pragma unroll
+    for (int w = 1; w < kMvWarps; ++w) s = s + part[w];
+    const size_t o = (size_t)rhs * N + row;
+    cx<double> v = mk<double>((double)s.re, (double)s.im);
+    if (acc) v = v + ldc<double>(y, o);
+    stc(y, o, v);
+  }
+}
+
 int launch_dense_matvec(int pm, int pin, int pout, int N, const void* inv, const void* x, void* y, int nrhs, int acc,
                         cudaStream_t st, void* scratch) {
+  if (nrhs < 4 || !scratch) {
+    const dim3 g((unsigned)N, (unsigned)nrhs);
+    if (pm == 0 && pin == 0 && pout == 0)
+      dense_matvec4_kernel<double2, double2, double2>
+          <<<g, 32 * kMvWarps, 0, st>>>(N, (const double2*)inv, (const double2*)x, (double2*)y, acc);
+    else if (pm == 1 && pin == 0 && pout == 0)
+      dense_matvec4_kernel<float2, double2, double2>
+          <<<g, 32 * kMvWarps, 0, st>>>(N, (const float2*)inv, (const double2*)x, (double2*)y, acc);
+    else if (pm == 1 && pin == 1 && pout == 1)
+      dense_matvec4_kernel<float2, float2, float2>
+          <<<g, 32 * kMvWarps, 0, st>>>(N, (const float2*)inv, (const float2*)x, (float2*)y, acc);
+    else
+      return -1;
+    return launched() ? 0 : -1;
+  }
   if (scratch && nrhs >= 4 && nrhs <= 64) {
     const int tiles = (N + kMmRows - 1) / kMmRows;
     int KS = (2 * 152 + tiles - 1) / tiles;  // about two CTAs per SM
@@ -793,19 +839,7 @@ int launch_dense_matvec(int pm, int pin, int pout, int N, const void* inv, const
       return -1;
     return launched() ? 0 : -1;
   }
-  dim3 grid((N * 32 + 255) / 256, nrhs);
-  if (pm == 0 && pin == 0 && pout == 0)
-    dense_matvec_kernel<double2, double2, double2>
-        <<<grid, 256, 0, st>>>(N, (const double2*)inv, (const double2*)x, (double2*)y, acc);
-  else if (pm == 1 && pin == 0 && pout == 0)
-    dense_matvec_kernel<float2, double2, double2>
-        <<<grid, 256, 0, st>>>(N, (const float2*)inv, (const double2*)x, (double2*)y, acc);
-  else if (pm == 1 && pin == 1 && pout == 1)
-    dense_matvec_kernel<float2, float2, float2>
-        <<<grid, 256, 0, st>>>(N, (const float2*)inv, (const float2*)x, (float2*)y, acc);
-  else
-    return -1;
-  return launched() ? 0 : -1;
+  return -1;
 }
 
 }  // namespace wmg

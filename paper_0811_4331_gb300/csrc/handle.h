@@ -70,6 +70,7 @@ struct Level {
   DevBuf inv;
   DevBuf mm_scratch;  // partial tiles and tickets of the many-right-hand-side inverse product
   int inv_prec = 0;
+  bool inv_pending = false;  // coarsest inverse deferred (mg_params.defer_coarsest), built on first use
   int N() const { return ncomp * V; }
   size_t n() const { return (size_t)ncomp * V; }
 };

@@ -48,6 +48,7 @@ class mg_params(ctypes.Structure):
         ("adapt_steps", ctypes.c_int),
         ("adapt_cycles", ctypes.c_int),
         ("adapt_nv", ctypes.c_int * 3),
+        ("defer_coarsest", ctypes.c_int),
     ]
 
 

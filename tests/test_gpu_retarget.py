@@ -68,3 +68,25 @@ def test_batched_retarget_equals_one_by_one(mixed):
         assert sb[0]["iters"] == ss[0]["iters"]
         assert np.array_equal(xb, xs), m
         assert np.linalg.norm(b - dirac.wilson_dirac(U, xb, m)) <= 1e-10 * np.linalg.norm(b) * 1.001
+
+
+def test_deferred_coarsest_is_built_on_first_use():
+    """defer_coarsest leaves the inverse to the first solve (or to mg_retarget_batch); the
+    result is bit for bit the one of a setup that built it at once."""
+    wm = require_gpu()
+    dims = (8, 8, 4, 8)
+    U = inputs.random_gauge(dims, 6)
+    b = inputs.gaussian_spinor(dims, 7)
+    xs = []
+    for defer in (0, 1):
+        p = wm.mg_default_params(n_levels=2, block=[(2, 2, 2, 2)], nv=[8], setup_sweeps=[20], mixed=1,
+                                 defer_coarsest=defer)
+        h = wm.mg_setup(U, dims, -0.1, p)
+        x = np.zeros_like(b)
+        wm.mg_solve(h, b, x, 1e-10)
+        xs.append(x)
+        hb = wm.mg_retarget_batch(h, [-0.1, 0.05])
+        xb = np.zeros_like(b)
+        wm.mg_solve(hb[0], b, xb, 1e-10)
+        assert np.array_equal(xb, x)
+    assert np.array_equal(xs[0], xs[1])
