@@ -271,7 +271,7 @@ int op_apply(mg_handle* h, int l, int prec, const void* in, void* out, const voi
     {
       DevBuf scratch;
       d.variant = tuned(h, tkey("dslash", {prec, a.L[0], a.L[1], a.L[2], a.L[3], nrhs, y != nullptr, z != nullptr}),
-                        wilson_variants(prec, z != nullptr, nrhs), [&](int v) {
+                        wilson_variants(prec, z != nullptr, nrhs, a.V), [&](int v) {
                           if (!scratch.p && !scratch.ensure((size_t)a.n() * nrhs * bytes_of(prec))) return -1;
                           DslashCall t = d;
                           t.out = scratch.p;

@@ -26,7 +26,7 @@ struct DslashCall {
   int variant = -1;   // launch shape (wilson_variants), -1 = default
 };
 int launch_wilson(const DslashCall& d, cudaStream_t st);
-int wilson_variants(int prec, bool dots, int nrhs);
+int wilson_variants(int prec, bool dots, int nrhs, int V);
 int wilson_blocks(int V);
 int launch_pack_links(int prec, const void* ext, void* out, int V, cudaStream_t st);
 

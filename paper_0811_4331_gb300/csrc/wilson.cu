@@ -132,6 +132,106 @@ __global__ void __launch_bounds__(NT) wilson_kernel(const WilsonArgs<S, G, NL> A
   }
 }
 
+// Small lattices (a few thousand sites): one thread per site leaves most of
+// the GPU idle, so a CTA of 8 warps takes 32 sites and warp w computes hop
+// w (direction w / 2, forward for even w) for all 32 of them; the eight
+// partial sums of each site are then added in direction order through shared
+// memory and warps 0-5 finish two colour-spin components each (output, y
+// term and fused dots).  Deterministic; a different association of the
+// same terms than the one-thread-per-site kernel.
+template <int MU, bool FWD, typename R, typename S, typename G, int NL>
+__device__ __forceinline__ void one_hop(cx<R> (&acc)[4][3], const WilsonArgs<S, G, NL>& A, const S* in, int s,
+                                        const int (&c)[4], const int (&stride)[4]) {
+  const int L = A.L[MU], st = stride[MU];
+  Link<R> u;
+  if (FWD) {
+    const int nb = (c[MU] == L - 1) ? s - (L - 1) * st : s + st;
+    load_link<R, G, NL>(u, A.U, MU, A.V, s);
+    hop<MU, true>(acc, in, A.V, nb, u);
+  } else {
+    const int nb = (c[MU] == 0) ? s + (L - 1) * st : s - st;
+    load_link<R, G, NL>(u, A.U, MU, A.V, nb);
+    hop<MU, false>(acc, in, A.V, nb, u);
+  }
+}
+
+template <typename S, typename G, int NL>
+__global__ void __launch_bounds__(256) wilson_small_kernel(const WilsonArgs<S, G, NL> A) {
+  typedef typename Store<S>::R R;
+  __shared__ R part[8][24][32];  // [hop][real component][site of the CTA]
+  const int V = A.V;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * 32 + lane;
+  const int rhs = blockIdx.y;
+  const S* in = A.in + rhs * A.vstride;
+  {
+    cx<R> acc[4][3];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) acc[sp][a] = zero<R>();
+    if (s < V) {
+      int c[4], stride[4];
+      int q = s;
+      c[0] = q % A.L[0];
+      q /= A.L[0];
+      c[1] = q % A.L[1];
+      q /= A.L[1];
+      c[2] = q % A.L[2];
+      c[3] = q / A.L[2];
+      stride[0] = 1;
+      stride[1] = A.L[0];
+      stride[2] = A.L[0] * A.L[1];
+      stride[3] = stride[2] * A.L[2];
+      switch (warp) {  // uniform across the warp
+        case 0: one_hop<0, true>(acc, A, in, s, c, stride); break;
+        case 1: one_hop<0, false>(acc, A, in, s, c, stride); break;
+        case 2: one_hop<1, true>(acc, A, in, s, c, stride); break;
+        case 3: one_hop<1, false>(acc, A, in, s, c, stride); break;
+        case 4: one_hop<2, true>(acc, A, in, s, c, stride); break;
+        case 5: one_hop<2, false>(acc, A, in, s, c, stride); break;
+        case 6: one_hop<3, true>(acc, A, in, s, c, stride); break;
+        default: one_hop<3, false>(acc, A, in, s, c, stride); break;
+      }
+    }
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        part[warp][2 * (sp * 3 + a)][lane] = acc[sp][a].re;
+        part[warp][2 * (sp * 3 + a) + 1][lane] = acc[sp][a].im;
+      }
+  }
+  __syncthreads();
+  R red[3] = {(R)0, (R)0, (R)0};
+  if (warp < 6 && s < V) {
+    const S* y = A.y ? A.y + rhs * A.vstride : nullptr;
+    const S* z = A.z ? A.z + rhs * A.vstride : nullptr;
+    S* out = A.out + rhs * A.vstride;
+    const R ca = (R)A.a, cb = (R)A.b, cc = (R)A.c;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int comp = 2 * warp + k;  // spin * 3 + colour
+      cx<R> h = zero<R>();
+#pragma unroll
+      for (int w = 0; w < 8; ++w) h = h + mk<R>(part[w][2 * comp][lane], part[w][2 * comp + 1][lane]);
+      const size_t i = (size_t)comp * V + s;
+      cx<R> v = cb * h;
+      v = v + ca * ldc<R>(in, i);
+      if (y) v = v + cc * ldc<R>(y, i);
+      stc(out, i, v);
+      if (z) {
+        const cx<R> vs = as_stored<S>(v);
+        const cx<R> d = cmul_conj(vs, ldc<R>(z, i));
+        red[0] += d.re;
+        red[1] += d.im;
+        red[2] += norm2(vs);
+      }
+    }
+  }
+  if (A.z) grid_reduce<3, 256, R>(red, A.red, rhs);
+}
+
 template <typename S, typename G, int NL, int NT, int NR>
 static int launch_nt(const WilsonArgs<S, G, NL>& A, int nrhs, cudaStream_t st) {
   dim3 grid((A.V + NT - 1) / NT, nrhs / NR);
@@ -146,11 +246,13 @@ static int launch_nt(const WilsonArgs<S, G, NL>& A, int nrhs, cudaStream_t st) {
 struct WShape {
   int nt, nr;
 };
+// Site x right-hand-side counts up to which the warp-per-hop kernel runs.
+constexpr int kSmallSites = 32768;
 static const WShape kShapesDots[] = {{128, 1}, {128, 2}};
 static const WShape kShapesFree[] = {{128, 1}, {64, 1}, {256, 1}, {128, 2}, {64, 2}, {256, 2}};
 
-int wilson_variants(int prec, bool dots, int nrhs) {
-  if (prec == 0) return 1;
+int wilson_variants(int prec, bool dots, int nrhs, int V) {
+  if (prec == 0 || (size_t)V * nrhs <= (size_t)kSmallSites) return 1;  // one shape: FP64, or the small-lattice kernel
   const bool even = nrhs % 2 == 0;
   if (dots) return even ? 2 : 1;
   return even ? 6 : 3;
@@ -173,9 +275,15 @@ static int launch_t(const DslashCall& d, cudaStream_t st) {
   A.red = d.red;
   if constexpr (NL == 9) {
     return launch_nt<S, G, NL, 128, 1>(A, d.nrhs, st);
+  } else {
+    if ((size_t)A.V * d.nrhs <= (size_t)kSmallSites) {  // small lattice: a warp per hop
+      dim3 grid((A.V + 31) / 32, d.nrhs);
+      wilson_small_kernel<S, G, NL><<<grid, 256, 0, st>>>(A);
+      return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
   }
   WShape sh = {128, 1};
-  if (d.variant >= 0 && d.variant < wilson_variants(1, d.z != nullptr, d.nrhs))
+  if (d.variant >= 0 && d.variant < wilson_variants(1, d.z != nullptr, d.nrhs, A.V))
     sh = d.z ? kShapesDots[d.variant] : kShapesFree[d.variant];
   if (sh.nr == 2) {
     if (sh.nt == 64) return launch_nt<S, G, NL, 64, 2>(A, d.nrhs, st);
@@ -187,7 +295,8 @@ static int launch_t(const DslashCall& d, cudaStream_t st) {
   return launch_nt<S, G, NL, 128, 1>(A, d.nrhs, st);
 }
 
-int wilson_blocks(int V) { return (V + 127) / 128; }
+// CTAs per right-hand side of a launch with fused dots (sizes the reduction partials).
+int wilson_blocks(int V) { return V <= kSmallSites ? (V + 31) / 32 : (V + 127) / 128; }
 
 int launch_wilson(const DslashCall& d, cudaStream_t st) {
   switch (d.prec) {
