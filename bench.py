@@ -569,6 +569,71 @@ def c3_workload(args):
     return out
 
 
+# ---------------------------------------------------------------------------- large lattice
+C5_DIMS = (32, 32, 32, 64)
+
+
+def tile_gauge(U, reps):
+    """A periodic field on the lattice reps times larger per direction: the same links repeated
+    (still a periodic SU(3) configuration with the source's plaquette; its Dirac spectrum contains the
+    source's, so it keeps a comparable critical mass)."""
+    lat = U.shape[1:5]  # (Lt, Lz, Ly, Lx)
+    out = U
+    for ax, r in zip(range(1, 5), reversed(reps)):
+        out = np.concatenate([out] * r, axis=ax)
+    assert out.shape[1:5] == tuple(l * r for l, r in zip(lat, reversed(reps)))
+    return np.ascontiguousarray(out)
+
+
+def c5_workload(args):
+    """32^3 x 64: MG with 4^4 then 2^4 blocks (Nv = 24/32) and a fourth level (2^4, Nv = 24) for an exact
+    coarsest solve, 12 Gaussian sources, the mixed multi-RHS solve against 12 single-RHS plain FP64
+    solves, at masses above the paper's m_crit."""
+    import torch
+    from paper_0811_4331_gb300 import wilson_mg as wm
+    stream = torch.cuda.current_stream()
+    U = tile_gauge(inputs.heatbath_gauge(C3_DIMS, BETA, HB_SWEEPS, HB_SEED), (2, 2, 2, 2))
+    Ud = torch.from_numpy(U).cuda()
+    del U
+    nrhs = args.c5_rhs
+    B = torch.from_numpy(np.stack([inputs.gaussian_spinor(C5_DIMS, 200 + r) for r in range(nrhs)])).cuda()
+    out = {"workload": "32^3x64: the 16^3x32 beta=6.0 heatbath field (200 sweeps, seed 0) tiled 2x2x2x2, "
+                       "4-level MG 4^4, 2^4, 2^4 blocks, Nv=24/32/24, %d Gaussian sources, tol 1e-10, GCR(%d)"
+                       % (nrhs, args.c5_restart), "masses": []}
+    for dm in args.c5_dm:
+        mass = C3_MCRIT + dm
+        row = {"m": round(mass, 4)}
+        for mixed in (1, 0):
+            # the third level (4^3 x 8 sites x 64 components = 32768 unknowns) is too large for the
+            # exact dense coarsest solve, so a fourth level (2^4 blocks, Nv = 24: 1536 unknowns) takes it
+            p = wm.mg_default_params(n_levels=4, block=[(4, 4, 4, 4), (2, 2, 2, 2), (2, 2, 2, 2)], nv=[24, 32, 24],
+                                     setup_sweeps=[300, 100, 100], mixed=mixed, seed=7, coarse_mma=mixed,
+                                     gcr_restart=args.c5_restart, max_iter=4000)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = wm.mg_setup(Ud, C5_DIMS, mass, p, stream=stream)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            X = torch.zeros_like(B)
+            if mixed:
+                _, st = wm.mg_solve(h, B, X, TOL, stream=stream)
+            else:
+                st = []
+                for r in range(nrhs):
+                    xr = torch.zeros_like(B[r])
+                    _, s1 = wm.mg_solve(h, B[r].contiguous(), xr, TOL, stream=stream)
+                    st += s1
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            row["mixed_multi_rhs" if mixed else "fp64_single_rhs"] = {
+                "setup_s": round(t1 - t0, 3), "solve_s": round(t2 - t1, 3), "iters": [s["iters"] for s in st],
+                "max_true_rel_residual": max(s["true_rel_residual"] for s in st)}
+            wm.mg_destroy(h)
+        row["speedup_solve"] = round(row["fp64_single_rhs"]["solve_s"] / row["mixed_multi_rhs"]["solve_s"], 3)
+        out["masses"].append(row)
+    return out
+
+
 # ---------------------------------------------------------------------------- serving workload
 def serve_workload(args):
     """Poisson stream of solve requests over three beta = 6.0 fields (8^4, 12^4, 16^3 x 32): masses
@@ -639,9 +704,12 @@ def main():
     ap.add_argument("--ncu", action="store_true",
                     help="profiler run: the timed mixed step only, no clock sampling (no child processes)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--workload", choices=["c2", "c3", "serve"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c3", "c5", "serve"], default="c2",
                     help="c2: the mass-sweep step (default bench line); c3: 24-source batched solve; serve: stream")
     ap.add_argument("--c3-dm", type=float, default=0.02)
+    ap.add_argument("--c5-dm", type=float, nargs="+", default=[0.06, 0.03])
+    ap.add_argument("--c5-rhs", type=int, default=12)
+    ap.add_argument("--c5-restart", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10.0, 20.0, 40.0, 80.0])
     args = ap.parse_args()
@@ -660,6 +728,9 @@ def main():
     import torch
     if args.workload == "c3":
         print(json.dumps(c3_workload(args)))
+        return
+    if args.workload == "c5":
+        print(json.dumps(c5_workload(args)))
         return
     if args.workload == "serve":
         print(json.dumps(serve_workload(args)))

@@ -163,3 +163,21 @@ def test_graph_replay_equals_eager_launches(mixed):
         its.append(st[0]["iters"])
     assert its[0] == its[1]
     assert np.array_equal(xs[0], xs[1])
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_four_level_solve(mixed):
+    """The deepest hierarchy the library builds (8^4 -> 4^4 -> 2^4 -> 1^4, K-cycles on levels 1 and 2,
+    exact solve on the one-site coarsest level): the true FP64 residual reaches 1e-10."""
+    wm = require_gpu()
+    dims = (8, 8, 8, 8)
+    mass = -0.2
+    U = inputs.random_gauge(dims, 8)
+    b = np.stack([inputs.gaussian_spinor(dims, 60 + r) for r in range(3)])
+    p = wm.mg_default_params(n_levels=4, block=[(2, 2, 2, 2)] * 3, nv=[8, 8, 6], setup_sweeps=[8, 8, 8],
+                             mixed=mixed, coarse_mma=mixed)
+    h = wm.mg_setup(U, dims, mass, p)
+    x = np.zeros_like(b)
+    _, st = wm.mg_solve(h, b, x, 1e-10)
+    for r in range(3):
+        assert _true_rel(U, mass, x[r], b[r]) <= 1e-10, r
