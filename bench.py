@@ -349,22 +349,24 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
-def dslash_bandwidth(wm, torch, stream):
+def dslash_bandwidth(wm, torch, stream, dims=BW_DIMS, precs=None):
     """Achieved GB/s of dslash_apply on 32^3 x 64 (inputs + links + output > L2) per storage precision."""
-    U = inputs.random_gauge_fast(BW_DIMS, 5)
+    U = inputs.random_gauge_fast(dims, 5)
     Ud = torch.from_numpy(U).cuda()
     del U
-    V = int(np.prod(BW_DIMS))
+    V = int(np.prod(dims))
     peak = measured_peaks().get("hbm_gbs", 6800.0)
-    out = {"dims": list(BW_DIMS), "peak_gbs": peak}
+    out = {"dims": list(dims), "peak_gbs": peak}
     # algorithmic bytes per site: spinor in + out (24 complex) + 4 stored links per site
     per_site = {wm.MG_F64: 24 * 16 + 4 * 9 * 16, wm.MG_F32: 24 * 8 + 4 * 6 * 8,
                 wm.MG_F16: 24 * 4 + 4 * 6 * 4, wm.MG_BF16: 24 * 4 + 4 * 6 * 4}
     flops_site = 1320 + 48
     for prec, name in ((wm.MG_F16, "f16"), (wm.MG_BF16, "bf16"), (wm.MG_F32, "f32"), (wm.MG_F64, "f64")):
+        if precs is not None and name not in precs:
+            continue
         p = wm.mg_default_params(n_levels=1, mixed=0 if prec == wm.MG_F64 else 1,
                                  fine_prec=prec if prec != wm.MG_F64 else wm.MG_F16)
-        h = wm.mg_setup(Ud, BW_DIMS, -0.79, p, stream=stream)
+        h = wm.mg_setup(Ud, dims, -0.79, p, stream=stream)
         a = wm.internal_empty(h, 0, prec)
         c = wm.internal_empty(h, 0, prec)
         if a.is_complex():
@@ -704,8 +706,11 @@ def main():
     ap.add_argument("--ncu", action="store_true",
                     help="profiler run: the timed mixed step only, no clock sampling (no child processes)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--workload", choices=["c2", "c3", "c5", "serve"], default="c2",
-                    help="c2: the mass-sweep step (default bench line); c3: 24-source batched solve; serve: stream")
+    ap.add_argument("--workload", choices=["c2", "c3", "c5", "serve", "dslash"], default="c2",
+                    help="c2: the mass-sweep step (default bench line); c3: 24-source batched solve; serve: stream; "
+                         "dslash: the fine stencil alone (--dslash-dims, --dslash-prec)")
+    ap.add_argument("--dslash-dims", type=int, nargs=4, default=list(BW_DIMS))
+    ap.add_argument("--dslash-prec", nargs="+", choices=["f16", "bf16", "f32", "f64"], default=None)
     ap.add_argument("--c3-dm", type=float, default=0.02)
     ap.add_argument("--c5-dm", type=float, nargs="+", default=[0.06, 0.03])
     ap.add_argument("--c5-rhs", type=int, default=12)
@@ -734,6 +739,11 @@ def main():
         return
     if args.workload == "serve":
         print(json.dumps(serve_workload(args)))
+        return
+    if args.workload == "dslash":
+        st = torch.cuda.Stream()
+        from paper_0811_4331_gb300 import wilson_mg as wm
+        print(json.dumps(dslash_bandwidth(wm, torch, st, tuple(args.dslash_dims), args.dslash_prec)))
         return
     if world > 1:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

@@ -733,6 +733,15 @@ static int init_level(mg_handle* h, int l) {
     set_error("level " + std::to_string(l) + ": nv must be in [1, ncomp/2 * block sites]");
     return MG_EINVAL;
   }
+  // The Galerkin product holds one block of a P column in shared memory.
+  const size_t gal = galerkin_smem_bytes(p.mixed ? MG_F32 : MG_F64, a.ncomp, a.bsites, a.nv);
+  if (gal > kGalerkinSmemMax) {
+    set_error("level " + std::to_string(l) + ": a block of " + std::to_string(a.bsites) + " sites x " +
+              std::to_string(a.ncomp) + " components needs " + std::to_string(gal) +
+              " B of shared memory in the Galerkin product (at most " + std::to_string(kGalerkinSmemMax) +
+              "); use smaller blocks");
+    return MG_EINVAL;
+  }
   return ensure_reducer(h, a.nv);
 }
 

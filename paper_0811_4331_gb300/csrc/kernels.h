@@ -205,6 +205,12 @@ int launch_block_gs(const Agg& g, const double2* cand, double2* P, int* err, cud
 // Columns j0 .. j0 + ncols - 1 at v + (j - j0) * ncomp * V, precision prec (0 or 1) of P and v.
 int launch_p_column(int prec, const Agg& g, const void* P, int j0, int ncols, void* v, cudaStream_t st);
 // Galerkin columns in the arithmetic of `prec` (0: FP64 inputs, 1: FP32 inputs); output always FP64 storage.
+// Shared memory of one Galerkin CTA: a block of the P column (ncomp x bsites)
+// plus 2 nv coefficients, complex in the setup's precision (0 FP64, 1 FP32).
+constexpr size_t kGalerkinSmemMax = 200 * 1024;
+inline size_t galerkin_smem_bytes(int prec, int ncomp, int bsites, int nv) {
+  return ((size_t)ncomp * bsites + 2 * (size_t)nv) * (prec == 0 ? 16 : 8);
+}
 int launch_galerkin_wilson(int prec, const Agg& g, const void* links, double mass, const void* vj, const void* P,
                            int j0, int ncols, double2* Cout, cudaStream_t st);
 int launch_galerkin_stencil(int prec, const Agg& g, const void* Cfine, const void* vj, const void* P, int j0,

@@ -273,7 +273,7 @@ static int galerkin_t(const Agg& g, const Op& op, const void* vj, const void* P,
   typedef typename Store<TP>::R R;
   constexpr int NT = 256;
   const size_t sm = ((size_t)g.ncomp * g.bsites + 2 * g.nv) * sizeof(cx<R>);
-  if (sm > 200 * 1024) return -1;
+  if (sm > kGalerkinSmemMax) return -1;  // mg_setup rejects such blocks up front
   if (sm > 48 * 1024)
     allow_big_smem(galerkin_kernel<Op, TP, NT>);
   galerkin_kernel<Op, TP, NT><<<dim3(g.Vc, ncols), NT, sm, st>>>(g, op, (const TP*)vj, (const TP*)P, j0, Cout);

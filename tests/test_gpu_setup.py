@@ -134,6 +134,20 @@ def test_rank_loss_is_reported():
     assert e.value.status == wm.MG_ERANK
 
 
+
+def test_block_too_large_for_the_galerkin_tile_is_refused():
+    """A block whose P column does not fit the Galerkin CTA's shared memory is refused with a message."""
+    wm = require_gpu()
+    dims = (8, 8, 8, 8)
+    U = inputs.random_gauge(dims, 0)
+    for mixed, ok in ((0, (4, 4, 4, 8)), (1, (4, 4, 8, 8))):  # 512 sites FP64, 1024 sites FP32 still fit
+        p = wm.mg_default_params(n_levels=2, block=[(8, 8, 8, 8)], nv=[4], setup_sweeps=[0], mixed=mixed)
+        with pytest.raises(wm.MgError) as e:
+            wm.mg_setup(U, dims, 0.1, p)
+        assert e.value.status == wm.MG_EINVAL and "shared memory" in str(e.value), str(e.value)
+        p = wm.mg_default_params(n_levels=2, block=[ok], nv=[4], setup_sweeps=[0], mixed=mixed)
+        wm.mg_destroy(wm.mg_setup(U, dims, 0.1, p))
+
 def _to_dev(wm, h, level, arr, prec=0, nrhs=1):
     t = wm.internal_empty(h, level, prec, nrhs)
     wm.mg_field_to_internal(h, level, prec, torch.from_numpy(np.ascontiguousarray(arr)).cuda(), t, nrhs)
