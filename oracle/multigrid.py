@@ -28,6 +28,11 @@ Every function follows a passage of the paper (Clark et al., Lattice 2008):
 * ``fgcr``                -- GCR(50) as the outer Krylov method (Sec. 5),
                              flexible because the preconditioner varies.
 
+Not in the paper: ``mg_setup(..., fine_smoother="eo")`` replaces the fine
+level's MR smoother by the even-odd one of ``evenodd.eo_smooth`` (MR on the
+Schur complement, odd sites solved exactly) in every cycle, including those
+the adaptive steps run.
+
 Readings where the paper is silent: one relaxation =
 one MR step; candidates start from independent Gaussian vectors, get l MR
 steps on A x = 0 with omega = 0.8 and are normalised to unit norm; the QR is
@@ -260,9 +265,18 @@ class Level:
         self.blk = None
         self.stencil = None
         self.lu = None
+        self.smooth = None  # (r, steps, omega) -> (e, r - A e); None = MR on A
 
 
-def mg_setup(U, mass, levels, starts, omega=0.8, nu_pre=2, nu_post=2, coarse_cycles=(4,), coarse_solver="gcr"):
+def smooth(lev, r, steps, omega):
+    """The level's smoother from e = 0: MR on A (Sec. 3) unless the level carries another."""
+    if lev.smooth is not None:
+        return lev.smooth(r, steps, omega)
+    return mr_relax(lev.apply, r, None, steps, omega)
+
+
+def mg_setup(U, mass, levels, starts, omega=0.8, nu_pre=2, nu_post=2, coarse_cycles=(4,), coarse_solver="gcr",
+             fine_smoother="mr"):
     """Build the multigrid hierarchy (Sec. 2 adaptive steps, Sec. 3, Sec. 5).
 
     ``levels`` lists, for every level that gets a coarser one below it, a dict
@@ -270,7 +284,8 @@ def mg_setup(U, mass, levels, starts, omega=0.8, nu_pre=2, nu_post=2, coarse_cyc
     ``adapt_nv``, ``adapt_steps`` and ``adapt_cycles`` (see ``build_levels``).
     ``starts[l]`` are the Nv random start vectors of level l (arrays shaped
     like that level's fields).  The coarsest level gets a dense LU
-    factorisation.  The cycle options are those the adaptive steps run.
+    factorisation.  The cycle options are those the adaptive steps run;
+    ``fine_smoother`` is "mr" (Sec. 3) or "eo" (even-odd, module header).
     """
     lat = U.shape[1:5]
     fine = Level(None, lat, 12)
@@ -280,6 +295,14 @@ def mg_setup(U, mass, levels, starts, omega=0.8, nu_pre=2, nu_post=2, coarse_cyc
         return dirac.wilson_dirac(U, y.reshape(lat + (4, 3)), mass).reshape(lat + (12,))
 
     fine.apply = apply_fine
+    if fine_smoother == "eo":  # even-odd smoother on the fine level (not in the paper)
+        from .evenodd import eo_smooth
+
+        def smooth_eo(r, steps, om):
+            e, res = eo_smooth(U, mass, r.reshape(lat + (4, 3)), steps, om)
+            return e.reshape(lat + (12,)), res.reshape(lat + (12,))
+
+        fine.smooth = smooth_eo
     hier = [fine]
     cycle = dict(nu_pre=nu_pre, nu_post=nu_post, omega=omega, coarse_cycles=coarse_cycles,
                  coarse_solver=coarse_solver)
@@ -413,7 +436,7 @@ def vcycle(hier, l, r, nu_pre=2, nu_post=2, omega=0.8, coarse_cycles=(4,), coars
     lev = hier[l]
     if l == len(hier) - 1:
         return coarsest_solve(lev, r)
-    e, res = mr_relax(lev.apply, r, None, nu_pre, omega)
+    e, res = smooth(lev, r, nu_pre, omega)
     rc = restrict(lev.P, lev.blk, res)
     if l + 1 == len(hier) - 1:
         ec = coarsest_solve(hier[l + 1], rc)
@@ -434,7 +457,7 @@ def vcycle(hier, l, r, nu_pre=2, nu_post=2, omega=0.8, coarse_cycles=(4,), coars
     alpha = minimal_residual_coefficient(Axc, res)
     e = e + alpha * xc
     res = res - alpha * Axc
-    de, res = mr_relax(lev.apply, res, None, nu_post, omega)
+    de, res = smooth(lev, res, nu_post, omega)
     return e + de
 
 
