@@ -102,6 +102,11 @@ typedef struct {
                                          handle (for a hierarchy that only feeds mg_retarget_batch, which
                                          builds every retargeted inverse in shared launches); ignored with
                                          adaptive steps, which need it during setup (default 0) */
+  int fine_smoother;                  /* level-0 smoother of the cycle: 0 = MR on D (Sec. 3, default);
+                                         1 = even-odd (not in the paper): the nu_pre / nu_post MR steps
+                                         run on the Schur complement S of the even sites (see
+                                         schur_apply) from zero, then the odd sites are solved exactly;
+                                         needs every lattice extent even */
 } mg_params;
 
 /* Per right-hand side solve statistics. */
@@ -181,7 +186,14 @@ int mg_solve(mg_handle* h, const double* b, double* x, int nrhs, int on_device, 
 /* Unpreconditioned Krylov solvers on level 0 alone: the methods the paper
  * measures multigrid against (Secs. 4-5).
  *   method : MG_KRYLOV_BICGSTAB -- BiCGstab (van der Vorst 1992) on D x = b;
- *            MG_KRYLOV_CGNR     -- CG on D^+ D x = D^+ b, D^+ = gamma5 D gamma5.
+ *            MG_KRYLOV_CGNR     -- CG on D^+ D x = D^+ b, D^+ = gamma5 D gamma5;
+ *            MG_KRYLOV_*_EO     -- the same method on the even-odd Schur system
+ *              S x_e = b_e + H_eo b_o / (2M) (see schur_apply; not in the
+ *              paper), then x_o = (b_o + H_oe x_e / 2) / M.  The full residual
+ *              of the reconstructed x equals the Schur residual, so the Schur
+ *              solve stops at tol ||b||; needs every lattice extent even.
+ *              stats.fine_dslash counts one per S application (two half-
+ *              lattice hops = one full stencil's work).
  *   FP64 throughout on the handle's FP64 links (any handle: the hierarchy is
  *   not used); one right-hand side after the other; b, x, nrhs, on_device,
  *   tol, stats as mg_solve (stats.iters = iterations, stats.fine_dslash =
@@ -191,6 +203,8 @@ int mg_solve(mg_handle* h, const double* b, double* x, int nrhs, int on_device, 
  * filled), MG_ENAN, MG_ECUDA. */
 #define MG_KRYLOV_BICGSTAB 0
 #define MG_KRYLOV_CGNR 1
+#define MG_KRYLOV_BICGSTAB_EO 2
+#define MG_KRYLOV_CGNR_EO 3
 int krylov_solve(mg_handle* h, int method, const double* b, double* x, int nrhs, int on_device, double tol,
                  int max_iter, mg_stats* stats, void* stream);
 
@@ -198,6 +212,31 @@ int krylov_solve(mg_handle* h, int method, const double* b, double* x, int nrhs,
  * spinors of precision `prec` (device memory; in and out must not overlap).
  * Arithmetic is FP64 for MG_F64 and FP32 otherwise.  Errors: MG_EINVAL. */
 int dslash_apply(mg_handle* h, int prec, const void* in, void* out, int nrhs, void* stream);
+
+/* ---------------------------------------------------------------- even-odd
+ * Not in the paper: the standard Schur-complement (red-black) reduction of
+ * the Sec. 1 operator.  With M = 4 + m and H the hopping term (D = M - H/2),
+ * H links only sites of opposite parity p(n) = (x + y + z + t) mod 2, so
+ *   D = [[M, -H_eo/2], [-H_oe/2, M]],   S = M - H_eo H_oe / (4 M)
+ * is the Schur complement on the even sites, gamma5-Hermitian like D.
+ * HALF layout: [nrhs][12][V/2] complex in precision prec, the sites of one
+ * parity in lexicographic order (half index = site / 2).  Every lattice
+ * extent must be even (MG_EINVAL otherwise).  Device memory; the calls do
+ * not synchronise; the parity-major link copy of precision prec is made on
+ * the first call (one more [4][NL][V] link array, held by the handle). */
+
+/* Split nrhs internal-layout level-0 spinors into their even and odd halves. */
+int eo_split(mg_handle* h, int prec, const void* full, void* even, void* odd, int nrhs, void* stream);
+/* full = merge(even, odd); a NULL half is taken as zero. */
+int eo_merge(mg_handle* h, int prec, const void* even, const void* odd, void* full, int nrhs, void* stream);
+/* out = a x + b H_{p,1-p} in on half fields: out and x (NULL: no a-term) have
+ * parity `parity_out`, in the other parity.  Arithmetic as dslash_apply.
+ * in and out must not overlap; x may equal out only if in does not. */
+int dslash_eo_apply(mg_handle* h, int prec, int parity_out, const void* x, const void* in, void* out, double a,
+                    double b, int nrhs, void* stream);
+/* out = S in on even half fields (two half-lattice hops; an odd half
+ * scratch is taken from the handle's work vectors). */
+int schur_apply(mg_handle* h, int prec, const void* in, void* out, int nrhs, void* stream);
 
 /* out = A_level in for the coarse stencil operator of `level` >= 1
  * (A_l = P^+ A_{l-1} P, Sec. 2), internal layout, device memory.

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libwilsonmg.so")
-SOURCES = ["wilson.cu", "blas.cu", "coarse.cu", "coarse_mma.cu", "transfer_mma.cu", "setup.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["wilson.cu", "wilson_eo.cu", "blas.cu", "coarse.cu", "coarse_mma.cu", "transfer_mma.cu", "setup.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
@@ -73,7 +74,7 @@ inline size_t slot_gcr_pre() { return slot_inner(MG_MAX_LEVELS); }  // <w|r>, ||
 inline size_t slot_total() { return slot_gcr_pre() + 4 * kMaxRhs; }
 const int kInnerBasis = 8;
 
-enum { WV_E, WV_RES, WV_P, WV_XC, WV_AXC, WV_RC, WV_EC, WV_T, WV_DT, WV_IN, WV_A, WV_B, WV_KW, WV_KZ, WV_PR, WV_PE, WV_COUNT };
+enum { WV_E, WV_RES, WV_P, WV_XC, WV_AXC, WV_RC, WV_EC, WV_T, WV_DT, WV_IN, WV_A, WV_B, WV_KW, WV_KZ, WV_PR, WV_PE, WV_EOA, WV_EOB, WV_EOC, WV_COUNT };
 
 int prec_of(const mg_handle* h, int l) {
   if (!h->p.mixed) return MG_F64;
@@ -324,10 +325,10 @@ int op_apply(mg_handle* h, int l, int prec, const void* in, void* out, const voi
 }
 
 int mr_update(mg_handle* h, int l, int prec, void* x_out, const void* x_in, const void* u, void* r_out,
-              const void* r_in, const void* p, size_t slot, double omega, int nrhs) {
+              const void* r_in, const void* p, size_t slot, double omega, int nrhs, size_t n = 0) {
   MrUpdate m;
   m.prec = prec;
-  m.n = h->lev[l]->n();
+  m.n = n ? n : h->lev[l]->n();
   m.nrhs = nrhs;
   m.x_out = x_out;
   m.x_in = x_in;
@@ -365,6 +366,106 @@ int mr_steps(mg_handle* h, int l, int prec, const void* b, void* x, bool x_zero,
     RET(op_apply(h, l, prec, rcur, p, nullptr, 1.0, 0.0, rcur, sl, nrhs));
     RET(mr_update(h, l, prec, x, (s == 0 && x_zero) ? nullptr : x, rcur, res, rcur, p, sl, omega, nrhs));
   }
+  return MG_OK;
+}
+
+// ------------------------------------------------------------------ even-odd (level 0)
+// Half fields hold the V/2 sites of one parity, [nrhs][12][V/2] (see
+// wilson_eo.cu); D = M - H/2 with M = 4 + m, H the hopping term.
+
+// Level-0 links reordered parity-major in precision prec, built on first use.
+int ensure_eo_links(mg_handle* h, int prec) {
+  Level& f = *h->lev[0];
+  if (f.links_eo[prec].p) return MG_OK;
+  if (!f.links[prec].p) {
+    set_error("level-0 operator not stored in this precision");
+    return MG_EINVAL;
+  }
+  if (f.L[0] % 2 || f.L[1] % 2 || f.L[2] % 2 || f.L[3] % 2) {
+    set_error("even-odd operators need every lattice extent even");
+    return MG_EINVAL;
+  }
+  if (h->capturing) {
+    set_error("even-odd links first needed inside a graph capture");
+    return MG_EINVAL;
+  }
+  const size_t NL = prec == MG_F64 ? 9 : 6, eb = bytes_of(prec);
+  if (!f.links_eo[prec].ensure((size_t)4 * NL * f.V * eb)) return MG_ENOMEM;
+  char* base = (char*)f.links_eo[prec].p;
+  LK(launch_eo_split(eb, f.links[prec].p, base, base + (size_t)(f.V / 2) * eb, f.L, 4 * NL, (size_t)f.V, h->st));
+  return MG_OK;
+}
+
+// out_p = a x_p + b H in_{1-p} + c y_p on half fields; with z, <out|z> and ||out||^2 into slot.
+int eo_apply(mg_handle* h, int prec, int parity, const void* x, const void* in, const void* y, void* out, double a_,
+             double b_, double c_, const void* z, size_t slot, int nrhs) {
+  RET(ensure_eo_links(h, prec));
+  Level& f = *h->lev[0];
+  EoCall d;
+  d.prec = prec;
+  d.parity = parity;
+  d.x = x;
+  d.in = in;
+  d.y = y;
+  d.z = z;
+  d.out = out;
+  d.links = f.links_eo[prec].p;
+  for (int m = 0; m < 4; ++m) d.L[m] = f.L[m];
+  d.a = a_;
+  d.b = b_;
+  d.c = c_;
+  d.nrhs = nrhs;
+  d.red = h->red.at(slot, 4);
+  // half spinors in, out, x, y and z where they are other vectors; every link once (forward hops read the
+  // links of the output sites, backward hops those of the other parity)
+  const double hb = 6.0 * f.V * bytes_of(prec);
+  const double lb = 4.0 * f.V * (prec == MG_F64 ? 9 : 6) * bytes_of(prec);
+  const int streams = 2 + (x != nullptr) + (y != nullptr) + (z && z != x && z != y);
+  Prof pf(h, MG_K_DSLASH, prec, nrhs * hb * streams + lb);
+  LK(launch_wilson_eo(d, h->st));
+  return MG_OK;
+}
+
+// out = S in (y null) or y - S in, S = M - H_eo H_oe / (4 M) on even half fields; t is an odd half
+// scratch; with z, <out|z> and ||out||^2 into slot.
+int schur_op(mg_handle* h, int prec, const void* in, void* out, void* t, const void* y, const void* z, size_t slot,
+             int nrhs) {
+  const double M = 4.0 + h->mass;
+  RET(eo_apply(h, prec, 1, nullptr, in, nullptr, t, 0.0, 1.0, 0.0, nullptr, 0, nrhs));
+  if (y) return eo_apply(h, prec, 0, in, t, y, out, -M, 1.0 / (4.0 * M), 1.0, z, slot, nrhs);
+  return eo_apply(h, prec, 0, in, t, nullptr, out, M, -1.0 / (4.0 * M), 0.0, z, slot, nrhs);
+}
+
+// Even-odd smoother on level 0 (not in the paper): e_e = `steps` under-relaxed
+// MR steps (Sec. 3) on S e_e = r^_e = r_e + H_eo r_o / (2 M) from e_e = 0, and
+// the odd sites solved exactly, e_o = (r_o + H_oe e_e / 2) / M.  e receives
+// e_e + e_o (added to e when `add`), res the new residual r - D e, which is the
+// Schur residual on even sites and 0 on odd ones.  res may alias r.
+int eo_smooth(mg_handle* h, int prec, const void* r, void* e, bool add, void* res, int steps, int nrhs) {
+  Level& f = *h->lev[0];
+  const size_t nh = f.n() / 2, hb = nh * nrhs * bytes_of(prec);
+  char* A = (char*)work(h, 0, prec, WV_EOA, nrhs);  // r_e | r_o
+  char* B = (char*)work(h, 0, prec, WV_EOB, nrhs);  // Schur residual | odd scratch
+  char* C = (char*)work(h, 0, prec, WV_EOC, nrhs);  // e_e | e_o
+  char* Pv = (char*)work(h, 0, prec, WV_P, nrhs);   // S applied to the Schur residual
+  if (!A || !B || !C || !Pv) return MG_ENOMEM;
+  void *re = A, *ro = A + hb, *rs = B, *t = B + hb, *ee = C, *eo = C + hb;
+  const double M = 4.0 + h->mass;
+  const size_t sl = slot_level(0);
+  {
+    Prof pf(h, MG_K_VECTOR, prec, 2.0 * hb * 2);
+    LK(launch_eo_split(bytes_of(prec), r, re, ro, f.L, (size_t)12 * nrhs, (size_t)(f.V / 2), h->st));
+  }
+  RET(eo_apply(h, prec, 0, re, ro, nullptr, rs, 1.0, 1.0 / (2.0 * M), 0.0, nullptr, 0, nrhs));
+  if (steps == 0) CK(cudaMemsetAsync(ee, 0, hb, h->st));
+  for (int s = 0; s < steps; ++s) {
+    RET(schur_op(h, prec, rs, Pv, t, nullptr, rs, sl, nrhs));
+    RET(mr_update(h, 0, prec, ee, s == 0 ? nullptr : ee, rs, rs, rs, Pv, sl, h->p.omega, nrhs, nh));
+  }
+  RET(eo_apply(h, prec, 1, ro, ee, nullptr, eo, 1.0 / M, 1.0 / (2.0 * M), 0.0, nullptr, 0, nrhs));
+  Prof pf(h, MG_K_VECTOR, prec, 2.0 * hb * (add ? 4 : 3));
+  LK(launch_eo_merge(prec, ee, eo, e, f.L, (size_t)12 * nrhs, add ? 1 : 0, h->st));
+  LK(launch_eo_merge(prec, rs, nullptr, res, f.L, (size_t)12 * nrhs, 0, h->st));
   return MG_OK;
 }
 
@@ -480,7 +581,11 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
     return MG_EINVAL;
   }
   // pre-smoothing from e = 0
-  RET(mr_steps(h, l, prec, r, e, true, res, h->p.nu_pre, nrhs));
+  const bool eo = l == 0 && h->p.fine_smoother == 1;
+  if (eo)
+    RET(eo_smooth(h, prec, r, e, false, res, h->p.nu_pre, nrhs));
+  else
+    RET(mr_steps(h, l, prec, r, e, true, res, h->p.nu_pre, nrhs));
   // restrict, coarse solve, prolong
   const Agg g = agg_of(a);
   const double pbytes = (double)a.Vc * 2 * a.nv * a.nhalf * a.bsites * bytes_of(prec);  // P once
@@ -532,6 +637,7 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
   RET(op_apply(h, l, prec, xc, axc, nullptr, 1.0, 0.0, res, sl, nrhs));
   RET(mr_update(h, l, prec, e, e, xc, res, res, axc, sl, 1.0, nrhs));
   // post-smoothing
+  if (eo) return eo_smooth(h, prec, res, e, true, res, h->p.nu_post, nrhs);
   RET(mr_steps(h, l, prec, res, e, false, res, h->p.nu_post, nrhs));
   return MG_OK;
 }
@@ -1039,6 +1145,14 @@ int mg_setup(mg_handle** hout, const double* gauge, int gauge_on_device, const i
     set_error("mixed precision needs coarse_prec == F32 or coarse_prec == fine_prec (the transfer kernels' pairs)");
     return MG_EINVAL;
   }
+  if (p->fine_smoother != 0 && p->fine_smoother != 1) {
+    set_error("fine_smoother must be 0 (MR) or 1 (even-odd)");
+    return MG_EINVAL;
+  }
+  if (p->fine_smoother == 1 && (dims[0] % 2 || dims[1] % 2 || dims[2] % 2 || dims[3] % 2)) {
+    set_error("the even-odd smoother needs every lattice extent even");
+    return MG_EINVAL;
+  }
   mg_handle* h = new mg_handle();
   h->p = *p;
   h->mass = mass;
@@ -1082,9 +1196,9 @@ static int retarget_impl(const mg_handle* src, mg_handle* h, bool coarsest = tru
     b.sweeps = a.sweeps;
     b.cycles = a.cycles;
     for (int pr = 0; pr < 4; ++pr) {
-      const DevBuf* from[3] = {&a.links[pr], &a.cop[pr], &a.P[pr]};
-      DevBuf* to[3] = {&b.links[pr], &b.cop[pr], &b.P[pr]};
-      for (int q = 0; q < 3; ++q) {
+      const DevBuf* from[4] = {&a.links[pr], &a.cop[pr], &a.P[pr], &a.links_eo[pr]};
+      DevBuf* to[4] = {&b.links[pr], &b.cop[pr], &b.P[pr], &b.links_eo[pr]};
+      for (int q = 0; q < 4; ++q) {
         if (!from[q]->p) continue;
         if (!to[q]->ensure(from[q]->bytes)) return MG_ENOMEM;
         CK(cudaMemcpyAsync(to[q]->p, from[q]->p, from[q]->bytes, cudaMemcpyDeviceToDevice, st));
@@ -1187,6 +1301,64 @@ int dslash_apply(mg_handle* h, int prec, const void* in, void* out, int nrhs, vo
   h->st = (cudaStream_t)stream;
   int rc = ensure_reducer(h, nrhs);
   if (rc == MG_OK) rc = op_apply(h, 0, prec, in, out, nullptr, 1.0, 0.0, nullptr, 0, nrhs);
+  h->st = keep;
+  return rc;
+}
+
+static int eo_args_ok(mg_handle* h, int prec, int nrhs, const char* who) {
+  if (!h || nrhs < 1 || check_prec(prec)) {
+    set_error(std::string(who) + ": bad argument");
+    return MG_EINVAL;
+  }
+  const Level& f = *h->lev[0];
+  if (f.L[0] % 2 || f.L[1] % 2 || f.L[2] % 2 || f.L[3] % 2) {
+    set_error(std::string(who) + ": every lattice extent must be even");
+    return MG_EINVAL;
+  }
+  return MG_OK;
+}
+
+int eo_split(mg_handle* h, int prec, const void* full, void* even, void* odd, int nrhs, void* stream) {
+  RET(eo_args_ok(h, prec, nrhs, "eo_split"));
+  if (!full || !even || !odd) return MG_EINVAL;
+  const Level& f = *h->lev[0];
+  LK(launch_eo_split(bytes_of(prec), full, even, odd, f.L, (size_t)12 * nrhs, (size_t)(f.V / 2),
+                     (cudaStream_t)stream));
+  return MG_OK;
+}
+
+int eo_merge(mg_handle* h, int prec, const void* even, const void* odd, void* full, int nrhs, void* stream) {
+  RET(eo_args_ok(h, prec, nrhs, "eo_merge"));
+  if (!full) return MG_EINVAL;
+  const Level& f = *h->lev[0];
+  LK(launch_eo_merge(prec, even, odd, full, f.L, (size_t)12 * nrhs, 0, (cudaStream_t)stream));
+  return MG_OK;
+}
+
+int dslash_eo_apply(mg_handle* h, int prec, int parity_out, const void* x, const void* in, void* out, double a,
+                    double b, int nrhs, void* stream) {
+  RET(eo_args_ok(h, prec, nrhs, "dslash_eo_apply"));
+  if (!in || !out || (parity_out != 0 && parity_out != 1)) {
+    set_error("dslash_eo_apply: bad argument");
+    return MG_EINVAL;
+  }
+  cudaStream_t keep = h->st;
+  h->st = (cudaStream_t)stream;
+  int rc = ensure_reducer(h, nrhs);
+  if (rc == MG_OK) rc = eo_apply(h, prec, parity_out, x, in, nullptr, out, x ? a : 0.0, b, 0.0, nullptr, 0, nrhs);
+  h->st = keep;
+  return rc;
+}
+
+int schur_apply(mg_handle* h, int prec, const void* in, void* out, int nrhs, void* stream) {
+  RET(eo_args_ok(h, prec, nrhs, "schur_apply"));
+  if (!in || !out) return MG_EINVAL;
+  cudaStream_t keep = h->st;
+  h->st = (cudaStream_t)stream;
+  int rc = ensure_reducer(h, nrhs);
+  void* t = rc == MG_OK ? work(h, 0, prec, WV_EOB, nrhs) : nullptr;
+  if (rc == MG_OK && !t) rc = MG_ENOMEM;
+  if (rc == MG_OK) rc = schur_op(h, prec, in, out, t, nullptr, nullptr, 0, nrhs);
   h->st = keep;
   return rc;
 }
@@ -1644,15 +1816,23 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
 // ====================================================================== Krylov baselines
 namespace {
 
-// D^+ v = gamma5 D gamma5 v (gamma5-Hermiticity, Sec. 1) on level 0, FP64:
-// components 6..11 (spins 2 and 3) change sign before and after the stencil.
-int dslash_dag(mg_handle* h, const void* in, void* out, void* tmp) {
-  Level& f = *h->lev[0];
-  const size_t half = (size_t)6 * f.V;
+// A level-0 FP64 system for the Krylov baselines: the full operator D on
+// [12][V] fields, or the even-odd Schur complement S on [12][V/2] halves.
+// Both are gamma5-Hermitian (Sec. 1), and in both layouts components 6..11
+// (spins 2 and 3, chirality -) are the second half of the vector.
+struct KSys {
+  size_t n;                                                     // complex elements of a vector
+  std::function<int(const void* in, void* out)> apply;          // out = A in
+  std::function<int(const void* x, void* r, const void* b)> resid;  // r = b - A x
+};
+
+// out = A^+ in = gamma5 A gamma5 in: the chirality - half changes sign before and after A.
+int apply_dag(mg_handle* h, const KSys& sys, const void* in, void* out, void* tmp) {
+  const size_t half = sys.n / 2;
   CK(cudaMemcpyAsync(tmp, in, half * 16, cudaMemcpyDeviceToDevice, h->st));
   LK(launch_convert(MG_F64, MG_F64, half, 1, (const char*)in + half * 16, (char*)tmp + half * 16, -1.0, nullptr, 0,
                     0.0, 0, h->st));
-  RET(op_apply(h, 0, MG_F64, tmp, out, nullptr, 1.0, 0.0, nullptr, 0, 1));
+  RET(sys.apply(tmp, out));
   LK(launch_convert(MG_F64, MG_F64, half, 1, (char*)out + half * 16, (char*)out + half * 16, -1.0, nullptr, 0, 0.0,
                     0, h->st));
   return MG_OK;
@@ -1668,8 +1848,8 @@ inline Cx cdiv(Cx a, Cx b) {
 inline Cx cmul(Cx a, Cx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
 
 // out = c0 x0 + c1 x1 + c2 x2, with <w|out>, ||out||^2 into slot (w optional)
-int lincomb(mg_handle* h, double2* out, std::initializer_list<std::pair<const void*, Cx>> terms, const void* w,
-            size_t slot) {
+int lincomb(mg_handle* h, size_t n, double2* out, std::initializer_list<std::pair<const void*, Cx>> terms,
+            const void* w, size_t slot) {
   LinComb L;
   L.out = out;
   L.w = (const double2*)w;
@@ -1683,15 +1863,13 @@ int lincomb(mg_handle* h, double2* out, std::initializer_list<std::pair<const vo
     L.x[t] = nullptr;
     L.c[t] = make_double2(0.0, 0.0);
   }
-  const size_t n = h->lev[0]->n();
   Prof pf(h, MG_K_VECTOR, MG_F64, (double)n * 16 * (terms.size() + 1 + (w != nullptr)));
   LK(launch_lincomb(n, L, h->red.at(slot, 4), h->st));
   return MG_OK;
 }
 
-// <a|b>, ||a||^2, ||b||^2 of two FP64 level-0 vectors, read back
-int dot3(mg_handle* h, const void* a, const void* b, Cx* ab, double* aa, double* bb) {
-  const size_t n = h->lev[0]->n();
+// <a|b>, ||a||^2, ||b||^2 of two FP64 vectors of n elements, read back
+int dot3(mg_handle* h, size_t n, const void* a, const void* b, Cx* ab, double* aa, double* bb) {
   {
     Prof pf(h, MG_K_VECTOR, MG_F64, (double)n * 16 * (a == b ? 1 : 2));
     LK(launch_dot(MG_F64, n, 1, a, b, h->red.at(slot_misc(), 4), h->st));
@@ -1704,8 +1882,9 @@ int dot3(mg_handle* h, const void* a, const void* b, Cx* ab, double* aa, double*
   return MG_OK;
 }
 
-int krylov_one(mg_handle* h, int method, double2* b, double2* x, double tol, int max_iter, mg_stats* st) {
-  const size_t n = h->lev[0]->n(), vb = n * 16;
+int krylov_one(mg_handle* h, const KSys& sys, int method, double2* b, double2* x, double tol, int max_iter,
+               mg_stats* st) {
+  const size_t n = sys.n, vb = n * 16;
   DevBuf buf;
   if (!buf.ensure(vb * 6)) return MG_ENOMEM;
   double2* r = buf.as<double2>();
@@ -1717,7 +1896,7 @@ int krylov_one(mg_handle* h, int method, double2* b, double2* x, double tol, int
   long long mv = 0;
   int iters = 0;
   double bb = 0.0, rr = 0.0;
-  RET(dot3(h, b, b, nullptr, &bb, nullptr));
+  RET(dot3(h, n, b, b, nullptr, &bb, nullptr));
   const double bn = sqrt(bb);
   if (!(bn > 0.0)) {
     set_error("krylov_solve: zero right-hand side");
@@ -1726,9 +1905,9 @@ int krylov_one(mg_handle* h, int method, double2* b, double2* x, double tol, int
   int status = MG_ENOCONV;
   const size_t sl = slot_misc() + 4;
   while (iters < max_iter) {
-    RET(op_apply(h, 0, MG_F64, x, r, b, -1.0, 1.0, nullptr, 0, 1));  // r = b - D x
+    RET(sys.resid(x, r, b));  // r = b - A x
     ++mv;
-    RET(dot3(h, r, r, nullptr, &rr, nullptr));
+    RET(dot3(h, n, r, r, nullptr, &rr, nullptr));
     if (!isfinite(rr)) {
       set_error("krylov_solve: residual is not finite");
       return MG_ENAN;
@@ -1745,27 +1924,27 @@ int krylov_one(mg_handle* h, int method, double2* b, double2* x, double tol, int
       while (iters < max_iter) {
         const Cx beta = cmul(cdiv(rho_new, rho), cdiv(alpha, omega));
         const Cx bo = cmul(beta, omega);
-        RET(lincomb(h, v2, {{r, {1, 0}}, {v2, beta}, {v3, {-bo.re, -bo.im}}}, nullptr, sl));  // p
-        RET(op_apply(h, 0, MG_F64, v2, v3, nullptr, 1.0, 0.0, nullptr, 0, 1));              // v = D p
+        RET(lincomb(h, n, v2, {{r, {1, 0}}, {v2, beta}, {v3, {-bo.re, -bo.im}}}, nullptr, sl));  // p
+        RET(sys.apply(v2, v3));  // v = A p
         ++mv;
         Cx rv;
-        RET(dot3(h, v1, v3, &rv, nullptr, nullptr));
+        RET(dot3(h, n, v1, v3, &rv, nullptr, nullptr));
         alpha = cdiv(rho_new, rv);
-        RET(lincomb(h, v4, {{r, {1, 0}}, {v3, {-alpha.re, -alpha.im}}}, v1, sl));  // s = r - alpha v
+        RET(lincomb(h, n, v4, {{r, {1, 0}}, {v3, {-alpha.re, -alpha.im}}}, v1, sl));  // s = r - alpha v
         RET(read_slots(h, sl, 4));
         ++iters;
         if (sqrt(h->host_slots[2]) <= tol * bn) {  // converged on the half step
-          RET(lincomb(h, x, {{x, {1, 0}}, {v2, alpha}}, nullptr, sl));
+          RET(lincomb(h, n, x, {{x, {1, 0}}, {v2, alpha}}, nullptr, sl));
           break;
         }
-        RET(op_apply(h, 0, MG_F64, v4, v5, nullptr, 1.0, 0.0, nullptr, 0, 1));  // t = D s
+        RET(sys.apply(v4, v5));  // t = A s
         ++mv;
         Cx ts;
         double tt = 0.0;
-        RET(dot3(h, v5, v4, &ts, &tt, nullptr));
+        RET(dot3(h, n, v5, v4, &ts, &tt, nullptr));
         omega = {ts.re / tt, ts.im / tt};
-        RET(lincomb(h, x, {{x, {1, 0}}, {v2, alpha}, {v4, omega}}, nullptr, sl));          // x += alpha p + omega s
-        RET(lincomb(h, r, {{v4, {1, 0}}, {v5, {-omega.re, -omega.im}}}, v1, sl));          // r = s - omega t
+        RET(lincomb(h, n, x, {{x, {1, 0}}, {v2, alpha}, {v4, omega}}, nullptr, sl));          // x += alpha p + omega s
+        RET(lincomb(h, n, r, {{v4, {1, 0}}, {v5, {-omega.re, -omega.im}}}, v1, sl));          // r = s - omega t
         RET(read_slots(h, sl, 4));
         rho = rho_new;
         rho_new = {h->host_slots[0], h->host_slots[1]};
@@ -1777,19 +1956,19 @@ int krylov_one(mg_handle* h, int method, double2* b, double2* x, double tol, int
         if (rn <= tol * bn) break;
       }
     } else {
-      RET(dslash_dag(h, r, v1, v4));  // z = D^+ r
+      RET(apply_dag(h, sys, r, v1, v4));  // z = A^+ r
       ++mv;
       CK(cudaMemcpyAsync(v2, v1, vb, cudaMemcpyDeviceToDevice, h->st));
       double zz = 0.0;
-      RET(dot3(h, v1, v1, nullptr, &zz, nullptr));
+      RET(dot3(h, n, v1, v1, nullptr, &zz, nullptr));
       while (iters < max_iter) {
-        RET(op_apply(h, 0, MG_F64, v2, v3, nullptr, 1.0, 0.0, nullptr, 0, 1));  // q = D p
+        RET(sys.apply(v2, v3));  // q = A p
         ++mv;
         double qq = 0.0;
-        RET(dot3(h, v3, v3, nullptr, &qq, nullptr));
+        RET(dot3(h, n, v3, v3, nullptr, &qq, nullptr));
         const double a = zz / qq;
-        RET(lincomb(h, x, {{x, {1, 0}}, {v2, {a, 0}}}, nullptr, sl));
-        RET(lincomb(h, r, {{r, {1, 0}}, {v3, {-a, 0}}}, r, sl));
+        RET(lincomb(h, n, x, {{x, {1, 0}}, {v2, {a, 0}}}, nullptr, sl));
+        RET(lincomb(h, n, r, {{r, {1, 0}}, {v3, {-a, 0}}}, r, sl));
         RET(read_slots(h, sl, 4));
         ++iters;
         const double rn = sqrt(h->host_slots[2]);
@@ -1798,19 +1977,19 @@ int krylov_one(mg_handle* h, int method, double2* b, double2* x, double tol, int
           return MG_ENAN;
         }
         if (rn <= tol * bn) break;
-        RET(dslash_dag(h, r, v1, v4));
+        RET(apply_dag(h, sys, r, v1, v4));
         ++mv;
         double zn = 0.0;
-        RET(dot3(h, v1, v1, nullptr, &zn, nullptr));
-        RET(lincomb(h, v2, {{v1, {1, 0}}, {v2, {zn / zz, 0}}}, nullptr, sl));
+        RET(dot3(h, n, v1, v1, nullptr, &zn, nullptr));
+        RET(lincomb(h, n, v2, {{v1, {1, 0}}, {v2, {zn / zz, 0}}}, nullptr, sl));
         zz = zn;
       }
     }
   }
   if (status != MG_OK) {  // the true residual at exit
-    RET(op_apply(h, 0, MG_F64, x, r, b, -1.0, 1.0, nullptr, 0, 1));
+    RET(sys.resid(x, r, b));
     ++mv;
-    RET(dot3(h, r, r, nullptr, &rr, nullptr));
+    RET(dot3(h, n, r, r, nullptr, &rr, nullptr));
     if (sqrt(rr) <= tol * bn) status = MG_OK;
   }
   if (st) {
@@ -1824,15 +2003,97 @@ int krylov_one(mg_handle* h, int method, double2* b, double2* x, double tol, int
   return status;
 }
 
+// One right-hand side through the even-odd Schur system (FP64): b^_e = b_e +
+// H_eo b_o / (2M), the Krylov method on S x_e = b^_e, x_o = (b_o + H_oe x_e / 2) / M.
+// The full residual of the reconstructed x equals the Schur residual (exactly,
+// up to rounding), so the Schur solve stops at tol ||b||; if rounding leaves the
+// full true residual above tol ||b||, the Schur solve continues with a tighter
+// target (at most 3 times).
+int krylov_eo_one(mg_handle* h, int method, double2* b, double2* x, double tol, int max_iter, mg_stats* st) {
+  Level& f = *h->lev[0];
+  const size_t n = f.n(), nh = n / 2;
+  const double M = 4.0 + h->mass;
+  DevBuf buf;
+  if (!buf.ensure(nh * 16 * 6 + n * 16)) return MG_ENOMEM;
+  double2* be = buf.as<double2>();
+  double2* bo = be + nh;
+  double2* bh = bo + nh;
+  double2* xe = bh + nh;
+  double2* xo = xe + nh;
+  double2* t = xo + nh;
+  double2* rf = t + nh;  // full residual
+  KSys sys;
+  sys.n = nh;
+  sys.apply = [&](const void* in, void* out) { return schur_op(h, MG_F64, in, out, t, nullptr, nullptr, 0, 1); };
+  sys.resid = [&](const void* xx, void* r, const void* bb) {
+    return schur_op(h, MG_F64, xx, r, t, bb, nullptr, 0, 1);
+  };
+  LK(launch_eo_split(16, b, be, bo, f.L, 12, nh / 12, h->st));
+  LK(launch_eo_split(16, x, xe, xo, f.L, 12, nh / 12, h->st));
+  RET(eo_apply(h, MG_F64, 0, be, bo, nullptr, bh, 1.0, 1.0 / (2.0 * M), 0.0, nullptr, 0, 1));
+  double b2 = 0.0, bh2 = 0.0;
+  RET(dot3(h, n, b, b, nullptr, &b2, nullptr));
+  RET(dot3(h, nh, bh, bh, nullptr, &bh2, nullptr));
+  const double bn = sqrt(b2);
+  if (!(bn > 0.0) || !(bh2 > 0.0)) {
+    set_error("krylov_solve: zero right-hand side");
+    return MG_EINVAL;
+  }
+  double target = tol * bn / sqrt(bh2);
+  long long mv = 1;  // the two half hops of b^_e and x_o
+  int iters = 0, status = MG_ENOCONV;
+  double rel = 0.0;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    mg_stats s1;
+    const int s = krylov_one(h, sys, method, bh, xe, target, max_iter - iters, &s1);
+    if (s != MG_OK && s != MG_ENOCONV) return s;
+    iters += s1.iters;
+    mv += s1.fine_dslash;
+    RET(eo_apply(h, MG_F64, 1, bo, xe, nullptr, xo, 1.0 / M, 1.0 / (2.0 * M), 0.0, nullptr, 0, 1));
+    LK(launch_eo_merge(MG_F64, xe, xo, x, f.L, 12, 0, h->st));
+    RET(op_apply(h, 0, MG_F64, x, rf, b, -1.0, 1.0, nullptr, 0, 1));  // the full true residual
+    ++mv;
+    double r2 = 0.0;
+    RET(dot3(h, n, rf, rf, nullptr, &r2, nullptr));
+    rel = sqrt(r2) / bn;
+    if (!isfinite(rel)) {
+      set_error("krylov_solve: residual is not finite");
+      return MG_ENAN;
+    }
+    if (rel <= tol) {
+      status = MG_OK;
+      break;
+    }
+    if (s == MG_ENOCONV || iters >= max_iter) break;
+    target *= 0.5 * tol / rel;
+  }
+  if (st) {
+    st->iters = iters;
+    st->restarts = 0;
+    st->reliable_updates = 0;
+    st->fine_dslash = mv;
+    st->fine_dslash_f64 = mv;
+    st->true_rel_residual = rel;
+  }
+  return status;
+}
+
 }  // namespace
 
 extern "C" int krylov_solve(mg_handle* h, int method, const double* b_ext, double* x_ext, int nrhs, int on_device,
                             double tol, int max_iter, mg_stats* stats, void* stream) {
-  if (!h || !b_ext || !x_ext || nrhs < 1 || !(tol > 0.0) || max_iter < 1 ||
-      (method != MG_KRYLOV_BICGSTAB && method != MG_KRYLOV_CGNR) || !h->lev[0]->links[MG_F64].p) {
+  const bool eo = method == MG_KRYLOV_BICGSTAB_EO || method == MG_KRYLOV_CGNR_EO;
+  if (!h || !b_ext || !x_ext || nrhs < 1 || !(tol > 0.0) || max_iter < 1 || method < 0 ||
+      method > MG_KRYLOV_CGNR_EO || !h->lev[0]->links[MG_F64].p) {
     set_error("krylov_solve: bad argument");
     return MG_EINVAL;
   }
+  const Level& f0 = *h->lev[0];
+  if (eo && (f0.L[0] % 2 || f0.L[1] % 2 || f0.L[2] % 2 || f0.L[3] % 2)) {
+    set_error("krylov_solve: the even-odd methods need every lattice extent even");
+    return MG_EINVAL;
+  }
+  const int base = eo ? method - MG_KRYLOV_BICGSTAB_EO : method;
   cudaStream_t keep = h->st;
   h->st = (cudaStream_t)stream;
   Level& f = *h->lev[0];
@@ -1843,6 +2104,12 @@ extern "C" int krylov_solve(mg_handle* h, int method, const double* b_ext, doubl
     h->st = keep;
     return MG_ENOMEM;
   }
+  KSys full;
+  full.n = n;
+  full.apply = [&](const void* in, void* out) { return op_apply(h, 0, MG_F64, in, out, nullptr, 1.0, 0.0, nullptr, 0, 1); };
+  full.resid = [&](const void* xx, void* r, const void* bb) {
+    return op_apply(h, 0, MG_F64, xx, r, bb, -1.0, 1.0, nullptr, 0, 1);
+  };
   auto body = [&]() -> int {
     RET(ensure_reducer(h, 1));
     const void* bs = b_ext;
@@ -1860,7 +2127,9 @@ extern "C" int krylov_solve(mg_handle* h, int method, const double* b_ext, doubl
     int worst = MG_OK;
     for (int r = 0; r < nrhs; ++r) {
       auto t0 = std::chrono::steady_clock::now();
-      const int s = krylov_one(h, method, B + n * r, X + n * r, tol, max_iter, stats ? stats + r : nullptr);
+      mg_stats* sr = stats ? stats + r : nullptr;
+      const int s = eo ? krylov_eo_one(h, base, B + n * r, X + n * r, tol, max_iter, sr)
+                       : krylov_one(h, full, base, B + n * r, X + n * r, tol, max_iter, sr);
       if (s != MG_OK && s != MG_ENOCONV) return s;
       if (s == MG_ENOCONV) worst = s;
       if (stats) stats[r].solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

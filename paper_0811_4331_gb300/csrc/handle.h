@@ -61,6 +61,7 @@ struct Level {
   int cycles = 1;
   // operator of this level, per storage precision (index = precision code)
   DevBuf links[4];  // level 0: [4][NL][V]
+  DevBuf links_eo[4];  // level 0, even-odd kernels: [4][NL][V], sites parity-major (built on first use)
   DevBuf cop[4];    // level >= 1: stencil [9][ncomp][ncomp][V]
   DevBuf cop_mma;   // level >= 1 (coarse_mma): BF16 stencil in MMA fragment order
   // prolongator to level l+1, per precision: [Vc][2][nv][nhalf][bsites]

@@ -30,6 +30,33 @@ int wilson_variants(int prec, bool dots, int nrhs, int V);
 int wilson_blocks(int V);
 int launch_pack_links(int prec, const void* ext, void* out, int V, cudaStream_t st);
 
+// Even-odd stencil on half-lattice fields [nrhs][12][V/2] (every extent even):
+// out_p = a x_p + b H_{p,1-p} in_{1-p} + c y_p, H the hopping term of D =
+// (4 + m) - H / 2; links parity-major [4][NL][V] (launch_eo_split of the
+// packed links with rows = 4 NL, hstride = V, odd = even + V/2).
+struct EoCall {
+  int prec;
+  int parity;  // of out
+  const void* x;  // may be null
+  const void* in;
+  const void* y;  // may be null
+  const void* z;  // optional: reduce <out|z>, ||out||^2 per right-hand side into red
+  void* out;
+  const void* links;
+  int L[4];
+  double a, b, c;
+  int nrhs;
+  RedArgs red;
+};
+int launch_wilson_eo(const EoCall& d, cudaStream_t st);
+int eo_blocks(int V);
+// full rows of V elements (elem_bytes each) -> even and odd rows of V/2 at stride hstride.
+int launch_eo_split(size_t elem_bytes, const void* full, void* even, void* odd, const int L[4], size_t rows,
+                    size_t hstride, cudaStream_t st);
+// full = (add ? full : 0) + merge(even, odd), rows of V / V/2 elements; a null half is zero.
+int launch_eo_merge(int prec, const void* even, const void* odd, void* full, const int L[4], size_t rows, int add,
+                    cudaStream_t st);
+
 // ------------------------------------------------------------------ vectors
 // Every vector kernel works on nrhs vectors of n complex elements each,
 // right-hand side r at offset r * n.  Grid sizes are a pure function of n.

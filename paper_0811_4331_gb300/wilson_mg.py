@@ -49,6 +49,7 @@ class mg_params(ctypes.Structure):
         ("adapt_cycles", ctypes.c_int),
         ("adapt_nv", ctypes.c_int * 3),
         ("defer_coarsest", ctypes.c_int),
+        ("fine_smoother", ctypes.c_int),
     ]
 
 
@@ -89,6 +90,10 @@ def _load():
         "mg_solve": (I, [VP, VP, VP, I, I, D, P(mg_stats), VP]),
         "krylov_solve": (I, [VP, I, VP, VP, I, I, D, I, P(mg_stats), VP]),
         "dslash_apply": (I, [VP, I, VP, VP, I, VP]),
+        "eo_split": (I, [VP, I, VP, VP, VP, I, VP]),
+        "eo_merge": (I, [VP, I, VP, VP, VP, I, VP]),
+        "dslash_eo_apply": (I, [VP, I, I, VP, VP, VP, D, D, I, VP]),
+        "schur_apply": (I, [VP, I, VP, VP, I, VP]),
         "coarse_apply": (I, [VP, I, I, VP, VP, I, VP]),
         "restrict_apply": (I, [VP, I, I, VP, VP, I, VP]),
         "prolong_apply": (I, [VP, I, I, VP, VP, I, VP]),
@@ -122,7 +127,8 @@ EXPORTS = ["mg_last_error", "mg_default_params", "mg_setup", "mg_retarget", "mg_
            "coarse_apply", "restrict_apply", "prolong_apply", "mr_apply", "vcycle_apply", "mg_field_to_internal",
            "mg_field_from_internal", "mg_level_info", "mg_get_prolongator", "mg_get_coarse_op", "mg_footprint",
            "mg_profile", "mg_profile_read", "mg_profile_bytes", "mg_launch_count", "mr_apply_noalloc", "mg_tune",
-           "mg_tune_report", "krylov_solve", "mg_retarget_batch"]
+           "mg_tune_report", "krylov_solve", "mg_retarget_batch", "eo_split", "eo_merge", "dslash_eo_apply",
+           "schur_apply"]
 
 (MG_K_DSLASH, MG_K_COARSE, MG_K_RESTRICT, MG_K_PROLONG, MG_K_VECTOR, MG_K_COARSEST, MG_K_SETUP, MG_K_GALERKIN,
  MG_K_INVERSE, MG_K_GRAM) = range(10)
@@ -262,12 +268,12 @@ def mg_solve(h, b, x, tol, stream=None, raise_on_noconv=True):
     return status, stats
 
 
-MG_KRYLOV_BICGSTAB, MG_KRYLOV_CGNR = 0, 1
+MG_KRYLOV_BICGSTAB, MG_KRYLOV_CGNR, MG_KRYLOV_BICGSTAB_EO, MG_KRYLOV_CGNR_EO = 0, 1, 2, 3
 
 
 def krylov_solve(h, method, b, x, tol, max_iter=100000, stream=None, raise_on_noconv=True):
-    """Unpreconditioned BiCGstab or CG-on-the-normal-equations solve (FP64) in place on x.
-    Returns (status, [stats dict per rhs])."""
+    """Unpreconditioned BiCGstab or CG-on-the-normal-equations solve (FP64) in place on x, on the full
+    system or (the *_EO methods) on its even-odd Schur complement.  Returns (status, [stats dict per rhs])."""
     shp = b.shape
     nrhs = 1 if len(shp) == 6 else int(shp[0])
     st = (mg_stats * nrhs)()
@@ -284,6 +290,28 @@ def krylov_solve(h, method, b, x, tol, max_iter=100000, stream=None, raise_on_no
 
 def dslash_apply(h, prec, inp, out, nrhs=1, stream=None):
     _check(LIB.dslash_apply(h.ptr, prec, _ptr(inp)[0], _ptr(out)[0], nrhs, _stream(stream)))
+
+
+def eo_split(h, prec, full, even, odd, nrhs=1, stream=None):
+    _check(LIB.eo_split(h.ptr, prec, _ptr(full)[0], _ptr(even)[0], _ptr(odd)[0], nrhs, _stream(stream)))
+
+
+def eo_merge(h, prec, even, odd, full, nrhs=1, stream=None):
+    """full = merge(even, odd); None for a half means zero."""
+    ep = _ptr(even)[0] if even is not None else None
+    op = _ptr(odd)[0] if odd is not None else None
+    _check(LIB.eo_merge(h.ptr, prec, ep, op, _ptr(full)[0], nrhs, _stream(stream)))
+
+
+def dslash_eo_apply(h, prec, parity_out, x, inp, out, a, b, nrhs=1, stream=None):
+    """out = a x + b H_{p,1-p} inp on half fields (x None: no a-term)."""
+    xp = _ptr(x)[0] if x is not None else None
+    _check(LIB.dslash_eo_apply(h.ptr, prec, int(parity_out), xp, _ptr(inp)[0], _ptr(out)[0], float(a), float(b),
+                               nrhs, _stream(stream)))
+
+
+def schur_apply(h, prec, inp, out, nrhs=1, stream=None):
+    _check(LIB.schur_apply(h.ptr, prec, _ptr(inp)[0], _ptr(out)[0], nrhs, _stream(stream)))
 
 
 def coarse_apply(h, level, prec, inp, out, nrhs=1, stream=None):
@@ -392,11 +420,12 @@ def mg_profile_bytes(h, kclass, prec):
     return b.value
 
 
-def internal_empty(h, level, prec, nrhs=1, device="cuda"):
-    """Allocate an internal-layout field of `level` (torch CUDA tensor)."""
+def internal_empty(h, level, prec, nrhs=1, device="cuda", half=False):
+    """Allocate an internal-layout field of `level` (torch CUDA tensor); half=True: a level-0 half field
+    (the V/2 sites of one parity)."""
     import torch
     dims, nc, _ = mg_level_info(h, level)
-    V = int(np.prod(dims))
+    V = int(np.prod(dims)) // (2 if half else 1)
     if prec == MG_F64:
         return torch.empty((nrhs, nc, V), dtype=torch.complex128, device=device)
     if prec == MG_F32:
