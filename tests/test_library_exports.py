@@ -14,7 +14,7 @@ def declared_symbols():
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
     return sorted(set(n for n in names if n.startswith(("mg_", "dslash", "coarse", "restrict", "prolong", "mr_",
-                                                         "vcycle", "krylov"))))
+                                                         "vcycle", "krylov", "eo_", "schur"))))
 
 
 @pytest.fixture(scope="module")
