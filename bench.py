@@ -139,6 +139,7 @@ def native(args, rank, world, U, b):
     Ud = torch.from_numpy(U).cuda()
     bd = torch.from_numpy(b).cuda()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    solve_streams = [torch.cuda.Stream() for _ in DMASSES]
 
     def step(mixed, host=False, stats_out=None, smoother=0):
         """One mass sweep: null-vector setup once at the lightest mass, every other mass
@@ -146,15 +147,18 @@ def native(args, rank, world, U, b):
         p = params(wm, mixed, smoother)
         p.defer_coarsest = 1  # the four coarsest inverses are built together by the batched retarget
         base = wm.mg_setup(U if host else Ud, DIMS, masses[-1], p, stream=stream)
-        hs = dict(zip(masses, wm.mg_retarget_batch(base, masses, stream=stream)))
-        for m in masses:
-            h = hs.pop(m)
-            if host:
-                x = np.zeros_like(b)
-                _, st = wm.mg_solve(h, b, x, TOL, stream=stream)
-            else:
-                x = torch.zeros_like(bd)
-                _, st = wm.mg_solve(h, bd, x, TOL, stream=stream)
+        hs = wm.mg_retarget_batch(base, masses, stream=stream)
+        # the four solves side by side, one host thread and stream each
+        if host:
+            bs = [b] * len(masses)
+            xs = [np.zeros_like(b) for _ in masses]
+        else:
+            bs = [bd] * len(masses)
+            xs = [torch.zeros_like(bd) for _ in masses]
+            for q in solve_streams:
+                q.wait_stream(stream)
+        _, sts = wm.mg_solve_many(hs, bs, xs, TOL, streams=solve_streams)
+        for m, h, x, st in zip(masses, hs, xs, sts):
             if stats_out is not None:
                 stats_out.append((m, st[0], x if host else x.cpu().numpy()))
             wm.mg_destroy(h)

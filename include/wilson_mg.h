@@ -183,6 +183,19 @@ int mg_destroy(mg_handle* h);
 int mg_solve(mg_handle* h, const double* b, double* x, int nrhs, int on_device, double tol,
              mg_stats* stats, void* stream);
 
+/* mg_solve on `count` distinct handles at once (e.g. one hierarchy per mass
+ * of a sweep, Sec. 5): handle i solves b[i] -> x[i] (nrhs right-hand sides
+ * each, layouts and on_device as mg_solve) on its own host thread and stream
+ * (streams[i], or a stream created for the call when streams is NULL), so
+ * the kernels of independent latency-bound solves run side by side on the
+ * GPU.  Not in the paper; each solve's arithmetic, and so its result, is
+ * that of mg_solve alone.  stats: NULL or count * nrhs entries, handle-major.
+ * Returns when every solve has finished; on failure, the first failing
+ * handle's status, with "handle i: " before its message.
+ * Errors: MG_EINVAL (also for a repeated handle), and those of mg_solve. */
+int mg_solve_many(mg_handle* const* hs, int count, const double* const* b, double* const* x, int nrhs,
+                  int on_device, double tol, mg_stats* stats, void* const* streams);
+
 /* Unpreconditioned Krylov solvers on level 0 alone: the methods the paper
  * measures multigrid against (Secs. 4-5).
  *   method : MG_KRYLOV_BICGSTAB -- BiCGstab (van der Vorst 1992) on D x = b;

@@ -14,6 +14,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "handle.h"
@@ -2156,4 +2157,51 @@ extern "C" int mg_solve(mg_handle* h, const double* b, double* x, int nrhs, int 
   int rc = gcr_solve(h, b, x, nrhs, on_device, tol, stats);
   h->st = keep;
   return rc;
+}
+
+// Independent solves on one GPU at once: one host thread per handle, each on
+// its own stream, so that the small launches of latency-bound solves (small
+// lattices, few right-hand sides) from different handles fill the SMs
+// together.  The first failing handle's status and message are returned.
+extern "C" int mg_solve_many(mg_handle* const* hs, int count, const double* const* b, double* const* x, int nrhs,
+                             int on_device, double tol, mg_stats* stats, void* const* streams) {
+  if (!hs || !b || !x || count < 1 || nrhs < 1 || !(tol > 0.0)) {
+    set_error("mg_solve_many: bad argument");
+    return MG_EINVAL;
+  }
+  for (int i = 0; i < count; ++i)
+    for (int j = 0; j < i; ++j)
+      if (!hs[i] || hs[i] == hs[j]) {
+        set_error("mg_solve_many: handles must be distinct and non-null (a handle is not thread-safe)");
+        return MG_EINVAL;
+      }
+  std::vector<int> rc(count, MG_OK);
+  std::vector<std::string> msg(count);
+  auto run = [&](int i) {
+    cudaStream_t st = streams ? (cudaStream_t)streams[i] : nullptr;
+    bool own = false;
+    if (!st) {
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        rc[i] = MG_ECUDA;
+        msg[i] = "mg_solve_many: stream creation failed";
+        return;
+      }
+      own = true;
+    }
+    rc[i] = mg_solve(hs[i], b[i], x[i], nrhs, on_device, tol, stats ? stats + (size_t)i * nrhs : nullptr, st);
+    if (rc[i] != MG_OK) msg[i] = mg_last_error();
+    if (own) cudaStreamDestroy(st);
+  };
+  std::vector<std::thread> pool;
+  pool.reserve(count - 1);
+  for (int i = 1; i < count; ++i) pool.emplace_back(run, i);
+  run(0);
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < count; ++i)
+    if (rc[i] != MG_OK) {
+      set_error("handle " + std::to_string(i) + ": " + msg[i]);
+      return rc[i];
+    }
+  return MG_OK;
 }

@@ -88,6 +88,7 @@ def _load():
         "mg_retarget": (I, [VP, D, P(VP), VP]),
         "mg_retarget_batch": (I, [VP, P(D), I, P(VP), VP]),
         "mg_solve": (I, [VP, VP, VP, I, I, D, P(mg_stats), VP]),
+        "mg_solve_many": (I, [P(VP), I, P(VP), P(VP), I, I, D, P(mg_stats), P(VP)]),
         "krylov_solve": (I, [VP, I, VP, VP, I, I, D, I, P(mg_stats), VP]),
         "dslash_apply": (I, [VP, I, VP, VP, I, VP]),
         "eo_split": (I, [VP, I, VP, VP, VP, I, VP]),
@@ -128,7 +129,7 @@ EXPORTS = ["mg_last_error", "mg_default_params", "mg_setup", "mg_retarget", "mg_
            "mg_field_from_internal", "mg_level_info", "mg_get_prolongator", "mg_get_coarse_op", "mg_footprint",
            "mg_profile", "mg_profile_read", "mg_profile_bytes", "mg_launch_count", "mr_apply_noalloc", "mg_tune",
            "mg_tune_report", "krylov_solve", "mg_retarget_batch", "eo_split", "eo_merge", "dslash_eo_apply",
-           "schur_apply"]
+           "schur_apply", "mg_solve_many"]
 
 (MG_K_DSLASH, MG_K_COARSE, MG_K_RESTRICT, MG_K_PROLONG, MG_K_VECTOR, MG_K_COARSEST, MG_K_SETUP, MG_K_GALERKIN,
  MG_K_INVERSE, MG_K_GRAM) = range(10)
@@ -263,6 +264,40 @@ def mg_solve(h, b, x, tol, stream=None, raise_on_noconv=True):
         raise ValueError("b and x must both be host arrays or both device tensors")
     status = LIB.mg_solve(h.ptr, bp, xp, nrhs, bdev, float(tol), st, _stream(stream))
     stats = [s.as_dict() for s in st]
+    if status != MG_OK and (status != MG_ENOCONV or raise_on_noconv):
+        raise MgError(status, mg_last_error(), stats)
+    return status, stats
+
+
+def mg_solve_many(hs, bs, xs, tol, streams=None, raise_on_noconv=True):
+    """Independent solves on distinct handles at once (one host thread and stream each): hs[i] solves
+    bs[i] -> xs[i] in place.  streams: None (a stream per solve is made for the call) or one per handle.
+    Returns (status, [[stats dict per rhs] per handle])."""
+    count = len(hs)
+    if not (len(bs) == len(xs) == count) or count < 1:
+        raise ValueError("need one b and one x per handle")
+    shp = bs[0].shape
+    nrhs = 1 if len(shp) == 6 else int(shp[0])
+    bp, xp, dev = [], [], set()
+    for b, x in zip(bs, xs):
+        if b.shape != shp or x.shape != shp:
+            raise ValueError("every b and x must have the same shape")
+        pb, db = _ptr(b)
+        px, dx = _ptr(x)
+        bp.append(pb.value)
+        xp.append(px.value)
+        dev |= {db, dx}
+    if len(dev) != 1:
+        raise ValueError("b and x must all be host arrays or all device tensors")
+    st = (mg_stats * (nrhs * count))()
+    sp = None
+    if streams is not None:
+        sp = (ctypes.c_void_p * count)(*[_stream(q).value for q in streams])
+    hp = [h.ptr.value if isinstance(h.ptr, ctypes.c_void_p) else h.ptr for h in hs]
+    status = LIB.mg_solve_many((ctypes.c_void_p * count)(*hp), count,
+                               (ctypes.c_void_p * count)(*bp), (ctypes.c_void_p * count)(*xp), nrhs, dev.pop(),
+                               float(tol), st, sp)
+    stats = [[st[i * nrhs + r].as_dict() for r in range(nrhs)] for i in range(count)]
     if status != MG_OK and (status != MG_ENOCONV or raise_on_noconv):
         raise MgError(status, mg_last_error(), stats)
     return status, stats

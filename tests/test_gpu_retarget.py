@@ -90,3 +90,44 @@ def test_deferred_coarsest_is_built_on_first_use():
         wm.mg_solve(hb[0], b, xb, 1e-10)
         assert np.array_equal(xb, x)
     assert np.array_equal(xs[0], xs[1])
+
+
+@pytest.mark.parametrize("mixed,device", [(1, True), (0, False), (1, False)])
+def test_concurrent_solves_equal_one_by_one(mixed, device):
+    """mg_solve_many runs independent handles side by side (a thread and stream each); every
+    kernel is deterministic, so each handle's x and iteration count are those of mg_solve alone."""
+    wm = require_gpu()
+    import torch
+    dims = (8, 8, 4, 8)
+    U = inputs.random_gauge(dims, 8)
+    p = wm.mg_default_params(n_levels=2, block=[(2, 2, 2, 2)], nv=[8], setup_sweeps=[20], mixed=mixed)
+    h0 = wm.mg_setup(U, dims, -0.1, p)
+    masses = [0.2, 0.05, 0.0, -0.05]
+    B = np.stack([inputs.gaussian_spinor(dims, 20 + r) for r in range(2)])
+    want = []
+    for m in masses:
+        h = wm.mg_retarget(h0, m)
+        x = np.zeros_like(B)
+        _, st = wm.mg_solve(h, B, x, 1e-10)
+        want.append((x, [s["iters"] for s in st]))
+    hs = wm.mg_retarget_batch(h0, masses)
+    if device:
+        bs = [torch.from_numpy(B).cuda() for _ in masses]
+        xs = [torch.zeros_like(bs[0]) for _ in masses]
+        torch.cuda.synchronize()
+        streams = [torch.cuda.Stream() for _ in masses]
+    else:
+        bs = [B] * len(masses)
+        xs = [np.zeros_like(B) for _ in masses]
+        streams = None
+    status, sts = wm.mg_solve_many(hs, bs, xs, 1e-10, streams=streams)
+    assert status == wm.MG_OK
+    for m, x, st, (xw, itw) in zip(masses, xs, sts, want):
+        x = x.cpu().numpy() if device else x
+        assert [s["iters"] for s in st] == itw, m
+        assert np.array_equal(x, xw), m
+        for r in range(B.shape[0]):
+            assert np.linalg.norm(B[r] - dirac.wilson_dirac(U, x[r], m)) <= 1e-10 * np.linalg.norm(B[r]) * 1.001
+    with pytest.raises(wm.MgError) as e:
+        wm.mg_solve_many([hs[0], hs[0]], [B, B], [np.zeros_like(B), np.zeros_like(B)], 1e-10)
+    assert e.value.status == wm.MG_EINVAL and "distinct" in str(e.value)
