@@ -348,6 +348,33 @@ int mr_update(mg_handle* h, int l, int prec, void* x_out, const void* x_in, cons
   return MG_OK;
 }
 
+// One level-0 MR step fused with the previous step's update (see
+// launch_wilson_mr): x += c r, rout = r - c p, pout = D rout with
+// <pout|rout>, ||pout||^2 into slot, c = omega <p|r>/<p|p> read from slot.
+int mr_fused(mg_handle* h, int prec, const void* r, const void* pv, void* x, void* rout, void* pout, size_t slot,
+             int nrhs) {
+  Level& a = *h->lev[0];
+  DslashCall d;
+  d.prec = prec;
+  d.in = r;
+  d.out = pout;
+  d.y = nullptr;
+  d.z = nullptr;
+  d.links = a.links[prec].p;
+  for (int m = 0; m < 4; ++m) d.L[m] = a.L[m];
+  d.a = 4.0 + h->mass;
+  d.b = -0.5;
+  d.c = 0.0;
+  d.nrhs = nrhs;
+  d.red = h->red.at(slot, 4);
+  // r, p and x read, x, r' and p' written, per right-hand side; links once
+  const double sb = 12.0 * a.V * bytes_of(prec);
+  const double lb = 4.0 * a.V * (prec == MG_F64 ? 9 : 6) * bytes_of(prec);
+  Prof pf(h, MG_K_DSLASH, prec, nrhs * sb * 6 + lb);
+  LK(launch_wilson_mr(d, pv, h->red.slot(slot), 4, h->p.omega, x, rout, h->st));
+  return MG_OK;
+}
+
 // `steps` MR steps on A_l x = b continuing from (x, res): if x_zero the
 // iterate is 0 and res is taken from b without an operator application.
 int mr_steps(mg_handle* h, int l, int prec, const void* b, void* x, bool x_zero, void* res, int steps, int nrhs) {
@@ -893,7 +920,7 @@ static int relax_candidates(mg_handle* h, int l, void* x64, int k) {
   cudaStream_t st = h->st;
   Level& a = *h->lev[l];
   const int rp = p.mixed ? MG_F32 : MG_F64;  // the mixed form relaxes in FP32
-  DevBuf candr, rr, pp;
+  DevBuf candr, rr, pp, rr2, pp2;
   void* x = x64;
   const size_t vr = a.n() * bytes_of(rp);
   if (rp != MG_F64) {
@@ -901,20 +928,36 @@ static int relax_candidates(mg_handle* h, int l, void* x64, int k) {
     LK(launch_convert(MG_F64, rp, a.n(), k, x64, candr.p, 1.0, nullptr, 0, 0.0, 0, st));
     x = candr.p;
   }
-  if (!rr.ensure(vr * k) || !pp.ensure(vr * k)) return MG_ENOMEM;
+  // level 0: each step's update is fused into the next step's stencil (r and p ping-pong)
+  const bool fuse = l == 0;
+  if (!rr.ensure(vr * k) || !pp.ensure(vr * k) || (fuse && (!rr2.ensure(vr * k) || !pp2.ensure(vr * k))))
+    return MG_ENOMEM;
   RET(ensure_reducer(h, k));
   const size_t sl = slot_level(l);
   if (a.sweeps > 0) {
-    RET(op_apply(h, l, rp, x, rr.p, nullptr, -1.0, 0.0, nullptr, 0, k));
+    void *r = rr.p, *pv = pp.p, *r2 = rr2.p, *p2 = pp2.p;
+    RET(op_apply(h, l, rp, x, r, nullptr, -1.0, 0.0, nullptr, 0, k));
+    bool owed = false;  // the update of (x, r) with the last p and its dots is still to be applied
     for (int s = 0; s < a.sweeps; ++s) {
       // FP32 relaxation: the recursively updated residual drifts from -A x
       // once it has shrunk by a few orders, so it is recomputed every
       // kTrueResidualEvery steps (FP64 follows the plain recursion).
-      if (rp != MG_F64 && s > 0 && s % kTrueResidualEvery == 0)
-        RET(op_apply(h, l, rp, x, rr.p, nullptr, -1.0, 0.0, nullptr, 0, k));
-      RET(op_apply(h, l, rp, rr.p, pp.p, nullptr, 1.0, 0.0, rr.p, sl, k));
-      RET(mr_update(h, l, rp, x, x, rr.p, rr.p, rr.p, pp.p, sl, p.omega, k));
+      const bool recompute = rp != MG_F64 && s > 0 && s % kTrueResidualEvery == 0;
+      if (owed && (!fuse || recompute)) {
+        RET(mr_update(h, l, rp, x, x, r, r, r, pv, sl, p.omega, k));
+        owed = false;
+      }
+      if (recompute) RET(op_apply(h, l, rp, x, r, nullptr, -1.0, 0.0, nullptr, 0, k));
+      if (owed) {  // x += c r, r' = r - c p, p' = A r' and its dots, in one launch
+        RET(mr_fused(h, rp, r, pv, x, r2, p2, sl, k));
+        std::swap(r, r2);
+        std::swap(pv, p2);
+      } else {
+        RET(op_apply(h, l, rp, r, pv, nullptr, 1.0, 0.0, r, sl, k));
+      }
+      owed = true;
     }
+    RET(mr_update(h, l, rp, x, x, r, r, r, pv, sl, p.omega, k));
   }
   LK(launch_dot(rp, a.n(), k, x, x, h->red.at(slot_misc(), 4), st));
   LK(launch_convert(rp, MG_F64, a.n(), k, x, x64, 1.0, h->red.slot(slot_misc() + 2), 4, -0.5, 0, st));

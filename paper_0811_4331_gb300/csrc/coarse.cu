@@ -435,6 +435,8 @@ static unsigned grid_for(size_t tot, size_t cap) {
 
 // Panel kernel: one CTA per matrix z (blockIdx.x), nt threads.  Shared:
 // panel [N][b] and tracker [N][b] of element type T.
+constexpr int kGjbBatch = 8;
+
 template <typename T, int B>
 __global__ void __launch_bounds__(1024) gjb_panel_kernel(T* aug0, int N, int kb, int b, unsigned long long* keys0,
                                                          int* used0, T* te0, T* prow0, int* err0) {
@@ -464,14 +466,32 @@ __global__ void __launch_bounds__(1024) gjb_panel_kernel(T* aug0, int N, int kb,
     return v;
   };
   unsigned long long best = 0;
-  for (int e = t; e < N * b; e += nt) {  // coalesced along the panel's row
-    const int i = e / b, j = e - i * b;
-    const cx<R> v = ldc<R>(aug, (size_t)i * ld + kb + j);
-    Ps[(size_t)j * N + i] = v;
-    Ts[(size_t)j * N + i] = zero<R>();
-    if (j == 0 && !used[i]) {
-      const unsigned long long key = pivot_key((float)norm2(v), i);
-      best = key > best ? key : best;
+  // kGjbBatch independent loads per thread in flight at once: one CTA moves the whole panel, so its
+  // time is a chain of L2 round trips unless they overlap
+  for (int e0 = t; e0 < N * b; e0 += nt * kGjbBatch) {  // coalesced along the panel's row
+    cx<R> v[kGjbBatch];
+    int fresh[kGjbBatch];
+#pragma unroll
+    for (int u = 0; u < kGjbBatch; ++u) {
+      const int e = e0 + u * nt;
+      if (e < N * b) {
+        const int i = e / b, j = e - i * b;
+        v[u] = ldc<R>(aug, (size_t)i * ld + kb + j);
+        fresh[u] = j == 0 && !used[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kGjbBatch; ++u) {
+      const int e = e0 + u * nt;
+      if (e < N * b) {
+        const int i = e / b, j = e - i * b;
+        Ps[(size_t)j * N + i] = v[u];
+        Ts[(size_t)j * N + i] = zero<R>();
+        if (fresh[u]) {
+          const unsigned long long key = pivot_key((float)norm2(v[u]), i);
+          best = key > best ? key : best;
+        }
+      }
     }
   }
   best = warp_max(best);
@@ -534,9 +554,24 @@ __global__ void __launch_bounds__(1024) gjb_panel_kernel(T* aug0, int N, int kb,
     stc(te, e, Ts[(size_t)j * N + i]);
   }
   const int c0 = kb + b, nc = 2 * N - c0;
-  for (int e = t; e < b * nc; e += nt) {
-    const int j = e / nc, c = e - j * nc;
-    prow[(size_t)j * 2 * N + c0 + c] = aug[(size_t)piv_s[j] * ld + c0 + c];
+  for (int e0 = t; e0 < b * nc; e0 += nt * kGjbBatch) {
+    T v[kGjbBatch];
+#pragma unroll
+    for (int u = 0; u < kGjbBatch; ++u) {
+      const int e = e0 + u * nt;
+      if (e < b * nc) {
+        const int j = e / nc, c = e - j * nc;
+        v[u] = aug[(size_t)piv_s[j] * ld + c0 + c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kGjbBatch; ++u) {
+      const int e = e0 + u * nt;
+      if (e < b * nc) {
+        const int j = e / nc, c = e - j * nc;
+        prow[(size_t)j * 2 * N + c0 + c] = v[u];
+      }
+    }
   }
 }
 

@@ -232,6 +232,110 @@ __global__ void __launch_bounds__(256) wilson_small_kernel(const WilsonArgs<S, G
   if (A.z) grid_reduce<3, 256, R>(red, A.red, rhs);
 }
 
+// ------------------------------------------------------------------ MR-fused stencil
+// One MR step (Sec. 3) that also finishes the previous step's update, for
+// the setup relaxation of Sec. 2 (MR on A x = 0).  With c = omega <p|r>/<p|p>
+// of the previous step (per right-hand side, from its reduction slot):
+//   r' = r - c p,   x += c r (in place),   out = a r' + b Hop(r') (= A r'),
+// and <out|r'>, ||out||^2 reduced for the next step.  r' at the neighbours is
+// formed on the fly from r and p with the same operations as at their own
+// sites, so every site sees the same r' values; r' is stored at the thread's
+// own site for the next step.  FP32 / FP64 storage (the value formed is the
+// value stored); one right-hand side per thread.
+template <typename R, typename S>
+struct ShiftedIn {
+  const S* r;
+  const S* p;
+  cx<R> c;
+  __device__ __forceinline__ cx<R> operator()(size_t i) const { return ldc<R>(r, i) - c * ldc<R>(p, i); }
+};
+
+template <int MU, typename R, typename S, typename G, int NL>
+__device__ __forceinline__ void hop_pair_in(cx<R> (&acc)[4][3], const WilsonArgs<S, G, NL>& A,
+                                            const ShiftedIn<R, S>& in, int s, const int (&c)[4],
+                                            const int (&stride)[4]) {
+  const int L = A.L[MU], st = stride[MU];
+  const int fwd = (c[MU] == L - 1) ? s - (L - 1) * st : s + st;
+  const int bwd = (c[MU] == 0) ? s + (L - 1) * st : s - st;
+  Link<R> u;
+  load_link<R, G, NL>(u, A.U, MU, A.V, s);
+  hop_from<MU, true, R>(acc, in, A.V, fwd, u);
+  load_link<R, G, NL>(u, A.U, MU, A.V, bwd);
+  hop_from<MU, false, R>(acc, in, A.V, bwd, u);
+}
+
+template <typename S, typename G, int NL, int NT>
+__global__ void __launch_bounds__(NT) wilson_mr_kernel(const WilsonArgs<S, G, NL> A, const S* pprev,
+                                                       const double* dots, int dstride, double omega, S* x,
+                                                       S* rout) {
+  typedef typename Store<S>::R R;
+  const int V = A.V;
+  const int s = blockIdx.x * NT + threadIdx.x;
+  const int rhs = blockIdx.y;
+  __shared__ double sc[2];
+  if (threadIdx.x == 0) {  // c once per CTA, in FP64 from the FP64 slot (as the MR update kernel forms it)
+    const double* d = dots + (size_t)rhs * dstride;
+    const double den = d[2];
+    double cr = 0.0, ci = 0.0;
+    if (den > 0.0 && isfinite(den)) {
+      cr = omega * d[0] / den;
+      ci = omega * d[1] / den;
+    }
+    sc[0] = cr;
+    sc[1] = ci;
+  }
+  __syncthreads();
+  const cx<R> cf = mk<R>((R)sc[0], (R)sc[1]);
+  const size_t ro = (size_t)rhs * A.vstride;
+  const ShiftedIn<R, S> in{A.in + ro, pprev + ro, cf};
+  R acc3[3] = {(R)0, (R)0, (R)0};
+  if (s < V) {
+    int c[4], stride[4];
+    int q = s;
+    c[0] = q % A.L[0];
+    q /= A.L[0];
+    c[1] = q % A.L[1];
+    q /= A.L[1];
+    c[2] = q % A.L[2];
+    c[3] = q / A.L[2];
+    stride[0] = 1;
+    stride[1] = A.L[0];
+    stride[2] = A.L[0] * A.L[1];
+    stride[3] = stride[2] * A.L[2];
+    cx<R> acc[4][3];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) acc[sp][a] = zero<R>();
+    hop_pair_in<0>(acc, A, in, s, c, stride);
+    hop_pair_in<1>(acc, A, in, s, c, stride);
+    hop_pair_in<2>(acc, A, in, s, c, stride);
+    hop_pair_in<3>(acc, A, in, s, c, stride);
+    const R ca = (R)A.a, cb = (R)A.b;
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const size_t i = (size_t)(sp * 3 + a) * V + s;
+        const cx<R> rold = ldc<R>(A.in + ro, i);
+        const cx<R> rn = in(i);
+        cx<R> xv = ldc<R>(x + ro, i);
+        xv = cfma(cf, rold, xv);
+        stc(x + ro, i, xv);
+        stc(rout + ro, i, rn);
+        cx<R> v = cb * acc[sp][a];
+        v = v + ca * rn;
+        stc(A.out + ro, i, v);
+        const cx<R> vs = as_stored<S>(v);
+        const cx<R> d = cmul_conj(vs, rn);
+        acc3[0] += d.re;
+        acc3[1] += d.im;
+        acc3[2] += norm2(vs);
+      }
+  }
+  grid_reduce<3, NT, R>(acc3, A.red, rhs);
+}
+
 template <typename S, typename G, int NL, int NT, int NR>
 static int launch_nt(const WilsonArgs<S, G, NL>& A, int nrhs, cudaStream_t st) {
   dim3 grid((A.V + NT - 1) / NT, nrhs / NR);
@@ -293,6 +397,40 @@ static int launch_t(const DslashCall& d, cudaStream_t st) {
   if (sh.nt == 64) return launch_nt<S, G, NL, 64, 1>(A, d.nrhs, st);
   if (sh.nt == 256) return launch_nt<S, G, NL, 256, 1>(A, d.nrhs, st);
   return launch_nt<S, G, NL, 128, 1>(A, d.nrhs, st);
+}
+
+int launch_wilson_mr(const DslashCall& d, const void* pprev, const double* dots, int dstride, double omega, void* x,
+                     void* rout, cudaStream_t st) {
+  const int V = d.L[0] * d.L[1] * d.L[2] * d.L[3];
+  const dim3 grid((V + 127) / 128, d.nrhs);
+  auto fill = [&](auto& A) {
+    A.in = (decltype(A.in))d.in;
+    A.out = (decltype(A.out))d.out;
+    A.y = nullptr;
+    A.z = nullptr;
+    A.U = (decltype(A.U))d.links;
+    for (int k = 0; k < 4; ++k) A.L[k] = d.L[k];
+    A.V = V;
+    A.a = d.a;
+    A.b = d.b;
+    A.c = 0.0;
+    A.vstride = (size_t)12 * V;
+    A.red = d.red;
+  };
+  if (d.prec == 0) {
+    WilsonArgs<double2, double2, 9> A;
+    fill(A);
+    wilson_mr_kernel<double2, double2, 9, 128><<<grid, 128, 0, st>>>(A, (const double2*)pprev, dots, dstride, omega,
+                                                                    (double2*)x, (double2*)rout);
+  } else if (d.prec == 1) {
+    WilsonArgs<float2, float2, 6> A;
+    fill(A);
+    wilson_mr_kernel<float2, float2, 6, 128><<<grid, 128, 0, st>>>(A, (const float2*)pprev, dots, dstride, omega,
+                                                                  (float2*)x, (float2*)rout);
+  } else {
+    return -1;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // CTAs per right-hand side of a launch with fused dots (sizes the reduction partials).

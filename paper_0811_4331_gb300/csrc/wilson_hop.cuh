@@ -39,17 +39,26 @@ __device__ __forceinline__ void su3_mul(const Link<R>& u, const cx<R> (&h)[3], c
   }
 }
 
+// Input of a hop: component i (= comp * V + site) of the field, as a value of
+// arithmetic type R.  StoredIn reads a stored field; the MR-fused stencil
+// passes one that forms r - c p on the fly.
+template <typename R, typename S>
+struct StoredIn {
+  const S* p;
+  __device__ __forceinline__ cx<R> operator()(size_t i) const { return ldc<R>(p, i); }
+};
+
 // One hop: project psi(nbr) with (1 - g_mu) (FWD) or (1 + g_mu), multiply by
 // U or U^+, reconstruct the lower spin pair, accumulate into acc.
-template <int MU, bool FWD, typename R, typename S>
-__device__ __forceinline__ void hop(cx<R> (&acc)[4][3], const S* in, int V, int nbr, const Link<R>& u) {
+template <int MU, bool FWD, typename R, typename In>
+__device__ __forceinline__ void hop_from(cx<R> (&acc)[4][3], const In& in, int V, int nbr, const Link<R>& u) {
   cx<R> h0[3], h1[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    cx<R> u0 = ldc<R>(in, (size_t)(0 * 3 + a) * V + nbr);
-    cx<R> u1 = ldc<R>(in, (size_t)(1 * 3 + a) * V + nbr);
-    cx<R> d0 = ldc<R>(in, (size_t)(2 * 3 + a) * V + nbr);
-    cx<R> d1 = ldc<R>(in, (size_t)(3 * 3 + a) * V + nbr);
+    cx<R> u0 = in((size_t)(0 * 3 + a) * V + nbr);
+    cx<R> u1 = in((size_t)(1 * 3 + a) * V + nbr);
+    cx<R> d0 = in((size_t)(2 * 3 + a) * V + nbr);
+    cx<R> d1 = in((size_t)(3 * 3 + a) * V + nbr);
     if (MU == 0) {
       h0[a] = FWD ? u0 + times_i(d1) : u0 - times_i(d1);
       h1[a] = FWD ? u1 + times_i(d0) : u1 - times_i(d0);
@@ -88,6 +97,11 @@ __device__ __forceinline__ void hop(cx<R> (&acc)[4][3], const S* in, int V, int 
     acc[2][a] = acc[2][a] + l0;
     acc[3][a] = acc[3][a] + l1;
   }
+}
+
+template <int MU, bool FWD, typename R, typename S>
+__device__ __forceinline__ void hop(cx<R> (&acc)[4][3], const S* in, int V, int nbr, const Link<R>& u) {
+  hop_from<MU, FWD, R>(acc, StoredIn<R, S>{in}, V, nbr, u);
 }
 
 }  // namespace wmg
