@@ -75,7 +75,7 @@ inline size_t slot_gcr_pre() { return slot_inner(MG_MAX_LEVELS); }  // <w|r>, ||
 inline size_t slot_total() { return slot_gcr_pre() + 4 * kMaxRhs; }
 const int kInnerBasis = 8;
 
-enum { WV_E, WV_RES, WV_P, WV_XC, WV_AXC, WV_RC, WV_EC, WV_T, WV_DT, WV_IN, WV_A, WV_B, WV_KW, WV_KZ, WV_PR, WV_PE, WV_EOA, WV_EOB, WV_EOC, WV_COUNT };
+enum { WV_E, WV_RES, WV_P, WV_XC, WV_AXC, WV_RC, WV_EC, WV_T, WV_DT, WV_IN, WV_A, WV_B, WV_KW, WV_KZ, WV_PR, WV_PE, WV_EOA, WV_EOB, WV_EOC, WV_FR0, WV_FR1, WV_FP0, WV_FP1, WV_COUNT };
 
 int prec_of(const mg_handle* h, int l) {
   if (!h->p.mixed) return MG_F64;
@@ -349,10 +349,12 @@ int mr_update(mg_handle* h, int l, int prec, void* x_out, const void* x_in, cons
 }
 
 // One level-0 MR step fused with the previous step's update (see
-// launch_wilson_mr): x += c r, rout = r - c p, pout = D rout with
-// <pout|rout>, ||pout||^2 into slot, c = omega <p|r>/<p|p> read from slot.
-int mr_fused(mg_handle* h, int prec, const void* r, const void* pv, void* x, void* rout, void* pout, size_t slot,
-             int nrhs) {
+// launch_wilson_mr): x = xin + c u (u null: r; xin null: 0), rout = r - c p,
+// pout = D rout with <pout|rout>, ||pout||^2 into slot; c = omega <p|r>/<p|p>
+// is read from the same slot (every CTA reads it before the reduction's last
+// CTA overwrites it).
+int mr_fused(mg_handle* h, int prec, const void* r, const void* pv, const void* u, const void* xin, void* x,
+             void* rout, void* pout, size_t slot, double omega, int nrhs) {
   Level& a = *h->lev[0];
   DslashCall d;
   d.prec = prec;
@@ -367,11 +369,39 @@ int mr_fused(mg_handle* h, int prec, const void* r, const void* pv, void* x, voi
   d.c = 0.0;
   d.nrhs = nrhs;
   d.red = h->red.at(slot, 4);
-  // r, p and x read, x, r' and p' written, per right-hand side; links once
+  // r, p, u (if not r) and xin read; x, r' and p' written, per right-hand side; links once
   const double sb = 12.0 * a.V * bytes_of(prec);
   const double lb = 4.0 * a.V * (prec == MG_F64 ? 9 : 6) * bytes_of(prec);
-  Prof pf(h, MG_K_DSLASH, prec, nrhs * sb * 6 + lb);
-  LK(launch_wilson_mr(d, pv, h->red.slot(slot), 4, h->p.omega, x, rout, h->st));
+  Prof pf(h, MG_K_DSLASH, prec, nrhs * sb * (5 + (u != nullptr) + (xin != nullptr)) + lb);
+  LK(launch_wilson_mr(d, pv, u, xin, x, rout, h->red.slot(slot), 4, omega, h->st));
+  return MG_OK;
+}
+
+// Level-0 MR sequence with each step's update fused into the next step's
+// stencil.  Owed describes the update still to be applied: x = xin + c u,
+// r' = r - c p with c from the level's slot and relaxation omega.
+struct Owed {
+  const void* r;
+  const void* p;
+  const void* u;    // null: u = r
+  const void* xin;  // null: x starts from 0
+  double omega;
+};
+
+// `steps` fused MR steps on D e = (owed residual) continuing the owed update;
+// returns the update still owed after the last stencil (r and p in the
+// ping-pong work vectors WV_FR*, WV_FP*).
+int fused_steps(mg_handle* h, int prec, void* x, Owed& ow, int steps, int nrhs) {
+  void* R[2] = {work(h, 0, prec, WV_FR0, nrhs), work(h, 0, prec, WV_FR1, nrhs)};
+  void* P[2] = {work(h, 0, prec, WV_FP0, nrhs), work(h, 0, prec, WV_FP1, nrhs)};
+  if (!R[0] || !R[1] || !P[0] || !P[1]) return MG_ENOMEM;
+  const size_t sl = slot_level(0);
+  for (int s = 0; s < steps; ++s) {
+    // ping-pong away from the buffers the owed update reads
+    const int q = (ow.r == R[0] || ow.p == P[0]) ? 1 : 0;
+    RET(mr_fused(h, prec, ow.r, ow.p, ow.u, ow.xin, x, R[q], P[q], sl, ow.omega, nrhs));
+    ow = Owed{R[q], P[q], nullptr, x, h->p.omega};
+  }
   return MG_OK;
 }
 
@@ -608,12 +638,22 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
     set_error("prolongator of level " + std::to_string(l) + " not stored in the cycle's precision");
     return MG_EINVAL;
   }
-  // pre-smoothing from e = 0
+  // pre-smoothing from e = 0; on level 0 each MR update rides on the next stencil launch
   const bool eo = l == 0 && h->p.fine_smoother == 1;
-  if (eo)
+  const bool fuse = l == 0 && !eo;
+  const size_t sl = slot_level(l);
+  if (eo) {
     RET(eo_smooth(h, prec, r, e, false, res, h->p.nu_pre, nrhs));
-  else
+  } else if (fuse && h->p.nu_pre >= 1) {
+    void* p0 = work(h, 0, prec, WV_FP0, nrhs);
+    if (!p0) return MG_ENOMEM;
+    RET(op_apply(h, 0, prec, r, p0, nullptr, 1.0, 0.0, r, sl, nrhs));
+    Owed ow{r, p0, nullptr, nullptr, h->p.omega};
+    RET(fused_steps(h, prec, e, ow, h->p.nu_pre - 1, nrhs));
+    RET(mr_update(h, 0, prec, e, ow.xin, ow.u ? ow.u : ow.r, res, ow.r, ow.p, sl, ow.omega, nrhs));
+  } else {
     RET(mr_steps(h, l, prec, r, e, true, res, h->p.nu_pre, nrhs));
+  }
   // restrict, coarse solve, prolong
   const Agg g = agg_of(a);
   const double pbytes = (double)a.Vc * 2 * a.nv * a.nhalf * a.bsites * bytes_of(prec);  // P once
@@ -661,8 +701,13 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
     LK(launch_prolong(pc, prec, prec, g, a.P[prec].p, ec, xc, nrhs, h->st, pvar));
   }
   // alpha = <A x_c|r0> / <A x_c|A x_c>  (Eq. 3.5);  e += alpha x_c, r0 -= alpha A x_c
-  const size_t sl = slot_level(l);
   RET(op_apply(h, l, prec, xc, axc, nullptr, 1.0, 0.0, res, sl, nrhs));
+  if (fuse && h->p.nu_post >= 1) {  // the alpha update rides on the first post-smoothing stencil
+    Owed ow{res, axc, xc, e, 1.0};
+    RET(fused_steps(h, prec, e, ow, h->p.nu_post, nrhs));
+    RET(mr_update(h, 0, prec, e, ow.xin, ow.u ? ow.u : ow.r, res, ow.r, ow.p, sl, ow.omega, nrhs));
+    return MG_OK;
+  }
   RET(mr_update(h, l, prec, e, e, xc, res, res, axc, sl, 1.0, nrhs));
   // post-smoothing
   if (eo) return eo_smooth(h, prec, res, e, true, res, h->p.nu_post, nrhs);
@@ -949,7 +994,7 @@ static int relax_candidates(mg_handle* h, int l, void* x64, int k) {
       }
       if (recompute) RET(op_apply(h, l, rp, x, r, nullptr, -1.0, 0.0, nullptr, 0, k));
       if (owed) {  // x += c r, r' = r - c p, p' = A r' and its dots, in one launch
-        RET(mr_fused(h, rp, r, pv, x, r2, p2, sl, k));
+        RET(mr_fused(h, rp, r, pv, nullptr, x, x, r2, p2, sl, p.omega, k));
         std::swap(r, r2);
         std::swap(pv, p2);
       } else {

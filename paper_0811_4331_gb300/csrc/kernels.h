@@ -26,12 +26,13 @@ struct DslashCall {
   int variant = -1;   // launch shape (wilson_variants), -1 = default
 };
 int launch_wilson(const DslashCall& d, cudaStream_t st);
-// MR step fused with the previous step's update (FP64 / FP32 only): with
-// c = omega dots[0..1] / dots[2] per right-hand side (stride dstride),
-// r' = d.in - c pprev, x += c d.in, rout = r', d.out = d.a r' + d.b Hop(r'),
-// <d.out|r'>, ||d.out||^2 into d.red.  d.in, pprev, rout, d.out distinct.
-int launch_wilson_mr(const DslashCall& d, const void* pprev, const double* dots, int dstride, double omega, void* x,
-                     void* rout, cudaStream_t st);
+// MR step fused with the previous step's update: with c = omega
+// dots[0..1] / dots[2] per right-hand side (stride dstride),
+//   x = xin + c u (xin null: 0; u null: d.in),  rout = d.in - c pprev,
+//   d.out = d.a rout + d.b Hop(rout),  <d.out|rout>, ||d.out||^2 into d.red.
+// d.in, pprev, rout and d.out distinct; x may equal xin.
+int launch_wilson_mr(const DslashCall& d, const void* pprev, const void* u, const void* xin, void* x, void* rout,
+                     const double* dots, int dstride, double omega, cudaStream_t st);
 int wilson_variants(int prec, bool dots, int nrhs, int V);
 int wilson_blocks(int V);
 int launch_pack_links(int prec, const void* ext, void* out, int V, cudaStream_t st);

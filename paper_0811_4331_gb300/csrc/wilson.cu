@@ -232,108 +232,226 @@ __global__ void __launch_bounds__(256) wilson_small_kernel(const WilsonArgs<S, G
   if (A.z) grid_reduce<3, 256, R>(red, A.red, rhs);
 }
 
+// Site x right-hand-side counts up to which the warp-per-hop kernel runs.
+constexpr int kSmallSites = 32768;
+
 // ------------------------------------------------------------------ MR-fused stencil
-// One MR step (Sec. 3) that also finishes the previous step's update, for
-// the setup relaxation of Sec. 2 (MR on A x = 0).  With c = omega <p|r>/<p|p>
-// of the previous step (per right-hand side, from its reduction slot):
-//   r' = r - c p,   x += c r (in place),   out = a r' + b Hop(r') (= A r'),
-// and <out|r'>, ||out||^2 reduced for the next step.  r' at the neighbours is
-// formed on the fly from r and p with the same operations as at their own
-// sites, so every site sees the same r' values; r' is stored at the thread's
-// own site for the next step.  FP32 / FP64 storage (the value formed is the
-// value stored); one right-hand side per thread.
+// One MR step (Sec. 3) that also finishes the previous step's update.  With
+// c = omega <p|r>/<p|p> of the previous step (per right-hand side, from its
+// reduction slot) and that step's update direction u (= r for an MR step,
+// the prolonged coarse correction for the alpha step of Eq. 3.5):
+//   x = xin + c u,   r' = r - c p,   out = a r' + b Hop(r') (= A r'),
+// with <out|r'>, ||out||^2 reduced for the next step.  r' at the neighbours
+// is formed on the fly from r and p with the same operations, and rounded to
+// the storage type the same way, as at their own sites, so every site sees
+// the r' that is stored; each thread stores r' and x at its own site.
 template <typename R, typename S>
 struct ShiftedIn {
   const S* r;
   const S* p;
   cx<R> c;
-  __device__ __forceinline__ cx<R> operator()(size_t i) const { return ldc<R>(r, i) - c * ldc<R>(p, i); }
+  __device__ __forceinline__ cx<R> operator()(size_t i) const {
+    return as_stored<S>(ldc<R>(r, i) - c * ldc<R>(p, i));
+  }
 };
 
-template <int MU, typename R, typename S, typename G, int NL>
-__device__ __forceinline__ void hop_pair_in(cx<R> (&acc)[4][3], const WilsonArgs<S, G, NL>& A,
-                                            const ShiftedIn<R, S>& in, int s, const int (&c)[4],
-                                            const int (&stride)[4]) {
-  const int L = A.L[MU], st = stride[MU];
-  const int fwd = (c[MU] == L - 1) ? s - (L - 1) * st : s + st;
-  const int bwd = (c[MU] == 0) ? s + (L - 1) * st : s - st;
-  Link<R> u;
-  load_link<R, G, NL>(u, A.U, MU, A.V, s);
-  hop_from<MU, true, R>(acc, in, A.V, fwd, u);
-  load_link<R, G, NL>(u, A.U, MU, A.V, bwd);
-  hop_from<MU, false, R>(acc, in, A.V, bwd, u);
-}
+struct MrFuseArgs {
+  const void* pprev;
+  const void* u;    // null: u = r
+  const void* xin;  // null: x starts from 0
+  void* x;
+  void* rout;
+  const double* dots;
+  int dstride;
+  double omega;
+};
 
-template <typename S, typename G, int NL, int NT>
-__global__ void __launch_bounds__(NT) wilson_mr_kernel(const WilsonArgs<S, G, NL> A, const S* pprev,
-                                                       const double* dots, int dstride, double omega, S* x,
-                                                       S* rout) {
-  typedef typename Store<S>::R R;
-  const int V = A.V;
-  const int s = blockIdx.x * NT + threadIdx.x;
-  const int rhs = blockIdx.y;
+// c of right-hand side rhs, once per CTA in FP64 from the FP64 slot (as the MR update kernel forms it).
+template <typename R>
+__device__ __forceinline__ cx<R> fused_coef(const MrFuseArgs& F, int rhs) {
   __shared__ double sc[2];
-  if (threadIdx.x == 0) {  // c once per CTA, in FP64 from the FP64 slot (as the MR update kernel forms it)
-    const double* d = dots + (size_t)rhs * dstride;
+  if (threadIdx.x == 0) {
+    const double* d = F.dots + (size_t)rhs * F.dstride;
     const double den = d[2];
     double cr = 0.0, ci = 0.0;
     if (den > 0.0 && isfinite(den)) {
-      cr = omega * d[0] / den;
-      ci = omega * d[1] / den;
+      cr = F.omega * d[0] / den;
+      ci = F.omega * d[1] / den;
     }
     sc[0] = cr;
     sc[1] = ci;
   }
   __syncthreads();
-  const cx<R> cf = mk<R>((R)sc[0], (R)sc[1]);
+  return mk<R>((R)sc[0], (R)sc[1]);
+}
+
+// Own-site part of a fused step for component i of one right-hand side
+// (pointers already offset to it): x and r' stored, out = a r' + b h, and the
+// dot partials of out against r'.
+template <typename R, typename S>
+__device__ __forceinline__ void fused_site(const MrFuseArgs& F, const ShiftedIn<R, S>& in, S* out, size_t ro,
+                                           size_t i, cx<R> h, R ca, R cb, R (&red)[3]) {
+  const cx<R> rn = in(i);
+  const S* u = F.u ? (const S*)F.u + ro : in.r;
+  cx<R> xv = F.xin ? ldc<R>((const S*)F.xin + ro, i) : zero<R>();
+  xv = cfma(in.c, ldc<R>(u, i), xv);
+  stc((S*)F.x + ro, i, xv);
+  stc((S*)F.rout + ro, i, rn);
+  cx<R> v = cb * h;
+  v = v + ca * rn;
+  stc(out, i, v);
+  const cx<R> vs = as_stored<S>(v);
+  const cx<R> d = cmul_conj(vs, rn);
+  red[0] += d.re;
+  red[1] += d.im;
+  red[2] += norm2(vs);
+}
+
+template <int MU, bool FWD, typename R, typename S, typename G, int NL>
+__device__ __forceinline__ void one_hop_in(cx<R> (&acc)[4][3], const WilsonArgs<S, G, NL>& A,
+                                           const ShiftedIn<R, S>& in, int s, const int (&c)[4],
+                                           const int (&stride)[4]) {
+  const int L = A.L[MU], st = stride[MU];
+  Link<R> u;
+  if (FWD) {
+    const int nb = (c[MU] == L - 1) ? s - (L - 1) * st : s + st;
+    load_link<R, G, NL>(u, A.U, MU, A.V, s);
+    hop_from<MU, true, R>(acc, in, A.V, nb, u);
+  } else {
+    const int nb = (c[MU] == 0) ? s + (L - 1) * st : s - st;
+    load_link<R, G, NL>(u, A.U, MU, A.V, nb);
+    hop_from<MU, false, R>(acc, in, A.V, nb, u);
+  }
+}
+
+__device__ __forceinline__ void site_coords(int s, const int (&L)[4], int (&c)[4], int (&stride)[4]) {
+  int q = s;
+  c[0] = q % L[0];
+  q /= L[0];
+  c[1] = q % L[1];
+  q /= L[1];
+  c[2] = q % L[2];
+  c[3] = q / L[2];
+  stride[0] = 1;
+  stride[1] = L[0];
+  stride[2] = L[0] * L[1];
+  stride[3] = stride[2] * L[2];
+}
+
+// One thread per site and right-hand side (the hop order of wilson_kernel).
+template <typename S, typename G, int NL, int NT>
+__global__ void __launch_bounds__(NT) wilson_mr_kernel(const WilsonArgs<S, G, NL> A, const MrFuseArgs F) {
+  typedef typename Store<S>::R R;
+  const int V = A.V;
+  const int s = blockIdx.x * NT + threadIdx.x;
+  const int rhs = blockIdx.y;
+  const cx<R> cf = fused_coef<R>(F, rhs);
   const size_t ro = (size_t)rhs * A.vstride;
-  const ShiftedIn<R, S> in{A.in + ro, pprev + ro, cf};
-  R acc3[3] = {(R)0, (R)0, (R)0};
+  const ShiftedIn<R, S> in{A.in + ro, (const S*)F.pprev + ro, cf};
+  R red[3] = {(R)0, (R)0, (R)0};
   if (s < V) {
     int c[4], stride[4];
-    int q = s;
-    c[0] = q % A.L[0];
-    q /= A.L[0];
-    c[1] = q % A.L[1];
-    q /= A.L[1];
-    c[2] = q % A.L[2];
-    c[3] = q / A.L[2];
-    stride[0] = 1;
-    stride[1] = A.L[0];
-    stride[2] = A.L[0] * A.L[1];
-    stride[3] = stride[2] * A.L[2];
+    site_coords(s, A.L, c, stride);
     cx<R> acc[4][3];
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
       for (int a = 0; a < 3; ++a) acc[sp][a] = zero<R>();
-    hop_pair_in<0>(acc, A, in, s, c, stride);
-    hop_pair_in<1>(acc, A, in, s, c, stride);
-    hop_pair_in<2>(acc, A, in, s, c, stride);
-    hop_pair_in<3>(acc, A, in, s, c, stride);
-    const R ca = (R)A.a, cb = (R)A.b;
+    one_hop_in<0, true>(acc, A, in, s, c, stride);
+    one_hop_in<0, false>(acc, A, in, s, c, stride);
+    one_hop_in<1, true>(acc, A, in, s, c, stride);
+    one_hop_in<1, false>(acc, A, in, s, c, stride);
+    one_hop_in<2, true>(acc, A, in, s, c, stride);
+    one_hop_in<2, false>(acc, A, in, s, c, stride);
+    one_hop_in<3, true>(acc, A, in, s, c, stride);
+    one_hop_in<3, false>(acc, A, in, s, c, stride);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        fused_site(F, in, A.out + ro, ro, (size_t)(sp * 3 + a) * V + s, acc[sp][a], (R)A.a, (R)A.b, red);
+  }
+  grid_reduce<3, NT, R>(red, A.red, rhs);
+}
+
+// Small lattices: the warp-per-hop layout of wilson_small_kernel.
+template <typename S, typename G, int NL>
+__global__ void __launch_bounds__(256) wilson_small_mr_kernel(const WilsonArgs<S, G, NL> A, const MrFuseArgs F) {
+  typedef typename Store<S>::R R;
+  __shared__ R part[8][24][32];
+  const int V = A.V;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * 32 + lane;
+  const int rhs = blockIdx.y;
+  const cx<R> cf = fused_coef<R>(F, rhs);
+  const size_t ro = (size_t)rhs * A.vstride;
+  const ShiftedIn<R, S> in{A.in + ro, (const S*)F.pprev + ro, cf};
+  {
+    cx<R> acc[4][3];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) acc[sp][a] = zero<R>();
+    if (s < V) {
+      int c[4], stride[4];
+      site_coords(s, A.L, c, stride);
+      switch (warp) {
+        case 0: one_hop_in<0, true>(acc, A, in, s, c, stride); break;
+        case 1: one_hop_in<0, false>(acc, A, in, s, c, stride); break;
+        case 2: one_hop_in<1, true>(acc, A, in, s, c, stride); break;
+        case 3: one_hop_in<1, false>(acc, A, in, s, c, stride); break;
+        case 4: one_hop_in<2, true>(acc, A, in, s, c, stride); break;
+        case 5: one_hop_in<2, false>(acc, A, in, s, c, stride); break;
+        case 6: one_hop_in<3, true>(acc, A, in, s, c, stride); break;
+        default: one_hop_in<3, false>(acc, A, in, s, c, stride); break;
+      }
+    }
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const size_t i = (size_t)(sp * 3 + a) * V + s;
-        const cx<R> rold = ldc<R>(A.in + ro, i);
-        const cx<R> rn = in(i);
-        cx<R> xv = ldc<R>(x + ro, i);
-        xv = cfma(cf, rold, xv);
-        stc(x + ro, i, xv);
-        stc(rout + ro, i, rn);
-        cx<R> v = cb * acc[sp][a];
-        v = v + ca * rn;
-        stc(A.out + ro, i, v);
-        const cx<R> vs = as_stored<S>(v);
-        const cx<R> d = cmul_conj(vs, rn);
-        acc3[0] += d.re;
-        acc3[1] += d.im;
-        acc3[2] += norm2(vs);
+        part[warp][2 * (sp * 3 + a)][lane] = acc[sp][a].re;
+        part[warp][2 * (sp * 3 + a) + 1][lane] = acc[sp][a].im;
       }
   }
-  grid_reduce<3, NT, R>(acc3, A.red, rhs);
+  __syncthreads();
+  R red[3] = {(R)0, (R)0, (R)0};
+  if (warp < 6 && s < V) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int comp = 2 * warp + k;
+      cx<R> h = zero<R>();
+#pragma unroll
+      for (int w = 0; w < 8; ++w) h = h + mk<R>(part[w][2 * comp][lane], part[w][2 * comp + 1][lane]);
+      fused_site(F, in, A.out + ro, ro, (size_t)comp * V + s, h, (R)A.a, (R)A.b, red);
+    }
+  }
+  grid_reduce<3, 256, R>(red, A.red, rhs);
+}
+
+template <typename S, typename G, int NL>
+static int launch_mr_t(const DslashCall& d, const MrFuseArgs& F, cudaStream_t st) {
+  WilsonArgs<S, G, NL> A;
+  A.in = (const S*)d.in;
+  A.out = (S*)d.out;
+  A.y = nullptr;
+  A.z = nullptr;
+  A.U = (const G*)d.links;
+  for (int k = 0; k < 4; ++k) A.L[k] = d.L[k];
+  A.V = d.L[0] * d.L[1] * d.L[2] * d.L[3];
+  A.a = d.a;
+  A.b = d.b;
+  A.c = 0.0;
+  A.vstride = (size_t)12 * A.V;
+  A.red = d.red;
+  if constexpr (NL != 9) {
+    if ((size_t)A.V * d.nrhs <= (size_t)kSmallSites) {  // the same split as the unfused stencil
+      wilson_small_mr_kernel<S, G, NL><<<dim3((A.V + 31) / 32, d.nrhs), 256, 0, st>>>(A, F);
+      return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
+  }
+  wilson_mr_kernel<S, G, NL, 128><<<dim3((A.V + 127) / 128, d.nrhs), 128, 0, st>>>(A, F);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <typename S, typename G, int NL, int NT, int NR>
@@ -350,8 +468,6 @@ static int launch_nt(const WilsonArgs<S, G, NL>& A, int nrhs, cudaStream_t st) {
 struct WShape {
   int nt, nr;
 };
-// Site x right-hand-side counts up to which the warp-per-hop kernel runs.
-constexpr int kSmallSites = 32768;
 static const WShape kShapesDots[] = {{128, 1}, {128, 2}};
 static const WShape kShapesFree[] = {{128, 1}, {64, 1}, {256, 1}, {128, 2}, {64, 2}, {256, 2}};
 
@@ -399,38 +515,16 @@ static int launch_t(const DslashCall& d, cudaStream_t st) {
   return launch_nt<S, G, NL, 128, 1>(A, d.nrhs, st);
 }
 
-int launch_wilson_mr(const DslashCall& d, const void* pprev, const double* dots, int dstride, double omega, void* x,
-                     void* rout, cudaStream_t st) {
-  const int V = d.L[0] * d.L[1] * d.L[2] * d.L[3];
-  const dim3 grid((V + 127) / 128, d.nrhs);
-  auto fill = [&](auto& A) {
-    A.in = (decltype(A.in))d.in;
-    A.out = (decltype(A.out))d.out;
-    A.y = nullptr;
-    A.z = nullptr;
-    A.U = (decltype(A.U))d.links;
-    for (int k = 0; k < 4; ++k) A.L[k] = d.L[k];
-    A.V = V;
-    A.a = d.a;
-    A.b = d.b;
-    A.c = 0.0;
-    A.vstride = (size_t)12 * V;
-    A.red = d.red;
-  };
-  if (d.prec == 0) {
-    WilsonArgs<double2, double2, 9> A;
-    fill(A);
-    wilson_mr_kernel<double2, double2, 9, 128><<<grid, 128, 0, st>>>(A, (const double2*)pprev, dots, dstride, omega,
-                                                                    (double2*)x, (double2*)rout);
-  } else if (d.prec == 1) {
-    WilsonArgs<float2, float2, 6> A;
-    fill(A);
-    wilson_mr_kernel<float2, float2, 6, 128><<<grid, 128, 0, st>>>(A, (const float2*)pprev, dots, dstride, omega,
-                                                                  (float2*)x, (float2*)rout);
-  } else {
-    return -1;
+int launch_wilson_mr(const DslashCall& d, const void* pprev, const void* u, const void* xin, void* x, void* rout,
+                     const double* dots, int dstride, double omega, cudaStream_t st) {
+  const MrFuseArgs F{pprev, u, xin, x, rout, dots, dstride, omega};
+  switch (d.prec) {
+    case 0: return launch_mr_t<double2, double2, 9>(d, F, st);
+    case 1: return launch_mr_t<float2, float2, 6>(d, F, st);
+    case 2: return launch_mr_t<__half2, __half2, 6>(d, F, st);
+    case 3: return launch_mr_t<__nv_bfloat162, __nv_bfloat162, 6>(d, F, st);
   }
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return -1;
 }
 
 // CTAs per right-hand side of a launch with fused dots (sizes the reduction partials).
