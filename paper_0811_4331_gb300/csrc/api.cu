@@ -75,7 +75,7 @@ inline size_t slot_gcr_pre() { return slot_inner(MG_MAX_LEVELS); }  // <w|r>, ||
 inline size_t slot_total() { return slot_gcr_pre() + 4 * kMaxRhs; }
 const int kInnerBasis = 8;
 
-enum { WV_E, WV_RES, WV_P, WV_XC, WV_AXC, WV_RC, WV_EC, WV_T, WV_DT, WV_IN, WV_A, WV_B, WV_KW, WV_KZ, WV_PR, WV_PE, WV_EOA, WV_EOB, WV_EOC, WV_FR0, WV_FR1, WV_FP0, WV_FP1, WV_COUNT };
+enum { WV_E, WV_RES, WV_P, WV_XC, WV_AXC, WV_RC, WV_EC, WV_T, WV_DT, WV_IN, WV_A, WV_B, WV_KW, WV_KZ, WV_PR, WV_PE, WV_EOA, WV_EOB, WV_EOC, WV_COUNT };
 
 int prec_of(const mg_handle* h, int l) {
   if (!h->p.mixed) return MG_F64;
@@ -377,34 +377,6 @@ int mr_fused(mg_handle* h, int prec, const void* r, const void* pv, const void* 
   return MG_OK;
 }
 
-// Level-0 MR sequence with each step's update fused into the next step's
-// stencil.  Owed describes the update still to be applied: x = xin + c u,
-// r' = r - c p with c from the level's slot and relaxation omega.
-struct Owed {
-  const void* r;
-  const void* p;
-  const void* u;    // null: u = r
-  const void* xin;  // null: x starts from 0
-  double omega;
-};
-
-// `steps` fused MR steps on D e = (owed residual) continuing the owed update;
-// returns the update still owed after the last stencil (r and p in the
-// ping-pong work vectors WV_FR*, WV_FP*).
-int fused_steps(mg_handle* h, int prec, void* x, Owed& ow, int steps, int nrhs) {
-  void* R[2] = {work(h, 0, prec, WV_FR0, nrhs), work(h, 0, prec, WV_FR1, nrhs)};
-  void* P[2] = {work(h, 0, prec, WV_FP0, nrhs), work(h, 0, prec, WV_FP1, nrhs)};
-  if (!R[0] || !R[1] || !P[0] || !P[1]) return MG_ENOMEM;
-  const size_t sl = slot_level(0);
-  for (int s = 0; s < steps; ++s) {
-    // ping-pong away from the buffers the owed update reads
-    const int q = (ow.r == R[0] || ow.p == P[0]) ? 1 : 0;
-    RET(mr_fused(h, prec, ow.r, ow.p, ow.u, ow.xin, x, R[q], P[q], sl, ow.omega, nrhs));
-    ow = Owed{R[q], P[q], nullptr, x, h->p.omega};
-  }
-  return MG_OK;
-}
-
 // `steps` MR steps on A_l x = b continuing from (x, res): if x_zero the
 // iterate is 0 and res is taken from b without an operator application.
 int mr_steps(mg_handle* h, int l, int prec, const void* b, void* x, bool x_zero, void* res, int steps, int nrhs) {
@@ -527,6 +499,11 @@ int eo_smooth(mg_handle* h, int prec, const void* r, void* e, bool add, void* re
   return MG_OK;
 }
 
+// Site x candidate counts up to which the level-0 setup relaxation fuses each
+// MR update into the next stencil launch (an 8^3 x 16 lattice with 20
+// candidates is 163,840).
+const size_t kFuseRelaxSites = 262144;
+
 // Setup relaxation in FP32: steps between recomputations of the true residual.
 const int kTrueResidualEvery = 25;
 
@@ -638,22 +615,12 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
     set_error("prolongator of level " + std::to_string(l) + " not stored in the cycle's precision");
     return MG_EINVAL;
   }
-  // pre-smoothing from e = 0; on level 0 each MR update rides on the next stencil launch
+  // pre-smoothing from e = 0
   const bool eo = l == 0 && h->p.fine_smoother == 1;
-  const bool fuse = l == 0 && !eo;
-  const size_t sl = slot_level(l);
-  if (eo) {
+  if (eo)
     RET(eo_smooth(h, prec, r, e, false, res, h->p.nu_pre, nrhs));
-  } else if (fuse && h->p.nu_pre >= 1) {
-    void* p0 = work(h, 0, prec, WV_FP0, nrhs);
-    if (!p0) return MG_ENOMEM;
-    RET(op_apply(h, 0, prec, r, p0, nullptr, 1.0, 0.0, r, sl, nrhs));
-    Owed ow{r, p0, nullptr, nullptr, h->p.omega};
-    RET(fused_steps(h, prec, e, ow, h->p.nu_pre - 1, nrhs));
-    RET(mr_update(h, 0, prec, e, ow.xin, ow.u ? ow.u : ow.r, res, ow.r, ow.p, sl, ow.omega, nrhs));
-  } else {
+  else
     RET(mr_steps(h, l, prec, r, e, true, res, h->p.nu_pre, nrhs));
-  }
   // restrict, coarse solve, prolong
   const Agg g = agg_of(a);
   const double pbytes = (double)a.Vc * 2 * a.nv * a.nhalf * a.bsites * bytes_of(prec);  // P once
@@ -701,13 +668,8 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
     LK(launch_prolong(pc, prec, prec, g, a.P[prec].p, ec, xc, nrhs, h->st, pvar));
   }
   // alpha = <A x_c|r0> / <A x_c|A x_c>  (Eq. 3.5);  e += alpha x_c, r0 -= alpha A x_c
+  const size_t sl = slot_level(l);
   RET(op_apply(h, l, prec, xc, axc, nullptr, 1.0, 0.0, res, sl, nrhs));
-  if (fuse && h->p.nu_post >= 1) {  // the alpha update rides on the first post-smoothing stencil
-    Owed ow{res, axc, xc, e, 1.0};
-    RET(fused_steps(h, prec, e, ow, h->p.nu_post, nrhs));
-    RET(mr_update(h, 0, prec, e, ow.xin, ow.u ? ow.u : ow.r, res, ow.r, ow.p, sl, ow.omega, nrhs));
-    return MG_OK;
-  }
   RET(mr_update(h, l, prec, e, e, xc, res, res, axc, sl, 1.0, nrhs));
   // post-smoothing
   if (eo) return eo_smooth(h, prec, res, e, true, res, h->p.nu_post, nrhs);
@@ -973,8 +935,10 @@ static int relax_candidates(mg_handle* h, int l, void* x64, int k) {
     LK(launch_convert(MG_F64, rp, a.n(), k, x64, candr.p, 1.0, nullptr, 0, 0.0, 0, st));
     x = candr.p;
   }
-  // level 0: each step's update is fused into the next step's stencil (r and p ping-pong)
-  const bool fuse = l == 0;
+  // level 0 on small lattices: each step's update is fused into the next step's stencil (r and p
+  // ping-pong).  The fused stencil reads r and p at all nine points; once the candidates no longer fit
+  // in L2 that costs more than the separate update pass it saves.
+  const bool fuse = l == 0 && (size_t)a.V * k <= kFuseRelaxSites;
   if (!rr.ensure(vr * k) || !pp.ensure(vr * k) || (fuse && (!rr2.ensure(vr * k) || !pp2.ensure(vr * k))))
     return MG_ENOMEM;
   RET(ensure_reducer(h, k));

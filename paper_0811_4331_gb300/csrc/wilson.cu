@@ -236,10 +236,10 @@ __global__ void __launch_bounds__(256) wilson_small_kernel(const WilsonArgs<S, G
 constexpr int kSmallSites = 32768;
 
 // ------------------------------------------------------------------ MR-fused stencil
-// One MR step (Sec. 3) that also finishes the previous step's update.  With
-// c = omega <p|r>/<p|p> of the previous step (per right-hand side, from its
-// reduction slot) and that step's update direction u (= r for an MR step,
-// the prolonged coarse correction for the alpha step of Eq. 3.5):
+// One MR step (Sec. 3) that also finishes the previous step's update (the
+// setup relaxation of Sec. 2 on small lattices).  With c = omega <p|r>/<p|p>
+// of the previous step (per right-hand side, from its reduction slot) and
+// that step's update direction u (null: u = r):
 //   x = xin + c u,   r' = r - c p,   out = a r' + b Hop(r') (= A r'),
 // with <out|r'>, ||out||^2 reduced for the next step.  r' at the neighbours
 // is formed on the fly from r and p with the same operations, and rounded to
