@@ -238,20 +238,11 @@ __global__ void __launch_bounds__(kVecThreads)
   grid_reduce<2 * kChunk, kVecThreads, R>(red, r2, rhs * gridDim.y + chunk);
 }
 
-// Blocks per chunk of the multi-dot: two elements per thread for short
-// vectors (a thread's loads of one element are 9 independent ones, so more
-// CTAs hide the L2 latency of small, cache-resident bases), at most 4 per SM.
-static int multidot_blocks(size_t n) {
-  size_t b = (n + 2 * kVecThreads - 1) / (2 * kVecThreads);
-  if (b > 608) b = 608;
-  return (int)(b < 1 ? 1 : b);
-}
-
 int launch_multidot(int prec, size_t n, int nrhs, int k, int kmax, const void* W, size_t jstride, const void* w,
                     RedArgs red, cudaStream_t st, const double* pre, const double* post, int cstride) {
   if (k <= 0) return 0;
   if (kmax % kChunk) return -1;
-  dim3 grid(multidot_blocks(n), (k + kChunk - 1) / kChunk, nrhs);
+  dim3 grid(red_blocks(n), (k + kChunk - 1) / kChunk, nrhs);
   switch (prec) {
     case 0:
       multidot_kernel<double2><<<grid, kVecThreads, 0, st>>>(n, k, kmax, (const double2*)W, jstride, (const double2*)w,
