@@ -298,9 +298,10 @@ def class_profile(wm, handles_run, peaks):
 PREC_NAMES = ["f64", "f32", "f16", "bf16"]
 
 
-def shares_and_roofline(tot, peaks, galerkin_flops=None, inverse_n=None):
+def shares_and_roofline(tot, peaks, galerkin_flops=None, inverse_n=None, traffic=None):
     """Device-time share of every class and the roofline of the dominant one: achieved =
-    algorithmic bytes (each operand once per launch) / summed CUDA-event time of its launches."""
+    algorithmic bytes (each operand once per launch) / summed CUDA-event time of its launches.
+    traffic: {(class, precision): DRAM bytes per launch from an ncu capture of this workload}."""
     all_ms = sum(v[1] for v in tot.values())
     hbm = peaks.get("hbm_gbs")
     shares = {}
@@ -313,7 +314,7 @@ def shares_and_roofline(tot, peaks, galerkin_flops=None, inverse_n=None):
     (top, tprec), (n, ms, nb) = max(tot.items(), key=lambda kv: kv[1][1])
     avg_s = ms / 1e3 / max(n, 1)
     roof = {"kernel": "%s/%s" % (top, PREC_NAMES[tprec]), "launches": n, "avg_us": round(avg_s * 1e6, 3),
-            "traffic": None}
+            "traffic": (traffic or {}).get((top, tprec))}
     if nb > 0:
         ach = nb / n / avg_s / 1e9
         roof.update(bound="hbm", achieved=round(ach, 1), peak=hbm, unit="GB/s", frac=round(ach / hbm, 4),
