@@ -298,6 +298,11 @@ def class_profile(wm, handles_run, peaks):
 PREC_NAMES = ["f64", "f32", "f16", "bf16"]
 
 
+# DRAM bytes per launch (dram__bytes read + write, cold cache) of this step's kernels, from one ncu capture
+# (profiles/dslash_small_f16_c2_step.md); valid while those kernels stay as captured.
+C2_TRAFFIC = {("dslash", 2): 1232000}
+
+
 def shares_and_roofline(tot, peaks, galerkin_flops=None, inverse_n=None, traffic=None):
     """Device-time share of every class and the roofline of the dominant one: achieved =
     algorithmic bytes (each operand once per launch) / summed CUDA-event time of its launches.
@@ -359,7 +364,7 @@ def profiled_step(wm, torch, Ud, bd, masses, stream):
     V = int(np.prod(DIMS))
     bs = int(np.prod(BLOCK))
     gal = 9 * (bs * 170 + 2 * NV * 6 * bs * 8) * (V // bs) * 2 * NV
-    return shares_and_roofline(tot, peaks, galerkin_flops=gal, inverse_n=2 * NV * (V // bs))
+    return shares_and_roofline(tot, peaks, galerkin_flops=gal, inverse_n=2 * NV * (V // bs), traffic=C2_TRAFFIC)
 
 
 def measured_peaks():
