@@ -126,6 +126,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------------------- ranks
+def max_over_ranks(times, world, device):
+    """Per-step times, each the maximum over the ranks of the process group (the slowest replica
+    bounds the job); `device` is where the reduction runs ("cuda" under NCCL, "cpu" under gloo)."""
+    t = np.asarray(times, dtype=np.float64)
+    if world <= 1:
+        return t
+    import torch
+    tt = torch.tensor(t, device=device)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return tt.cpu().numpy()
+
+
 # ---------------------------------------------------------------------------- native arm
 def native(args, rank, world, U, b):
     import torch
@@ -186,12 +199,7 @@ def native(args, rank, world, U, b):
                 torch.distributed.barrier()
             times.append(e0.elapsed_time(e1) / 1e3)
         launches[0] = wm.mg_launch_count() - n0
-        t = np.array(times)
-        if world > 1:
-            tt = torch.tensor(t, device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            t = tt.cpu().numpy()
-        return t
+        return max_over_ranks(times, world, "cuda")
 
     clk = ClockSampler(dev)
     if not args.ncu:
