@@ -49,3 +49,18 @@ def test_host_only_entry_points(lib):
     st = wm.LIB.mg_setup(ctypes.byref(h), ctypes.c_void_p(1), 0, d, 0.1, ctypes.byref(p), None, None)
     assert st == wm.MG_EINVAL and not h.value
     assert "dims" in wm.mg_last_error()
+    # parameters validated before any device work
+    d = (ctypes.c_int * 4)(4, 3, 4, 4)
+    p.fine_smoother = 1
+    st = wm.LIB.mg_setup(ctypes.byref(h), ctypes.c_void_p(1), 0, d, 0.1, ctypes.byref(p), None, None)
+    assert st == wm.MG_EINVAL and "even" in wm.mg_last_error()
+    p.fine_smoother = 2
+    st = wm.LIB.mg_setup(ctypes.byref(h), ctypes.c_void_p(1), 0, (ctypes.c_int * 4)(4, 4, 4, 4), 0.1,
+                         ctypes.byref(p), None, None)
+    assert st == wm.MG_EINVAL and "fine_smoother" in wm.mg_last_error()
+    # null handles and empty batches are refused without touching a device
+    assert wm.LIB.mg_solve_many(None, 0, None, None, 1, 1, 1e-10, None, None) == wm.MG_EINVAL
+    assert wm.LIB.eo_split(None, 0, None, None, None, 1, None) == wm.MG_EINVAL
+    assert wm.LIB.schur_apply(None, 0, None, None, 1, None) == wm.MG_EINVAL
+    assert wm.LIB.krylov_solve(None, wm.MG_KRYLOV_BICGSTAB_EO, None, None, 1, 1, 1e-10, 100, None, None) \
+        == wm.MG_EINVAL
