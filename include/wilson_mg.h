@@ -147,7 +147,10 @@ int mg_default_params(mg_params* p);
  * FP64 modified Gram-Schmidt (two passes, candidate order) per aggregate and
  * chirality into P, then A_{l+1} = P^+ A_l P as a 9-point stencil of
  * 2Nv x 2Nv blocks; the coarsest level gets a dense FP64 inverse.
- * Errors: MG_EINVAL, MG_ENOMEM, MG_ERANK, MG_ECUDA.  On error *h is NULL. */
+ * Errors: MG_EINVAL (also when a link deviates from SU(3), max |U U^+ - 1|
+ * or |det U - 1| above 1e-10: the FP32 / 16-bit operators store two rows and
+ * rebuild the third as for SU(3)), MG_ENOMEM, MG_ERANK, MG_ECUDA.  On error
+ * *h is NULL. */
 int mg_setup(mg_handle** h, const double* gauge, int gauge_on_device, const int dims[4],
              double mass, const mg_params* p, const double* const* starts, void* stream);
 

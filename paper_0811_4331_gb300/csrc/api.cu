@@ -6,6 +6,7 @@
 // kernels of this library; the host only sequences launches and reads the
 // residual norms that decide when to stop.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -1132,6 +1133,9 @@ static int build_from(mg_handle* h, int l, const double* const* starts) {
   return MG_OK;
 }
 
+// Largest deviation of an input link from SU(3) that mg_setup accepts.
+const double kSu3Tolerance = 1e-10;
+
 static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, const double* const* starts) {
   const mg_params& p = h->p;
   cudaStream_t st = h->st;
@@ -1150,6 +1154,25 @@ static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, co
       if (!ext.ensure(gbytes)) return MG_ENOMEM;
       CK(cudaMemcpyAsync(ext.p, gauge, gbytes, cudaMemcpyHostToDevice, st));
       gdev = ext.as<double>();
+    }
+    // the 12-real link storage of the FP32 / 16-bit operators rebuilds the third row as for SU(3)
+    {
+      DevBuf chk;
+      if (!chk.ensure(sizeof(unsigned))) return MG_ENOMEM;
+      CK(cudaMemsetAsync(chk.p, 0, sizeof(unsigned), st));
+      LK(launch_su3_check(gdev, f.V, chk.as<unsigned>(), st));
+      unsigned bits = 0u;
+      CK(cudaMemcpyAsync(&bits, chk.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      float dev = 0.f;
+      memcpy(&dev, &bits, sizeof(dev));
+      if (!(dev <= kSu3Tolerance)) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "gauge field is not SU(3): max |U U^+ - 1|, |det U - 1| over the links = %.3g",
+                 (double)dev);
+        set_error(msg);
+        return MG_EINVAL;
+      }
     }
     std::vector<int> precs = {MG_F64};
     if (p.mixed) {

@@ -36,6 +36,8 @@ int launch_wilson_mr(const DslashCall& d, const void* pprev, const void* u, cons
 int wilson_variants(int prec, bool dots, int nrhs, int V);
 int wilson_blocks(int V);
 int launch_pack_links(int prec, const void* ext, void* out, int V, cudaStream_t st);
+// *worst = max over links of |U U^+ - 1|, |det U - 1| as float bits (caller zeroes it first).
+int launch_su3_check(const void* ext, int V, unsigned* worst, cudaStream_t st);
 
 // Even-odd stencil on half-lattice fields [nrhs][12][V/2] (every extent even):
 // out_p = a x_p + b H_{p,1-p} in_{1-p} + c y_p, H the hopping term of D =

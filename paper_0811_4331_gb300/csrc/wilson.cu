@@ -555,6 +555,56 @@ __global__ void pack_links_kernel(const double2* __restrict__ ext, G* __restrict
   stc(out, i, mk<double>(v.x, v.y));
 }
 
+// ------------------------------------------------------------------ link check
+// Largest deviation of an external FP64 gauge field [4][V][3][3] from SU(3):
+// max over links of |U U^+ - 1| and |det U - 1| (largest real or imaginary
+// part).  A non-negative float's bits order like the float, so the maximum
+// goes through an integer atomicMax; NaN counts as infinite.
+__global__ void su3_check_kernel(const double2* __restrict__ ext, size_t nlinks, unsigned* worst) {
+  unsigned best = 0u;
+  for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < nlinks; l += (size_t)gridDim.x * blockDim.x) {
+    cx<double> u[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double2 v = ext[l * 9 + i * 3 + j];
+        u[i][j] = mk<double>(v.x, v.y);
+      }
+    double dev = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        cx<double> g = zero<double>();
+#pragma unroll
+        for (int k = 0; k < 3; ++k) g = cfma_conj(u[j][k], u[i][k], g);  // (U U^+)_ij
+        if (i == j) g.re -= 1.0;
+        dev = fmax(dev, fmax(fabs(g.re), fabs(g.im)));
+      }
+    const cx<double> det = u[0][0] * (u[1][1] * u[2][2] - u[1][2] * u[2][1]) -
+                           u[0][1] * (u[1][0] * u[2][2] - u[1][2] * u[2][0]) +
+                           u[0][2] * (u[1][0] * u[2][1] - u[1][1] * u[2][0]);
+    dev = fmax(dev, fmax(fabs(det.re - 1.0), fabs(det.im)));
+    const unsigned bits = (dev == dev) ? __float_as_uint((float)dev) : 0x7f800000u;
+    best = bits > best ? bits : best;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned other = __shfl_down_sync(0xffffffffu, best, o);
+    best = other > best ? other : best;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(worst, best);
+}
+
+int launch_su3_check(const void* ext, int V, unsigned* worst, cudaStream_t st) {
+  const size_t n = (size_t)4 * V;
+  size_t nb = (n + 255) / 256;
+  if (nb > 1216) nb = 1216;
+  su3_check_kernel<<<(unsigned)(nb < 1 ? 1 : nb), 256, 0, st>>>((const double2*)ext, n, worst);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_pack_links(int prec, const void* ext, void* out, int V, cudaStream_t st) {
   const int NL = prec == 0 ? 9 : 6;
   const size_t tot = (size_t)4 * V * NL;

@@ -135,6 +135,24 @@ def test_rank_loss_is_reported():
 
 
 
+
+def test_non_su3_gauge_field_is_refused():
+    """The mixed operators rebuild each link's third row as for SU(3), so mg_setup checks every link."""
+    wm = require_gpu()
+    dims = (4, 4, 4, 4)
+    U = inputs.random_gauge(dims, 0)
+    p = wm.mg_default_params(n_levels=1, mixed=1)
+    wm.mg_destroy(wm.mg_setup(U, dims, 0.1, p))  # SU(3) to rounding: accepted
+    bad = U.copy()
+    bad[2, 1, 3, 0, 2] *= 1.0 + 1e-6  # one link (mu = z, t = 1, z = 3, y = 0, x = 2) off by 1e-6
+    with pytest.raises(wm.MgError) as e:
+        wm.mg_setup(bad, dims, 0.1, p)
+    assert e.value.status == wm.MG_EINVAL and "SU(3)" in str(e.value)
+    phase = U.copy()
+    phase[0, 0, 0, 0, 1] *= np.exp(0.5j)  # unitary, det != 1
+    with pytest.raises(wm.MgError):
+        wm.mg_setup(phase, dims, 0.1, p)
+
 def test_block_too_large_for_the_galerkin_tile_is_refused():
     """A block whose P column does not fit the Galerkin CTA's shared memory is refused with a message."""
     wm = require_gpu()
