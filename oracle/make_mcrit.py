@@ -11,6 +11,8 @@ Re(lambda_min) -> 0; Sec. 5 quotes m_crit = -0.8049 for its own beta = 6.0,
 (scipy's ARPACK binding, which='SR') on the oracle operator.
 
 Usage: python -m oracle.make_mcrit [--dims 8 8 8 16] [--sweeps 200] [--seed 0]
+       python -m oracle.make_mcrit --field random --dims 4 4 4 4 --seed 0
+         (the exp(0.3 i H) field of the small workload instead of a heatbath field)
 """
 import argparse
 import json
@@ -45,27 +47,35 @@ def main():
     ap.add_argument("--beta", type=float, default=6.0)
     ap.add_argument("--sweeps", type=int, default=200)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--field", choices=["heatbath", "random"], default="heatbath")
     a = ap.parse_args()
     t0 = time.time()
-    U = inputs.heatbath_gauge(tuple(a.dims), a.beta, a.sweeps, a.seed)
+    if a.field == "random":
+        U = inputs.random_gauge(tuple(a.dims), a.seed)
+        key = "%dx%dx%dx%d_random0.3_seed%d" % (*a.dims, a.seed)
+        how = "python -m oracle.make_mcrit --field random --dims %d %d %d %d --seed %d" % (*a.dims, a.seed)
+    else:
+        U = inputs.heatbath_gauge(tuple(a.dims), a.beta, a.sweeps, a.seed)
+        key = "%dx%dx%dx%d_beta%.1f_sweeps%d_seed%d" % (*a.dims, a.beta, a.sweeps, a.seed)
+        how = "python -m oracle.make_mcrit --dims %d %d %d %d --sweeps %d --seed %d" % (*a.dims, a.sweeps, a.seed)
     t1 = time.time()
     lam, vals = smallest_real_part(U)
     t2 = time.time()
-    key = "%dx%dx%dx%d_beta%.1f_sweeps%d_seed%d" % (*a.dims, a.beta, a.sweeps, a.seed)
     data = {}
     if os.path.exists(GOLDEN):
         with open(GOLDEN) as f:
             data = json.load(f)
     data[key] = {
-        "dims": a.dims, "beta": a.beta, "sweeps": a.sweeps, "seed": a.seed,
+        "dims": a.dims, "field": a.field, "seed": a.seed,
         "plaquette": inputs.plaquette(U),
         "min_re_lambda_m0": lam,
         "m_crit": -lam,
         "lowest_eigenvalues_m0": [[v.real, v.imag] for v in vals],
-        "how": "python -m oracle.make_mcrit --dims %d %d %d %d --sweeps %d --seed %d"
-               % (*a.dims, a.sweeps, a.seed),
-        "seconds": {"heatbath": round(t1 - t0, 1), "arnoldi": round(t2 - t1, 1)},
+        "how": how,
+        "seconds": {"field": round(t1 - t0, 1), "arnoldi": round(t2 - t1, 1)},
     }
+    if a.field == "heatbath":
+        data[key].update(beta=a.beta, sweeps=a.sweeps)
     with open(GOLDEN, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)
     print(key, data[key]["m_crit"], data[key]["plaquette"])
