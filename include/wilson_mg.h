@@ -136,8 +136,12 @@ int mg_default_params(mg_params* p);
  *                  device memory otherwise.  Copied; the caller keeps ownership.
  *   dims         : {Lx, Ly, Lz, Lt}, each >= 1.
  *   p            : parameters (copied).  For every level l < n_levels - 1 the
- *                  level's extent must be divisible by block[l], and
- *                  nv[l] <= (components per chirality) * (sites per block).
+ *                  level's extent must be divisible by block[l],
+ *                  nv[l] <= (components per chirality) * (sites per block),
+ *                  and one block of a P column (components x sites, complex
+ *                  in the setup's precision: FP64 plain, FP32 mixed) must fit
+ *                  the Galerkin product's 200 KB of shared memory (a 4^4
+ *                  fine block in FP64 takes 48 KB).
  *   starts       : NULL, or an array of n_levels - 1 host pointers; starts[l]
  *                  holds nv[l] FP64 start vectors of level l in the external
  *                  layout [nv][V_l][ncomp_l].  NULL entries (or NULL starts)
@@ -146,7 +150,8 @@ int mg_default_params(mg_params* p);
  * MR steps (omega) on A x = 0 from each start, unit-normalise, blockwise
  * FP64 modified Gram-Schmidt (two passes, candidate order) per aggregate and
  * chirality into P, then A_{l+1} = P^+ A_l P as a 9-point stencil of
- * 2Nv x 2Nv blocks; the coarsest level gets a dense FP64 inverse.
+ * 2Nv x 2Nv blocks; the coarsest level gets a dense inverse (FP64 plain;
+ * FP32 mixed, applied with one FP64 refinement step).
  * Errors: MG_EINVAL (also when a link deviates from SU(3), max |U U^+ - 1|
  * or |det U - 1| above 1e-10: the FP32 / 16-bit operators store two rows and
  * rebuild the third as for SU(3)), MG_ENOMEM, MG_ERANK, MG_ECUDA.  On error
