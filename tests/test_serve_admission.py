@@ -1,0 +1,73 @@
+"""Host-side admission of the solve server, on CPU (no device work).
+
+The server admits requests first-in first-out while the device bytes in flight plus the head request's
+footprint (mg_footprint, a host computation) stay within the HBM budget; a request larger than the whole
+budget is refused at submission.  The object is built without its worker threads and streams, so the
+real submit/_admit code runs with nothing on a GPU.
+"""
+import collections
+import os
+import threading
+
+import numpy as np
+import pytest
+
+LIB = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_0811_4331_gb300",
+                   "libwilsonmg.so")
+
+
+@pytest.fixture(scope="module")
+def serve_mod():
+    if not os.path.exists(LIB):
+        from paper_0811_4331_gb300 import build
+        build.build()
+    from paper_0811_4331_gb300 import serve
+    return serve
+
+
+def _server(serve, budget, fields, params):
+    s = object.__new__(serve.SolveServer)
+    s.fields, s.params, s.budget = fields, params, int(budget)
+    s.inflight_bytes = s.inflight = s.max_inflight = s.max_inflight_bytes = 0
+    s.queue = collections.deque()
+    s.lock = threading.Condition()
+    return s
+
+
+def _req(serve, rid, field, nrhs, dims):
+    shp = (nrhs,) + (dims[3], dims[2], dims[1], dims[0], 4, 3)
+    return serve.Request(rid, field, 0.1, np.zeros(shp if nrhs > 1 else shp[1:], np.complex128), 1e-10, 0.0)
+
+
+def test_fifo_admission_within_the_budget(serve_mod):
+    wm = serve_mod.wm
+    p = wm.mg_default_params(n_levels=2, block=[(2, 2, 2, 2)], nv=[8], mixed=1)
+    dims = (8, 8, 8, 8)
+    f1 = wm.mg_footprint(dims, p, 1)
+    f4 = wm.mg_footprint(dims, p, 4)
+    assert 0 < f1 < f4
+    s = _server(serve_mod, f4 + f1, {"a": (None, dims, 0.1)}, p)
+    reqs = [_req(serve_mod, 0, "a", 4, dims), _req(serve_mod, 1, "a", 1, dims), _req(serve_mod, 2, "a", 4, dims),
+            _req(serve_mod, 3, "a", 1, dims)]
+    for r in reqs:
+        s.submit(r)
+    assert [r.footprint for r in reqs] == [f4, f1, f4, f1]
+    a = s._admit()
+    b = s._admit()
+    assert (a.rid, b.rid) == (0, 1) and s.inflight_bytes == f4 + f1
+    assert s._admit() is None            # the head (a 4-RHS request) waits for room
+    assert [r.rid for r in s.queue] == [2, 3]  # first in, first out: no request overtakes the head
+    s.inflight_bytes -= a.footprint      # request 0 completes
+    s.inflight -= 1
+    c = s._admit()
+    assert c.rid == 2 and s._admit() is None
+    assert s.max_inflight == 2 and s.max_inflight_bytes == f4 + f1
+
+
+def test_request_larger_than_the_budget_is_refused(serve_mod):
+    wm = serve_mod.wm
+    p = wm.mg_default_params(n_levels=2, block=[(2, 2, 2, 2)], nv=[8], mixed=1)
+    dims = (8, 8, 8, 8)
+    s = _server(serve_mod, wm.mg_footprint(dims, p, 1), {"a": (None, dims, 0.1)}, p)
+    r = s.submit(_req(serve_mod, 0, "a", 4, dims))
+    assert r.error and "budget" in r.error and r.event.is_set() and not s.queue
