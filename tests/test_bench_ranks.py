@@ -60,3 +60,19 @@ def test_reference_arm_other_ranks_exit_without_work():
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_roofline_arithmetic():
+    """achieved = algorithmic bytes per launch / mean launch time; frac = achieved / measured peak; the
+    dominant class is the one with the most device time; traffic comes from the capture table."""
+    sys.path.insert(0, ROOT)
+    import bench
+    tot = {("dslash", 2): [1000, 20.0, 1000 * 2.0e6],   # 20 us per launch, 2 MB each -> 100 GB/s
+           ("vector", 1): [500, 5.0, 500 * 1.0e6]}
+    roof, shares = bench.shares_and_roofline(tot, {"hbm_gbs": 5000.0}, traffic={("dslash", 2): 1.5e6})
+    assert roof["kernel"] == "dslash/f16" and roof["launches"] == 1000
+    assert abs(roof["avg_us"] - 20.0) < 1e-9 and abs(roof["achieved"] - 100.0) < 1e-6
+    assert abs(roof["frac"] - 0.02) < 1e-9 and roof["peak"] == 5000.0 and roof["traffic"] == 1.5e6
+    assert abs(shares["dslash/f16"]["share"] - 0.8) < 1e-9 and abs(shares["vector/f32"]["share"] - 0.2) < 1e-9
+    roof, _ = bench.shares_and_roofline({("vector", 1): [10, 1.0, 1e7]}, {"hbm_gbs": 5000.0})
+    assert roof["traffic"] is None
