@@ -2244,12 +2244,15 @@ extern "C" int mg_solve_many(mg_handle* const* hs, int count, const double* cons
     set_error("mg_solve_many: bad argument");
     return MG_EINVAL;
   }
-  for (int i = 0; i < count; ++i)
-    for (int j = 0; j < i; ++j)
-      if (!hs[i] || hs[i] == hs[j]) {
-        set_error("mg_solve_many: handles must be distinct and non-null (a handle is not thread-safe)");
-        return MG_EINVAL;
-      }
+  for (int i = 0; i < count; ++i) {
+    bool bad = !hs[i] || !b[i] || !x[i];
+    for (int j = 0; j < i; ++j) bad |= hs[i] == hs[j];
+    if (bad) {
+      set_error("mg_solve_many: handles must be distinct and non-null (a handle is not thread-safe), b and x "
+                "non-null");
+      return MG_EINVAL;
+    }
+  }
   std::vector<int> rc(count, MG_OK);
   std::vector<std::string> msg(count);
   auto run = [&](int i) {
@@ -2270,8 +2273,16 @@ extern "C" int mg_solve_many(mg_handle* const* hs, int count, const double* cons
   };
   std::vector<std::thread> pool;
   pool.reserve(count - 1);
-  for (int i = 1; i < count; ++i) pool.emplace_back(run, i);
+  int started = 1;
+  for (; started < count; ++started) {
+    try {
+      pool.emplace_back(run, started);
+    } catch (const std::exception&) {  // no thread to be had: the rest run on this one
+      break;
+    }
+  }
   run(0);
+  for (int i = started; i < count; ++i) run(i);
   for (auto& t : pool) t.join();
   for (int i = 0; i < count; ++i)
     if (rc[i] != MG_OK) {
