@@ -134,3 +134,22 @@ def test_mg_gcr_with_the_even_odd_smoother_converges():
         assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b)
         its[sm] = info["iters"]
     assert its["eo"] <= its["mr"] + 2, its
+
+
+def test_schur_identity_on_random_shapes():
+    """The block-elimination pin over random even extents (2 or 4 per direction), masses and fields."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=6, deadline=None, derandomize=True)
+    @hyp.given(ext=st.tuples(*[st.sampled_from([2, 4])] * 4).filter(lambda e: e[0] * e[1] * e[2] * e[3] <= 64),
+               m=st.floats(-0.9, 0.9), seed=st.integers(0, 1000))
+    def check(ext, m, seed):
+        U = inputs.random_gauge(ext, seed)
+        D, de = _dense_blocks(U, m)
+        S_blocks = D[np.ix_(de, de)] - D[np.ix_(de, ~de)] @ np.linalg.solve(D[np.ix_(~de, ~de)], D[np.ix_(~de, de)])
+        half = (de.sum() // 12, 4, 3)
+        S = dirac.dense_matrix(lambda v: evenodd.schur(U, m, v), half)
+        assert np.max(np.abs(S - S_blocks)) < 1e-11 * max(1.0, np.max(np.abs(S_blocks)))
+
+    check()
