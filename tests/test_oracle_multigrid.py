@@ -319,3 +319,27 @@ def test_adaptive_prototype_is_a_minimal_residual_solve_of_the_null_equation():
     y0 = inputs.null_vector_starts(l2, 12, 1, 41)[0]
     y1 = mg.adaptive_prototype(h2, 0, y0, 1, dict(cyc, nu_pre=0, nu_post=0))
     assert np.sqrt(mg.norm2(y1)) < 1e-10 * np.sqrt(mg.norm2(y0))
+
+
+def test_coarse_stencil_brute_force_on_random_shapes():
+    """The stencil Galerkin product against dense P^+ D P over random lattice and block shapes (coarse
+    extents 1, 2, 3 in any direction), numbers of vectors and fields."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @st.composite
+    def shapes(draw):
+        block = tuple(draw(st.sampled_from([1, 2])) for _ in range(4))
+        coarse = tuple(draw(st.sampled_from([1, 2, 3])) for _ in range(4))
+        dims = tuple(b * c for b, c in zip(block, coarse))
+        hyp.assume(int(np.prod(dims)) <= 48 and int(np.prod(block)) >= 2)
+        nv = draw(st.integers(1, min(4, 6 * int(np.prod(block)))))
+        return dims, block, nv
+
+    @hyp.settings(max_examples=6, deadline=None, derandomize=True)
+    @hyp.given(shape=shapes(), seed=st.integers(0, 1000))
+    def check(shape, seed):
+        dims, block, nv = shape
+        _dense_check(dims, block, nv, 2, seed)
+
+    check()
