@@ -153,3 +153,32 @@ def test_single_site_operator_matches_field_operator():
     for site in [(0, 0, 0, 0), (2, 3, 1, 4), (1, 0, 1, 2), (2, 0, 0, 0)]:
         x, y, z, t = site
         assert np.max(np.abs(dirac.wilson_dirac_site(U, psi, 0.3, site) - full[t, z, y, x])) < 1e-13
+
+
+def test_covariance_and_gamma5_hermiticity_on_random_shapes():
+    """Gauge covariance and gamma5-Hermiticity over random extents 1..5 (odd, even, length 1), masses and
+    fields: a wrong hop direction, link index or boundary wrap breaks one of the two."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=8, deadline=None, derandomize=True)
+    @hyp.given(dims=st.tuples(*[st.integers(1, 5)] * 4), m=st.floats(-1.0, 1.0), seed=st.integers(0, 10 ** 6))
+    def check(dims, m, seed):
+        U = inputs.random_gauge(dims, seed)
+        lat = _lat(dims)
+        rng = np.random.default_rng(seed + 1)
+        G = inputs.random_su3(rng, int(np.prod(lat)), 1.0).reshape(lat + (3, 3))
+        Ug = np.empty_like(U)
+        for mu in range(4):
+            Ug[mu] = G @ U[mu] @ np.conj(np.swapaxes(dirac.shift(G, mu, +1), -1, -2))
+        x = inputs.gaussian_spinor(dims, seed + 2)
+        y = inputs.gaussian_spinor(dims, seed + 3)
+        Gx = np.einsum("...ab,...sb->...sa", G, x)
+        lhs = dirac.wilson_dirac(Ug, Gx, m)
+        rhs = np.einsum("...ab,...sb->...sa", G, dirac.wilson_dirac(U, x, m))
+        assert np.max(np.abs(lhs - rhs)) <= 1e-12 * max(1.0, np.max(np.abs(rhs)))
+        a = np.vdot(y, dirac.apply_gamma5(dirac.wilson_dirac(U, x, m)))
+        b = np.vdot(x, dirac.apply_gamma5(dirac.wilson_dirac(U, y, m)))
+        assert abs(a - np.conj(b)) <= 1e-12 * max(1.0, abs(a))
+
+    check()
