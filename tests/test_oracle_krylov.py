@@ -8,6 +8,7 @@
 * a multiple of the identity is solved by BiCGstab in one iteration.
 """
 import numpy as np
+import pytest
 import scipy.linalg
 import scipy.sparse.linalg as sla
 
@@ -73,3 +74,22 @@ def test_identity_is_one_iteration():
     x, info = krylov.bicgstab(lambda v: 2.5 * v, b, tol=1e-12)
     assert info["iters"] == 1
     assert np.allclose(x, b / 2.5, rtol=1e-14)
+
+
+def test_methods_reach_the_dense_solution_on_random_shapes():
+    """BiCGstab and CGNR against a dense solve over random small lattices (extents 1..3), masses and fields."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=6, deadline=None, derandomize=True)
+    @hyp.given(dims=st.tuples(*[st.integers(1, 3)] * 4), m=st.floats(0.05, 1.0), seed=st.integers(0, 1000))
+    def check(dims, m, seed):
+        A, Ad, b, shp = _system(dims, m, seed)
+        D = dirac.dense_matrix(A, (b.size,))
+        xl = np.linalg.solve(D, b)
+        for x, info in (krylov.bicgstab(A, b, tol=1e-11), krylov.cgnr(A, Ad, b, tol=1e-11)):
+            assert info["true_rel_residual"] <= 1e-11
+            assert np.linalg.norm(D @ x - b) <= 1.01e-11 * np.linalg.norm(b)
+            assert np.linalg.norm(x - xl) <= 1e-7 * np.linalg.norm(xl)
+
+    check()

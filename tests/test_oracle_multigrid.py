@@ -343,3 +343,37 @@ def test_coarse_stencil_brute_force_on_random_shapes():
         _dense_check(dims, block, nv, 2, seed)
 
     check()
+
+
+def test_prolongator_invariants_on_random_shapes():
+    """P^+ P = 1, the chirality zeros and P P^+ v = v for every candidate (Eq. 2.3), and R = P^+ the
+    adjoint of P, over random lattice and block shapes, vector counts and fields."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @st.composite
+    def shapes(draw):
+        block = tuple(draw(st.sampled_from([1, 2])) for _ in range(4))
+        coarse = tuple(draw(st.sampled_from([1, 2])) for _ in range(4))
+        hyp.assume(int(np.prod(block)) >= 2)
+        nv = draw(st.integers(1, min(6, 6 * int(np.prod(block)))))
+        return tuple(b * c for b, c in zip(block, coarse)), block, nv
+
+    @hyp.settings(max_examples=8, deadline=None, derandomize=True)
+    @hyp.given(shape=shapes(), seed=st.integers(0, 1000))
+    def check(shape, seed):
+        dims, block, nv = shape
+        U, A, cands, blk, P = _hierarchy_pieces(dims, block, nv, 2, seed)
+        assert np.all(P[..., :6, nv:] == 0) and np.all(P[..., 6:, :nv] == 0)
+        G = blk.block_sum(np.einsum("...ci,...cj->...ij", np.conj(P), P))
+        assert np.max(np.abs(G - np.eye(2 * nv))) < 1e-13
+        for v in cands:
+            assert np.max(np.abs(mg.prolong(P, blk, mg.restrict(P, blk, v)) - v)) < 1e-12
+        rng = np.random.default_rng(seed)
+        r = rng.standard_normal(v.shape) + 1j * rng.standard_normal(v.shape)
+        xc = rng.standard_normal(blk.coarse + (2 * nv,)) + 1j * rng.standard_normal(blk.coarse + (2 * nv,))
+        lhs = np.vdot(mg.prolong(P, blk, xc), r)
+        rhs = np.vdot(xc, mg.restrict(P, blk, r))
+        assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+
+    check()
