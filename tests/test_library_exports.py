@@ -67,3 +67,16 @@ def test_host_only_entry_points(lib):
     two = (ctypes.c_void_p * 2)(None, None)
     assert wm.LIB.mg_solve_many(two, 2, two, two, 1, 1, 1e-10, None, None) == wm.MG_EINVAL
     assert "distinct and non-null" in wm.mg_last_error()
+
+
+def test_header_is_plain_c_and_cpp():
+    """include/wilson_mg.h compiles as C and as C++ (a C ABI: no C++ types in the declarations)."""
+    import shutil
+    import subprocess
+    hdr = os.path.join(ROOT, "include", "wilson_mg.h")
+    for cc, lang in (("gcc", "c"), ("g++", "c++")):
+        if not shutil.which(cc):
+            pytest.skip(cc + " not available")
+        r = subprocess.run([cc, "-fsyntax-only", "-Wall", "-Wextra", "-Werror", "-x", lang, hdr],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
