@@ -191,6 +191,18 @@ int mg_destroy(mg_handle* h);
 int mg_solve(mg_handle* h, const double* b, double* x, int nrhs, int on_device, double tol,
              mg_stats* stats, void* stream);
 
+/* One multi-right-hand-side solve in which right-hand side r has its own mass
+ * masses[r] (a mass sweep as one solve).  D(m) = D(0) + m 1 (Sec. 1) and
+ * P^+ P = 1 (Eq. 2.3) make every level's operator at m_r the handle's plus
+ * (m_r - mass) on the diagonal, applied per right-hand side inside the
+ * stencil kernels; the coarsest solve takes the inverse of its own mass
+ * (built for the distinct masses on first use and kept until other masses
+ * come).  The handle's null vectors serve every mass (as for mg_retarget).
+ * b, x, nrhs (1..64), on_device, tol, stats as mg_solve.  Not with the
+ * even-odd smoother.  Errors: MG_EINVAL, and those of mg_solve. */
+int mg_solve_masses(mg_handle* h, const double* masses, const double* b, double* x, int nrhs, int on_device,
+                    double tol, mg_stats* stats, void* stream);
+
 /* mg_solve on `count` distinct handles at once (e.g. one hierarchy per mass
  * of a sweep, Sec. 5): handle i solves b[i] -> x[i] (nrhs right-hand sides
  * each, layouts and on_device as mg_solve) on its own host thread and stream

@@ -263,7 +263,8 @@ int op_apply(mg_handle* h, int l, int prec, const void* in, void* out, const voi
     d.z = z;
     d.links = a.links[prec].p;
     for (int m = 0; m < 4; ++m) d.L[m] = a.L[m];
-    d.a = a_ * (4.0 + h->mass);
+    d.a = h->mm_active ? a_ : a_ * (4.0 + h->mass);
+    d.adiag = h->mm_active ? h->mm_adiag.as<double>() : nullptr;
     d.b = -0.5 * a_;
     d.c = c_;
     d.nrhs = nrhs;
@@ -285,16 +286,17 @@ int op_apply(mg_handle* h, int l, int prec, const void* in, void* out, const voi
     Prof pf(h, MG_K_DSLASH, prec, nrhs * sb * (2 + (y && y != in) + (z && z != in && z != y)) + lb);
     LK(launch_wilson(d, h->st));
   } else if (a.cop_mma.p && prec == MG_F32 && nrhs <= 64) {
+    const double* mmshift = h->mm_active ? h->mm_shift.as<double>() : nullptr;
     // tensor cores: out = a_ A in + c_ y, then the dots in a separate deterministic pass
     const double vb = (double)a.n() * bytes_of(prec);
     {
       DevBuf scratch;
       const int var = tuned(h, tkey("coarse_mma", {prec, a.ncomp, a.V, nrhs}), coarse_mma_variants(nrhs), [&](int v) {
         if (!scratch.p && !scratch.ensure((size_t)vb * nrhs)) return -1;
-        return launch_coarse_mma(prec, a.cop_mma.p, in, scratch.p, y, a.L, a.ncomp, nrhs, a_, c_, h->st, v);
+        return launch_coarse_mma(prec, a.cop_mma.p, in, scratch.p, y, a.L, a.ncomp, nrhs, a_, c_, h->st, v, mmshift);
       });
       Prof pf(h, MG_K_COARSE, MG_BF16, (double)mma_pack_bytes(a.ncomp, a.V) + nrhs * vb * (2 + (y != nullptr)));
-      LK(launch_coarse_mma(prec, a.cop_mma.p, in, out, y, a.L, a.ncomp, nrhs, a_, c_, h->st, var));
+      LK(launch_coarse_mma(prec, a.cop_mma.p, in, out, y, a.L, a.ncomp, nrhs, a_, c_, h->st, var, mmshift));
     }
     if (z) {
       Prof pf(h, MG_K_VECTOR, prec, nrhs * vb * (z == out ? 1 : 2));
@@ -318,6 +320,7 @@ int op_apply(mg_handle* h, int l, int prec, const void* in, void* out, const voi
     k.c = c_;
     k.nrhs = nrhs;
     k.red = h->red.at(slot, 4);
+    k.shift = h->mm_active ? h->mm_shift.as<double>() : nullptr;
     const double vb = (double)a.n() * bytes_of(prec);
     Prof pf(h, MG_K_COARSE, prec,
             9.0 * a.ncomp * a.ncomp * a.V * bytes_of(prec) + nrhs * vb * (2 + (y && y != in) + (z && z != in && z != y)));
@@ -516,10 +519,13 @@ const int kCoarsestRefine = 1;
 // e = X r, then kCoarsestRefine times e += X (r - A e) with the FP64 stencil.
 int coarsest_solve(mg_handle* h, int l, int prec, const void* r, void* e, int nrhs) {
   Level& a = *h->lev[l];
+  // a mass per right-hand side: right-hand side r takes the inverse of its own mass
+  const void* inv = h->mm_active ? h->mm_inv.p : a.inv.p;
+  const int* midx = h->mm_active ? h->mm_idx.as<int>() : nullptr;
   const double mvb = (double)a.N() * a.N() * bytes_of(a.inv_prec) + 2.0 * nrhs * a.N() * 16;  // inverse once, x and y
   if (a.inv_prec == MG_F64 && prec == MG_F64) {
     Prof pf(h, MG_K_COARSEST, prec, mvb);
-    LK(launch_dense_matvec(0, 0, 0, a.N(), a.inv.p, r, e, nrhs, 0, h->st, a.mm_scratch.p));
+    LK(launch_dense_matvec(0, 0, 0, a.N(), inv, r, e, nrhs, 0, h->st, a.mm_scratch.p, midx));
     return MG_OK;
   }
   void* r64 = work(h, l, MG_F64, WV_A, nrhs);
@@ -533,12 +539,12 @@ int coarsest_solve(mg_handle* h, int l, int prec, const void* r, void* e, int nr
   }
   {
     Prof pf(h, MG_K_COARSEST, MG_F32, mvb);
-    LK(launch_dense_matvec(a.inv_prec, 0, 0, a.N(), a.inv.p, r64, e64, nrhs, 0, h->st, a.mm_scratch.p));
+    LK(launch_dense_matvec(a.inv_prec, 0, 0, a.N(), inv, r64, e64, nrhs, 0, h->st, a.mm_scratch.p, midx));
   }
   for (int it = 0; it < kCoarsestRefine; ++it) {
     RET(op_apply(h, l, MG_F64, e64, t64, r64, -1.0, 1.0, nullptr, 0, nrhs));
     Prof pf(h, MG_K_COARSEST, MG_F32, mvb + (double)nrhs * a.N() * 16);
-    LK(launch_dense_matvec(a.inv_prec, 0, 0, a.N(), a.inv.p, t64, e64, nrhs, 1, h->st, a.mm_scratch.p));
+    LK(launch_dense_matvec(a.inv_prec, 0, 0, a.N(), inv, t64, e64, nrhs, 1, h->st, a.mm_scratch.p, midx));
   }
   Prof pf(h, MG_K_VECTOR, prec);
   LK(launch_convert(MG_F64, prec, n, nrhs, e64, e, 1.0, nullptr, 0, 0.0, 0, h->st));
@@ -685,7 +691,7 @@ int vcycle(mg_handle* h, int l, const void* r, void* e, int nrhs) {
 int vcycle_graph(mg_handle* h, const void* r, void* e, int nrhs) {
   if (!h->use_graphs || h->prof_mask) return vcycle(h, 0, r, e, nrhs);  // the profiler times launches one by one
   for (auto& g : h->graphs) {
-    if (g.nrhs == nrhs && g.in == r && g.out == e && g.gen == h->buf_gen) {
+    if (g.mm == h->mm_active && g.nrhs == nrhs && g.in == r && g.out == e && g.gen == h->buf_gen) {
       CK(cudaGraphLaunch(g.exec, h->st));
       count_launches(g.nodes);
       return MG_OK;
@@ -732,7 +738,7 @@ int vcycle_graph(mg_handle* h, const void* r, void* e, int nrhs) {
       ++it;
     }
   }
-  h->graphs.push_back({nrhs, r, e, gen, nodes, exec});
+  h->graphs.push_back({h->mm_active, nrhs, r, e, gen, nodes, exec});
   return MG_OK;
 }
 
@@ -841,6 +847,57 @@ static int build_coarsest_many(mg_handle* const* hs, int count) {
 static int build_coarsest(mg_handle* h) {
   RET(build_coarsest_many(&h, 1));
   if (h->lev.size() >= 2) h->lev.back()->inv_pending = false;
+  return MG_OK;
+}
+
+// Inverses of the coarsest operator at each of `ms` (the level's FP64 stencil
+// shifted by m - mass on the diagonal, as mg_retarget does), built together
+// into h->mm_inv = [count][N][N] for solves with a mass per right-hand side.
+static int build_mass_inverses(mg_handle* h, const std::vector<double>& ms) {
+  cudaStream_t st = h->st;
+  Level& c = *h->lev.back();
+  const size_t N = c.n();
+  if (N > 8192) {
+    set_error("coarsest level has " + std::to_string(N) + " unknowns; the dense solve takes at most 8192");
+    return MG_EINVAL;
+  }
+  const int count = (int)ms.size();
+  const int prec = h->p.mixed ? MG_F32 : MG_F64;
+  const size_t eb = bytes_of(prec), cb = (size_t)9 * c.ncomp * c.ncomp * c.V * 16;
+  DevBuf shifted, aug, col, errflag, blk;
+  const size_t bb = gjb_scratch_bytes((int)N, eb, count);
+  const void* before = h->mm_inv.p;
+  if (!shifted.ensure(cb * count) || !aug.ensure(N * 2 * N * eb * count) ||
+      !col.ensure(dense_inverse_scratch_bytes(prec, (int)N) * count) || !errflag.ensure(sizeof(int) * count) ||
+      (bb && !blk.ensure(bb)) || !h->mm_inv.ensure(N * N * eb * count))
+    return MG_ENOMEM;
+  if (h->mm_inv.p != before) ++h->buf_gen;  // captured cycles hold the old address
+  std::vector<const double2*> C(count);
+  std::vector<void*> inv(count);
+  for (int z = 0; z < count; ++z) {
+    char* sz = (char*)shifted.p + cb * z;
+    CK(cudaMemcpyAsync(sz, c.cop[MG_F64].p, cb, cudaMemcpyDeviceToDevice, st));
+    if (ms[z] != h->mass) LK(launch_diag_shift((double2*)sz, c.ncomp, c.V, ms[z] - h->mass, st));
+    C[z] = (const double2*)sz;
+    inv[z] = (char*)h->mm_inv.p + N * N * eb * z;
+  }
+  CK(cudaMemsetAsync(errflag.p, 0, sizeof(int) * count, st));
+  {
+    Prof pf(h, MG_K_INVERSE, prec);
+    LK(dense_inverse_batch(prec, C.data(), c.L, c.ncomp, count, aug.p, col.p, errflag.as<int>(), inv.data(), blk.p,
+                           st));
+  }
+  count_launches(N + 3 * (size_t)count - 1);
+  std::vector<int> herr(count, 0);
+  CK(cudaMemcpyAsync(herr.data(), errflag.p, sizeof(int) * count, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int z = 0; z < count; ++z)
+    if (herr[z]) {
+      set_error("coarsest operator is singular (zero pivot) at one of the masses");
+      return MG_EINVAL;
+    }
+  c.inv_prec = prec;
+  h->mm_masses = ms;
   return MG_OK;
 }
 
@@ -2238,6 +2295,58 @@ extern "C" int mg_solve(mg_handle* h, const double* b, double* x, int nrhs, int 
 // its own stream, so that the small launches of latency-bound solves (small
 // lattices, few right-hand sides) from different handles fill the SMs
 // together.  The first failing handle's status and message are returned.
+// One multi-right-hand-side solve in which right-hand side r has its own mass
+// m_r: D(m) = D(0) + m 1 and P^+ P = 1 (Eq. 2.3), so every level's operator
+// at m_r is the handle's plus (m_r - mass) on the diagonal, applied per
+// right-hand side inside the stencil kernels; the coarsest solve takes the
+// inverse of its own mass.  The null vectors (built at the handle's mass)
+// serve every mass, as for mg_retarget.
+extern "C" int mg_solve_masses(mg_handle* h, const double* masses, const double* b, double* x, int nrhs, int on_device,
+                               double tol, mg_stats* stats, void* stream) {
+  if (!h || !masses || !b || !x || nrhs < 1 || nrhs > kMaxRhs || !(tol > 0.0)) {
+    set_error("mg_solve_masses: bad argument");
+    return MG_EINVAL;
+  }
+  if (h->p.fine_smoother != 0) {
+    set_error("mg_solve_masses: a mass per right-hand side needs the MR fine smoother (fine_smoother = 0)");
+    return MG_EINVAL;
+  }
+  std::vector<double> ms;
+  std::vector<int> idx(kMaxRhs, 0);
+  std::vector<double> adiag(kMaxRhs, 4.0 + h->mass), shift(kMaxRhs, 0.0);
+  for (int r = 0; r < nrhs; ++r) {
+    if (!isfinite(masses[r])) {
+      set_error("mg_solve_masses: mass is not finite");
+      return MG_EINVAL;
+    }
+    int z = 0;
+    while (z < (int)ms.size() && ms[z] != masses[r]) ++z;
+    if (z == (int)ms.size()) ms.push_back(masses[r]);
+    idx[r] = z;
+    adiag[r] = 4.0 + masses[r];
+    shift[r] = masses[r] - h->mass;
+  }
+  cudaStream_t keep = h->st;
+  h->st = (cudaStream_t)stream;
+  auto body = [&]() -> int {
+    if (!h->mm_adiag.ensure(kMaxRhs * sizeof(double)) || !h->mm_shift.ensure(kMaxRhs * sizeof(double)) ||
+        !h->mm_idx.ensure(kMaxRhs * sizeof(int)))
+      return MG_ENOMEM;
+    if (h->lev.size() >= 2 && ms != h->mm_masses) RET(build_mass_inverses(h, ms));
+    CK(cudaMemcpyAsync(h->mm_adiag.p, adiag.data(), kMaxRhs * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->mm_shift.p, shift.data(), kMaxRhs * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->mm_idx.p, idx.data(), kMaxRhs * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    h->mm_active = true;
+    const int rc = gcr_solve(h, b, x, nrhs, on_device, tol, stats);
+    h->mm_active = false;
+    return rc;
+  };
+  const int rc = body();
+  h->mm_active = false;
+  h->st = keep;
+  return rc;
+}
+
 extern "C" int mg_solve_many(mg_handle* const* hs, int count, const double* const* b, double* const* x, int nrhs,
                              int on_device, double tol, mg_stats* stats, void* const* streams) {
   if (!hs || !b || !x || count < 1 || nrhs < 1 || !(tol > 0.0)) {

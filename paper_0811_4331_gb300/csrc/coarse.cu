@@ -31,6 +31,7 @@ struct CoarseArgs {
   int n;  // ncomp
   double a, c;
   RedArgs red;
+  const double* shift;  // null, or a diagonal shift per right-hand side
 };
 
 // G lanes cooperate on one output (i, B): lane q of the group sums the
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(NT) coarse_apply_kernel(const CoarseArgs<S> A)
   }
   if (live && q == 0) {
     const size_t oo = voff + (size_t)i * V + B;
+    if (A.shift) acc = cfma(mk<R>((R)A.shift[rhs], (R)0), ldc<R>(A.in, oo), acc);
     cx<R> v = (R)A.a * acc;
     if (A.y) v = v + (R)A.c * ldc<R>(A.y, oo);
     stc(A.out, oo, v);
@@ -117,6 +119,7 @@ int launch_coarse_apply(const CoarseCall& k, cudaStream_t st) {
     A.a = k.a;                                               \
     A.c = k.c;                                               \
     A.red = k.red;                                           \
+    A.shift = k.shift;                                       \
     switch (G) {                                             \
       case 1: WMG_COARSE_G(S, 1); break;                     \
       case 2: WMG_COARSE_G(S, 2); break;                     \
@@ -801,13 +804,13 @@ constexpr int kMvWarps = 4;
 
 template <typename TM, typename SI, typename SO>
 __global__ void __launch_bounds__(32 * kMvWarps) dense_matvec4_kernel(int N, const TM* inv, const SI* x, SO* y,
-                                                                      int acc) {
+                                                                      int acc, const int* midx) {
   typedef typename Store<TM>::R R;
   __shared__ cx<R> part[kMvWarps];
   const int row = blockIdx.x, rhs = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c0 = (int)((long)warp * N / kMvWarps), c1 = (int)((long)(warp + 1) * N / kMvWarps);
-  const TM* rp = inv + (size_t)row * N;
+  const TM* rp = inv + (midx ? (size_t)midx[rhs] * N * N : (size_t)0) + (size_t)row * N;
   const SI* xr = x + (size_t)rhs * N;
   cx<R> a = zero<R>(), b = zero<R>();
   int j = c0 + lane;
@@ -836,18 +839,18 @@ __global__ void __launch_bounds__(32 * kMvWarps) dense_matvec4_kernel(int N, con
 }
 
 int launch_dense_matvec(int pm, int pin, int pout, int N, const void* inv, const void* x, void* y, int nrhs, int acc,
-                        cudaStream_t st, void* scratch) {
-  if (nrhs < 4 || !scratch) {
+                        cudaStream_t st, void* scratch, const int* midx) {
+  if (nrhs < 4 || !scratch || midx) {
     const dim3 g((unsigned)N, (unsigned)nrhs);
     if (pm == 0 && pin == 0 && pout == 0)
       dense_matvec4_kernel<double2, double2, double2>
-          <<<g, 32 * kMvWarps, 0, st>>>(N, (const double2*)inv, (const double2*)x, (double2*)y, acc);
+          <<<g, 32 * kMvWarps, 0, st>>>(N, (const double2*)inv, (const double2*)x, (double2*)y, acc, midx);
     else if (pm == 1 && pin == 0 && pout == 0)
       dense_matvec4_kernel<float2, double2, double2>
-          <<<g, 32 * kMvWarps, 0, st>>>(N, (const float2*)inv, (const double2*)x, (double2*)y, acc);
+          <<<g, 32 * kMvWarps, 0, st>>>(N, (const float2*)inv, (const double2*)x, (double2*)y, acc, midx);
     else if (pm == 1 && pin == 1 && pout == 1)
       dense_matvec4_kernel<float2, float2, float2>
-          <<<g, 32 * kMvWarps, 0, st>>>(N, (const float2*)inv, (const float2*)x, (float2*)y, acc);
+          <<<g, 32 * kMvWarps, 0, st>>>(N, (const float2*)inv, (const float2*)x, (float2*)y, acc, midx);
     else
       return -1;
     return launched() ? 0 : -1;

@@ -93,7 +93,7 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 
 template <typename S, int NT8>
 __global__ void coarse_mma_kernel(const uint4* Cf, const S* in, S* out, const S* y2, int L0, int L1, int L2, int L3,
-                                  int n, int npad, int R, float a, float c) {
+                                  int n, int npad, int R, float a, float c, const double* shift) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __nv_bfloat16* Ys = (__nv_bfloat16*)smem_raw;  // [9][Rpad][2 npad]
   const int L[4] = {L0, L1, L2, L3};
@@ -158,7 +158,9 @@ __global__ void coarse_mma_kernel(const uint4* Cf, const S* in, S* out, const S*
       const int r = r0 + q * 8 + 2 * tig + (k & 1);
       if (i < n && r < R) {
         const size_t o = ((size_t)r * n + i) * V + B;
-        cx<float> v = mk<float>(a * accr[q][k], a * acci[q][k]);
+        cx<float> acc = mk<float>(accr[q][k], acci[q][k]);
+        if (shift) acc = cfma(mk<float>((float)shift[r], 0.f), ldc<float>(in, o), acc);
+        cx<float> v = mk<float>(a * acc.re, a * acc.im);
         if (y2) v = v + c * ldc<float>(y2, o);
         stc(out, o, v);
       }
@@ -178,7 +180,7 @@ int coarse_mma_variants(int R) {
 }
 
 int launch_coarse_mma(int prec, const void* Cf, const void* in, void* out, const void* y2, const int L[4], int n, int R,
-                      double a, double c, cudaStream_t st, int variant) {
+                      double a, double c, cudaStream_t st, int variant, const double* shift) {
   if (prec != 1 && prec != 3) return -1;
   const int npad = (n + 15) / 16 * 16, T = npad / 16;
   const int V = L[0] * L[1] * L[2] * L[3];
@@ -198,7 +200,7 @@ int launch_coarse_mma(int prec, const void* Cf, const void* in, void* out, const
     if (sm > 48 * 1024) allow_big_smem(kern);                                                            \
     kern<<<dim3(V, splits), 32 * T, sm, st>>>((const uint4*)Cf, (const S*)in, (S*)out, (const S*)y2, L[0], L[1],    \
                                               L[2], L[3], n,                                                       \
-                                npad, R, (float)a, (float)c);                                            \
+                                npad, R, (float)a, (float)c, shift);                                     \
   }
 #define WMG_MMA_R(S)                       \
   switch (NT8) {                           \

@@ -130,6 +130,7 @@ struct mg_handle {
   std::vector<ProfMark> prof_marks;
   // CUDA graphs of the V-cycle, keyed by (nrhs, input, output, buffer generation)
   struct CycleGraph {
+    bool mm;  // captured with a mass per right-hand side
     int nrhs;
     const void* in;
     void* out;
@@ -138,6 +139,12 @@ struct mg_handle {
     cudaGraphExec_t exec;
   };
   std::vector<CycleGraph> graphs;
+  // solves with a mass per right-hand side (mg_solve_masses): per right-hand side 4 + m_r and m_r - mass
+  // (FP64, kMaxRhs each), the index of its coarsest inverse, and the inverses [count][N][N] of the
+  // distinct masses in mm_masses
+  bool mm_active = false;
+  wmg::DevBuf mm_adiag, mm_shift, mm_idx, mm_inv;
+  std::vector<double> mm_masses;
   unsigned long long buf_gen = 1;  // bumped whenever a work buffer or the reducer is reallocated
   cudaStream_t cap_st = nullptr;   // private stream used only for capture
   bool capturing = false;

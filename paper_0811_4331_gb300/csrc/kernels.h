@@ -24,6 +24,7 @@ struct DslashCall {
   int nrhs;
   RedArgs red;        // lane = right-hand side, 3 values
   int variant = -1;   // launch shape (wilson_variants), -1 = default
+  const double* adiag = nullptr;  // per right-hand side: a is a * adiag[r] (a mass per right-hand side)
 };
 int launch_wilson(const DslashCall& d, cudaStream_t st);
 // MR step fused with the previous step's update: with c = omega
@@ -168,6 +169,7 @@ struct CoarseCall {
   double a, c;
   int nrhs;
   RedArgs red;
+  const double* shift = nullptr;  // per right-hand side: out = a (A + shift[r] 1) in + c y
 };
 int launch_coarse_apply(const CoarseCall& k, cudaStream_t st);
 int coarse_blocks(int ncomp, int V);
@@ -179,7 +181,7 @@ int launch_mma_pack(const double2* C, int n, int V, void* out, cudaStream_t st);
 // variant >= 0 picks one of coarse_mma_variants(R) launch shapes (right-hand
 // sides split over CTAs); every shape gives bit-identical results.
 int launch_coarse_mma(int prec, const void* Cf, const void* in, void* out, const void* y2, const int L[4], int n, int R,
-                      double a, double c, cudaStream_t st, int variant = -1);
+                      double a, double c, cudaStream_t st, int variant = -1, const double* shift = nullptr);
 int coarse_mma_variants(int R);
 
 // Aggregation of level l (fine side) into level l+1 (coarse side).
@@ -230,9 +232,10 @@ size_t gjb_scratch_bytes(int N, size_t eb, int batch);
 // y = inv x (+ y if acc); (matrix, in, out) precisions (0,0,0), (1,0,0), (1,1,1).
 // With scratch (dense_matvec_scratch_bytes(N), tickets zeroed once) 4..64
 // right-hand sides run as one tiled product; otherwise one warp per row and
-// right-hand side.
+// right-hand side.  midx (device, optional): right-hand side r uses matrix
+// midx[r] of inv = [count][N][N] (always the row-per-warp form).
 int launch_dense_matvec(int pm, int pin, int pout, int N, const void* inv, const void* x, void* y, int nrhs,
-                        int acc, cudaStream_t st, void* scratch);
+                        int acc, cudaStream_t st, void* scratch, const int* midx = nullptr);
 size_t dense_matvec_scratch_bytes(int N);
 
 // Setup: blockwise Gram-Schmidt (err = 2 on rank loss), prolongator

@@ -38,6 +38,7 @@ struct WilsonArgs {
   double a, b, c;
   size_t vstride;  // complex elements per right-hand side (12 V)
   RedArgs red;
+  const double* adiag;  // null, or per right-hand side multiplier of a
 };
 
 // The two hops of direction MU for NR right-hand sides: each link is loaded
@@ -97,9 +98,10 @@ __global__ void __launch_bounds__(NT) wilson_kernel(const WilsonArgs<S, G, NL> A
     hop_pair<1, NR>(acc, A, in, s, c, stride);
     hop_pair<2, NR>(acc, A, in, s, c, stride);
     hop_pair<3, NR>(acc, A, in, s, c, stride);
-    const R ca = (R)A.a, cb = (R)A.b, cc = (R)A.c;
+    const R cb = (R)A.b, cc = (R)A.c;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
+      const R ca = (R)(A.adiag ? A.a * A.adiag[rhs0 + r] : A.a);
       const size_t ro = (size_t)(rhs0 + r) * A.vstride;
       S* out = A.out + ro;
       const S* inr = A.in + ro;
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(256) wilson_small_kernel(const WilsonArgs<S, G
     const S* y = A.y ? A.y + rhs * A.vstride : nullptr;
     const S* z = A.z ? A.z + rhs * A.vstride : nullptr;
     S* out = A.out + rhs * A.vstride;
-    const R ca = (R)A.a, cb = (R)A.b, cc = (R)A.c;
+    const R ca = (R)(A.adiag ? A.a * A.adiag[rhs] : A.a), cb = (R)A.b, cc = (R)A.c;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const int comp = 2 * warp + k;  // spin * 3 + colour
@@ -444,6 +446,7 @@ static int launch_mr_t(const DslashCall& d, const MrFuseArgs& F, cudaStream_t st
   A.c = 0.0;
   A.vstride = (size_t)12 * A.V;
   A.red = d.red;
+  A.adiag = nullptr;
   if constexpr (NL != 9) {
     if ((size_t)A.V * d.nrhs <= (size_t)kSmallSites) {  // the same split as the unfused stencil
       wilson_small_mr_kernel<S, G, NL><<<dim3((A.V + 31) / 32, d.nrhs), 256, 0, st>>>(A, F);
@@ -493,6 +496,7 @@ static int launch_t(const DslashCall& d, cudaStream_t st) {
   A.c = d.c;
   A.vstride = (size_t)12 * A.V;
   A.red = d.red;
+  A.adiag = d.adiag;
   if constexpr (NL == 9) {
     return launch_nt<S, G, NL, 128, 1>(A, d.nrhs, st);
   } else {

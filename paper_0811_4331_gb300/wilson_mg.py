@@ -88,6 +88,7 @@ def _load():
         "mg_retarget": (I, [VP, D, P(VP), VP]),
         "mg_retarget_batch": (I, [VP, P(D), I, P(VP), VP]),
         "mg_solve": (I, [VP, VP, VP, I, I, D, P(mg_stats), VP]),
+        "mg_solve_masses": (I, [VP, P(D), VP, VP, I, I, D, P(mg_stats), VP]),
         "mg_solve_many": (I, [P(VP), I, P(VP), P(VP), I, I, D, P(mg_stats), P(VP)]),
         "krylov_solve": (I, [VP, I, VP, VP, I, I, D, I, P(mg_stats), VP]),
         "dslash_apply": (I, [VP, I, VP, VP, I, VP]),
@@ -129,7 +130,7 @@ EXPORTS = ["mg_last_error", "mg_default_params", "mg_setup", "mg_retarget", "mg_
            "mg_field_from_internal", "mg_level_info", "mg_get_prolongator", "mg_get_coarse_op", "mg_footprint",
            "mg_profile", "mg_profile_read", "mg_profile_bytes", "mg_launch_count", "mr_apply_noalloc", "mg_tune",
            "mg_tune_report", "krylov_solve", "mg_retarget_batch", "eo_split", "eo_merge", "dslash_eo_apply",
-           "schur_apply", "mg_solve_many"]
+           "schur_apply", "mg_solve_many", "mg_solve_masses"]
 
 (MG_K_DSLASH, MG_K_COARSE, MG_K_RESTRICT, MG_K_PROLONG, MG_K_VECTOR, MG_K_COARSEST, MG_K_SETUP, MG_K_GALERKIN,
  MG_K_INVERSE, MG_K_GRAM) = range(10)
@@ -298,6 +299,26 @@ def mg_solve_many(hs, bs, xs, tol, streams=None, raise_on_noconv=True):
                                (ctypes.c_void_p * count)(*bp), (ctypes.c_void_p * count)(*xp), nrhs, dev.pop(),
                                float(tol), st, sp)
     stats = [[st[i * nrhs + r].as_dict() for r in range(nrhs)] for i in range(count)]
+    if status != MG_OK and (status != MG_ENOCONV or raise_on_noconv):
+        raise MgError(status, mg_last_error(), stats)
+    return status, stats
+
+
+def mg_solve_masses(h, masses, b, x, tol, stream=None, raise_on_noconv=True):
+    """One multi-RHS solve with a mass per right-hand side (masses[r] for b[r]), in place on x.
+    Returns (status, [stats dict per rhs])."""
+    shp = b.shape
+    nrhs = 1 if len(shp) == 6 else int(shp[0])
+    if len(masses) != nrhs:
+        raise ValueError("one mass per right-hand side")
+    ms = (ctypes.c_double * nrhs)(*[float(m) for m in masses])
+    st = (mg_stats * nrhs)()
+    bp, bdev = _ptr(b)
+    xp, xdev = _ptr(x)
+    if bdev != xdev:
+        raise ValueError("b and x must both be host arrays or both device tensors")
+    status = LIB.mg_solve_masses(h.ptr, ms, bp, xp, nrhs, bdev, float(tol), st, _stream(stream))
+    stats = [s.as_dict() for s in st]
     if status != MG_OK and (status != MG_ENOCONV or raise_on_noconv):
         raise MgError(status, mg_last_error(), stats)
     return status, stats

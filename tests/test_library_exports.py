@@ -64,6 +64,8 @@ def test_host_only_entry_points(lib):
     assert wm.LIB.schur_apply(None, 0, None, None, 1, None) == wm.MG_EINVAL
     assert wm.LIB.krylov_solve(None, wm.MG_KRYLOV_BICGSTAB_EO, None, None, 1, 1, 1e-10, 100, None, None) \
         == wm.MG_EINVAL
+    ms = (ctypes.c_double * 2)(0.1, 0.2)
+    assert wm.LIB.mg_solve_masses(None, ms, None, None, 2, 1, 1e-10, None, None) == wm.MG_EINVAL
     two = (ctypes.c_void_p * 2)(None, None)
     assert wm.LIB.mg_solve_many(two, 2, two, two, 1, 1, 1e-10, None, None) == wm.MG_EINVAL
     assert "distinct and non-null" in wm.mg_last_error()
