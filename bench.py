@@ -160,6 +160,15 @@ def native(args, rank, world, U, b):
         p = params(wm, mixed, smoother)
         p.defer_coarsest = 1  # the four coarsest inverses are built together by the batched retarget
         base = wm.mg_setup(U if host else Ud, DIMS, masses[-1], p, stream=stream)
+        if args.sweep == "masses" and smoother == 0:  # one solve, a mass per right-hand side
+            B4 = np.stack([b] * len(masses)) if host else torch.stack([bd] * len(masses))
+            X4 = np.zeros_like(B4) if host else torch.zeros_like(B4)
+            _, sts = wm.mg_solve_masses(base, masses, B4, X4, TOL, stream=stream)
+            if stats_out is not None:
+                for r, m in enumerate(masses):
+                    stats_out.append((m, sts[r], X4[r] if host else X4[r].cpu().numpy()))
+            wm.mg_destroy(base)
+            return
         hs = wm.mg_retarget_batch(base, masses, stream=stream)
         # the four solves side by side, one host thread and stream each
         if host:
@@ -745,6 +754,9 @@ def main():
     ap.add_argument("--workload", choices=["c2", "c3", "c5", "serve", "dslash"], default="c2",
                     help="c2: the mass-sweep step (default bench line); c3: 24-source batched solve; serve: stream; "
                          "dslash: the fine stencil alone (--dslash-dims, --dslash-prec)")
+    ap.add_argument("--sweep", choices=["many", "masses"], default="many",
+                    help="c2 step: the four masses as concurrent handles (mg_solve_many) or as one solve with a "
+                         "mass per right-hand side (mg_solve_masses)")
     ap.add_argument("--dslash-dims", type=int, nargs=4, default=list(BW_DIMS))
     ap.add_argument("--dslash-prec", nargs="+", choices=["f16", "bf16", "f32", "f64"], default=None)
     ap.add_argument("--c3-dm", type=float, default=0.02)
@@ -797,6 +809,9 @@ def main():
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded beta=6.0 heatbath gauge field, Gaussian source)",
                 "config": {"workload": WORKLOAD, "l2": "256 MB buffer written between timed steps",
+                           "sweep": ("the four masses as concurrent handles (retarget batch + mg_solve_many)"
+                                     if args.sweep == "many" else
+                                     "one solve with a mass per right-hand side (mg_solve_masses)"),
                            "precision": "fine smoother FP16 storage / FP32 math, Krylov FP32, FP64 reliable "
                                         "updates, Gram-Schmidt and coarsest solve"},
                 "solves_per_s": round(world * len(DMASSES) / v, 3)}

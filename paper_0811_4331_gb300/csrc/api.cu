@@ -1753,7 +1753,7 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
   const size_t bi = bytes_of(pin);
   const int restart = h->p.gcr_restart;
   RET(ensure_reducer(h, nrhs));
-  RET(ensure_coarsest(h));
+  if (!h->mm_active) RET(ensure_coarsest(h));  // a mass per right-hand side uses the inverses of its masses
   auto t0 = std::chrono::steady_clock::now();
   // FP64 x, b, r in the internal layout
   if (!h->gx64.ensure(n * nrhs * 16) || !h->gb64.ensure(n * nrhs * 16) || !h->gr64.ensure(n * nrhs * 16) ||
