@@ -328,11 +328,16 @@ int mg_get_coarse_op(mg_handle* h, int level, double* out);
  * slot) from buffers the handle allocates on demand; this entry point takes
  * it from one fixed array of 16 MiB compiled into the library, which every
  * GPU that loads the library holds until the process exits.  The paper has
- * no counterpart; it is a deployment variant of the Sec. 3 smoother.
- *   - The level's scratch (one vector of the level in `prec`, plus
- *     3 doubles per thread block of the operator kernel, plus 512 bytes)
- *     must fit in 16 MiB, else MG_EINVAL and a message naming the sizes
- *     (an FP64 level-0 vector alone is 192 bytes per site).
+ * no counterpart.
+ *   - The level's scratch (one vector of the level in `prec`, plus the
+ *     reduction partials: 3 doubles per thread block of the operator kernel,
+ *     or 4 per block of the separate dot pass where a coarse level in FP32
+ *     runs on the tensor-core stencil, plus 512 bytes) must fit in 16 MiB,
+ *     else MG_EINVAL and a message naming the sizes (an FP64 level-0 vector
+ *     alone is 192 bytes per site).
+ *   - It runs the operator kernels mr_apply runs for the same handle, level
+ *     and precision (the tensor-core stencil on such a coarse level), in
+ *     their default launch shapes; every shape gives the same bits.
  *   - The first call on a device looks up the array's device address once
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
@@ -402,6 +407,12 @@ int mg_tune_report(char* buf, int cap);
 /* Number of kernels this library has launched since it was loaded, over
  * all handles and threads (a monotonic counter). */
 unsigned long long mg_launch_count(void);
+
+/* Number of device allocations (cudaMalloc calls that succeeded) this library
+ * has made since it was loaded, over all handles and threads (a monotonic
+ * counter; frees do not lower it).  Lets a caller check that a call allocated
+ * nothing. */
+unsigned long long mg_alloc_count(void);
 
 /* Device bytes that mg_setup + mg_solve(nrhs) need for these sizes. */
 size_t mg_footprint(const int dims[4], const mg_params* p, int nrhs);

@@ -1651,6 +1651,8 @@ int mg_get_coarse_op(mg_handle* h, int level, double* out) {
 
 unsigned long long mg_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
+unsigned long long mg_alloc_count(void) { return wmg::g_dev_allocs.load(std::memory_order_relaxed); }
+
 int mg_tune(int mode) {
   if (mode < 0 || mode > 4) return -1;
   std::lock_guard<std::mutex> lk(g_tune_mu);

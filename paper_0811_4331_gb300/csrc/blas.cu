@@ -2,10 +2,12 @@
 // Gram-Schmidt and updates (Sec. 5), precision conversion, layout transposes
 // and the counter-based start vectors of the null-vector setup (Sec. 2).
 //
-// All reductions are deterministic (fixed grid, last-block finish, see
-// grid_reduce) and accumulate in FP64 per thread.  Grids are capped at
-// 8 blocks per SM (1216 on 152 SMs) with grid-stride loops, so every vector
-// kernel is one coalesced streaming pass over its operands.
+// All reductions are deterministic (a grid fixed by the vector length and the
+// device's SM count, last-block finish, see grid_reduce).  The FP64 kernels
+// accumulate in FP64; the FP32 and 16-bit kernels accumulate per thread and
+// within a block in FP32 and sum the per-block partials in FP64.  Grids are
+// capped at 8 blocks per SM (at most kMaxVecBlocks) with grid-stride loops, so
+// every vector kernel is one coalesced streaming pass over its operands.
 #include <math.h>
 
 #include "common.cuh"
@@ -15,7 +17,8 @@ namespace wmg {
 
 int vec_blocks(size_t n) {
   size_t b = (n + kVecThreads - 1) / kVecThreads;
-  if (b > (size_t)kMaxVecBlocks) b = kMaxVecBlocks;
+  const size_t cap = (size_t)8 * sm_count() < (size_t)kMaxVecBlocks ? (size_t)8 * sm_count() : (size_t)kMaxVecBlocks;
+  if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (int)b;
 }
@@ -25,7 +28,8 @@ static inline bool launched() { return cudaGetLastError() == cudaSuccess; }
 // Blocks of the dot kernels: at least 8 elements per thread, at most one block per SM.
 int red_blocks(size_t n) {
   size_t b = (n + 8 * kVecThreads - 1) / (8 * kVecThreads);
-  if (b > 152) b = 152;
+  const size_t cap = (size_t)sm_count() < (size_t)kMaxVecBlocks ? (size_t)sm_count() : (size_t)kMaxVecBlocks;
+  if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
 }
 

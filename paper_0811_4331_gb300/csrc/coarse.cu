@@ -857,7 +857,7 @@ int launch_dense_matvec(int pm, int pin, int pout, int N, const void* inv, const
   }
   if (scratch && nrhs >= 4 && nrhs <= 64) {
     const int tiles = (N + kMmRows - 1) / kMmRows;
-    int KS = (2 * 152 + tiles - 1) / tiles;  // about two CTAs per SM
+    int KS = (2 * sm_count() + tiles - 1) / tiles;  // about two CTAs per SM
     KS = KS < 1 ? 1 : (KS > 8 ? 8 : KS);
     int kper = (N + KS - 1) / KS;
     kper = (kper + kMmK - 1) / kMmK * kMmK;

@@ -26,6 +26,20 @@ inline int smem_optin_bytes() {
   }();
   return v;
 }
+// Streaming multiprocessors of the current device (queried once; 152 on GB300).
+inline int sm_count() {
+  static const int v = [] {
+    int d = 0, x = 152;
+    if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&x, cudaDevAttrMultiProcessorCount, d) != cudaSuccess ||
+        x < 1) {
+      cudaGetLastError();
+      x = 152;
+    }
+    return x;
+  }();
+  return v;
+}
+
 template <typename K>
 inline void allow_big_smem(K kern) {
   cudaFuncAttributes fa;

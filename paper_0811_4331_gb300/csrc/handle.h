@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <memory>
 #include <string>
 #include <vector>
@@ -12,6 +13,9 @@
 namespace wmg {
 
 void set_error(const std::string& msg);
+
+// Device allocations the library has made since it was loaded (successful cudaMalloc calls).
+inline std::atomic<unsigned long long> g_dev_allocs{0};
 
 // Owning device buffer.  The library allocates with cudaMalloc and frees on
 // destruction; nothing is shared between handles.
@@ -37,6 +41,7 @@ struct DevBuf {
       p = nullptr;
       return false;
     }
+    g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
     bytes = n;
     return true;
   }

@@ -73,7 +73,7 @@ int launch_eo_merge(int prec, const void* even, const void* odd, void* full, con
 int vec_blocks(size_t n);
 int red_blocks(size_t n);
 const int kVecThreads = 256;
-const int kMaxVecBlocks = 1216;  // 152 SMs x 8
+const int kMaxVecBlocks = 1216;  // upper bound of vector-kernel grids (8 per SM, 152 SMs on GB300); sizes partial buffers
 
 // x_out = (x_in or 0) + alpha u;  r_out = r_in - alpha p, with per-rhs
 // alpha = omega * (d[0] + i d[1]) / d[2] read from dots[rhs * dstride]

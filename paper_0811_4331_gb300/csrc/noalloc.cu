@@ -56,12 +56,19 @@ inline size_t elem_bytes(int prec) { return prec == MG_F64 ? 16 : (prec == MG_F3
 
 using namespace wmg;
 
-// out = a_ A_l in + c_ y, optional dots into `red` (same kernels as mr_apply).
+// A coarse level in FP32 with the tensor-core stencil runs on it, as in mr_apply.
+static bool uses_mma(const Level& a, int l, int prec) { return l > 0 && a.cop_mma.p && prec == MG_F32; }
+
+// out = a_ A_l in + c_ y, optional dots into `red` (the kernels mr_apply runs).
 static int apply_level(mg_handle* h, int l, int prec, const void* in, void* out, const void* y, double a_,
                        double c_, const void* z, const RedArgs& red, cudaStream_t st) {
   Level& a = *h->lev[l];
   int rc;
-  if (l == 0) {
+  if (uses_mma(a, l, prec)) {
+    // tensor cores: out = a_ A in + c_ y, then the dots in a separate deterministic pass
+    rc = launch_coarse_mma(prec, a.cop_mma.p, in, out, y, a.L, a.ncomp, 1, a_, c_, st);
+    if (rc == 0 && z) rc = launch_dot(prec, a.n(), 1, out, z, red, st);
+  } else if (l == 0) {
     DslashCall d;
     d.prec = prec;
     d.in = in;
@@ -102,16 +109,18 @@ extern "C" int mr_apply_noalloc(mg_handle* h, int level, int prec, const void* b
     return MG_EINVAL;
   }
   Level& a = *h->lev[level];
-  if ((level == 0 && !a.links[prec].p) || (level > 0 && !a.cop[prec].p)) {
+  const bool mma = uses_mma(a, level, prec);
+  if ((level == 0 && !a.links[prec].p) || (level > 0 && !mma && !a.cop[prec].p)) {
     set_error("mr_apply_noalloc: operator not stored in this precision");
     return MG_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
   // carve the fixed scratch: p | partial sums | tickets | result slot
   const size_t n = a.n();
-  const size_t blocks = level == 0 ? (size_t)wilson_blocks(a.V) : (size_t)coarse_blocks(a.ncomp, a.V);
+  const size_t partials = mma ? (size_t)red_blocks(n) * 4
+                               : (level == 0 ? (size_t)wilson_blocks(a.V) : (size_t)coarse_blocks(a.ncomp, a.V)) * 3;
   const size_t off_part = align256(n * elem_bytes(prec));
-  const size_t off_tick = off_part + align256(blocks * 3 * sizeof(double));
+  const size_t off_tick = off_part + align256(partials * sizeof(double));
   const size_t off_slot = off_tick + 256;
   const size_t need = off_slot + 256;
   if (need > kNoAllocScratchBytes) {
@@ -135,7 +144,7 @@ extern "C" int mr_apply_noalloc(mg_handle* h, int level, int prec, const void* b
     set_error(std::string("mr_apply_noalloc: ") + cudaGetErrorString(e));
     return MG_ECUDA;
   }
-  // r = b - A x, then `steps` under-relaxed MR steps (Sec. 3)
+  // r = b - A x, then `steps` under-relaxed MR steps
   rc = apply_level(h, level, prec, x, r, b, -1.0, 1.0, nullptr, red, st);
   for (int k = 0; k < steps && rc == MG_OK; ++k) {
     rc = apply_level(h, level, prec, r, p, nullptr, 1.0, 0.0, r, red, st);
