@@ -95,6 +95,7 @@ Agg agg_of(const Level& a) {
   }
   g.V = a.V;
   g.ncomp = a.ncomp;
+  g.q = a.q;
   g.nhalf = a.nhalf;
   g.nv = a.nv;
   g.bsites = a.bsites;
@@ -130,7 +131,7 @@ int ensure_reducer(mg_handle* h, int nrhs) {
   size_t need = (size_t)kMaxVecBlocks * 16 * ((kMaxBasis / 8) * (size_t)nrhs + 1);
   for (auto& lp : h->lev) {
     const Level& a = *lp;
-    size_t b = a.ncomp == 12 ? (size_t)wilson_blocks(a.V) : (size_t)coarse_blocks(a.ncomp, a.V);
+    size_t b = a.q == 4 ? (size_t)wilson_blocks(a.V) : (size_t)coarse_blocks(a.ncomp, a.V);  // level 0: the stencil
     need = std::max(need, b * 3 * (size_t)nrhs);
   }
   if (need <= h->red.max_partials && h->red.nslots) return MG_OK;
@@ -426,7 +427,7 @@ int ensure_eo_links(mg_handle* h, int prec) {
   const size_t NL = prec == MG_F64 ? 9 : 6, eb = bytes_of(prec);
   if (!f.links_eo[prec].ensure((size_t)4 * NL * f.V * eb)) return MG_ENOMEM;
   char* base = (char*)f.links_eo[prec].p;
-  LK(launch_eo_split(eb, f.links[prec].p, base, base + (size_t)(f.V / 2) * eb, f.L, 4 * NL, (size_t)f.V, h->st));
+  LK(launch_eo_links(prec, f.links[prec].p, base, f.L, h->st));
   return MG_OK;
 }
 
@@ -488,7 +489,7 @@ int eo_smooth(mg_handle* h, int prec, const void* r, void* e, bool add, void* re
   const size_t sl = slot_level(0);
   {
     Prof pf(h, MG_K_VECTOR, prec, 2.0 * hb * 2);
-    LK(launch_eo_split(bytes_of(prec), r, re, ro, f.L, (size_t)12 * nrhs, (size_t)(f.V / 2), h->st));
+    LK(launch_eo_split(4 * bytes_of(prec), r, re, ro, f.L, (size_t)3 * nrhs, (size_t)(f.V / 2), h->st));
   }
   RET(eo_apply(h, prec, 0, re, ro, nullptr, rs, 1.0, 1.0 / (2.0 * M), 0.0, nullptr, 0, nrhs));
   if (steps == 0) CK(cudaMemsetAsync(ee, 0, hb, h->st));
@@ -498,8 +499,8 @@ int eo_smooth(mg_handle* h, int prec, const void* r, void* e, bool add, void* re
   }
   RET(eo_apply(h, prec, 1, ro, ee, nullptr, eo, 1.0 / M, 1.0 / (2.0 * M), 0.0, nullptr, 0, nrhs));
   Prof pf(h, MG_K_VECTOR, prec, 2.0 * hb * (add ? 4 : 3));
-  LK(launch_eo_merge(prec, ee, eo, e, f.L, (size_t)12 * nrhs, add ? 1 : 0, h->st));
-  LK(launch_eo_merge(prec, rs, nullptr, res, f.L, (size_t)12 * nrhs, 0, h->st));
+  LK(launch_eo_merge(prec, ee, eo, e, f.L, (size_t)3 * nrhs, add ? 1 : 0, h->st));
+  LK(launch_eo_merge(prec, rs, nullptr, res, f.L, (size_t)3 * nrhs, 0, h->st));
   return MG_OK;
 }
 
@@ -960,10 +961,10 @@ static int make_starts(mg_handle* h, int l, const double* start, DevBuf& S) {
     DevBuf ext;
     if (!ext.ensure(vbf * a.nv)) return MG_ENOMEM;
     CK(cudaMemcpyAsync(ext.p, start, vbf * a.nv, cudaMemcpyHostToDevice, st));
-    LK(launch_ext_to_int(MG_F64, nfull, a.V, a.nv, ext.p, full.p, st));
+    LK(launch_ext_to_int(MG_F64, nfull, a.q, a.V, a.nv, ext.p, full.p, st));
   } else {
     Prof pf(h, MG_K_SETUP, MG_F64);
-    LK(launch_gaussian_starts(h->p.seed + (uint64_t)l, a.nv, nfull, a.V, full.p, st));
+    LK(launch_gaussian_starts(h->p.seed + (uint64_t)l, a.nv, nfull, a.q, a.V, full.p, st));
   }
   if (nfull == a.ncomp) {
     CK(cudaMemcpyAsync(S.p, full.p, vb * a.nv, cudaMemcpyDeviceToDevice, st));
@@ -1203,6 +1204,7 @@ static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, co
   for (int m = 0; m < 4; ++m) f.L[m] = h->dims[m];
   f.V = f.L[0] * f.L[1] * f.L[2] * f.L[3];
   f.ncomp = 12;
+  f.q = 4;
   {
     DevBuf ext;
     const double* gdev = gauge;
@@ -1322,6 +1324,7 @@ static int retarget_impl(const mg_handle* src, mg_handle* h, bool coarsest = tru
     }
     b.V = a.V;
     b.ncomp = a.ncomp;
+    b.q = a.q;
     b.nv = a.nv;
     b.bsites = a.bsites;
     b.nhalf = a.nhalf;
@@ -1455,7 +1458,7 @@ int eo_split(mg_handle* h, int prec, const void* full, void* even, void* odd, in
   RET(eo_args_ok(h, prec, nrhs, "eo_split"));
   if (!full || !even || !odd) return MG_EINVAL;
   const Level& f = *h->lev[0];
-  LK(launch_eo_split(bytes_of(prec), full, even, odd, f.L, (size_t)12 * nrhs, (size_t)(f.V / 2),
+  LK(launch_eo_split(4 * bytes_of(prec), full, even, odd, f.L, (size_t)3 * nrhs, (size_t)(f.V / 2),
                      (cudaStream_t)stream));
   return MG_OK;
 }
@@ -1464,7 +1467,7 @@ int eo_merge(mg_handle* h, int prec, const void* even, const void* odd, void* fu
   RET(eo_args_ok(h, prec, nrhs, "eo_merge"));
   if (!full) return MG_EINVAL;
   const Level& f = *h->lev[0];
-  LK(launch_eo_merge(prec, even, odd, full, f.L, (size_t)12 * nrhs, 0, (cudaStream_t)stream));
+  LK(launch_eo_merge(prec, even, odd, full, f.L, (size_t)3 * nrhs, 0, (cudaStream_t)stream));
   return MG_OK;
 }
 
@@ -1576,7 +1579,7 @@ int mg_field_to_internal(mg_handle* h, int level, int prec, const double* ext, i
     CK(cudaMemcpyAsync(tmp.p, ext, a.n() * nrhs * 16, cudaMemcpyHostToDevice, st));
     src = tmp.p;
   }
-  LK(launch_ext_to_int(prec, a.ncomp, a.V, nrhs, src, internal, st));
+  LK(launch_ext_to_int(prec, a.ncomp, a.q, a.V, nrhs, src, internal, st));
   if (!on_device) CK(cudaStreamSynchronize(st));
   return MG_OK;
 }
@@ -1590,12 +1593,12 @@ int mg_field_from_internal(mg_handle* h, int level, int prec, const void* intern
   Level& a = *h->lev[level];
   cudaStream_t st = (cudaStream_t)stream;
   if (on_device) {
-    LK(launch_int_to_ext(prec, a.ncomp, a.V, nrhs, internal, ext, st));
+    LK(launch_int_to_ext(prec, a.ncomp, a.q, a.V, nrhs, internal, ext, st));
     return MG_OK;
   }
   DevBuf tmp;
   if (!tmp.ensure(a.n() * nrhs * 16)) return MG_ENOMEM;
-  LK(launch_int_to_ext(prec, a.ncomp, a.V, nrhs, internal, tmp.p, st));
+  LK(launch_int_to_ext(prec, a.ncomp, a.q, a.V, nrhs, internal, tmp.p, st));
   CK(cudaMemcpyAsync(ext, tmp.p, a.n() * nrhs * 16, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return MG_OK;
@@ -1622,7 +1625,7 @@ int mg_get_prolongator(mg_handle* h, int level, double* out) {
     LK(launch_p_column(MG_F64, g, a.P[MG_F64].p, k, 1, tot.p, st));
     LK(launch_p_column(MG_F64, g, a.P[MG_F64].p, a.nv + k, 1, f.p, st));
     LK(launch_convert(MG_F64, MG_F64, a.n(), 1, f.p, tot.p, 1.0, nullptr, 0, 0.0, 1, st));
-    LK(launch_int_to_ext(MG_F64, a.ncomp, a.V, 1, tot.p, ext.p, st));
+    LK(launch_int_to_ext(MG_F64, a.ncomp, a.q, a.V, 1, tot.p, ext.p, st));
     CK(cudaMemcpyAsync(out + (size_t)k * a.n() * 2, ext.p, a.n() * 16, cudaMemcpyDeviceToHost, st));
   }
   CK(cudaStreamSynchronize(st));
@@ -1772,8 +1775,8 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
       bsrc = stage.p;
       xsrc = (char*)stage.p + n * nrhs * 16;
     }
-    LK(launch_ext_to_int(MG_F64, 12, f.V, nrhs, bsrc, h->gb64.p, st));
-    LK(launch_ext_to_int(MG_F64, 12, f.V, nrhs, xsrc, h->gx64.p, st));
+    LK(launch_ext_to_int(MG_F64, 12, 4, f.V, nrhs, bsrc, h->gb64.p, st));
+    LK(launch_ext_to_int(MG_F64, 12, 4, f.V, nrhs, xsrc, h->gx64.p, st));
     CK(cudaStreamSynchronize(st));
   }
   // Krylov buffers in precision pin: basis W, Z [restart][nrhs][n], x, r
@@ -1927,7 +1930,7 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
       if (!stage.ensure(n * nrhs * 16)) return MG_ENOMEM;
       dst = stage.p;
     }
-    LK(launch_int_to_ext(MG_F64, 12, f.V, nrhs, h->gx64.p, dst, st));
+    LK(launch_int_to_ext(MG_F64, 12, 4, f.V, nrhs, h->gx64.p, dst, st));
     if (!on_device) CK(cudaMemcpyAsync(x_ext, stage.p, n * nrhs * 16, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
   }
@@ -1952,24 +1955,20 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
 namespace {
 
 // A level-0 FP64 system for the Krylov baselines: the full operator D on
-// [12][V] fields, or the even-odd Schur complement S on [12][V/2] halves.
-// Both are gamma5-Hermitian (Sec. 1), and in both layouts components 6..11
-// (spins 2 and 3, chirality -) are the second half of the vector.
+// level-0 fields, or the even-odd Schur complement S on half fields (both in
+// the chunked layout; n = 12 x sites).  Both are gamma5-Hermitian (Sec. 1).
 struct KSys {
   size_t n;                                                     // complex elements of a vector
   std::function<int(const void* in, void* out)> apply;          // out = A in
   std::function<int(const void* x, void* r, const void* b)> resid;  // r = b - A x
 };
 
-// out = A^+ in = gamma5 A gamma5 in: the chirality - half changes sign before and after A.
+// out = A^+ in = gamma5 A gamma5 in: the chirality - components change sign before and after A.
 int apply_dag(mg_handle* h, const KSys& sys, const void* in, void* out, void* tmp) {
-  const size_t half = sys.n / 2;
-  CK(cudaMemcpyAsync(tmp, in, half * 16, cudaMemcpyDeviceToDevice, h->st));
-  LK(launch_convert(MG_F64, MG_F64, half, 1, (const char*)in + half * 16, (char*)tmp + half * 16, -1.0, nullptr, 0,
-                    0.0, 0, h->st));
+  const size_t sites = sys.n / 12;
+  LK(launch_gamma5(sites, 1, in, tmp, h->st));
   RET(sys.apply(tmp, out));
-  LK(launch_convert(MG_F64, MG_F64, half, 1, (char*)out + half * 16, (char*)out + half * 16, -1.0, nullptr, 0, 0.0,
-                    0, h->st));
+  LK(launch_gamma5(sites, 1, out, out, h->st));
   return MG_OK;
 }
 
@@ -2163,8 +2162,8 @@ int krylov_eo_one(mg_handle* h, int method, double2* b, double2* x, double tol, 
   sys.resid = [&](const void* xx, void* r, const void* bb) {
     return schur_op(h, MG_F64, xx, r, t, bb, nullptr, 0, 1);
   };
-  LK(launch_eo_split(16, b, be, bo, f.L, 12, nh / 12, h->st));
-  LK(launch_eo_split(16, x, xe, xo, f.L, 12, nh / 12, h->st));
+  LK(launch_eo_split(64, b, be, bo, f.L, 3, nh / 12, h->st));
+  LK(launch_eo_split(64, x, xe, xo, f.L, 3, nh / 12, h->st));
   RET(eo_apply(h, MG_F64, 0, be, bo, nullptr, bh, 1.0, 1.0 / (2.0 * M), 0.0, nullptr, 0, 1));
   double b2 = 0.0, bh2 = 0.0;
   RET(dot3(h, n, b, b, nullptr, &b2, nullptr));
@@ -2185,7 +2184,7 @@ int krylov_eo_one(mg_handle* h, int method, double2* b, double2* x, double tol, 
     iters += s1.iters;
     mv += s1.fine_dslash;
     RET(eo_apply(h, MG_F64, 1, bo, xe, nullptr, xo, 1.0 / M, 1.0 / (2.0 * M), 0.0, nullptr, 0, 1));
-    LK(launch_eo_merge(MG_F64, xe, xo, x, f.L, 12, 0, h->st));
+    LK(launch_eo_merge(MG_F64, xe, xo, x, f.L, 3, 0, h->st));
     RET(op_apply(h, 0, MG_F64, x, rf, b, -1.0, 1.0, nullptr, 0, 1));  // the full true residual
     ++mv;
     double r2 = 0.0;
@@ -2257,8 +2256,8 @@ extern "C" int krylov_solve(mg_handle* h, int method, const double* b_ext, doubl
     }
     double2* B = bx.as<double2>();
     double2* X = B + n * nrhs;
-    LK(launch_ext_to_int(MG_F64, 12, f.V, nrhs, bs, B, h->st));
-    LK(launch_ext_to_int(MG_F64, 12, f.V, nrhs, xs, X, h->st));
+    LK(launch_ext_to_int(MG_F64, 12, 4, f.V, nrhs, bs, B, h->st));
+    LK(launch_ext_to_int(MG_F64, 12, 4, f.V, nrhs, xs, X, h->st));
     int worst = MG_OK;
     for (int r = 0; r < nrhs; ++r) {
       auto t0 = std::chrono::steady_clock::now();
@@ -2270,7 +2269,7 @@ extern "C" int krylov_solve(mg_handle* h, int method, const double* b_ext, doubl
       if (stats) stats[r].solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     void* dst = on_device ? (void*)x_ext : stage.p;
-    LK(launch_int_to_ext(MG_F64, 12, f.V, nrhs, X, dst, h->st));
+    LK(launch_int_to_ext(MG_F64, 12, 4, f.V, nrhs, X, dst, h->st));
     if (!on_device) CK(cudaMemcpyAsync(x_ext, stage.p, vb * nrhs, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     return worst;

@@ -672,22 +672,9 @@ int launch_convert(int pin, int pout, size_t n, int nrhs, const void* in, void* 
 }
 
 // ------------------------------------------------------------------ layouts
+// External [nrhs][V][ncomp] FP64 <-> internal [nrhs] x (field of chunk q).
 template <typename S>
-__global__ void ext_to_int_kernel(int ncomp, int V, int nrhs, const double2* ext, S* out) {
-  const size_t tot = (size_t)nrhs * ncomp * V;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
-    // i indexes the internal layout [r][c][s]
-    const int s = (int)(i % V);
-    const size_t rc = i / V;
-    const int c = (int)(rc % ncomp);
-    const size_t r = rc / ncomp;
-    const double2 v = ext[(r * V + s) * ncomp + c];
-    stc(out, i, mk<double>(v.x, v.y));
-  }
-}
-
-template <typename S>
-__global__ void int_to_ext_kernel(int ncomp, int V, int nrhs, const S* in, double2* ext) {
+__global__ void ext_to_int_kernel(int ncomp, int q, int V, int nrhs, const double2* ext, S* out) {
   const size_t tot = (size_t)nrhs * ncomp * V;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
     // i indexes the external layout [r][s][c]
@@ -695,7 +682,21 @@ __global__ void int_to_ext_kernel(int ncomp, int V, int nrhs, const S* in, doubl
     const size_t rs = i / ncomp;
     const int s = (int)(rs % V);
     const size_t r = rs / V;
-    const cx<double> v = ldc<double>(in, (r * ncomp + c) * V + s);
+    const double2 v = ext[i];
+    stc(out, r * ncomp * V + fidx_q(c, s, V, q), mk<double>(v.x, v.y));
+  }
+}
+
+template <typename S>
+__global__ void int_to_ext_kernel(int ncomp, int q, int V, int nrhs, const S* in, double2* ext) {
+  const size_t tot = (size_t)nrhs * ncomp * V;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
+    // i indexes the external layout [r][s][c]
+    const int c = (int)(i % ncomp);
+    const size_t rs = i / ncomp;
+    const int s = (int)(rs % V);
+    const size_t r = rs / V;
+    const cx<double> v = ldc<double>(in, r * ncomp * V + fidx_q(c, s, V, q));
     ext[i] = make_double2(v.re, v.im);
   }
 }
@@ -706,31 +707,52 @@ static unsigned grid_for(size_t tot) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-int launch_ext_to_int(int prec, int ncomp, int V, int nrhs, const void* ext, void* internal, cudaStream_t st) {
+int launch_ext_to_int(int prec, int ncomp, int q, int V, int nrhs, const void* ext, void* internal, cudaStream_t st) {
   const unsigned g = grid_for((size_t)nrhs * ncomp * V);
   const double2* e = (const double2*)ext;
   switch (prec) {
-    case 0: ext_to_int_kernel<double2><<<g, 256, 0, st>>>(ncomp, V, nrhs, e, (double2*)internal); break;
-    case 1: ext_to_int_kernel<float2><<<g, 256, 0, st>>>(ncomp, V, nrhs, e, (float2*)internal); break;
-    case 2: ext_to_int_kernel<__half2><<<g, 256, 0, st>>>(ncomp, V, nrhs, e, (__half2*)internal); break;
-    case 3: ext_to_int_kernel<__nv_bfloat162><<<g, 256, 0, st>>>(ncomp, V, nrhs, e, (__nv_bfloat162*)internal); break;
+    case 0: ext_to_int_kernel<double2><<<g, 256, 0, st>>>(ncomp, q, V, nrhs, e, (double2*)internal); break;
+    case 1: ext_to_int_kernel<float2><<<g, 256, 0, st>>>(ncomp, q, V, nrhs, e, (float2*)internal); break;
+    case 2: ext_to_int_kernel<__half2><<<g, 256, 0, st>>>(ncomp, q, V, nrhs, e, (__half2*)internal); break;
+    case 3: ext_to_int_kernel<__nv_bfloat162><<<g, 256, 0, st>>>(ncomp, q, V, nrhs, e, (__nv_bfloat162*)internal); break;
     default: return -1;
   }
   return launched() ? 0 : -1;
 }
 
-int launch_int_to_ext(int prec, int ncomp, int V, int nrhs, const void* internal, void* ext, cudaStream_t st) {
+int launch_int_to_ext(int prec, int ncomp, int q, int V, int nrhs, const void* internal, void* ext, cudaStream_t st) {
   const unsigned g = grid_for((size_t)nrhs * ncomp * V);
   double2* e = (double2*)ext;
   switch (prec) {
-    case 0: int_to_ext_kernel<double2><<<g, 256, 0, st>>>(ncomp, V, nrhs, (const double2*)internal, e); break;
-    case 1: int_to_ext_kernel<float2><<<g, 256, 0, st>>>(ncomp, V, nrhs, (const float2*)internal, e); break;
-    case 2: int_to_ext_kernel<__half2><<<g, 256, 0, st>>>(ncomp, V, nrhs, (const __half2*)internal, e); break;
+    case 0: int_to_ext_kernel<double2><<<g, 256, 0, st>>>(ncomp, q, V, nrhs, (const double2*)internal, e); break;
+    case 1: int_to_ext_kernel<float2><<<g, 256, 0, st>>>(ncomp, q, V, nrhs, (const float2*)internal, e); break;
+    case 2: int_to_ext_kernel<__half2><<<g, 256, 0, st>>>(ncomp, q, V, nrhs, (const __half2*)internal, e); break;
     case 3:
-      int_to_ext_kernel<__nv_bfloat162><<<g, 256, 0, st>>>(ncomp, V, nrhs, (const __nv_bfloat162*)internal, e);
+      int_to_ext_kernel<__nv_bfloat162><<<g, 256, 0, st>>>(ncomp, q, V, nrhs, (const __nv_bfloat162*)internal, e);
       break;
     default: return -1;
   }
+  return launched() ? 0 : -1;
+}
+
+// ------------------------------------------------------------------ gamma5
+// out = gamma5 in on FP64 level-0 fields of V sites (chunked layout, nrhs of
+// them): gamma5 = diag(1, 1, -1, -1) on spin in the chiral basis (Sec. 1), so
+// components c = 6..11 change sign.  in and out may be the same.
+__global__ void gamma5_kernel(size_t V, size_t tot, const double2* in, double2* out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t e = i % (12 * V);
+    const int c = (int)(e / (4 * V)) * 4 + (int)(e & 3);
+    const double2 v = in[i];
+    out[i] = c >= 6 ? make_double2(-v.x, -v.y) : v;
+  }
+}
+
+int launch_gamma5(size_t V, int nrhs, const void* in, void* out, cudaStream_t st) {
+  const size_t tot = (size_t)nrhs * 12 * V;
+  size_t b = (tot + 255) / 256;
+  if (b > 8192) b = 8192;
+  gamma5_kernel<<<(unsigned)(b < 1 ? 1 : b), 256, 0, st>>>(V, tot, (const double2*)in, (double2*)out);
   return launched() ? 0 : -1;
 }
 
@@ -742,27 +764,26 @@ __device__ __forceinline__ uint64_t splitmix64_out(uint64_t state, uint64_t m) {
   return z ^ (z >> 31);
 }
 
-__global__ void gaussian_starts_kernel(uint64_t seed, int nv, int ncomp, int V, double2* out) {
+__global__ void gaussian_starts_kernel(uint64_t seed, int nv, int ncomp, int q, int V, double2* out) {
   const size_t tot = (size_t)nv * ncomp * V;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
-    // i indexes the internal layout [k][c][s]; the stream index is k V ncomp + s ncomp + c
-    const int s = (int)(i % V);
-    const size_t kc = i / V;
-    const int c = (int)(kc % ncomp);
-    const size_t k = kc / ncomp;
-    const uint64_t e = (k * V + s) * ncomp + c;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    // e is the stream index k V ncomp + s ncomp + c of element (k, s, c)
+    const int c = (int)(e % ncomp);
+    const size_t ks = e / ncomp;
+    const int s = (int)(ks % V);
+    const size_t k = ks / V;
     const uint64_t x1 = splitmix64_out(seed, 2 * e), x2 = splitmix64_out(seed, 2 * e + 1);
     const double u1 = ((double)(x1 >> 11) + 1.0) * 0x1.0p-53;
     const double u2 = ((double)(x2 >> 11) + 1.0) * 0x1.0p-53;
     const double rad = sqrt(-2.0 * log(u1));
     double sn, cs;
     sincospi(2.0 * u2, &sn, &cs);
-    out[i] = make_double2(rad * cs, rad * sn);
+    out[k * ncomp * V + fidx_q(c, s, V, q)] = make_double2(rad * cs, rad * sn);
   }
 }
 
-int launch_gaussian_starts(uint64_t seed, int nv, int ncomp, int V, void* out, cudaStream_t st) {
-  gaussian_starts_kernel<<<grid_for((size_t)nv * ncomp * V), 256, 0, st>>>(seed, nv, ncomp, V, (double2*)out);
+int launch_gaussian_starts(uint64_t seed, int nv, int ncomp, int q, int V, void* out, cudaStream_t st) {
+  gaussian_starts_kernel<<<grid_for((size_t)nv * ncomp * V), 256, 0, st>>>(seed, nv, ncomp, q, V, (double2*)out);
   return launched() ? 0 : -1;
 }
 

@@ -157,6 +157,7 @@ __device__ __forceinline__ int agg_site(const Agg& g, int B, int s) {
 }
 
 // r_c[(chi nv + k)][B] = sum_{c, s} conj(P[B][chi][k][c][s]) r[(chi nhalf + c)][site(B, s)]
+// (fine field of chunk g.q, see fidx_q)
 // One CTA per (aggregate, group of NT/32 rows): small coarse grids still fill the GPU.
 template <typename SI, typename SP, typename SO, int NT>
 __global__ void __launch_bounds__(NT) restrict_kernel(const Agg g, const SP* P, const SI* in, SO* out) {
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(NT) restrict_kernel(const Agg g, const SP* P, 
   const SI* vin = in + (size_t)rhs * g.ncomp * g.V;
   for (int e = threadIdx.x; e < g.ncomp * bs; e += NT) {
     const int c = e / bs, s = e - c * bs;
-    sm[e] = ldc<R>(vin, (size_t)c * g.V + agg_site(g, B, s));
+    sm[e] = ldc<R>(vin, fidx_q(c, agg_site(g, B, s), g.V, g.q));
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(NT) prolong_kernel(const Agg g, const SP* P, c
     const SP* pc = P + ((size_t)B * 2 + chi) * nv * len + (size_t)cl * bs + s;
     cx<R> acc = zero<R>();
     for (int k = 0; k < nv; ++k) acc = cfma(ldc<R>(pc, (size_t)k * len), xc[chi * nv + k], acc);
-    stc(out, ((size_t)rhs * g.ncomp + c) * g.V + agg_site(g, B, s), acc);
+    stc(out, (size_t)rhs * g.ncomp * g.V + fidx_q(c, agg_site(g, B, s), g.V, g.q), acc);
   }
 }
 

@@ -235,6 +235,19 @@ __host__ __device__ __forceinline__ int neighbor(const int (&c)[4], const int (&
   return site_index(n, L);
 }
 
+// ------------------------------------------------------------------ field layouts
+// Level-0 fields (12 complex components c = spin * 3 + colour per site) are
+// stored in three chunks of four components, each chunk site-major:
+// component c of site s at complex index ((c / 4) V + s) 4 + c % 4 (per
+// right-hand side; wilson_hop.cuh gives the reason).  Coarse-level fields
+// are component-major, [ncomp][V].  The chunk q of a field is 4 or 1.
+__host__ __device__ __forceinline__ size_t fidx(int c, size_t s, size_t V) {
+  return (((size_t)(c >> 2) * V + s) << 2) + (c & 3);
+}
+__host__ __device__ __forceinline__ size_t fidx_q(int c, size_t s, size_t V, int q) {
+  return q == 4 ? fidx(c, s, V) : (size_t)c * V + s;
+}
+
 // ------------------------------------------------------------------ reductions
 // Deterministic grid reductions: every block writes NV partial doubles, then
 // the last block to finish (atomic ticket after a fence) sums the partials of

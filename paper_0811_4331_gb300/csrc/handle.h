@@ -55,6 +55,7 @@ struct Level {
   int L[4] = {0, 0, 0, 0};
   int V = 0;
   int ncomp = 0;  // 12 on level 0, 2 nv_{l-1} on level l >= 1
+  int q = 1;      // chunk of the level's fields: 4 on level 0 (chunked layout), 1 on coarse levels
   // coarsening to level l+1 (nv == 0 on the coarsest level)
   int nv = 0;
   int blk[4] = {1, 1, 1, 1};
@@ -65,8 +66,8 @@ struct Level {
   int sweeps = 0;
   int cycles = 1;
   // operator of this level, per storage precision (index = precision code)
-  DevBuf links[4];  // level 0: [4][NL][V]
-  DevBuf links_eo[4];  // level 0, even-odd kernels: [4][NL][V], sites parity-major (built on first use)
+  DevBuf links[4];  // level 0: 4 V NL complex in the link layout of wilson_hop.cuh
+  DevBuf links_eo[4];  // level 0, even-odd kernels: the same with the sites parity-major (built on first use)
   DevBuf cop[4];    // level >= 1: stencil [9][ncomp][ncomp][V]
   DevBuf cop_mma;   // level >= 1 (coarse_mma): BF16 stencil in MMA fragment order
   // prolongator to level l+1, per precision: [Vc][2][nv][nhalf][bsites]

@@ -40,10 +40,10 @@ int launch_pack_links(int prec, const void* ext, void* out, int V, cudaStream_t 
 // *worst = max over links of |U U^+ - 1|, |det U - 1| as float bits (caller zeroes it first).
 int launch_su3_check(const void* ext, int V, unsigned* worst, cudaStream_t st);
 
-// Even-odd stencil on half-lattice fields [nrhs][12][V/2] (every extent even):
-// out_p = a x_p + b H_{p,1-p} in_{1-p} + c y_p, H the hopping term of D =
-// (4 + m) - H / 2; links parity-major [4][NL][V] (launch_eo_split of the
-// packed links with rows = 4 NL, hstride = V, odd = even + V/2).
+// Even-odd stencil on half-lattice fields [nrhs][3][V/2][4] (every extent
+// even): out_p = a x_p + b H_{p,1-p} in_{1-p} + c y_p, H the hopping term of
+// D = (4 + m) - H / 2; links in the layout of wilson_hop.cuh with the sites
+// parity-major (launch_eo_links).
 struct EoCall {
   int prec;
   int parity;  // of out
@@ -60,10 +60,15 @@ struct EoCall {
 };
 int launch_wilson_eo(const EoCall& d, cudaStream_t st);
 int eo_blocks(int V);
-// full rows of V elements (elem_bytes each) -> even and odd rows of V/2 at stride hstride.
+// full rows of V elements (elem_bytes each: 4, 8, 16, 32 or 64) -> even and
+// odd rows of V/2 at stride hstride.  A chunked level-0 field is 3 nrhs rows
+// of 4-complex chunks.
 int launch_eo_split(size_t elem_bytes, const void* full, void* even, void* odd, const int L[4], size_t rows,
                     size_t hstride, cudaStream_t st);
-// full = (add ? full : 0) + merge(even, odd), rows of V / V/2 elements; a null half is zero.
+// Packed links of precision prec -> the same links with the sites parity-major.
+int launch_eo_links(int prec, const void* links, void* out, const int L[4], cudaStream_t st);
+// full = (add ? full : 0) + merge(even, odd), rows of V / V/2 four-complex
+// chunks (3 nrhs rows for a level-0 field); a null half is zero.
 int launch_eo_merge(int prec, const void* even, const void* odd, void* full, const int L[4], size_t rows, int add,
                     cudaStream_t st);
 
@@ -147,14 +152,18 @@ int launch_gcr_update(int prec, int xprec, size_t n, int nrhs, const double* dot
 int launch_convert(int pin, int pout, size_t n, int nrhs, const void* in, void* out, double s0,
                    const double* slot, int sstride, double sexp, int accumulate, cudaStream_t st);
 
-// External [nrhs][V][ncomp] FP64 complex <-> internal [nrhs][ncomp][V] of precision prec.
-int launch_ext_to_int(int prec, int ncomp, int V, int nrhs, const void* ext, void* internal, cudaStream_t st);
-int launch_int_to_ext(int prec, int ncomp, int V, int nrhs, const void* internal, void* ext, cudaStream_t st);
+// External [nrhs][V][ncomp] FP64 complex <-> internal fields of precision
+// prec and chunk q (4: level 0, 1: coarse levels; see fidx_q).
+int launch_ext_to_int(int prec, int ncomp, int q, int V, int nrhs, const void* ext, void* internal, cudaStream_t st);
+int launch_int_to_ext(int prec, int ncomp, int q, int V, int nrhs, const void* internal, void* ext, cudaStream_t st);
+
+// out = gamma5 in on FP64 level-0 fields of V sites (chunked layout; in == out allowed).
+int launch_gamma5(size_t V, int nrhs, const void* in, void* out, cudaStream_t st);
 
 // Counter-based Gaussian start vectors (SplitMix64 + Box-Muller), FP64
-// internal layout [nv][ncomp][V]; element (k, site, comp) is stream element
-// k V ncomp + site ncomp + comp of stream `seed`.
-int launch_gaussian_starts(uint64_t seed, int nv, int ncomp, int V, void* out, cudaStream_t st);
+// internal fields of chunk q, nv of them; element (k, site, comp) is stream
+// element k V ncomp + site ncomp + comp of stream `seed`.
+int launch_gaussian_starts(uint64_t seed, int nv, int ncomp, int q, int V, void* out, cudaStream_t st);
 
 // ------------------------------------------------------------------ coarse levels
 struct CoarseCall {
@@ -189,6 +198,7 @@ struct Agg {
   int L[4];
   int V;
   int ncomp;
+  int q;  // chunk of the fine-side fields (4 on level 0, 1 on coarse levels)
   int nhalf;
   int nv;
   int blk[4];

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(NT) block_gs_kernel(const Agg g, const double2
     double nrm0 = 0.0;
     for (int e = threadIdx.x; e < len; e += NT) {
       const int c = e / bs, s = e - c * bs;
-      const double2 v = cand[((size_t)k * g.ncomp + chi * nh + c) * g.V + agg_site2(g, B, s)];
+      const double2 v = cand[(size_t)k * g.ncomp * g.V + fidx_q(chi * nh + c, agg_site2(g, B, s), g.V, g.q)];
       q[e] = v;
       nrm0 += v.x * v.x + v.y * v.y;
     }
@@ -95,7 +95,7 @@ int launch_block_gs(const Agg& g, const double2* cand, double2* P, int* err, cud
   return launched() ? 0 : -1;
 }
 
-// Column j of P (j = chi' nv + k') as a level-l field [ncomp][V]: the k'-th
+// Column j of P (j = chi' nv + k') as a level-l field (chunk g.q): the k'-th
 // orthonormal vector on its chirality chi' half, zero on the other half.
 template <typename TP>
 __global__ void p_column_kernel(const Agg g, const TP* P, int j0, TP* vbase) {
@@ -105,7 +105,15 @@ __global__ void p_column_kernel(const Agg g, const TP* P, int j0, TP* vbase) {
   const int chi = j / g.nv, k = j - chi * g.nv;
   const int len = g.nhalf * g.bsites;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / g.V), site = (int)(e % g.V);
+    // element e of the field (chunk g.q): component c of site `site`
+    int c, site;
+    if (g.q == 4) {
+      c = (int)((e / ((size_t)4 * g.V)) * 4 + (e & 3));
+      site = (int)((e >> 2) % g.V);
+    } else {
+      c = (int)(e / g.V);
+      site = (int)(e % g.V);
+    }
     TP val;
     stc(&val, 0, zero<double>());
     if (c / g.nhalf == chi) {
@@ -143,7 +151,7 @@ int launch_p_column(int prec, const Agg& g, const void* P, int j0, int ncols, vo
 template <typename TV, typename TL, int NL>
 struct WilsonHopOp {
   typedef typename Store<TV>::R R;
-  const TL* U;  // links [4][NL][V]
+  const TL* U;  // links, layout of wilson_hop.cuh
   double mass;
   __device__ void apply(const Agg& g, int B, int d, const TV* v, cx<R>* h, int nt) const {
     for (int s = threadIdx.x; s < g.bsites; s += nt) {
@@ -157,7 +165,7 @@ struct WilsonHopOp {
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-          for (int a = 0; a < 3; ++a) acc[sp][a] = (R)(4.0 + mass) * ldc<R>(v, (size_t)(sp * 3 + a) * g.V + n);
+          for (int a = 0; a < 3; ++a) acc[sp][a] = (R)(4.0 + mass) * ldc<R>(v, fidx(sp * 3 + a, n, g.V));
       } else {
         int c[4];
         site_coords(n, g.L, c);

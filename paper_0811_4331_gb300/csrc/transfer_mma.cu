@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kTThreads)
       size_t base = 0;
       if (live) {
         const int c = e / g.bsites, s = e - c * g.bsites;
-        base = (size_t)(chi * g.nhalf + c) * g.V + sidx[s];
+        base = fidx_q(chi * g.nhalf + c, sidx[s], g.V, g.q);
       }
       const size_t rstride = (size_t)g.ncomp * g.V;
 #pragma unroll 4
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kTThreads)
       const int e = e0 + warp * 16 + gid + 8 * h;
       if (e >= len) continue;
       const int c = e / g.bsites, s = e - c * g.bsites;
-      const size_t o = (size_t)(chi * g.nhalf + c) * g.V + sidx[s];
+      const size_t o = fidx_q(chi * g.nhalf + c, sidx[s], g.V, g.q);
 #pragma unroll
       for (int q = 0; q < NT8; ++q)
 #pragma unroll

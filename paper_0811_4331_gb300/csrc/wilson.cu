@@ -5,21 +5,25 @@
 // differences and a second-order Wilson term (r = 1, spacing 1):
 //   (D psi)(n) = (4 + m) psi(n)
 //     - 1/2 sum_mu [(1 - g_mu) U_mu(n) psi(n+mu) + (1 + g_mu) U_mu(n-mu)^+ psi(n-mu)].
-// The kernel computes   out = a * in + b * Hop(in) + c * y
+// The kernels compute   out = a * in + b * Hop(in) + c * y
 // where Hop(in)(n) = sum_mu [(1 - g_mu) U psi(n+mu) + (1 + g_mu) U^+ psi(n-mu)],
 // so D = (a = 4 + m, b = -1/2) and the residual y - D x = (a = -(4 + m),
-// b = +1/2, c = 1).  Optionally it also reduces <out|z> and ||out||^2 per
+// b = +1/2, c = 1).  Optionally they also reduce <out|z> and ||out||^2 per
 // right-hand side (used by the MR smoother, the alpha step and GCR).
 //
-// GB300 design: one thread per site and right-hand side; spinors and links
-// are component-major ([comp][site]) so each of the 12 spinor loads and 6/9
-// link loads of a warp is one coalesced 128-512 byte transaction.  In the
-// chiral basis every (1 -+ g_mu) has rank 2 and its projection is a sum of
-// +-1 / +-i multiples of two spin components, so each hop multiplies one 3x3
-// link into two colour vectors only.  FP32/FP16/BF16 links store two rows
-// (12 reals) and rebuild the third as conj(row0 x row1) (exact for SU(3));
-// FP64 links keep all 18 reals because FP64 arithmetic, not memory, bounds
-// the FP64 stencil on this part.
+// GB300 design: one thread per site and right-hand side (or two right-hand
+// sides sharing each link).  Fields use the chunked level-0 layout of
+// wilson_hop.cuh, so a neighbour's spinor is three 16-byte loads in
+// FP16/BF16 (six in FP32) and each load of a warp is one contiguous
+// transaction.  In the chiral basis every (1 -+ g_mu) has rank 2 and its
+// projection is a sum of +-1 / +-i multiples of two spin components, so each
+// hop multiplies one 3x3 link into two colour vectors only.  FP32/FP16/BF16
+// links store two rows (12 reals) and rebuild the third as conj(row0 x row1)
+// (exact for SU(3)); FP64 links keep all 18 reals because FP64 arithmetic,
+// not memory, bounds the FP64 stencil on this part.  The FP32-arithmetic
+// stencil runs its SU(3) products as paired FP32 FMAs over the two projected
+// spin rows (one instruction per two products): with 16-bit storage the
+// stencil is bound by the FP32 pipes, not by HBM, on this part.
 #include "common.cuh"
 #include "kernels.h"
 #include "wilson_hop.cuh"
@@ -32,7 +36,7 @@ struct WilsonArgs {
   S* out;
   const S* y;  // may be null
   const S* z;  // dot partner, may be null (then no reduction)
-  const G* U;  // [4][NL][V]
+  const G* U;  // links, layout of wilson_hop.cuh
   int L[4];
   int V;
   double a, b, c;
@@ -41,21 +45,123 @@ struct WilsonArgs {
   const double* adiag;  // null, or per right-hand side multiplier of a
 };
 
+__device__ __forceinline__ void site_coords(int s, const int (&L)[4], int (&c)[4], int (&stride)[4]) {
+  int q = s;
+  c[0] = q % L[0];
+  q /= L[0];
+  c[1] = q % L[1];
+  q /= L[1];
+  c[2] = q % L[2];
+  c[3] = q / L[2];
+  stride[0] = 1;
+  stride[1] = L[0];
+  stride[2] = L[0] * L[1];
+  stride[3] = stride[2] * L[2];
+}
+
+// Hopping term of NR right-hand sides at one site: FP32 arithmetic in paired
+// form (Acc2), FP64 in the scalar form.
+template <typename R, int NR>
+struct HopAcc;
+template <int NR>
+struct HopAcc<float, NR> {
+  Acc2 a[NR];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc2_zero(a[r]);
+  }
+  template <int MU, bool FWD>
+  __device__ __forceinline__ void add(int r, const cx<float> (&psi)[12], const Link<float>& u) {
+    hop_packed<MU, FWD>(a[r], psi, u);
+  }
+  __device__ __forceinline__ cx<float> get(int r, int c) const { return acc2_get(a[r], c); }
+};
+template <int NR>
+struct HopAcc<double, NR> {
+  cx<double> a[NR][4][3];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[r][sp][k] = wmg::zero<double>();
+  }
+  template <int MU, bool FWD>
+  __device__ __forceinline__ void add(int r, const cx<double> (&psi)[12], const Link<double>& u) {
+    hop_vals<MU, FWD, double>(a[r], psi, u);
+  }
+  __device__ __forceinline__ cx<double> get(int r, int c) const { return a[r][c / 3][c % 3]; }
+};
+
 // The two hops of direction MU for NR right-hand sides: each link is loaded
 // (and its third row rebuilt) once and applied to every right-hand side.
 template <int MU, int NR, typename R, typename S, typename G, int NL>
-__device__ __forceinline__ void hop_pair(cx<R> (&acc)[NR][4][3], const WilsonArgs<S, G, NL>& A, const S* in,
-                                         int s, const int (&c)[4], const int (&stride)[4]) {
+__device__ __forceinline__ void hop_pair(HopAcc<R, NR>& acc, const WilsonArgs<S, G, NL>& A, const S* in, int s,
+                                         const int (&c)[4], const int (&stride)[4]) {
   const int L = A.L[MU], st = stride[MU];
   const int fwd = (c[MU] == L - 1) ? s - (L - 1) * st : s + st;
   const int bwd = (c[MU] == 0) ? s + (L - 1) * st : s - st;
   Link<R> u;
   load_link<R, G, NL>(u, A.U, MU, A.V, s);
 #pragma unroll
-  for (int r = 0; r < NR; ++r) hop<MU, true>(acc[r], in + r * A.vstride, A.V, fwd, u);
+  for (int r = 0; r < NR; ++r) {
+    cx<R> psi[12];
+    ld_spinor<R, S>(in + r * A.vstride, A.V, fwd, psi);
+    acc.template add<MU, true>(r, psi, u);
+  }
   load_link<R, G, NL>(u, A.U, MU, A.V, bwd);
 #pragma unroll
-  for (int r = 0; r < NR; ++r) hop<MU, false>(acc[r], in + r * A.vstride, A.V, bwd, u);
+  for (int r = 0; r < NR; ++r) {
+    cx<R> psi[12];
+    ld_spinor<R, S>(in + r * A.vstride, A.V, bwd, psi);
+    acc.template add<MU, false>(r, psi, u);
+  }
+}
+
+// Own-site part of chunk j of a site's output for one right-hand side
+// (pointers offset to it): out = ca in + cb h + cc y, with the dot partials of
+// the value as stored against z.  y or z may alias out, so they are read
+// through the L2 (coherent with this thread's earlier stores).
+template <typename R, typename S>
+__device__ __forceinline__ void finish_chunk(const cx<R> (&h)[4], int j, const S* in, S* out, const S* y, const S* z,
+                                             size_t V, int s, R ca, R cb, R cc, R (&red)[3]) {
+  const size_t i0 = (j * V + s) << 2;
+  cx<R> xin[4], yv[4], v[4];
+  ld_chunk<R, S>(in, i0, xin);
+  if (y) ld_chunk_cg<R, S>(y, i0, yv);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = cb * h[k];
+    v[k] = v[k] + ca * xin[k];
+    if (y) v[k] = v[k] + cc * yv[k];
+  }
+  st_chunk<S, R>(out, i0, v);
+  if (z) {
+    // reduce the value as stored, so dots see exactly the vector kept
+    cx<R> zz[4];
+    ld_chunk_cg<R, S>(z, i0, zz);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const cx<R> vs = as_stored<S>(v[k]);
+      const cx<R> d = cmul_conj(vs, zz[k]);
+      red[0] += d.re;
+      red[1] += d.im;
+      red[2] += norm2(vs);
+    }
+  }
+}
+
+template <typename R, typename S, typename HA>
+__device__ __forceinline__ void finish_site(const HA& acc, int r, const S* in, S* out, const S* y, const S* z, size_t V,
+                                            int s, R ca, R cb, R cc, R (&red)[3]) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    cx<R> h[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = acc.get(r, 4 * j + k);
+    finish_chunk<R, S>(h, j, in, out, y, z, V, s, ca, cb, cc, red);
+  }
 }
 
 // Thread = (site, NR consecutive right-hand sides).  Every right-hand side's
@@ -69,31 +175,14 @@ __global__ void __launch_bounds__(NT) wilson_kernel(const WilsonArgs<S, G, NL> A
   const int s = blockIdx.x * NT + threadIdx.x;
   const int rhs0 = blockIdx.y * NR;
   const S* in = A.in + rhs0 * A.vstride;
-  R acc3[NR][3];  // per-thread partial dots in the arithmetic type
+  R red[NR][3];  // per-thread partial dots in the arithmetic type
 #pragma unroll
-  for (int r = 0; r < NR; ++r) acc3[r][0] = acc3[r][1] = acc3[r][2] = (R)0;
+  for (int r = 0; r < NR; ++r) red[r][0] = red[r][1] = red[r][2] = (R)0;
   if (s < V) {
     int c[4], stride[4];
-    {
-      int q = s;
-      c[0] = q % A.L[0];
-      q /= A.L[0];
-      c[1] = q % A.L[1];
-      q /= A.L[1];
-      c[2] = q % A.L[2];
-      c[3] = q / A.L[2];
-      stride[0] = 1;
-      stride[1] = A.L[0];
-      stride[2] = A.L[0] * A.L[1];
-      stride[3] = stride[2] * A.L[2];
-    }
-    cx<R> acc[NR][4][3];
-#pragma unroll
-    for (int r = 0; r < NR; ++r)
-#pragma unroll
-      for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) acc[r][sp][a] = zero<R>();
+    site_coords(s, A.L, c, stride);
+    HopAcc<R, NR> acc;
+    acc.zero();
     hop_pair<0, NR>(acc, A, in, s, c, stride);
     hop_pair<1, NR>(acc, A, in, s, c, stride);
     hop_pair<2, NR>(acc, A, in, s, c, stride);
@@ -103,34 +192,13 @@ __global__ void __launch_bounds__(NT) wilson_kernel(const WilsonArgs<S, G, NL> A
     for (int r = 0; r < NR; ++r) {
       const R ca = (R)(A.adiag ? A.a * A.adiag[rhs0 + r] : A.a);
       const size_t ro = (size_t)(rhs0 + r) * A.vstride;
-      S* out = A.out + ro;
-      const S* inr = A.in + ro;
-      const S* y = A.y ? A.y + ro : nullptr;
-      const S* z = A.z ? A.z + ro : nullptr;
-#pragma unroll
-      for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const size_t i = (size_t)(sp * 3 + a) * V + s;
-          cx<R> v = cb * acc[r][sp][a];
-          v = v + ca * ldc<R>(inr, i);
-          if (y) v = v + cc * ldc<R>(y, i);
-          stc(out, i, v);
-          if (z) {
-            // reduce the value as stored, so dots see exactly the vector kept
-            cx<R> vs = as_stored<S>(v);
-            cx<R> zz = ldc<R>(z, i);
-            cx<R> d = cmul_conj(vs, zz);
-            acc3[r][0] += d.re;
-            acc3[r][1] += d.im;
-            acc3[r][2] += norm2(vs);
-          }
-        }
+      finish_site<R, S>(acc, r, A.in + ro, A.out + ro, A.y ? A.y + ro : nullptr, A.z ? A.z + ro : nullptr,
+                        (size_t)V, s, ca, cb, cc, red[r]);
     }
   }
   if (A.z) {
 #pragma unroll
-    for (int r = 0; r < NR; ++r) grid_reduce<3, NT, R>(acc3[r], A.red, rhs0 + r);
+    for (int r = 0; r < NR; ++r) grid_reduce<3, NT, R>(red[r], A.red, rhs0 + r);
   }
 }
 
@@ -138,22 +206,78 @@ __global__ void __launch_bounds__(NT) wilson_kernel(const WilsonArgs<S, G, NL> A
 // the GPU idle, so a CTA of 8 warps takes 32 sites and warp w computes hop
 // w (direction w / 2, forward for even w) for all 32 of them; the eight
 // partial sums of each site are then added in direction order through shared
-// memory and warps 0-5 finish two colour-spin components each (output, y
-// term and fused dots).  Deterministic; a different association of the
-// same terms than the one-thread-per-site kernel.
-template <int MU, bool FWD, typename R, typename S, typename G, int NL>
-__device__ __forceinline__ void one_hop(cx<R> (&acc)[4][3], const WilsonArgs<S, G, NL>& A, const S* in, int s,
-                                        const int (&c)[4], const int (&stride)[4]) {
-  const int L = A.L[MU], st = stride[MU];
+// memory and warps 0-2 finish one four-component chunk each (output, y term
+// and fused dots).  Deterministic; a different association of the same terms
+// than the one-thread-per-site kernel.
+template <int MU, bool FWD, typename R, typename G, int NL, typename In>
+__device__ __forceinline__ void one_hop(cx<R> (&acc)[4][3], const G* U, int V, const In& in, int s, const int (&c)[4],
+                                        const int (&stride)[4], int L) {
+  const int st = stride[MU];
   Link<R> u;
+  cx<R> psi[12];
   if (FWD) {
     const int nb = (c[MU] == L - 1) ? s - (L - 1) * st : s + st;
-    load_link<R, G, NL>(u, A.U, MU, A.V, s);
-    hop<MU, true>(acc, in, A.V, nb, u);
+    load_link<R, G, NL>(u, U, MU, V, s);
+    in(nb, psi);
   } else {
     const int nb = (c[MU] == 0) ? s + (L - 1) * st : s - st;
-    load_link<R, G, NL>(u, A.U, MU, A.V, nb);
-    hop<MU, false>(acc, in, A.V, nb, u);
+    load_link<R, G, NL>(u, U, MU, V, nb);
+    in(nb, psi);
+  }
+  hop_vals<MU, FWD, R>(acc, psi, u);
+}
+
+// Input of a hop: the 12 components of a site of a stored field.
+template <typename R, typename S>
+struct StoredIn {
+  const S* p;
+  size_t V;
+  __device__ __forceinline__ void operator()(int site, cx<R> (&v)[12]) const { ld_spinor<R, S>(p, V, site, v); }
+};
+
+// The hop of warp w (direction w / 2, forward for even w) into the CTA's partial sums.
+template <typename R, typename G, int NL, typename In>
+__device__ __forceinline__ void warp_hop(R (&part)[8][24][32], const G* U, const int (&Lat)[4], int V, const In& in,
+                                         int s, bool valid) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  cx<R> acc[4][3];
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) acc[sp][a] = zero<R>();
+  if (valid) {
+    int c[4], stride[4];
+    site_coords(s, Lat, c, stride);
+    switch (warp) {  // uniform across the warp
+      case 0: one_hop<0, true, R, G, NL>(acc, U, V, in, s, c, stride, Lat[0]); break;
+      case 1: one_hop<0, false, R, G, NL>(acc, U, V, in, s, c, stride, Lat[0]); break;
+      case 2: one_hop<1, true, R, G, NL>(acc, U, V, in, s, c, stride, Lat[1]); break;
+      case 3: one_hop<1, false, R, G, NL>(acc, U, V, in, s, c, stride, Lat[1]); break;
+      case 4: one_hop<2, true, R, G, NL>(acc, U, V, in, s, c, stride, Lat[2]); break;
+      case 5: one_hop<2, false, R, G, NL>(acc, U, V, in, s, c, stride, Lat[2]); break;
+      case 6: one_hop<3, true, R, G, NL>(acc, U, V, in, s, c, stride, Lat[3]); break;
+      default: one_hop<3, false, R, G, NL>(acc, U, V, in, s, c, stride, Lat[3]); break;
+    }
+  }
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      part[warp][2 * (sp * 3 + a)][lane] = acc[sp][a].re;
+      part[warp][2 * (sp * 3 + a) + 1][lane] = acc[sp][a].im;
+    }
+}
+
+// Chunk j of the hopping term of this lane's site, summed over the eight hops in order.
+template <typename R>
+__device__ __forceinline__ void warp_hop_sum(const R (&part)[8][24][32], int j, cx<R> (&h)[4]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int comp = 4 * j + k;
+    h[k] = zero<R>();
+#pragma unroll
+    for (int w = 0; w < 8; ++w) h[k] = h[k] + mk<R>(part[w][2 * comp][lane], part[w][2 * comp + 1][lane]);
   }
 }
 
@@ -162,74 +286,19 @@ __global__ void __launch_bounds__(256) wilson_small_kernel(const WilsonArgs<S, G
   typedef typename Store<S>::R R;
   __shared__ R part[8][24][32];  // [hop][real component][site of the CTA]
   const int V = A.V;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.x * 32 + lane;
+  const int warp = threadIdx.x >> 5;
+  const int s = blockIdx.x * 32 + (threadIdx.x & 31);
   const int rhs = blockIdx.y;
-  const S* in = A.in + rhs * A.vstride;
-  {
-    cx<R> acc[4][3];
-#pragma unroll
-    for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) acc[sp][a] = zero<R>();
-    if (s < V) {
-      int c[4], stride[4];
-      int q = s;
-      c[0] = q % A.L[0];
-      q /= A.L[0];
-      c[1] = q % A.L[1];
-      q /= A.L[1];
-      c[2] = q % A.L[2];
-      c[3] = q / A.L[2];
-      stride[0] = 1;
-      stride[1] = A.L[0];
-      stride[2] = A.L[0] * A.L[1];
-      stride[3] = stride[2] * A.L[2];
-      switch (warp) {  // uniform across the warp
-        case 0: one_hop<0, true>(acc, A, in, s, c, stride); break;
-        case 1: one_hop<0, false>(acc, A, in, s, c, stride); break;
-        case 2: one_hop<1, true>(acc, A, in, s, c, stride); break;
-        case 3: one_hop<1, false>(acc, A, in, s, c, stride); break;
-        case 4: one_hop<2, true>(acc, A, in, s, c, stride); break;
-        case 5: one_hop<2, false>(acc, A, in, s, c, stride); break;
-        case 6: one_hop<3, true>(acc, A, in, s, c, stride); break;
-        default: one_hop<3, false>(acc, A, in, s, c, stride); break;
-      }
-    }
-#pragma unroll
-    for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        part[warp][2 * (sp * 3 + a)][lane] = acc[sp][a].re;
-        part[warp][2 * (sp * 3 + a) + 1][lane] = acc[sp][a].im;
-      }
-  }
+  const size_t ro = (size_t)rhs * A.vstride;
+  warp_hop<R, G, NL>(part, A.U, A.L, V, StoredIn<R, S>{A.in + ro, (size_t)V}, s, s < V);
   __syncthreads();
   R red[3] = {(R)0, (R)0, (R)0};
-  if (warp < 6 && s < V) {
-    const S* y = A.y ? A.y + rhs * A.vstride : nullptr;
-    const S* z = A.z ? A.z + rhs * A.vstride : nullptr;
-    S* out = A.out + rhs * A.vstride;
+  if (warp < 3 && s < V) {
     const R ca = (R)(A.adiag ? A.a * A.adiag[rhs] : A.a), cb = (R)A.b, cc = (R)A.c;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int comp = 2 * warp + k;  // spin * 3 + colour
-      cx<R> h = zero<R>();
-#pragma unroll
-      for (int w = 0; w < 8; ++w) h = h + mk<R>(part[w][2 * comp][lane], part[w][2 * comp + 1][lane]);
-      const size_t i = (size_t)comp * V + s;
-      cx<R> v = cb * h;
-      v = v + ca * ldc<R>(in, i);
-      if (y) v = v + cc * ldc<R>(y, i);
-      stc(out, i, v);
-      if (z) {
-        const cx<R> vs = as_stored<S>(v);
-        const cx<R> d = cmul_conj(vs, ldc<R>(z, i));
-        red[0] += d.re;
-        red[1] += d.im;
-        red[2] += norm2(vs);
-      }
-    }
+    cx<R> h[4];
+    warp_hop_sum<R>(part, warp, h);
+    finish_chunk<R, S>(h, warp, A.in + ro, A.out + ro, A.y ? A.y + ro : nullptr, A.z ? A.z + ro : nullptr,
+                       (size_t)V, s, ca, cb, cc, red);
   }
   if (A.z) grid_reduce<3, 256, R>(red, A.red, rhs);
 }
@@ -251,9 +320,14 @@ template <typename R, typename S>
 struct ShiftedIn {
   const S* r;
   const S* p;
+  size_t V;
   cx<R> c;
-  __device__ __forceinline__ cx<R> operator()(size_t i) const {
-    return as_stored<S>(ldc<R>(r, i) - c * ldc<R>(p, i));
+  __device__ __forceinline__ void operator()(int site, cx<R> (&v)[12]) const {
+    cx<R> pv[12];
+    ld_spinor<R, S>(r, V, site, v);
+    ld_spinor<R, S>(p, V, site, pv);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = as_stored<S>(v[k] - c * pv[k]);
   }
 };
 
@@ -287,60 +361,41 @@ __device__ __forceinline__ cx<R> fused_coef(const MrFuseArgs& F, int rhs) {
   return mk<R>((R)sc[0], (R)sc[1]);
 }
 
-// Own-site part of a fused step for component i of one right-hand side
-// (pointers already offset to it): x and r' stored, out = a r' + b h, and the
-// dot partials of out against r'.
+// Own-site part of chunk j of a fused step for one right-hand side (offset
+// ro): x and r' stored, out = a r' + b h, and the dot partials of out
+// against r'.
 template <typename R, typename S>
-__device__ __forceinline__ void fused_site(const MrFuseArgs& F, const ShiftedIn<R, S>& in, S* out, size_t ro,
-                                           size_t i, cx<R> h, R ca, R cb, R (&red)[3]) {
-  const cx<R> rn = in(i);
-  const S* u = F.u ? (const S*)F.u + ro : in.r;
-  cx<R> xv = F.xin ? ldc<R>((const S*)F.xin + ro, i) : zero<R>();
-  xv = cfma(in.c, ldc<R>(u, i), xv);
-  stc((S*)F.x + ro, i, xv);
-  stc((S*)F.rout + ro, i, rn);
-  cx<R> v = cb * h;
-  v = v + ca * rn;
-  stc(out, i, v);
-  const cx<R> vs = as_stored<S>(v);
-  const cx<R> d = cmul_conj(vs, rn);
-  red[0] += d.re;
-  red[1] += d.im;
-  red[2] += norm2(vs);
-}
-
-template <int MU, bool FWD, typename R, typename S, typename G, int NL>
-__device__ __forceinline__ void one_hop_in(cx<R> (&acc)[4][3], const WilsonArgs<S, G, NL>& A,
-                                           const ShiftedIn<R, S>& in, int s, const int (&c)[4],
-                                           const int (&stride)[4]) {
-  const int L = A.L[MU], st = stride[MU];
-  Link<R> u;
-  if (FWD) {
-    const int nb = (c[MU] == L - 1) ? s - (L - 1) * st : s + st;
-    load_link<R, G, NL>(u, A.U, MU, A.V, s);
-    hop_from<MU, true, R>(acc, in, A.V, nb, u);
-  } else {
-    const int nb = (c[MU] == 0) ? s + (L - 1) * st : s - st;
-    load_link<R, G, NL>(u, A.U, MU, A.V, nb);
-    hop_from<MU, false, R>(acc, in, A.V, nb, u);
+__device__ __forceinline__ void fused_chunk(const MrFuseArgs& F, const ShiftedIn<R, S>& in, S* out, size_t ro, int j,
+                                            int s, const cx<R> (&h)[4], R ca, R cb, R (&red)[3]) {
+  const size_t i0 = (j * in.V + s) << 2;
+  cx<R> rv[4], pv[4], uv[4], xv[4], v[4];
+  ld_chunk<R, S>(in.r, i0, rv);
+  ld_chunk<R, S>(in.p, i0, pv);
+  if (F.u) ld_chunk<R, S>((const S*)F.u + ro, i0, uv);
+  if (F.xin) ld_chunk<R, S>((const S*)F.xin + ro, i0, xv);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const cx<R> rn = as_stored<S>(rv[k] - in.c * pv[k]);
+    if (!F.xin) xv[k] = zero<R>();
+    xv[k] = cfma(in.c, F.u ? uv[k] : rv[k], xv[k]);
+    rv[k] = rn;
+    v[k] = cb * h[k];
+    v[k] = v[k] + ca * rn;
+  }
+  st_chunk<S, R>((S*)F.x + ro, i0, xv);
+  st_chunk<S, R>((S*)F.rout + ro, i0, rv);
+  st_chunk<S, R>(out, i0, v);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const cx<R> vs = as_stored<S>(v[k]);
+    const cx<R> d = cmul_conj(vs, rv[k]);
+    red[0] += d.re;
+    red[1] += d.im;
+    red[2] += norm2(vs);
   }
 }
 
-__device__ __forceinline__ void site_coords(int s, const int (&L)[4], int (&c)[4], int (&stride)[4]) {
-  int q = s;
-  c[0] = q % L[0];
-  q /= L[0];
-  c[1] = q % L[1];
-  q /= L[1];
-  c[2] = q % L[2];
-  c[3] = q / L[2];
-  stride[0] = 1;
-  stride[1] = L[0];
-  stride[2] = L[0] * L[1];
-  stride[3] = stride[2] * L[2];
-}
-
-// One thread per site and right-hand side (the hop order of wilson_kernel).
+// One thread per site and right-hand side (the hop order of the scalar hop).
 template <typename S, typename G, int NL, int NT>
 __global__ void __launch_bounds__(NT) wilson_mr_kernel(const WilsonArgs<S, G, NL> A, const MrFuseArgs F) {
   typedef typename Store<S>::R R;
@@ -349,7 +404,7 @@ __global__ void __launch_bounds__(NT) wilson_mr_kernel(const WilsonArgs<S, G, NL
   const int rhs = blockIdx.y;
   const cx<R> cf = fused_coef<R>(F, rhs);
   const size_t ro = (size_t)rhs * A.vstride;
-  const ShiftedIn<R, S> in{A.in + ro, (const S*)F.pprev + ro, cf};
+  const ShiftedIn<R, S> in{A.in + ro, (const S*)F.pprev + ro, (size_t)V, cf};
   R red[3] = {(R)0, (R)0, (R)0};
   if (s < V) {
     int c[4], stride[4];
@@ -359,19 +414,21 @@ __global__ void __launch_bounds__(NT) wilson_mr_kernel(const WilsonArgs<S, G, NL
     for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
       for (int a = 0; a < 3; ++a) acc[sp][a] = zero<R>();
-    one_hop_in<0, true>(acc, A, in, s, c, stride);
-    one_hop_in<0, false>(acc, A, in, s, c, stride);
-    one_hop_in<1, true>(acc, A, in, s, c, stride);
-    one_hop_in<1, false>(acc, A, in, s, c, stride);
-    one_hop_in<2, true>(acc, A, in, s, c, stride);
-    one_hop_in<2, false>(acc, A, in, s, c, stride);
-    one_hop_in<3, true>(acc, A, in, s, c, stride);
-    one_hop_in<3, false>(acc, A, in, s, c, stride);
+    one_hop<0, true, R, G, NL>(acc, A.U, V, in, s, c, stride, A.L[0]);
+    one_hop<0, false, R, G, NL>(acc, A.U, V, in, s, c, stride, A.L[0]);
+    one_hop<1, true, R, G, NL>(acc, A.U, V, in, s, c, stride, A.L[1]);
+    one_hop<1, false, R, G, NL>(acc, A.U, V, in, s, c, stride, A.L[1]);
+    one_hop<2, true, R, G, NL>(acc, A.U, V, in, s, c, stride, A.L[2]);
+    one_hop<2, false, R, G, NL>(acc, A.U, V, in, s, c, stride, A.L[2]);
+    one_hop<3, true, R, G, NL>(acc, A.U, V, in, s, c, stride, A.L[3]);
+    one_hop<3, false, R, G, NL>(acc, A.U, V, in, s, c, stride, A.L[3]);
 #pragma unroll
-    for (int sp = 0; sp < 4; ++sp)
+    for (int j = 0; j < 3; ++j) {
+      cx<R> h[4];
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
-        fused_site(F, in, A.out + ro, ro, (size_t)(sp * 3 + a) * V + s, acc[sp][a], (R)A.a, (R)A.b, red);
+      for (int k = 0; k < 4; ++k) h[k] = acc[(4 * j + k) / 3][(4 * j + k) % 3];
+      fused_chunk<R, S>(F, in, A.out + ro, ro, j, s, h, (R)A.a, (R)A.b, red);
+    }
   }
   grid_reduce<3, NT, R>(red, A.red, rhs);
 }
@@ -382,55 +439,22 @@ __global__ void __launch_bounds__(256) wilson_small_mr_kernel(const WilsonArgs<S
   typedef typename Store<S>::R R;
   __shared__ R part[8][24][32];
   const int V = A.V;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.x * 32 + lane;
+  const int warp = threadIdx.x >> 5;
+  const int s = blockIdx.x * 32 + (threadIdx.x & 31);
   const int rhs = blockIdx.y;
   const cx<R> cf = fused_coef<R>(F, rhs);
   const size_t ro = (size_t)rhs * A.vstride;
-  const ShiftedIn<R, S> in{A.in + ro, (const S*)F.pprev + ro, cf};
-  {
-    cx<R> acc[4][3];
-#pragma unroll
-    for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) acc[sp][a] = zero<R>();
-    if (s < V) {
-      int c[4], stride[4];
-      site_coords(s, A.L, c, stride);
-      switch (warp) {
-        case 0: one_hop_in<0, true>(acc, A, in, s, c, stride); break;
-        case 1: one_hop_in<0, false>(acc, A, in, s, c, stride); break;
-        case 2: one_hop_in<1, true>(acc, A, in, s, c, stride); break;
-        case 3: one_hop_in<1, false>(acc, A, in, s, c, stride); break;
-        case 4: one_hop_in<2, true>(acc, A, in, s, c, stride); break;
-        case 5: one_hop_in<2, false>(acc, A, in, s, c, stride); break;
-        case 6: one_hop_in<3, true>(acc, A, in, s, c, stride); break;
-        default: one_hop_in<3, false>(acc, A, in, s, c, stride); break;
-      }
-    }
-#pragma unroll
-    for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        part[warp][2 * (sp * 3 + a)][lane] = acc[sp][a].re;
-        part[warp][2 * (sp * 3 + a) + 1][lane] = acc[sp][a].im;
-      }
-  }
+  const ShiftedIn<R, S> in{A.in + ro, (const S*)F.pprev + ro, (size_t)V, cf};
+  warp_hop<R, G, NL>(part, A.U, A.L, V, in, s, s < V);
   __syncthreads();
   R red[3] = {(R)0, (R)0, (R)0};
-  if (warp < 6 && s < V) {
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int comp = 2 * warp + k;
-      cx<R> h = zero<R>();
-#pragma unroll
-      for (int w = 0; w < 8; ++w) h = h + mk<R>(part[w][2 * comp][lane], part[w][2 * comp + 1][lane]);
-      fused_site(F, in, A.out + ro, ro, (size_t)comp * V + s, h, (R)A.a, (R)A.b, red);
-    }
+  if (warp < 3 && s < V) {
+    cx<R> h[4];
+    warp_hop_sum<R>(part, warp, h);
+    fused_chunk<R, S>(F, in, A.out + ro, ro, warp, s, h, (R)A.a, (R)A.b, red);
   }
   grid_reduce<3, 256, R>(red, A.red, rhs);
 }
-
 template <typename S, typename G, int NL>
 static int launch_mr_t(const DslashCall& d, const MrFuseArgs& F, cudaStream_t st) {
   WilsonArgs<S, G, NL> A;
@@ -505,18 +529,18 @@ static int launch_t(const DslashCall& d, cudaStream_t st) {
       wilson_small_kernel<S, G, NL><<<grid, 256, 0, st>>>(A);
       return cudaGetLastError() == cudaSuccess ? 0 : -1;
     }
+    WShape sh = {128, 1};
+    if (d.variant >= 0 && d.variant < wilson_variants(1, d.z != nullptr, d.nrhs, A.V))
+      sh = d.z ? kShapesDots[d.variant] : kShapesFree[d.variant];
+    if (sh.nr == 2) {
+      if (sh.nt == 64) return launch_nt<S, G, NL, 64, 2>(A, d.nrhs, st);
+      if (sh.nt == 256) return launch_nt<S, G, NL, 256, 2>(A, d.nrhs, st);
+      return launch_nt<S, G, NL, 128, 2>(A, d.nrhs, st);
+    }
+    if (sh.nt == 64) return launch_nt<S, G, NL, 64, 1>(A, d.nrhs, st);
+    if (sh.nt == 256) return launch_nt<S, G, NL, 256, 1>(A, d.nrhs, st);
+    return launch_nt<S, G, NL, 128, 1>(A, d.nrhs, st);
   }
-  WShape sh = {128, 1};
-  if (d.variant >= 0 && d.variant < wilson_variants(1, d.z != nullptr, d.nrhs, A.V))
-    sh = d.z ? kShapesDots[d.variant] : kShapesFree[d.variant];
-  if (sh.nr == 2) {
-    if (sh.nt == 64) return launch_nt<S, G, NL, 64, 2>(A, d.nrhs, st);
-    if (sh.nt == 256) return launch_nt<S, G, NL, 256, 2>(A, d.nrhs, st);
-    return launch_nt<S, G, NL, 128, 2>(A, d.nrhs, st);
-  }
-  if (sh.nt == 64) return launch_nt<S, G, NL, 64, 1>(A, d.nrhs, st);
-  if (sh.nt == 256) return launch_nt<S, G, NL, 256, 1>(A, d.nrhs, st);
-  return launch_nt<S, G, NL, 128, 1>(A, d.nrhs, st);
 }
 
 int launch_wilson_mr(const DslashCall& d, const void* pprev, const void* u, const void* xin, void* x, void* rout,
@@ -544,9 +568,11 @@ int launch_wilson(const DslashCall& d, cudaStream_t st) {
   return -1;
 }
 
+
 // ------------------------------------------------------------------ links
-// External gauge layout [4][V][3][3] complex FP64 -> internal [4][NL][V] in
-// the storage precision (NL = 9 for FP64, 6 = two rows otherwise).
+// External gauge layout [4][V][3][3] complex FP64 -> the internal link layout
+// of wilson_hop.cuh in the storage precision (NL = 9 for FP64, 6 = two rows
+// otherwise).
 template <typename G, int NL>
 __global__ void pack_links_kernel(const double2* __restrict__ ext, G* __restrict__ out, int V) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over 4 V sites x NL
@@ -556,7 +582,7 @@ __global__ void pack_links_kernel(const double2* __restrict__ ext, G* __restrict
   const int k = (int)((i / V) % NL);
   const int mu = (int)(i / ((size_t)V * NL));
   double2 v = ext[((size_t)mu * V + site) * 9 + k];
-  stc(out, i, mk<double>(v.x, v.y));
+  stc(out, lidx<G, NL>(mu, k, site, V), mk<double>(v.x, v.y));
 }
 
 // ------------------------------------------------------------------ link check

@@ -13,12 +13,14 @@
 //                      reorder the links parity-major);
 //   eo_merge_kernel  : (even, odd) -> full field, optionally added to it.
 //
-// Half-field layout: [nrhs][12][V/2] complex, the sites of one parity in
-// lexicographic order (needs an even Lx: each x-row then holds Lx/2 sites of
-// either parity, and the k-th site of a parity has lexicographic index 2k or
-// 2k + 1, so its half index is lex / 2).  Links: [4][NL][V] with the site
-// index parity-major (even sites 0..V/2-1, then odd), so the links a thread
-// reads for its forward hops are contiguous across a warp.
+// Half-field layout: the chunked level-0 layout of wilson_hop.cuh on V/2
+// sites, [nrhs][3][V/2][4] complex, the sites of one parity in lexicographic
+// order (needs an even Lx: each x-row then holds Lx/2 sites of either
+// parity, and the k-th site of a parity has lexicographic index 2k or
+// 2k + 1, so its half index is lex / 2).  Links: the link layout of
+// wilson_hop.cuh with the site index parity-major (even sites 0..V/2-1, then
+// odd), so the links a thread reads for its forward hops are contiguous
+// across a warp.
 #include "common.cuh"
 #include "kernels.h"
 #include "wilson_hop.cuh"
@@ -91,22 +93,33 @@ __global__ void __launch_bounds__(NT) wilson_eo_kernel(const EoArgs<S, G, NL> A)
     eo_hop_pair<3>(acc, A, in, s, h, c, stride);
     const R ca = (R)A.a, cb = (R)A.b, cc = (R)A.c;
 #pragma unroll
-    for (int sp = 0; sp < 4; ++sp)
+    for (int j = 0; j < 3; ++j) {
+      // x, y or z may alias out: read them through the L2 (coherent with this thread's stores)
+      const size_t i0 = ro + (((size_t)j * A.Vh + h) << 2);
+      cx<R> xv[4], yv[4], v[4];
+      if (A.x) ld_chunk_cg<R, S>(A.x, i0, xv);
+      if (A.y) ld_chunk_cg<R, S>(A.y, i0, yv);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const size_t i = ro + (size_t)(sp * 3 + k) * A.Vh + h;
-        cx<R> v = cb * acc[sp][k];
-        if (A.x) v = v + ca * ldc<R>(A.x, i);
-        if (A.y) v = v + cc * ldc<R>(A.y, i);
-        stc(A.out, i, v);
-        if (A.z) {
-          const cx<R> vs = as_stored<S>(v);
-          const cx<R> d = cmul_conj(vs, ldc<R>(A.z, i));
+      for (int k = 0; k < 4; ++k) {
+        const int c = 4 * j + k;
+        v[k] = cb * acc[c / 3][c % 3];
+        if (A.x) v[k] = v[k] + ca * xv[k];
+        if (A.y) v[k] = v[k] + cc * yv[k];
+      }
+      st_chunk<S, R>(A.out, i0, v);
+      if (A.z) {
+        cx<R> zz[4];
+        ld_chunk_cg<R, S>(A.z, i0, zz);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const cx<R> vs = as_stored<S>(v[k]);
+          const cx<R> d = cmul_conj(vs, zz[k]);
           red[0] += d.re;
           red[1] += d.im;
           red[2] += norm2(vs);
         }
       }
+    }
   }
   if (A.z) grid_reduce<3, NT, R>(red, A.red, rhs);
 }
@@ -171,7 +184,8 @@ __global__ void eo_split_kernel(const T* __restrict__ full, T* __restrict__ even
   odd[row * hstride + h] = odd_first ? a : b;
 }
 
-// full = (add ? full : 0) + merge(even, odd); a null half is zero.
+// full = (add ? full : 0) + merge(even, odd) on chunked level-0 fields (rows
+// of V four-component chunks); a null half is zero.
 template <typename S>
 __global__ void eo_merge_kernel(const S* __restrict__ even, const S* __restrict__ odd, S* full, int L0, int L1, int L2,
                                 int Vh, int add) {
@@ -185,16 +199,29 @@ __global__ void eo_merge_kernel(const S* __restrict__ even, const S* __restrict_
   q /= L1;
   const int z = q % L2, t = q / L2;
   const int odd_first = (y + z + t) & 1;
-  const size_t hi = row * (size_t)Vh + h;
-  const size_t fe = row * (size_t)(2 * Vh) + lex0 + odd_first, fo = row * (size_t)(2 * Vh) + lex0 + 1 - odd_first;
-  cx<R> ve = even ? ldc<R>(even, hi) : zero<R>();
-  cx<R> vo = odd ? ldc<R>(odd, hi) : zero<R>();
+  // rows of 4-complex chunks (one chunk of one site per element)
+  const size_t hi = (row * (size_t)Vh + h) << 2;
+  const size_t fe = (row * (size_t)(2 * Vh) + lex0 + odd_first) << 2;
+  const size_t fo = (row * (size_t)(2 * Vh) + lex0 + 1 - odd_first) << 2;
+  cx<R> ve[4], vo[4];
+  if (even) ld_chunk<R, S>(even, hi, ve);
+  if (odd) ld_chunk<R, S>(odd, hi, vo);
+  cx<R> fv[4], gv[4];
   if (add) {
-    ve = ve + ldc<R>(full, fe);
-    vo = vo + ldc<R>(full, fo);
+    ld_chunk_cg<R, S>(full, fe, fv);
+    ld_chunk_cg<R, S>(full, fo, gv);
   }
-  stc(full, fe, ve);
-  stc(full, fo, vo);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!even) ve[k] = zero<R>();
+    if (!odd) vo[k] = zero<R>();
+    if (add) {
+      ve[k] = ve[k] + fv[k];
+      vo[k] = vo[k] + gv[k];
+    }
+  }
+  st_chunk<S, R>(full, fe, ve);
+  st_chunk<S, R>(full, fo, vo);
 }
 
 template <typename T>
@@ -206,14 +233,38 @@ static int split_t(const void* full, void* even, void* odd, const int L[4], size
   return launched() ? 0 : -1;
 }
 
+struct alignas(16) Bytes32 {
+  uint4 a, b;
+};
+struct alignas(16) Bytes64 {
+  uint4 a, b, c, d;
+};
+
 int launch_eo_split(size_t elem_bytes, const void* full, void* even, void* odd, const int L[4], size_t rows,
                     size_t hstride, cudaStream_t st) {
   if (L[0] % 2 || rows == 0 || rows > 65535) return -1;
   switch (elem_bytes) {
-    case 16: return split_t<double2>(full, even, odd, L, rows, hstride, st);
+    case 64: return split_t<Bytes64>(full, even, odd, L, rows, hstride, st);
+    case 32: return split_t<Bytes32>(full, even, odd, L, rows, hstride, st);
+    case 16: return split_t<uint4>(full, even, odd, L, rows, hstride, st);
     case 8: return split_t<float2>(full, even, odd, L, rows, hstride, st);
     case 4: return split_t<unsigned>(full, even, odd, L, rows, hstride, st);
   }
+  return -1;
+}
+
+// Links in the layout of wilson_hop.cuh -> the same with the sites parity-major:
+// every run of V site-indexed elements is split into its even and odd halves.
+int launch_eo_links(int prec, const void* links, void* out, const int L[4], cudaStream_t st) {
+  const size_t V = (size_t)L[0] * L[1] * L[2] * L[3], Vh = V / 2;
+  const char* src = (const char*)links;
+  char* dst = (char*)out;
+  if (prec == 2 || prec == 3) {  // [4][V] 16-byte elements (k 0..3), then [4][V] 8-byte elements (k 4, 5)
+    if (launch_eo_split(16, src, dst, dst + Vh * 16, L, 4, V, st)) return -1;
+    return launch_eo_split(8, src + 64 * V, dst + 64 * V, dst + 64 * V + Vh * 8, L, 4, V, st);
+  }
+  if (prec == 1) return launch_eo_split(16, src, dst, dst + Vh * 16, L, 12, V, st);  // [12][V] x 16 bytes
+  if (prec == 0) return launch_eo_split(16, src, dst, dst + Vh * 16, L, 36, V, st);  // [36][V] x 16 bytes
   return -1;
 }
 

@@ -7,9 +7,10 @@ import of this module fails, there is no fallback.
 
 Layouts (see the header): external spinors are complex128 arrays shaped
 (nrhs, Lt, Lz, Ly, Lx, 4, 3) (or without the leading nrhs); internal fields
-are (nrhs, ncomp, V) complex in the precision named by ``prec``: complex128
-(MG_F64), complex64 (MG_F32), or a trailing pair of float16 / bfloat16
-(MG_F16 / MG_BF16).
+are complex in the precision named by ``prec``: complex128 (MG_F64),
+complex64 (MG_F32), or a trailing pair of float16 / bfloat16 (MG_F16 /
+MG_BF16), shaped (nrhs, 3, V, 4) on level 0 (component c = spin * 3 + colour
+at [c // 4, site, c % 4]) and (nrhs, ncomp, V) on coarse levels.
 """
 import ctypes
 import os
@@ -488,9 +489,10 @@ def internal_empty(h, level, prec, nrhs=1, device="cuda", half=False):
     import torch
     dims, nc, _ = mg_level_info(h, level)
     V = int(np.prod(dims)) // (2 if half else 1)
+    shape = (nrhs, 3, V, 4) if level == 0 else (nrhs, nc, V)
     if prec == MG_F64:
-        return torch.empty((nrhs, nc, V), dtype=torch.complex128, device=device)
+        return torch.empty(shape, dtype=torch.complex128, device=device)
     if prec == MG_F32:
-        return torch.empty((nrhs, nc, V), dtype=torch.complex64, device=device)
+        return torch.empty(shape, dtype=torch.complex64, device=device)
     dt = torch.float16 if prec == MG_F16 else torch.bfloat16
-    return torch.empty((nrhs, nc, V, 2), dtype=dt, device=device)
+    return torch.empty(shape + (2,), dtype=dt, device=device)

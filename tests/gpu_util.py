@@ -17,11 +17,5 @@ def lattice(dims):
     return (Lt, Lz, Ly, Lx)
 
 
-def to_internal(ext, ncomp):
-    """External (..., V, ncomp) complex -> internal (nrhs, ncomp, V), numpy."""
-    a = np.asarray(ext).reshape(-1, int(np.prod(ext.shape[-5:-1])) if ncomp == 12 else ext.shape[-2], ncomp)
-    return np.ascontiguousarray(np.swapaxes(a, 1, 2))
-
-
 def rel_err(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))

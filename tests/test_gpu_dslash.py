@@ -118,3 +118,71 @@ def test_dslash_fused_residual_and_reduction_deterministic():
     xo, ro = mg.mr_relax(A, b.reshape(lat + (12,)), x.reshape(lat + (12,)), 3, 0.8)
     assert rel_err(outs[0][0].reshape(xo.shape), xo) < 1e-13
     assert rel_err(outs[0][1].reshape(ro.shape), ro) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("mode", [4, 3])
+def test_dslash_large_lattice_whole_field(prec, mode):
+    """16x8x8x8 with 6 right-hand sides (49,152 site x right-hand sides, above the 32,768 up to
+    which the warp-per-hop kernel runs), so the one-thread-per-site stencil runs: every element
+    against the oracle applied to the input as stored.  Tuner mode 4 forces the first launch
+    shape (128 threads, one right-hand side per thread), mode 3 the last (256 threads, two per
+    thread, each link shared by both); FP64 has one shape."""
+    wm = require_gpu()
+    dims = (16, 8, 8, 8)
+    mass = -0.37
+    h, U = _handle(wm, dims, mass, None if prec == 0 else prec)
+    nrhs = 6
+    psi = np.stack([inputs.gaussian_spinor(dims, 40 + r) for r in range(nrhs)])
+    ext = torch.from_numpy(psi).cuda()
+    inp = wm.internal_empty(h, 0, prec, nrhs)
+    out = wm.internal_empty(h, 0, prec, nrhs)
+    wm.mg_field_to_internal(h, 0, prec, ext, inp, nrhs)
+    old = wm.mg_tune(mode)
+    try:
+        wm.dslash_apply(h, prec, inp, out, nrhs)
+        torch.cuda.synchronize()
+    finally:
+        wm.mg_tune(old)
+    got = torch.empty_like(ext)
+    wm.mg_field_from_internal(h, 0, prec, out, got, nrhs)
+    back = torch.empty_like(ext)
+    wm.mg_field_from_internal(h, 0, prec, inp, back, nrhs)
+    got, back = got.cpu().numpy(), back.cpu().numpy()
+    for r in range(nrhs):
+        expect = dirac.wilson_dirac(U, back[r], mass)
+        assert rel_err(got[r], expect) < TOL[prec], (r, rel_err(got[r], expect))
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_mr_large_lattice_fused_dots(prec):
+    """mr_apply on 16^4 (65,536 sites: the one-thread-per-site stencil with its fused dot
+    products <A r|r>, ||A r||^2 feeding each MR coefficient) against the oracle's MR on the
+    input as stored, one step and three steps."""
+    wm = require_gpu()
+    dims = (16, 16, 16, 16)
+    mass = 0.05
+    h, U = _handle(wm, dims, mass, None if prec == 0 else prec)
+    b = inputs.gaussian_spinor(dims, 3)
+    x = inputs.gaussian_spinor(dims, 4)
+    from oracle import multigrid as mg
+    lat = lattice(dims)
+    A = lambda v: dirac.wilson_dirac(U, v.reshape(lat + (4, 3)), mass).reshape(lat + (12,))
+    tol = {0: 1e-12, 1: 1e-5, 2: 1e-2, 3: 6e-2}[prec]
+    for steps in (1, 3):
+        bi, xi, ri = (wm.internal_empty(h, 0, prec) for _ in range(3))
+        wm.mg_field_to_internal(h, 0, prec, torch.from_numpy(b).cuda(), bi)
+        wm.mg_field_to_internal(h, 0, prec, torch.from_numpy(x).cuda(), xi)
+        bs, xs = torch.empty(b.shape, dtype=torch.complex128, device="cuda"), torch.empty(
+            b.shape, dtype=torch.complex128, device="cuda")
+        wm.mg_field_from_internal(h, 0, prec, bi, bs)
+        wm.mg_field_from_internal(h, 0, prec, xi, xs)
+        wm.mr_apply(h, 0, prec, bi, xi, ri, steps)
+        xext = torch.empty(b.shape, dtype=torch.complex128, device="cuda")
+        rext = torch.empty(b.shape, dtype=torch.complex128, device="cuda")
+        wm.mg_field_from_internal(h, 0, prec, xi, xext)
+        wm.mg_field_from_internal(h, 0, prec, ri, rext)
+        xo, ro = mg.mr_relax(A, bs.cpu().numpy().reshape(lat + (12,)), xs.cpu().numpy().reshape(lat + (12,)),
+                             steps, 0.8)
+        assert rel_err(xext.cpu().numpy().reshape(xo.shape), xo) < tol, (steps, "x")
+        assert rel_err(rext.cpu().numpy().reshape(ro.shape), ro) < tol, (steps, "r")

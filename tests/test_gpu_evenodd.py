@@ -55,8 +55,8 @@ def _stored_full(wm, h, prec, psi):
 
 
 def _half_of(o):
-    """Oracle half field (V/2, 4, 3) -> internal half (12, V/2)."""
-    return o.reshape(o.shape[0], 12).T
+    """Oracle half field (V/2, 4, 3) -> internal half (3, V/2, 4): component c at [c // 4, site, c % 4]."""
+    return np.ascontiguousarray(np.moveaxis(o.reshape(o.shape[0], 3, 4), 1, 0))
 
 
 def _split_dev(wm, h, prec, full, nrhs):
@@ -85,7 +85,7 @@ def test_split_and_merge_move_bits(prec):
     assert torch.equal(back, full)
     wm.eo_merge(h, prec, e, None, back, nrhs)
     for r in range(nrhs):
-        be, bo = evenodd.split(np.moveaxis(_as_np(back)[r], 0, -1).reshape(lattice(DIMS) + (4, 3)))
+        be, bo = evenodd.split(np.moveaxis(_as_np(back)[r], 0, 1).reshape(lattice(DIMS) + (4, 3)))
         assert np.array_equal(be, evenodd.split(stored[r])[0]) and not np.any(bo)
 
 

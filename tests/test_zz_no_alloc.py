@@ -40,8 +40,12 @@ def test_no_alloc_mr_matches_mr_apply_twice(level, prec, mma):
     dims = (8, 4, 4, 8)
     U = inputs.random_gauge(dims, 3)
     mixed = 1 if prec == 1 else 0
-    p = wm.mg_default_params(n_levels=2, block=[(2, 2, 2, 2)], nv=[6], setup_sweeps=[4], mixed=mixed,
-                             fine_prec=wm.MG_F32, coarse_prec=wm.MG_F32, coarse_mma=mma)
+    if mma:  # the tensor-core stencil lives on coarse levels above the coarsest: three levels
+        p = wm.mg_default_params(n_levels=3, block=[(2, 2, 2, 2), (2, 2, 2, 2)], nv=[8, 4], setup_sweeps=[4, 4],
+                                 mixed=mixed, fine_prec=wm.MG_F32, coarse_prec=wm.MG_F32, coarse_mma=1)
+    else:
+        p = wm.mg_default_params(n_levels=2, block=[(2, 2, 2, 2)], nv=[6], setup_sweeps=[4], mixed=mixed,
+                                 fine_prec=wm.MG_F32, coarse_prec=wm.MG_F32)
     h = wm.mg_setup(U, dims, -0.1, p)
     ldims, nc, _ = wm.mg_level_info(h, level)
     shape = (ldims[3], ldims[2], ldims[1], ldims[0], nc)
