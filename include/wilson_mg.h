@@ -23,9 +23,13 @@
  *   level-l field (l >= 1): double complex [nrhs][V_l][2 Nv_l]; components
  *             [0, Nv_l) have chirality +, [Nv_l, 2 Nv_l) chirality -.
  * INTERNAL layout (what dslash_apply / coarse_apply / restrict / prolong /
- * mr_apply operate on, in the precision named by `prec`): component-major,
- *   [nrhs][ncomp][V_l] complex, element (r, c, s) at (r * ncomp + c) * V_l + s,
- * with ncomp = 12 on level 0 (c = spin * 3 + colour) and 2 Nv_l on level l.
+ * mr_apply operate on, in the precision named by `prec`):
+ *   level 0: [nrhs][3][V][4] complex, element (r, c, s) at
+ *            r * 12 V + ((c / 4) V + s) 4 + c % 4 (c = spin * 3 + colour):
+ *            three chunks of four components, each chunk site-major, so one
+ *            site's chunk is a single 16-byte load in FP16 / BF16;
+ *   level l >= 1: component-major [nrhs][ncomp][V_l] complex, element
+ *            (r, c, s) at (r * ncomp + c) * V_l + s, ncomp = 2 Nv_l.
  * Complex element types: MG_F64 = 2 x double, MG_F32 = 2 x float,
  * MG_F16 = 2 x IEEE binary16, MG_BF16 = 2 x bfloat16.  mg_field_to_internal /
  * mg_field_from_internal convert between the two.
@@ -134,7 +138,7 @@ int mg_default_params(mg_params* p);
  *   h            : out, a new handle owning every device buffer of the hierarchy.
  *   gauge        : external layout, FP64; host memory if gauge_on_device == 0,
  *                  device memory otherwise.  Copied; the caller keeps ownership.
- *   dims         : {Lx, Ly, Lz, Lt}, each >= 1.
+ *   dims         : {Lx, Ly, Lz, Lt}, each >= 1, at most 2^26 sites in all.
  *   p            : parameters (copied).  For every level l < n_levels - 1 the
  *                  level's extent must be divisible by block[l],
  *                  nv[l] <= (components per chirality) * (sites per block),
@@ -252,11 +256,12 @@ int dslash_apply(mg_handle* h, int prec, const void* in, void* out, int nrhs, vo
  * H links only sites of opposite parity p(n) = (x + y + z + t) mod 2, so
  *   D = [[M, -H_eo/2], [-H_oe/2, M]],   S = M - H_eo H_oe / (4 M)
  * is the Schur complement on the even sites, gamma5-Hermitian like D.
- * HALF layout: [nrhs][12][V/2] complex in precision prec, the sites of one
- * parity in lexicographic order (half index = site / 2).  Every lattice
- * extent must be even (MG_EINVAL otherwise).  Device memory; the calls do
- * not synchronise; the parity-major link copy of precision prec is made on
- * the first call (one more [4][NL][V] link array, held by the handle). */
+ * HALF layout: the level-0 internal layout on the V/2 sites of one parity,
+ * [nrhs][3][V/2][4] complex in precision prec, the sites in lexicographic
+ * order (half index = site / 2).  Every lattice extent must be even
+ * (MG_EINVAL otherwise).  Device memory; the calls do not synchronise; the
+ * parity-major link copy of precision prec is made on the first call (one
+ * more link array of 4 NL V complex, held by the handle). */
 
 /* Split nrhs internal-layout level-0 spinors into their even and odd halves. */
 int eo_split(mg_handle* h, int prec, const void* full, void* even, void* odd, int nrhs, void* stream);

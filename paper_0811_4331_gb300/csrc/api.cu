@@ -1266,6 +1266,10 @@ int mg_setup(mg_handle** hout, const double* gauge, int gauge_on_device, const i
       set_error("dims must be >= 1");
       return MG_EINVAL;
     }
+  if ((double)dims[0] * dims[1] * dims[2] * dims[3] > (double)kMaxSites) {
+    set_error("lattice above 2^26 sites (the level-0 kernels index one field in 32 bits)");
+    return MG_EINVAL;
+  }
   if (p->n_levels < 1 || p->n_levels > MG_MAX_LEVELS || p->nu_pre < 0 || p->nu_post < 0 || p->gcr_restart < 1 ||
       p->gcr_restart > kMaxBasis || !(p->omega > 0.0)) {
     set_error("invalid mg_params (levels 1..4, restart 1..64, nu >= 0, omega > 0)");

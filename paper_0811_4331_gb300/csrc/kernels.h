@@ -11,6 +11,10 @@
 
 namespace wmg {
 
+// Largest lattice (sites): the level-0 kernels index within one field and the
+// links in 32-bit arithmetic (36 V < 2^32).
+constexpr long long kMaxSites = 1LL << 26;
+
 // ------------------------------------------------------------------ fine stencil
 struct DslashCall {
   int prec;

@@ -126,15 +126,14 @@ __device__ __forceinline__ void hop_pair(HopAcc<R, NR>& acc, const WilsonArgs<S,
 template <typename R, typename S>
 __device__ __forceinline__ void finish_chunk(const cx<R> (&h)[4], int j, const S* in, S* out, const S* y, const S* z,
                                              size_t V, int s, R ca, R cb, R cc, R (&red)[3]) {
-  const size_t i0 = (j * V + s) << 2;
+  const size_t i0 = (size_t)(((unsigned)j * (unsigned)V + (unsigned)s) << 2);
   cx<R> xin[4], yv[4], v[4];
   ld_chunk<R, S>(in, i0, xin);
   if (y) ld_chunk_cg<R, S>(y, i0, yv);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    v[k] = cb * h[k];
-    v[k] = v[k] + ca * xin[k];
-    if (y) v[k] = v[k] + cc * yv[k];
+    v[k] = mk<R>(fma(cb, h[k].re, ca * xin[k].re), fma(cb, h[k].im, ca * xin[k].im));
+    if (y) v[k] = mk<R>(fma(cc, yv[k].re, v[k].re), fma(cc, yv[k].im, v[k].im));
   }
   st_chunk<S, R>(out, i0, v);
   if (z) {
@@ -168,8 +167,11 @@ __device__ __forceinline__ void finish_site(const HA& acc, int r, const S* in, S
 // output and dot partials are computed with the same operations in the same
 // order for any NT and NR, and the dots of right-hand side r are reduced over
 // the same CTAs of NT sites, so a launch shape never changes a result bit.
-template <typename S, typename G, int NL, int NT, int NR>
-__global__ void __launch_bounds__(NT) wilson_kernel(const WilsonArgs<S, G, NL> A) {
+// DOTS: the launch reduces <out|z>, ||out||^2 (then every thread of a CTA
+// takes part in the reduction); without it threads past the lattice leave at
+// once and no reduction code runs.
+template <typename S, typename G, int NL, int NT, int NR, bool DOTS>
+__device__ __forceinline__ void wilson_body(const WilsonArgs<S, G, NL>& A) {
   typedef typename Store<S>::R R;
   const int V = A.V;
   const int s = blockIdx.x * NT + threadIdx.x;
@@ -178,6 +180,7 @@ __global__ void __launch_bounds__(NT) wilson_kernel(const WilsonArgs<S, G, NL> A
   R red[NR][3];  // per-thread partial dots in the arithmetic type
 #pragma unroll
   for (int r = 0; r < NR; ++r) red[r][0] = red[r][1] = red[r][2] = (R)0;
+  if (!DOTS && s >= V) return;
   if (s < V) {
     int c[4], stride[4];
     site_coords(s, A.L, c, stride);
@@ -192,14 +195,28 @@ __global__ void __launch_bounds__(NT) wilson_kernel(const WilsonArgs<S, G, NL> A
     for (int r = 0; r < NR; ++r) {
       const R ca = (R)(A.adiag ? A.a * A.adiag[rhs0 + r] : A.a);
       const size_t ro = (size_t)(rhs0 + r) * A.vstride;
-      finish_site<R, S>(acc, r, A.in + ro, A.out + ro, A.y ? A.y + ro : nullptr, A.z ? A.z + ro : nullptr,
+      finish_site<R, S>(acc, r, A.in + ro, A.out + ro, A.y ? A.y + ro : nullptr, DOTS ? A.z + ro : nullptr,
                         (size_t)V, s, ca, cb, cc, red[r]);
     }
   }
-  if (A.z) {
+  if (DOTS) {
 #pragma unroll
     for (int r = 0; r < NR; ++r) grid_reduce<3, NT, R>(red[r], A.red, rhs0 + r);
   }
+}
+
+// The plain single-right-hand-side form (no dots) on 16-bit fields is bound
+// by the FP32 pipes: its register budget is capped so that 512 threads fit
+// on an SM.  The other forms keep the compiler's own choice (with FP32
+// fields more registers keep more loads in flight, which is what that
+// memory-bound form needs).
+template <typename S, typename G, int NL, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) wilson_plain_kernel(const WilsonArgs<S, G, NL> A) {
+  wilson_body<S, G, NL, NT, 1, false>(A);
+}
+template <typename S, typename G, int NL, int NT, int NR, bool DOTS>
+__global__ void __launch_bounds__(NT) wilson_kernel(const WilsonArgs<S, G, NL> A) {
+  wilson_body<S, G, NL, NT, NR, DOTS>(A);
 }
 
 // Small lattices (a few thousand sites): one thread per site leaves most of
@@ -484,7 +501,14 @@ static int launch_mr_t(const DslashCall& d, const MrFuseArgs& F, cudaStream_t st
 template <typename S, typename G, int NL, int NT, int NR>
 static int launch_nt(const WilsonArgs<S, G, NL>& A, int nrhs, cudaStream_t st) {
   dim3 grid((A.V + NT - 1) / NT, nrhs / NR);
-  wilson_kernel<S, G, NL, NT, NR><<<grid, NT, 0, st>>>(A);
+  if (A.z) {
+    wilson_kernel<S, G, NL, NT, NR, true><<<grid, NT, 0, st>>>(A);
+  } else {
+    if constexpr (NR == 1 && sizeof(S) == 4)
+      wilson_plain_kernel<S, G, NL, NT><<<grid, NT, 0, st>>>(A);
+    else
+      wilson_kernel<S, G, NL, NT, NR, false><<<grid, NT, 0, st>>>(A);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -26,14 +26,16 @@
 namespace wmg {
 
 // Complex index of stored element k of link (mu, s), storage element type G.
+// (The link arrays hold 4 NL V < 2^32 complex elements: offsets in 32 bits.)
 template <typename G, int NL>
 __host__ __device__ __forceinline__ size_t lidx(int mu, int k, size_t s, size_t V) {
+  const unsigned u = (unsigned)s, W = (unsigned)V;
   if constexpr (sizeof(G) == 4)
-    return k < 4 ? ((((size_t)mu * V + s) << 2) + k) : ((size_t)16 * V + (((size_t)mu * V + s) << 1) + (k - 4));
+    return k < 4 ? (size_t)((((unsigned)mu * W + u) << 2) + k) : (size_t)(16u * W + (((unsigned)mu * W + u) << 1) + (k - 4));
   else if constexpr (sizeof(G) == 8)
-    return ((((size_t)(3 * mu + (k >> 1))) * V + s) << 1) + (k & 1);
+    return (size_t)((((unsigned)(3 * mu + (k >> 1)) * W + u) << 1) + (k & 1));
   else
-    return ((size_t)mu * NL + k) * V + s;
+    return (size_t)(((unsigned)(mu * NL + k)) * W + u);
 }
 
 // ------------------------------------------------------------------ conversions of 4-byte complex words
@@ -131,13 +133,14 @@ __device__ __forceinline__ void st_chunk(S* p, size_t i, const cx<R> (&v)[4]) {
   }
 }
 
-// All 12 components of site s of a level-0 field with V sites.
+// All 12 components of site s of a level-0 field with V sites (offsets within
+// one field in 32-bit arithmetic: 12 V < 2^32).
 template <typename R, typename S>
 __device__ __forceinline__ void ld_spinor(const S* in, size_t V, size_t s, cx<R> (&v)[12]) {
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     cx<R> t[4];
-    ld_chunk<R, S>(in, (j * V + s) << 2, t);
+    ld_chunk<R, S>(in, (size_t)(((unsigned)j * (unsigned)V + (unsigned)s) << 2), t);
 #pragma unroll
     for (int k = 0; k < 4; ++k) v[4 * j + k] = t[k];
   }
