@@ -439,6 +439,60 @@ def dslash_bandwidth(wm, torch, stream, dims=BW_DIMS, precs=None):
     return out
 
 
+# ---------------------------------------------------------------------------- tensor-core contractions
+def mma_workload(args):
+    """The tensor-core contractions alone at the 16^3 x 32 sizes of the batched solve: the level-1
+    coarse stencil (BF16 operator, FP32 vectors, 48 x 48 blocks), the FP16 restriction and prolongation
+    of 24 right-hand sides (P of Nv = 24 on 4^4 aggregates); CUDA events around `reps` launches each,
+    algorithmic bytes as the library's profiler counts them (every operand once per launch)."""
+    import torch
+    from paper_0811_4331_gb300 import wilson_mg as wm
+    stream = torch.cuda.current_stream()
+    U = inputs.heatbath_gauge(C3_DIMS, BETA, HB_SWEEPS, HB_SEED)
+    Ud = torch.from_numpy(U).cuda()
+    p = wm.mg_default_params(n_levels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 24],
+                             setup_sweeps=[args.mma_sweeps, args.mma_sweeps], mixed=1, seed=7, coarse_mma=1)
+    h = wm.mg_setup(Ud, C3_DIMS, C3_MCRIT + args.c3_dm, p, stream=stream)
+    R = args.mma_rhs
+    d1, nc1, _ = wm.mg_level_info(h, 1)
+    V0, V1 = int(np.prod(C3_DIMS)), int(np.prod(d1))
+    fine = wm.internal_empty(h, 0, wm.MG_F16, R)
+    fine.copy_(torch.randn(fine.shape, device="cuda").to(fine.dtype))
+    c_in = wm.internal_empty(h, 1, wm.MG_F32, R)
+    c_in.copy_(torch.randn(c_in.shape, dtype=c_in.dtype, device="cuda"))
+    c_out = wm.internal_empty(h, 1, wm.MG_F32, R)
+    f_out = wm.internal_empty(h, 0, wm.MG_F16, R)
+    nv = 24
+    pbytes = V0 * 12 * nv * 4                     # P once, FP16 complex
+    fbytes, cbytes = V0 * 12 * 4 * R, V1 * nc1 * 8 * R
+    kern = {
+        "coarse_mma": (lambda: wm.coarse_apply(h, 1, wm.MG_F32, c_in, c_out, R, stream),
+                       9 * nc1 * nc1 * 4 * V1 + 2 * cbytes, 9 * nc1 * nc1 * 8 * V1 * R),
+        "restrict_mma": (lambda: wm.restrict_apply(h, 0, wm.MG_F16, fine, c_out, R, stream),
+                         pbytes + fbytes + cbytes, 8 * 12 * nv * V0 * R),
+        "prolong_mma": (lambda: wm.prolong_apply(h, 0, wm.MG_F16, c_in, f_out, R, stream),
+                        pbytes + fbytes + cbytes, 8 * 12 * nv * V0 * R),
+    }
+    peak = measured_peaks()
+    out = {"workload": "16^3x32 beta=6.0 field, 3-level mixed hierarchy (4^4 then 2^4 blocks, Nv=24/24), "
+                       "%d right-hand sides" % R, "rhs": R}
+    for name, (fn, nbytes, flops) in kern.items():
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.mma_reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / args.mma_reps
+        out[name] = {"us": round(t * 1e6, 2), "bytes": int(nbytes), "achieved_gbs": round(nbytes / t / 1e9, 1),
+                     "frac_of_measured_hbm": round(nbytes / t / 1e9 / peak.get("hbm_gbs", 6800.0), 4),
+                     "tflops": round(flops / t / 1e12, 3)}
+    wm.mg_destroy(h)
+    return out
+
+
 # ---------------------------------------------------------------------------- oracle (cpu) arm
 # The FP64 numpy oracle runs the bench step (setup at the lightest mass, then
 # the four masses) on the host cores: a spawn process pool takes the
@@ -828,15 +882,19 @@ def main():
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-full", action="store_true",
                     help="time the whole oracle step (setup + four mass solves to 1e-10) on the host cores and exit")
-    ap.add_argument("--workload", choices=["c2", "c3", "c5", "serve", "dslash"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c3", "c5", "serve", "dslash", "mma"], default="c2",
                     help="c2: the mass-sweep step (default bench line); c3: 24-source batched solve; serve: stream; "
-                         "dslash: the fine stencil alone (--dslash-dims, --dslash-prec)")
+                         "dslash: the fine stencil alone (--dslash-dims, --dslash-prec); mma: the tensor-core "
+                         "contractions alone at the 16^3x32 sizes")
     ap.add_argument("--sweep", choices=["many", "masses"], default="many",
                     help="c2 step: the four masses as concurrent handles (mg_solve_many) or as one solve with a "
                          "mass per right-hand side (mg_solve_masses)")
     ap.add_argument("--dslash-dims", type=int, nargs=4, default=list(BW_DIMS))
     ap.add_argument("--dslash-prec", nargs="+", choices=["f16", "bf16", "f32", "f64"], default=None)
     ap.add_argument("--c3-dm", type=float, default=0.02)
+    ap.add_argument("--mma-rhs", type=int, default=24)
+    ap.add_argument("--mma-reps", type=int, default=20)
+    ap.add_argument("--mma-sweeps", type=int, default=20, help="setup sweeps of the mma workload's hierarchy")
     ap.add_argument("--c5-dm", type=float, nargs="+", default=[0.06, 0.03])
     ap.add_argument("--c5-rhs", type=int, default=12)
     ap.add_argument("--c5-restart", type=int, default=16)
@@ -871,6 +929,9 @@ def main():
         return
     if args.workload == "serve":
         print(json.dumps(serve_workload(args)))
+        return
+    if args.workload == "mma":
+        print(json.dumps(mma_workload(args)))
         return
     if args.workload == "dslash":
         st = torch.cuda.Stream()

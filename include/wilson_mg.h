@@ -111,6 +111,9 @@ typedef struct {
                                          run on the Schur complement S of the even sites (see
                                          schur_apply) from zero, then the odd sites are solved exactly;
                                          needs every lattice extent even */
+  int coarsest_f64;                   /* mixed: 1 = the coarsest inverse in FP64 and the coarsest solve in FP64
+                                         (no refinement); 0 = an FP32 inverse with one FP64 refinement step
+                                         (default).  Plain hierarchies are FP64 throughout */
 } mg_params;
 
 /* Per right-hand side solve statistics. */
@@ -179,7 +182,9 @@ int mg_retarget(const mg_handle* src, double mass, mg_handle** h, void* stream);
  * returned (h[z] = NULL). */
 int mg_retarget_batch(const mg_handle* src, const double* masses, int count, mg_handle** h, void* stream);
 
-/* Free every device buffer of `h` (NULL is allowed). */
+/* Release every device buffer of `h` (NULL is allowed) into the library's
+ * memory cache (mg_trim_cache).  Synchronises the device first: no work on
+ * any stream may still use the handle. */
 int mg_destroy(mg_handle* h);
 
 /* Solve D x_r = b_r for r = 0..nrhs-1 to ||b - D x|| / ||b|| <= tol with
@@ -413,11 +418,18 @@ int mg_tune_report(char* buf, int cap);
  * all handles and threads (a monotonic counter). */
 unsigned long long mg_launch_count(void);
 
-/* Number of device allocations (cudaMalloc calls that succeeded) this library
- * has made since it was loaded, over all handles and threads (a monotonic
- * counter; frees do not lower it).  Lets a caller check that a call allocated
- * nothing. */
+/* Number of device buffers this library has taken since it was loaded, from
+ * the driver or from its cache of freed buffers, over all handles and threads
+ * (a monotonic counter; frees do not lower it).  Lets a caller check that a
+ * call allocated nothing. */
 unsigned long long mg_alloc_count(void);
+
+/* Device memory that handles free (mg_destroy, temporaries) is kept in a
+ * process-wide cache by size class and reused by later handles, so building
+ * hierarchies repeatedly does not call the driver's allocator each time.
+ * mg_trim_cache synchronises the device, hands every cached block back to
+ * the driver and returns the bytes freed.  Call it between solves only. */
+size_t mg_trim_cache(void);
 
 /* Device bytes that mg_setup + mg_solve(nrhs) need for these sizes. */
 size_t mg_footprint(const int dims[4], const mg_params* p, int nrhs);

@@ -516,7 +516,8 @@ const int kTrueResidualEvery = 25;
 const int kCoarsestRefine = 1;
 
 // Exact solve on the coarsest level.  Plain: e = A^-1 r with the FP64
-// inverse.  Mixed: the inverse is FP32; the solve runs in FP64 as
+// inverse.  Mixed: with an FP64 inverse (coarsest_f64) e = A^-1 r in FP64
+// from the converted input; with an FP32 inverse X the solve runs in FP64 as
 // e = X r, then kCoarsestRefine times e += X (r - A e) with the FP64 stencil.
 int coarsest_solve(mg_handle* h, int l, int prec, const void* r, void* e, int nrhs) {
   Level& a = *h->lev[l];
@@ -539,10 +540,11 @@ int coarsest_solve(mg_handle* h, int l, int prec, const void* r, void* e, int nr
     LK(launch_convert(prec, MG_F64, n, nrhs, r, r64, 1.0, nullptr, 0, 0.0, 0, h->st));
   }
   {
-    Prof pf(h, MG_K_COARSEST, MG_F32, mvb);
+    Prof pf(h, MG_K_COARSEST, a.inv_prec, mvb);
     LK(launch_dense_matvec(a.inv_prec, 0, 0, a.N(), inv, r64, e64, nrhs, 0, h->st, a.mm_scratch.p, midx));
   }
-  for (int it = 0; it < kCoarsestRefine; ++it) {
+  const int refine = a.inv_prec == MG_F64 ? 0 : kCoarsestRefine;
+  for (int it = 0; it < refine; ++it) {
     RET(op_apply(h, l, MG_F64, e64, t64, r64, -1.0, 1.0, nullptr, 0, nrhs));
     Prof pf(h, MG_K_COARSEST, MG_F32, mvb + (double)nrhs * a.N() * 16);
     LK(launch_dense_matvec(a.inv_prec, 0, 0, a.N(), inv, t64, e64, nrhs, 1, h->st, a.mm_scratch.p, midx));
@@ -784,14 +786,19 @@ int mg_default_params(mg_params* p) {
 
 int mg_destroy(mg_handle* h) {
   if (!h) return MG_OK;
-  if (h->st) cudaStreamSynchronize(h->st);
+  // the handle's buffers may have served any stream a caller passed: wait for all of them once,
+  // then return the buffers to the cache without a synchronisation each
+  cudaDeviceSynchronize();
   if (h->host_slots) cudaFreeHost(h->host_slots);
   for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  DevIdleScope idle;
   delete h;
   return MG_OK;
 }
+
+size_t mg_trim_cache(void) { return wmg::dev_cache().trim(); }
 
 // Dense inverse of the coarsest level (FP64, or FP32 refined in FP64 in the mixed form).
 // Dense inverse of the coarsest operator of each handle (Sec. 4: exact
@@ -809,7 +816,7 @@ static int build_coarsest_many(mg_handle* const* hs, int count) {
     set_error("coarsest level has " + std::to_string(N) + " unknowns; the dense solve takes at most 8192");
     return MG_EINVAL;
   }
-  const int prec = h0->p.mixed ? MG_F32 : MG_F64;
+  const int prec = (h0->p.mixed && !h0->p.coarsest_f64) ? MG_F32 : MG_F64;
   const size_t eb = bytes_of(prec);
   DevBuf aug, col, errflag, blk;
   const size_t bb = gjb_scratch_bytes((int)N, eb, count);
@@ -863,7 +870,7 @@ static int build_mass_inverses(mg_handle* h, const std::vector<double>& ms) {
     return MG_EINVAL;
   }
   const int count = (int)ms.size();
-  const int prec = h->p.mixed ? MG_F32 : MG_F64;
+  const int prec = (h->p.mixed && !h->p.coarsest_f64) ? MG_F32 : MG_F64;
   const size_t eb = bytes_of(prec), cb = (size_t)9 * c.ncomp * c.ncomp * c.V * 16;
   DevBuf shifted, aug, col, errflag, blk;
   const size_t bb = gjb_scratch_bytes((int)N, eb, count);

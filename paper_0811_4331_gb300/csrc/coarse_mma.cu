@@ -128,11 +128,28 @@ __global__ void coarse_mma_kernel(const uint4* Cf, const S* in, S* out, const S*
 #pragma unroll
     for (int k = 0; k < 4; ++k) accr[q][k] = acci[q][k] = 0.f;
   const uint4* Cs = Cf + (size_t)B * 9 * T * T * 2 * 32;
-  for (int d = 0; d < 9; ++d) {
+  // (d, s) steps in order; the operator fragments of the next two steps are
+  // loaded while the current one runs, so three 512-byte loads per warp stay
+  // in flight (the stencil is bound by the latency of these reads otherwise)
+  const int KS = 9 * T;
+  auto frag = [&](int k) { return ((((size_t)(k / T) * T + t) * T + (k % T)) * 2) * 32 + lane; };
+  uint4 f0r = __ldg(Cs + frag(0)), f0i = __ldg(Cs + frag(0) + 32);
+  uint4 f1r = f0r, f1i = f0i;
+  if (KS > 1) {
+    f1r = __ldg(Cs + frag(1));
+    f1i = __ldg(Cs + frag(1) + 32);
+  }
+  for (int k = 0; k < KS; ++k) {
+    const int d = k / T, s = k - d * T;
     const __nv_bfloat16* Yd = Ys + (size_t)d * Rpad * KW;
-    for (int s = 0; s < T; ++s) {
-      const size_t fo = ((((size_t)d * T + t) * T + s) * 2) * 32 + lane;
-      const uint4 fr = Cs[fo], fi = Cs[fo + 32];
+    const uint4 fr = f0r, fi = f0i;
+    f0r = f1r;
+    f0i = f1i;
+    if (k + 2 < KS) {
+      f1r = __ldg(Cs + frag(k + 2));
+      f1i = __ldg(Cs + frag(k + 2) + 32);
+    }
+    {
       const uint32_t Ar[4] = {fr.x, fr.y, fr.z, fr.w};
       const uint32_t Ai[4] = {fi.x, fi.y, fi.z, fi.w};
       const uint32_t An[4] = {fi.x ^ 0x80008000u, fi.y ^ 0x80008000u, fi.z ^ 0x80008000u, fi.w ^ 0x80008000u};

@@ -3,7 +3,9 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -14,11 +16,73 @@ namespace wmg {
 
 void set_error(const std::string& msg);
 
-// Device allocations the library has made since it was loaded (successful cudaMalloc calls).
+// Device buffers the library has taken since it was loaded, from the driver
+// or from its cache of freed buffers (a monotonic count).
 inline std::atomic<unsigned long long> g_dev_allocs{0};
 
-// Owning device buffer.  The library allocates with cudaMalloc and frees on
-// destruction; nothing is shared between handles.
+// Cache of device memory.  A buffer the library frees goes back to a
+// process-wide list keyed by its size class, and the next buffer of that
+// class is taken from the list instead of from cudaMalloc: a solve that
+// builds and destroys hierarchies (the mass sweep builds five per step) then
+// allocates from the driver only the first time.  A block enters the list
+// only when no GPU work can still use it: release() synchronises the device
+// first (what cudaFree does implicitly), except inside a DevIdleScope, whose
+// creator has already synchronised (mg_destroy).  mg_trim_cache hands the
+// cached blocks back to the driver.
+struct DevCache {
+  std::mutex mu;
+  std::map<size_t, std::vector<void*>> blocks;
+  // size classes: powers of two up to 4 KiB, then eight steps per octave (at most 1/8 unused)
+  static size_t size_class(size_t n) {
+    if (n <= 4096) {
+      size_t c = 256;
+      while (c < n) c <<= 1;
+      return c;
+    }
+    size_t k = 4096;
+    while (k * 2 <= n) k <<= 1;
+    const size_t step = k / 8;
+    return (n + step - 1) / step * step;
+  }
+  void* take(size_t c) {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = blocks.find(c);
+    if (it == blocks.end() || it->second.empty()) return nullptr;
+    void* p = it->second.back();
+    it->second.pop_back();
+    return p;
+  }
+  void give(void* p, size_t c) {
+    std::lock_guard<std::mutex> lk(mu);
+    blocks[c].push_back(p);
+  }
+  // Free every cached block (after a device synchronisation); returns the bytes freed.
+  size_t trim() {
+    cudaDeviceSynchronize();
+    std::lock_guard<std::mutex> lk(mu);
+    size_t freed = 0;
+    for (auto& kv : blocks) {
+      for (void* p : kv.second) cudaFree(p);
+      freed += kv.first * kv.second.size();
+    }
+    blocks.clear();
+    return freed;
+  }
+};
+inline DevCache& dev_cache() {
+  static DevCache* c = new DevCache();  // never destroyed: buffers may be released at process exit
+  return *c;
+}
+inline thread_local bool tl_dev_idle = false;
+// While alive, buffers released on this thread skip the device synchronisation.
+struct DevIdleScope {
+  bool prev;
+  DevIdleScope() : prev(tl_dev_idle) { tl_dev_idle = true; }
+  ~DevIdleScope() { tl_dev_idle = prev; }
+};
+
+// Owning device buffer (capacity `bytes`, a size class of DevCache).  Nothing
+// is shared between handles.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -27,7 +91,10 @@ struct DevBuf {
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (!tl_dev_idle) cudaDeviceSynchronize();
+      dev_cache().give(p, bytes);
+    }
     p = nullptr;
     bytes = 0;
   }
@@ -36,13 +103,19 @@ struct DevBuf {
     if (n <= bytes && p) return true;
     release();
     if (n == 0) n = 16;
-    if (cudaMalloc(&p, n) != cudaSuccess) {
+    const size_t c = DevCache::size_class(n);
+    p = dev_cache().take(c);
+    if (!p && cudaMalloc(&p, c) != cudaSuccess) {
       cudaGetLastError();
-      p = nullptr;
-      return false;
+      dev_cache().trim();  // retry once with the cached blocks handed back
+      if (cudaMalloc(&p, c) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        return false;
+      }
     }
     g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
-    bytes = n;
+    bytes = c;
     return true;
   }
   template <typename T>

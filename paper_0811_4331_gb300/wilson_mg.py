@@ -51,6 +51,7 @@ class mg_params(ctypes.Structure):
         ("adapt_nv", ctypes.c_int * 3),
         ("defer_coarsest", ctypes.c_int),
         ("fine_smoother", ctypes.c_int),
+        ("coarsest_f64", ctypes.c_int),
     ]
 
 
@@ -112,6 +113,7 @@ def _load():
         "mg_profile": (I, [VP, ctypes.c_uint]),
         "mg_launch_count": (ctypes.c_ulonglong, []),
         "mg_alloc_count": (ctypes.c_ulonglong, []),
+        "mg_trim_cache": (ctypes.c_size_t, []),
         "mg_profile_read": (I, [VP, I, I, P(ctypes.c_longlong), P(D)]),
         "mg_profile_bytes": (I, [VP, I, I, P(D)]),
         "mg_tune": (I, [I]),
@@ -130,7 +132,7 @@ LIB = _load()
 EXPORTS = ["mg_last_error", "mg_default_params", "mg_setup", "mg_retarget", "mg_destroy", "mg_solve", "dslash_apply",
            "coarse_apply", "restrict_apply", "prolong_apply", "mr_apply", "vcycle_apply", "mg_field_to_internal",
            "mg_field_from_internal", "mg_level_info", "mg_get_prolongator", "mg_get_coarse_op", "mg_footprint",
-           "mg_profile", "mg_profile_read", "mg_profile_bytes", "mg_launch_count", "mg_alloc_count", "mr_apply_noalloc", "mg_tune",
+           "mg_profile", "mg_profile_read", "mg_profile_bytes", "mg_launch_count", "mg_alloc_count", "mg_trim_cache", "mr_apply_noalloc", "mg_tune",
            "mg_tune_report", "krylov_solve", "mg_retarget_batch", "eo_split", "eo_merge", "dslash_eo_apply",
            "schur_apply", "mg_solve_many", "mg_solve_masses"]
 
@@ -441,8 +443,13 @@ def mg_launch_count():
 
 
 def mg_alloc_count():
-    """Device allocations the library has made since it was loaded."""
+    """Device buffers the library has taken since it was loaded (from the driver or its cache)."""
     return int(LIB.mg_alloc_count())
+
+
+def mg_trim_cache():
+    """Hand the library's cached device memory back to the driver; returns the bytes freed."""
+    return int(LIB.mg_trim_cache())
 
 
 def mg_profile(h, mask):

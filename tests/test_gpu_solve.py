@@ -84,6 +84,7 @@ def test_unpreconditioned_gcr(lu_small):
 
 
 @pytest.mark.parametrize("mixed,extra", [(0, {}), (1, {}), (1, dict(coarse_mma=1)), (1, dict(coarse_prec=2)),
+                                         (1, dict(coarsest_f64=1)),
                                          (1, dict(fine_prec=3, coarse_prec=3))])
 def test_three_level_solve_and_multi_rhs(mixed, extra):
     """Five right-hand sides (the coarsest inverse is applied as one tiled product), every
@@ -181,3 +182,23 @@ def test_four_level_solve(mixed):
     _, st = wm.mg_solve(h, b, x, 1e-10)
     for r in range(3):
         assert _true_rel(U, mass, x[r], b[r]) <= 1e-10, r
+
+
+def test_mixed_coarsest_solve_in_fp64():
+    """coarsest_f64 = 1: the mixed hierarchy's coarsest solve is A^-1 r with an FP64 inverse; the
+    solve reaches the tolerance with the iteration count of the FP32-inverse form within 2."""
+    wm = require_gpu()
+    dims = (4, 4, 4, 4)
+    mass = 0.1
+    U = inputs.random_gauge(dims, 0)
+    b = inputs.gaussian_spinor(dims, 1)
+    its = {}
+    for f64 in (0, 1):
+        p = wm.mg_default_params(n_levels=2, block=[(2, 2, 2, 2)], nv=[8], setup_sweeps=[10], mixed=1,
+                                 coarsest_f64=f64)
+        h = wm.mg_setup(U, dims, mass, p)
+        x = np.zeros_like(b)
+        _, st = wm.mg_solve(h, b, x, 1e-10)
+        assert _true_rel(U, mass, x, b) <= 1e-10
+        its[f64] = st[0]["iters"]
+    assert abs(its[1] - its[0]) <= 2, its
