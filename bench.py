@@ -508,7 +508,7 @@ ORACLE_SAMPLE = ("FP64 numpy oracle on the same inputs, spawn process pool (one 
                  "relaxation, then one per mass): %d of the %d setup MR sweeps of all %d candidates, block QR + "
                  "Galerkin P^+DP + dense LU per mass, %d outer MG-GCR iterations per mass; value = relaxation "
                  "wall x %d/%d + max over the masses of (QR/Galerkin/LU + oracle iteration count from "
-                 "tests/golden/c2_reference.json x time per iteration)"
+                 "tests/golden/c2_reference.json, sweep form, x time per iteration)"
                  % (SWEEPS_SAMPLE, SETUP_SWEEPS, NV, ITERS_SAMPLE, SETUP_SWEEPS, SWEEPS_SAMPLE))
 
 _ORACLE_U = None
@@ -575,9 +575,10 @@ def _oracle_mass(job):
 
 
 def oracle_iters():
+    """The oracle's own MG-GCR iteration counts of the step's form (setup at the lightest mass)."""
     with open(os.path.join(ROOT, "tests", "golden", "c2_reference.json")) as f:
         ref = json.load(f)
-    return [m["iters"] for m in ref["masses"]]
+    return [m["iters"] for m in ref["sweep"]["masses"]]
 
 
 def oracle_step(pool, nproc, full=False):
