@@ -431,6 +431,10 @@ unsigned long long mg_alloc_count(void);
  * the driver and returns the bytes freed.  Call it between solves only. */
 size_t mg_trim_cache(void);
 
+/* Device bytes the handle holds now (hierarchy, work vectors, solver
+ * buffers; capacities of its buffers), for admission by memory budget. */
+size_t mg_handle_bytes(const mg_handle* h);
+
 /* Device bytes that mg_setup + mg_solve(nrhs) need for these sizes. */
 size_t mg_footprint(const int dims[4], const mg_params* p, int nrhs);
 

@@ -47,6 +47,7 @@ using namespace wmg;
     count_launches(1);                                                                 \
     if ((x) != 0) {                                                                    \
       cudaError_t e_ = cudaGetLastError();                                             \
+      if (e_ == cudaSuccess) e_ = take_launch_error();                                 \
       set_error(std::string("launch failed: ") + #x + ": " + cudaGetErrorString(e_));  \
       return e_ == cudaSuccess ? MG_EINVAL : MG_ECUDA;                                 \
     }                                                                                  \
@@ -710,19 +711,26 @@ int vcycle_graph(mg_handle* h, const void* r, void* e, int nrhs) {
   h->capturing = true;
   cudaGraph_t graph = nullptr;
   int rc = MG_OK;
-  cudaError_t ce = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal);
-  if (ce == cudaSuccess) {
-    rc = vcycle(h, 0, r, e, nrhs);
-    ce = cudaStreamEndCapture(h->cap_st, &graph);
+  cudaError_t ce;
+  {
+    // no device-wide synchronisation (which would invalidate the capture) while it runs
+    std::shared_lock<std::shared_mutex> nosync(g_capture_mu);
+    ce = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+      rc = vcycle(h, 0, r, e, nrhs);
+      ce = cudaStreamEndCapture(h->cap_st, &graph);
+    }
   }
   h->capturing = false;
   h->st = keep;
   const unsigned long long nodes = mg_launch_count() - n0;
   if (ce != cudaSuccess || rc != MG_OK || gen != h->buf_gen) {
+    // the eager run above already produced e; a capture that failed only costs the graph
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
+    take_launch_error();
     h->use_graphs = false;  // fall back to eager launches for this handle
-    return rc != MG_OK ? rc : MG_OK;
+    return MG_OK;
   }
   cudaGraphExec_t exec = nullptr;
   ce = cudaGraphInstantiate(&exec, graph, 0);
@@ -743,6 +751,32 @@ int vcycle_graph(mg_handle* h, const void* r, void* e, int nrhs) {
   }
   h->graphs.push_back({h->mm_active, nrhs, r, e, gen, nodes, exec});
   return MG_OK;
+}
+
+// Pinned host mirrors of the reduction slots, reused across handles (freeing
+// pinned memory synchronises the device, which a graph capture on another
+// thread must not see).
+std::mutex g_host_slots_mu;
+std::vector<double*> g_host_slots;
+double* take_host_slots() {
+  {
+    std::lock_guard<std::mutex> lk(g_host_slots_mu);
+    if (!g_host_slots.empty()) {
+      double* p = g_host_slots.back();
+      g_host_slots.pop_back();
+      return p;
+    }
+  }
+  double* p = nullptr;
+  if (cudaMallocHost((void**)&p, slot_total() * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+void give_host_slots(double* p) {
+  std::lock_guard<std::mutex> lk(g_host_slots_mu);
+  g_host_slots.push_back(p);
 }
 
 int read_slots(mg_handle* h, size_t off, int count) {
@@ -787,18 +821,61 @@ int mg_default_params(mg_params* p) {
 int mg_destroy(mg_handle* h) {
   if (!h) return MG_OK;
   // the handle's buffers may have served any stream a caller passed: wait for all of them once,
-  // then return the buffers to the cache without a synchronisation each
-  cudaDeviceSynchronize();
-  if (h->host_slots) cudaFreeHost(h->host_slots);
+  // then return the buffers to the cache without a synchronisation each (if the synchronisation
+  // fails, every buffer takes the cautious path of DevBuf::release)
+  bool synced = false;
+  {
+    std::unique_lock<std::shared_mutex> nocapture(g_capture_mu, std::try_to_lock);
+    if (nocapture.owns_lock()) synced = cudaDeviceSynchronize() == cudaSuccess;
+  }
+  if (!synced) {
+    cudaGetLastError();
+    if (h->st) cudaStreamSynchronize(h->st);  // at least the handle's own stream; buffers take the cautious path
+  }
+  if (h->host_slots) give_host_slots(h->host_slots);
   for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
-  DevIdleScope idle;
-  delete h;
+  if (synced) {
+    DevIdleScope idle;
+    delete h;
+  } else {
+    delete h;
+  }
+  cudaGetLastError();
   return MG_OK;
 }
 
 size_t mg_trim_cache(void) { return wmg::dev_cache().trim(); }
+
+size_t mg_handle_bytes(const mg_handle* h) {
+  if (!h) return 0;
+  size_t b = 0;
+  auto add = [&](const DevBuf& d) { b += d.p ? d.bytes : 0; };
+  for (const auto& lp : h->lev) {
+    const Level& a = *lp;
+    for (int q = 0; q < 4; ++q) {
+      add(a.links[q]);
+      add(a.links_eo[q]);
+      add(a.cop[q]);
+      add(a.P[q]);
+    }
+    add(a.cop_mma);
+    add(a.inv);
+    add(a.mm_scratch);
+  }
+  for (const auto& byprec : h->work)
+    for (const auto& vecs : byprec)
+      for (const auto& v : vecs)
+        if (v) add(*v);
+  add(h->red.partials);
+  add(h->red.tickets);
+  add(h->red.slots);
+  for (const DevBuf* d : {&h->gr, &h->gW, &h->gZ, &h->gb64, &h->gx64, &h->gr64, &h->gtmp, &h->gH, &h->galpha, &h->gy,
+                          &h->err_flag, &h->mm_adiag, &h->mm_shift, &h->mm_idx, &h->mm_inv})
+    add(*d);
+  return b;
+}
 
 // Dense inverse of the coarsest level (FP64, or FP32 refined in FP64 in the mixed form).
 // Dense inverse of the coarsest operator of each handle (Sec. 4: exact
@@ -844,6 +921,7 @@ static int build_coarsest_many(mg_handle* const* hs, int count) {
   std::vector<int> herr(count, 0);
   CK(cudaMemcpyAsync(herr.data(), errflag.p, sizeof(int) * count, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  for (DevBuf* t : {&aug, &col, &errflag, &blk}) t->release_idle();  // their only stream is done
   for (int z = 0; z < count; ++z)
     if (herr[z]) {
       set_error("coarsest operator is singular (zero pivot)");
@@ -899,6 +977,7 @@ static int build_mass_inverses(mg_handle* h, const std::vector<double>& ms) {
   std::vector<int> herr(count, 0);
   CK(cudaMemcpyAsync(herr.data(), errflag.p, sizeof(int) * count, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  for (DevBuf* t : {&shifted, &aug, &col, &errflag, &blk}) t->release_idle();  // their only stream is done
   for (int z = 0; z < count; ++z)
     if (herr[z]) {
       set_error("coarsest operator is singular (zero pivot) at one of the masses");
@@ -1306,7 +1385,7 @@ int mg_setup(mg_handle** hout, const double* gauge, int gauge_on_device, const i
   h->st = (cudaStream_t)stream;
   h->use_graphs = p->use_graphs != 0;
   h->prof_mask = __atomic_load_n(&g_default_prof_mask, __ATOMIC_RELAXED);
-  if (cudaMallocHost((void**)&h->host_slots, slot_total() * sizeof(double)) != cudaSuccess) {
+  if ((h->host_slots = take_host_slots()) == nullptr) {
     cudaGetLastError();
     delete h;
     set_error("pinned host allocation failed");
@@ -1383,7 +1462,7 @@ int mg_retarget(const mg_handle* src, double mass, mg_handle** hout, void* strea
   h->st = (cudaStream_t)stream;
   h->use_graphs = src->use_graphs;
   h->prof_mask = __atomic_load_n(&g_default_prof_mask, __ATOMIC_RELAXED);
-  if (cudaMallocHost((void**)&h->host_slots, slot_total() * sizeof(double)) != cudaSuccess) {
+  if ((h->host_slots = take_host_slots()) == nullptr) {
     cudaGetLastError();
     delete h;
     set_error("pinned host allocation failed");
@@ -1425,7 +1504,7 @@ int mg_retarget_batch(const mg_handle* src, const double* masses, int count, mg_
     h->use_graphs = src->use_graphs;
     h->prof_mask = __atomic_load_n(&g_default_prof_mask, __ATOMIC_RELAXED);
     hs.push_back(h);
-    if (cudaMallocHost((void**)&h->host_slots, slot_total() * sizeof(double)) != cudaSuccess) {
+    if ((h->host_slots = take_host_slots()) == nullptr) {
       cudaGetLastError();
       set_error("pinned host allocation failed");
       return fail(MG_ENOMEM);
@@ -1789,6 +1868,7 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
     LK(launch_ext_to_int(MG_F64, 12, 4, f.V, nrhs, bsrc, h->gb64.p, st));
     LK(launch_ext_to_int(MG_F64, 12, 4, f.V, nrhs, xsrc, h->gx64.p, st));
     CK(cudaStreamSynchronize(st));
+    stage.release_idle();
   }
   // Krylov buffers in precision pin: basis W, Z [restart][nrhs][n], x, r
   const size_t vbytes = n * nrhs * bi;
@@ -1944,6 +2024,7 @@ int gcr_solve(mg_handle* h, const double* b_ext, double* x_ext, int nrhs, int on
     LK(launch_int_to_ext(MG_F64, 12, 4, f.V, nrhs, h->gx64.p, dst, st));
     if (!on_device) CK(cudaMemcpyAsync(x_ext, stage.p, n * nrhs * 16, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    stage.release_idle();
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats) {

@@ -23,7 +23,7 @@ int vec_blocks(size_t n) {
   return (int)b;
 }
 
-static inline bool launched() { return cudaGetLastError() == cudaSuccess; }
+static inline bool launched() { return launch_ok(); }
 
 // Blocks of the dot kernels: at least 8 elements per thread, at most one block per SM.
 int red_blocks(size_t n) {

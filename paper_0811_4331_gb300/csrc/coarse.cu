@@ -16,7 +16,7 @@
 
 namespace wmg {
 
-static inline bool launched() { return cudaGetLastError() == cudaSuccess; }
+static inline bool launched() { return launch_ok(); }
 
 // ------------------------------------------------------------------ apply
 template <typename S>

@@ -21,7 +21,7 @@
 
 namespace wmg {
 
-static inline bool launched() { return cudaGetLastError() == cudaSuccess; }
+static inline bool launched() { return launch_ok(); }
 
 // ------------------------------------------------------------------ operator in fragment order
 // One thread per (B, d, tile, kstep, part, lane): 8 bf16 of the A fragment

@@ -9,6 +9,21 @@
 
 namespace wmg {
 
+// Launch checks: a launcher reads (and so clears) the thread's last CUDA error
+// right after its launch; the error is kept here so that the caller's message
+// names it.
+inline thread_local cudaError_t tl_launch_error = cudaSuccess;
+inline bool launch_ok() {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) tl_launch_error = e;
+  return e == cudaSuccess;
+}
+inline cudaError_t take_launch_error() {
+  const cudaError_t e = tl_launch_error;
+  tl_launch_error = cudaSuccess;
+  return e;
+}
+
 // Dynamic shared memory above 48 KB needs a per-kernel opt-in.  The attribute
 // is global to the kernel, so a value chosen per launch would race between
 // host threads launching the same kernel with different sizes; every caller

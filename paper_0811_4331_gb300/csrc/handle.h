@@ -6,6 +6,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <shared_mutex>
 #include <string>
 #include <vector>
 
@@ -15,6 +16,11 @@
 namespace wmg {
 
 void set_error(const std::string& msg);
+
+// Graph captures hold this shared; a device-wide synchronisation (which would
+// invalidate a capture running on another thread) needs it exclusively and is
+// skipped when it cannot have it at once.
+inline std::shared_mutex g_capture_mu;
 
 // Device buffers the library has taken since it was loaded, from the driver
 // or from its cache of freed buffers (a monotonic count).
@@ -26,12 +32,17 @@ inline std::atomic<unsigned long long> g_dev_allocs{0};
 // builds and destroys hierarchies (the mass sweep builds five per step) then
 // allocates from the driver only the first time.  A block enters the list
 // only when no GPU work can still use it: release() synchronises the device
-// first (what cudaFree does implicitly), except inside a DevIdleScope, whose
-// creator has already synchronised (mg_destroy).  mg_trim_cache hands the
+// first (what cudaFree does implicitly) and, if that synchronisation fails,
+// holds the block back until a later one succeeds; inside a DevIdleScope,
+// whose creator has synchronised, blocks go back at once (mg_destroy, and
+// temporaries whose stream was synchronised).  mg_trim_cache hands the
 // cached blocks back to the driver.
 struct DevCache {
   std::mutex mu;
   std::map<size_t, std::vector<void*>> blocks;
+  // blocks released when a device synchronisation failed (e.g. while another thread was capturing a
+  // graph): they join `blocks` after the next successful one
+  std::vector<std::pair<void*, size_t>> pending;
   // size classes: powers of two up to 4 KiB, then eight steps per octave (at most 1/8 unused)
   static size_t size_class(size_t n) {
     if (n <= 4096) {
@@ -56,9 +67,28 @@ struct DevCache {
     std::lock_guard<std::mutex> lk(mu);
     blocks[c].push_back(p);
   }
+  // A block that work still queued on any stream may use: reusable once the device has synchronised.
+  void give_after_sync(void* p, size_t c) {
+    bool synced = false;
+    {
+      std::unique_lock<std::shared_mutex> nocapture(g_capture_mu, std::try_to_lock);
+      if (nocapture.owns_lock()) synced = cudaDeviceSynchronize() == cudaSuccess;
+    }
+    if (!synced) cudaGetLastError();  // leave no error behind for this thread's next launch check
+    std::lock_guard<std::mutex> lk(mu);
+    if (synced) {
+      for (auto& q : pending) blocks[q.second].push_back(q.first);
+      pending.clear();
+      blocks[c].push_back(p);
+    } else {
+      pending.push_back({p, c});
+    }
+  }
   // Free every cached block (after a device synchronisation); returns the bytes freed.
   size_t trim() {
-    cudaDeviceSynchronize();
+    std::unique_lock<std::shared_mutex> nocapture(g_capture_mu);
+    const bool synced = cudaDeviceSynchronize() == cudaSuccess;
+    if (!synced) cudaGetLastError();
     std::lock_guard<std::mutex> lk(mu);
     size_t freed = 0;
     for (auto& kv : blocks) {
@@ -66,6 +96,13 @@ struct DevCache {
       freed += kv.first * kv.second.size();
     }
     blocks.clear();
+    if (synced) {
+      for (auto& q : pending) {
+        cudaFree(q.first);
+        freed += q.second;
+      }
+      pending.clear();
+    }
     return freed;
   }
 };
@@ -92,9 +129,17 @@ struct DevBuf {
   ~DevBuf() { release(); }
   void release() {
     if (p) {
-      if (!tl_dev_idle) cudaDeviceSynchronize();
-      dev_cache().give(p, bytes);
+      if (tl_dev_idle)
+        dev_cache().give(p, bytes);
+      else
+        dev_cache().give_after_sync(p, bytes);
     }
+    p = nullptr;
+    bytes = 0;
+  }
+  // Release after the caller has synchronised every stream that used the buffer.
+  void release_idle() {
+    if (p) dev_cache().give(p, bytes);
     p = nullptr;
     bytes = 0;
   }

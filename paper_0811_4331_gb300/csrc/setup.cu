@@ -16,7 +16,7 @@
 
 namespace wmg {
 
-static inline bool launched() { return cudaGetLastError() == cudaSuccess; }
+static inline bool launched() { return launch_ok(); }
 
 __device__ __forceinline__ int agg_site2(const Agg& g, int B, int s) {
   int cb[4], cl[4], cf[4];

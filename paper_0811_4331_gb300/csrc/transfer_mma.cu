@@ -28,7 +28,7 @@
 
 namespace wmg {
 
-static inline bool launched() { return cudaGetLastError() == cudaSuccess; }
+static inline bool launched() { return launch_ok(); }
 
 template <typename T>
 struct MmaT;

@@ -491,11 +491,11 @@ static int launch_mr_t(const DslashCall& d, const MrFuseArgs& F, cudaStream_t st
   if constexpr (NL != 9) {
     if ((size_t)A.V * d.nrhs <= (size_t)kSmallSites) {  // the same split as the unfused stencil
       wilson_small_mr_kernel<S, G, NL><<<dim3((A.V + 31) / 32, d.nrhs), 256, 0, st>>>(A, F);
-      return cudaGetLastError() == cudaSuccess ? 0 : -1;
+      return launch_ok() ? 0 : -1;
     }
   }
   wilson_mr_kernel<S, G, NL, 128><<<dim3((A.V + 127) / 128, d.nrhs), 128, 0, st>>>(A, F);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return launch_ok() ? 0 : -1;
 }
 
 template <typename S, typename G, int NL, int NT, int NR>
@@ -509,7 +509,7 @@ static int launch_nt(const WilsonArgs<S, G, NL>& A, int nrhs, cudaStream_t st) {
     else
       wilson_kernel<S, G, NL, NT, NR, false><<<grid, NT, 0, st>>>(A);
   }
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return launch_ok() ? 0 : -1;
 }
 
 // Launch shapes (threads per CTA NT, right-hand sides per thread NR), in the
@@ -551,7 +551,7 @@ static int launch_t(const DslashCall& d, cudaStream_t st) {
     if ((size_t)A.V * d.nrhs <= (size_t)kSmallSites) {  // small lattice: a warp per hop
       dim3 grid((A.V + 31) / 32, d.nrhs);
       wilson_small_kernel<S, G, NL><<<grid, 256, 0, st>>>(A);
-      return cudaGetLastError() == cudaSuccess ? 0 : -1;
+      return launch_ok() ? 0 : -1;
     }
     WShape sh = {128, 1};
     if (d.variant >= 0 && d.variant < wilson_variants(1, d.z != nullptr, d.nrhs, A.V))
@@ -656,7 +656,7 @@ int launch_su3_check(const void* ext, int V, unsigned* worst, cudaStream_t st) {
   size_t nb = (n + 255) / 256;
   if (nb > 1216) nb = 1216;
   su3_check_kernel<<<(unsigned)(nb < 1 ? 1 : nb), 256, 0, st>>>((const double2*)ext, n, worst);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return launch_ok() ? 0 : -1;
 }
 
 int launch_pack_links(int prec, const void* ext, void* out, int V, cudaStream_t st) {
@@ -673,7 +673,7 @@ int launch_pack_links(int prec, const void* ext, void* out, int V, cudaStream_t 
       break;
     default: return -1;
   }
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return launch_ok() ? 0 : -1;
 }
 
 }  // namespace wmg

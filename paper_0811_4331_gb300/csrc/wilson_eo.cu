@@ -27,7 +27,7 @@
 
 namespace wmg {
 
-static inline bool launched() { return cudaGetLastError() == cudaSuccess; }
+static inline bool launched() { return launch_ok(); }
 
 template <typename S, typename G, int NL>
 struct EoArgs {

@@ -3,15 +3,21 @@
 Requests -- (gauge field, mass, 1..12 right-hand sides, tolerance) -- arrive
 while others are running.  The server keeps, per gauge field, one resident
 multigrid hierarchy (the null-vector setup of Sec. 2, done once on the first
-request for that field) and serves every request from it through
+request for that field) and, per worker, a private copy of it made by
 ``mg_retarget``: D(m) = D(0) + m 1 has the same eigenvectors at every mass
-(Sec. 1) and P^+ P = 1 (Eq. 2.3), so the coarse operators of another mass are
-the cached ones shifted on the diagonal; only the coarsest inverse is
-rebuilt.  A request is admitted when a worker is free and the device bytes in
-flight plus its own (``mg_footprint``) stay within the HBM budget; each worker
-owns a CUDA stream, so admitted requests overlap on the GPU.  All arithmetic
-runs in the library's kernels; results do not depend on what else is running
-(every reduction is per handle and deterministic).
+(Sec. 1) and P^+ P = 1 (Eq. 2.3), so the coarse operators of any mass are the
+cached ones shifted on the diagonal.  A free worker takes the oldest waiting
+request and merges into it the waiting requests of the same field, up to 64
+right-hand sides, and runs them as one ``mg_solve_masses`` call (a mass per
+right-hand side: every kernel of the solve processes the whole batch, and one
+coarsest inverse per distinct mass is built in shared launches).  A batch is
+admitted while the device bytes of the resident hierarchies, of the batches
+in flight (``mg_footprint``) and its own stay within the HBM budget; each
+worker owns a CUDA stream, so batches overlap on the GPU.  All arithmetic
+runs in the library's kernels.  A request's result meets its tolerance
+whether it is solved alone or in a batch (the batch's outer solve stops when
+every right-hand side has converged, so a result solved in a batch can
+differ from the one solved alone by the solve's own error, not more).
 """
 import collections
 import threading
@@ -43,27 +49,33 @@ class Request:
 
 
 class SolveServer:
-    """Admit, run and complete solve requests on one GPU.
+    """Admit, batch, run and complete solve requests on one GPU.
 
     fields: {name: (gauge numpy array, dims, setup_mass[, mg_params])}; params:
-    the mg_params of fields that bring none; hbm_budget: device bytes the
-    in-flight requests may use; workers: maximum number of concurrent requests
-    (one CUDA stream each).
+    the mg_params of fields that bring none; hbm_budget: device bytes for the
+    resident hierarchies plus the batches in flight; workers: maximum number
+    of concurrent batches (one CUDA stream each); max_batch_rhs: right-hand
+    sides per batch (1..64); merge: False serves every request alone.
     """
 
-    def __init__(self, fields, params, hbm_budget, workers=4):
+    def __init__(self, fields, params, hbm_budget, workers=4, max_batch_rhs=64, merge=True):
         import torch
         self.torch = torch
         self.fields = fields
         self.params = params
         self.budget = int(hbm_budget)
+        self.max_batch_rhs = int(max_batch_rhs)
+        self.merge = merge
         self.inflight_bytes = 0
         self.inflight = 0
         self.max_inflight = 0
         self.max_inflight_bytes = 0
+        self.resident_bytes = 0
+        self.batches = []  # sizes (requests, right-hand sides) of the batches run
         self.queue = collections.deque()
         self.lock = threading.Condition()
         self.bases = {}
+        self.copies = {}
         self.base_lock = threading.Lock()
         self.completed = []
         self.stop = False
@@ -77,10 +89,15 @@ class SolveServer:
         f = self.fields[field]
         return f[3] if len(f) > 3 else self.params
 
+    @staticmethod
+    def nrhs_of(req):
+        return req.b.shape[0] if req.b.ndim == 7 else 1
+
+    def footprint(self, field, nrhs):
+        return wm.mg_footprint(self.fields[field][1], self.params_of(field), nrhs)
+
     def submit(self, req):
-        dims = self.fields[req.field][1]
-        nrhs = req.b.shape[0] if req.b.ndim == 7 else 1
-        req.footprint = wm.mg_footprint(dims, self.params_of(req.field), nrhs)
+        req.footprint = self.footprint(req.field, self.nrhs_of(req))
         if req.footprint > self.budget:
             req.error = "request needs %d bytes, budget is %d" % (req.footprint, self.budget)
             req.done = time.perf_counter()
@@ -97,6 +114,7 @@ class SolveServer:
             self.lock.notify_all()
         for t in self.workers:
             t.join()
+        self.copies.clear()
         self.bases.clear()
 
     def base(self, field):
@@ -108,54 +126,109 @@ class SolveServer:
                 h = wm.mg_setup(U, dims, m0, self.params_of(field), stream=self.torch.cuda.current_stream())
                 self.torch.cuda.synchronize()
                 self.bases[field] = h
+                with self.lock:
+                    self.resident_bytes += wm.mg_handle_bytes(h)
             return h
+
+    def copy(self, wid, field, stream):
+        """Worker wid's private copy of the field's hierarchy (a handle serves one thread at a time)."""
+        key = (wid, field)
+        h = self.copies.get(key)
+        if h is None:
+            base = self.base(field)
+            with self.base_lock:
+                h = wm.mg_retarget(base, self.fields[field][2], stream=stream)
+            self.copies[key] = h
+            with self.lock:
+                self.resident_bytes += wm.mg_handle_bytes(h)
+        return h
 
     # ------------------------------------------------------------------ workers
     def _admit(self):
-        """Next request (FIFO) whose footprint fits the free budget, or None."""
+        """The next batch: the oldest waiting request whose footprint fits the free budget, with the
+        waiting requests of its field merged in (oldest first) while the batch stays within
+        max_batch_rhs right-hand sides and the budget; None when the oldest does not fit."""
         if not self.queue:
             return None
-        req = self.queue[0]
-        if self.inflight_bytes + req.footprint > self.budget:
+        head = self.queue[0]
+        free = self.budget - self.resident_bytes - self.inflight_bytes
+        if head.footprint > free:
+            if self.inflight == 0:  # the resident hierarchies alone leave it no room: it would wait forever
+                self.queue.popleft()
+                head.error = "request needs %d bytes, %d of the budget %d are left beside the resident " \
+                             "hierarchies" % (head.footprint, free, self.budget)
+                head.done = time.perf_counter()
+                head.event.set()
             return None
-        self.queue.popleft()
-        self.inflight_bytes += req.footprint
+        batch, nrhs = [head], self.nrhs_of(head)
+        if self.merge:
+            for req in list(self.queue)[1:]:
+                k = self.nrhs_of(req)
+                if req.field == head.field and nrhs + k <= self.max_batch_rhs and \
+                        self.footprint(head.field, nrhs + k) <= free:
+                    batch.append(req)
+                    nrhs += k
+        for req in batch:
+            self.queue.remove(req)
+        fp = self.footprint(head.field, nrhs)
+        for req in batch:
+            req.footprint = fp if req is head else 0
+        self.inflight_bytes += fp
         self.inflight += 1
         self.max_inflight = max(self.max_inflight, self.inflight)
         self.max_inflight_bytes = max(self.max_inflight_bytes, self.inflight_bytes)
-        return req
+        self.batches.append((len(batch), nrhs))
+        return batch
+
+    def _run(self, wid, batch, stream):
+        """One batch: every right-hand side of every request in one solve, a mass per right-hand side."""
+        field = batch[0].field
+        h = self.copy(wid, field, stream)
+        bs = [r.b if r.b.ndim == 7 else r.b[None] for r in batch]
+        masses = [r.mass for r, b in zip(batch, bs) for _ in range(b.shape[0])]
+        B = np.ascontiguousarray(np.concatenate(bs)) if len(bs) > 1 else np.ascontiguousarray(bs[0])
+        X = np.zeros_like(B)
+        status, st = wm.mg_solve_masses(h, masses, B, X, min(r.tol for r in batch), stream=stream,
+                                        raise_on_noconv=False)
+        k = 0
+        for r, b in zip(batch, bs):
+            n = b.shape[0]
+            r.x = X[k:k + n] if r.b.ndim == 7 else X[k]
+            r.stats = st[k:k + n]
+            if status != wm.MG_OK:
+                r.error = wm.STATUS_NAMES[status]
+            k += n
 
     def _worker(self, wid):
         torch = self.torch
         stream = self.streams[wid]
         while True:
             with self.lock:
-                req = self._admit()
-                while req is None:
+                batch = self._admit()
+                while batch is None:
                     if self.stop and not self.queue:
                         return
                     self.lock.wait(0.01)
-                    req = self._admit()
-            req.admitted = time.perf_counter()
+                    batch = self._admit()
+            t = time.perf_counter()
+            for req in batch:
+                req.admitted = t
             try:
-                base = self.base(req.field)
                 with torch.cuda.stream(stream):
-                    h = wm.mg_retarget(base, req.mass, stream=stream)
-                    x = np.zeros_like(req.b)
-                    status, st = wm.mg_solve(h, req.b, x, req.tol, stream=stream, raise_on_noconv=False)
-                    wm.mg_destroy(h)
-                req.x, req.stats = x, st
-                if status != wm.MG_OK:
-                    req.error = wm.STATUS_NAMES[status]
-            except Exception as e:  # a failed request must not stop the server
-                req.error = str(e)
-            req.done = time.perf_counter()
+                    self._run(wid, batch, stream)
+            except Exception as e:  # a failed batch must not stop the server
+                for req in batch:
+                    req.error = str(e)
+            t = time.perf_counter()
             with self.lock:
-                self.inflight_bytes -= req.footprint
+                for req in batch:
+                    req.done = t
+                    self.inflight_bytes -= req.footprint
+                    self.completed.append(req)
                 self.inflight -= 1
-                self.completed.append(req)
                 self.lock.notify_all()
-            req.event.set()
+            for req in batch:
+                req.event.set()
 
 
 def poisson_arrivals(rate, n, seed):

@@ -114,6 +114,7 @@ def _load():
         "mg_launch_count": (ctypes.c_ulonglong, []),
         "mg_alloc_count": (ctypes.c_ulonglong, []),
         "mg_trim_cache": (ctypes.c_size_t, []),
+        "mg_handle_bytes": (ctypes.c_size_t, [VP]),
         "mg_profile_read": (I, [VP, I, I, P(ctypes.c_longlong), P(D)]),
         "mg_profile_bytes": (I, [VP, I, I, P(D)]),
         "mg_tune": (I, [I]),
@@ -131,8 +132,9 @@ LIB = _load()
 # every entry point declared in include/wilson_mg.h
 EXPORTS = ["mg_last_error", "mg_default_params", "mg_setup", "mg_retarget", "mg_destroy", "mg_solve", "dslash_apply",
            "coarse_apply", "restrict_apply", "prolong_apply", "mr_apply", "vcycle_apply", "mg_field_to_internal",
-           "mg_field_from_internal", "mg_level_info", "mg_get_prolongator", "mg_get_coarse_op", "mg_footprint",
-           "mg_profile", "mg_profile_read", "mg_profile_bytes", "mg_launch_count", "mg_alloc_count", "mg_trim_cache", "mr_apply_noalloc", "mg_tune",
+           "mg_field_from_internal", "mg_level_info", "mg_get_prolongator", "mg_get_coarse_op",
+           "mg_footprint", "mg_profile", "mg_profile_read", "mg_profile_bytes",
+           "mg_launch_count", "mg_alloc_count", "mg_trim_cache", "mg_handle_bytes", "mr_apply_noalloc", "mg_tune",
            "mg_tune_report", "krylov_solve", "mg_retarget_batch", "eo_split", "eo_merge", "dslash_eo_apply",
            "schur_apply", "mg_solve_many", "mg_solve_masses"]
 
@@ -445,6 +447,11 @@ def mg_launch_count():
 def mg_alloc_count():
     """Device buffers the library has taken since it was loaded (from the driver or its cache)."""
     return int(LIB.mg_alloc_count())
+
+
+def mg_handle_bytes(h):
+    """Device bytes the handle holds now."""
+    return int(LIB.mg_handle_bytes(h.ptr))
 
 
 def mg_trim_cache():

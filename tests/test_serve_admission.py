@@ -1,9 +1,10 @@
-"""Host-side admission of the solve server, on CPU (no device work).
+"""Host-side admission and batching of the solve server, on CPU (no device work).
 
-The server admits requests first-in first-out while the device bytes in flight plus the head request's
-footprint (mg_footprint, a host computation) stay within the HBM budget; a request larger than the whole
-budget is refused at submission.  The object is built without its worker threads and streams, so the
-real submit/_admit code runs with nothing on a GPU.
+The server admits the oldest waiting request while the device bytes of the resident hierarchies and of
+the batches in flight plus its footprint (mg_footprint, a host computation) stay within the HBM budget,
+and merges into it the waiting requests of the same field (oldest first) up to the batch's right-hand-side
+limit and the budget; a request larger than the whole budget is refused at submission.  The object is
+built without its worker threads and streams, so the real submit/_admit code runs with nothing on a GPU.
 """
 import collections
 import os
@@ -25,10 +26,13 @@ def serve_mod():
     return serve
 
 
-def _server(serve, budget, fields, params):
+def _server(serve, budget, fields, params, merge=False, max_batch_rhs=64, resident=0):
     s = object.__new__(serve.SolveServer)
     s.fields, s.params, s.budget = fields, params, int(budget)
     s.inflight_bytes = s.inflight = s.max_inflight = s.max_inflight_bytes = 0
+    s.resident_bytes = resident
+    s.merge, s.max_batch_rhs = merge, max_batch_rhs
+    s.batches = []
     s.queue = collections.deque()
     s.lock = threading.Condition()
     return s
@@ -52,14 +56,14 @@ def test_fifo_admission_within_the_budget(serve_mod):
     for r in reqs:
         s.submit(r)
     assert [r.footprint for r in reqs] == [f4, f1, f4, f1]
-    a = s._admit()
-    b = s._admit()
+    (a,) = s._admit()
+    (b,) = s._admit()
     assert (a.rid, b.rid) == (0, 1) and s.inflight_bytes == f4 + f1
     assert s._admit() is None            # the head (a 4-RHS request) waits for room
     assert [r.rid for r in s.queue] == [2, 3]  # first in, first out: no request overtakes the head
     s.inflight_bytes -= a.footprint      # request 0 completes
     s.inflight -= 1
-    c = s._admit()
+    (c,) = s._admit()
     assert c.rid == 2 and s._admit() is None
     assert s.max_inflight == 2 and s.max_inflight_bytes == f4 + f1
 
@@ -71,3 +75,28 @@ def test_request_larger_than_the_budget_is_refused(serve_mod):
     s = _server(serve_mod, wm.mg_footprint(dims, p, 1), {"a": (None, dims, 0.1)}, p)
     r = s.submit(_req(serve_mod, 0, "a", 4, dims))
     assert r.error and "budget" in r.error and r.event.is_set() and not s.queue
+
+
+def test_same_field_requests_merge_into_one_batch(serve_mod):
+    """With merging, the oldest request takes the waiting requests of its field (oldest first) up to the
+    right-hand-side limit; other fields keep their place; resident hierarchies count in the budget."""
+    wm = serve_mod.wm
+    p = wm.mg_default_params(n_levels=2, block=[(2, 2, 2, 2)], nv=[8], mixed=1)
+    dims = (8, 8, 8, 8)
+    fields = {"a": (None, dims, 0.1), "b": (None, dims, 0.1)}
+    s = _server(serve_mod, 100 * wm.mg_footprint(dims, p, 64), fields, p, merge=True, max_batch_rhs=8)
+    reqs = [_req(serve_mod, 0, "a", 3, dims), _req(serve_mod, 1, "b", 2, dims), _req(serve_mod, 2, "a", 4, dims),
+            _req(serve_mod, 3, "a", 2, dims), _req(serve_mod, 4, "a", 1, dims)]
+    for r in reqs:
+        s.submit(r)
+    batch = s._admit()
+    assert [r.rid for r in batch] == [0, 2, 4]            # 3 + 4 + 1 = 8 right-hand sides; request 3 would exceed
+    assert [r.rid for r in s.queue] == [1, 3]
+    assert s.inflight_bytes == wm.mg_footprint(dims, p, 8) and s.batches == [(3, 8)]
+    assert sum(r.footprint for r in batch) == s.inflight_bytes
+    assert [r.rid for r in s._admit()] == [1]             # the other field's request is next
+    # resident hierarchies leave no room: nothing is admitted
+    t = _server(serve_mod, wm.mg_footprint(dims, p, 4), fields, p, merge=True,
+                resident=wm.mg_footprint(dims, p, 4) - wm.mg_footprint(dims, p, 1) + 1)
+    t.submit(_req(serve_mod, 5, "a", 1, dims))
+    assert t._admit() is None
