@@ -459,7 +459,7 @@ def mma_workload(args):
     Ud = torch.from_numpy(U).cuda()
     p = wm.mg_default_params(n_levels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 24],
                              setup_sweeps=[args.mma_sweeps, args.mma_sweeps], mixed=1, seed=7, coarse_mma=1)
-    h = wm.mg_setup(Ud, C3_DIMS, C3_MCRIT + args.c3_dm, p, stream=stream)
+    h = wm.mg_setup(Ud, C3_DIMS, c3_mcrit() + args.c3_dm, p, stream=stream)
     R = args.mma_rhs
     d1, nc1, _ = wm.mg_level_info(h, 1)
     V0, V1 = int(np.prod(C3_DIMS)), int(np.prod(d1))
@@ -687,7 +687,14 @@ def reference_arm(args, rank, world):
 
 # ---------------------------------------------------------------------------- multi-RHS workload
 C3_DIMS = (16, 16, 16, 32)
-C3_MCRIT = -0.8049  # Sec. 5: m_crit of the paper's beta = 6.0, 16^3 x 32 ensemble (our field is a stand-in)
+
+
+def c3_mcrit():
+    """m_crit of the 16^3 x 32 beta = 6.0 field: minus the smallest real part of the spectrum of D(m = 0),
+    from the oracle's Arnoldi run (tests/golden/mcrit.json)."""
+    key = "%dx%dx%dx%d_beta%.1f_sweeps%d_seed%d" % (*C3_DIMS, BETA, HB_SWEEPS, HB_SEED)
+    with open(os.path.join(ROOT, "tests", "golden", "mcrit.json")) as f:
+        return json.load(f)[key]["m_crit"]
 
 
 def c3_workload(args):
@@ -701,9 +708,10 @@ def c3_workload(args):
     srcs = [inputs.point_source(C3_DIMS, s, c) for s in range(4) for c in range(3)]
     srcs += [inputs.gaussian_spinor(C3_DIMS, 100 + r) for r in range(12)]
     B = torch.from_numpy(np.stack(srcs)).cuda()
-    mass = C3_MCRIT + args.c3_dm
+    mass = c3_mcrit() + args.c3_dm
     out = {"workload": "16^3x32 beta=6.0 heatbath (200 sweeps, seed 0), 3-level MG 4^4 then 2^4 blocks, Nv=24/24, "
-                       "m = -0.8049 + %g, 12 point + 12 Gaussian sources, tol 1e-10" % args.c3_dm}
+                       "m = m_crit + %g (m_crit = %.4f from Arnoldi), 12 point + 12 Gaussian sources, tol 1e-10"
+                       % (args.c3_dm, c3_mcrit())}
     res = {}
     for mixed in ((1,) if args.no_plain else (1, 0)):
         # the mixed form applies the level-1 stencil to all right-hand sides on tensor cores
@@ -771,7 +779,8 @@ def tile_gauge(U, reps):
 def c5_workload(args):
     """32^3 x 64: MG with 4^4 then 2^4 blocks (Nv = 24/32) and a fourth level (2^4, Nv = 24) for an exact
     coarsest solve, 12 Gaussian sources, the mixed multi-RHS solve against 12 single-RHS plain FP64
-    solves, at masses above the paper's m_crit."""
+    solves, at masses above the m_crit of the 16^3 x 32 field it tiles (the tiled lattice holds that
+    field's spectrum and more momenta, so its own m_crit lies at or below it: the dm are kept >= 0.03)."""
     import torch
     from paper_0811_4331_gb300 import wilson_mg as wm
     stream = torch.cuda.current_stream()
@@ -784,7 +793,7 @@ def c5_workload(args):
                        "4-level MG 4^4, 2^4, 2^4 blocks, Nv=24/32/24, %d Gaussian sources, tol 1e-10, GCR(%d)"
                        % (nrhs, args.c5_restart), "masses": []}
     for dm in args.c5_dm:
-        mass = C3_MCRIT + dm
+        mass = c3_mcrit() + dm
         row = {"m": round(mass, 4)}
         for mixed in ((1,) if args.no_plain else (1, 0)):
             # the third level (4^3 x 8 sites x 64 components = 32768 unknowns) is too large for the
@@ -828,12 +837,10 @@ def serve_workload(args):
     from paper_0811_4331_gb300 import wilson_mg as wm
     with open(os.path.join(ROOT, "tests", "golden", "mcrit.json")) as f:
         mc = json.load(f)
-    # m_crit of each field from the oracle where it has been computed; otherwise the paper's
-    # 16^3 x 32 value (Sec. 5) with the lightest masses kept 0.03 above it (the stand-in field's own
-    # critical mass is not known to better than that)
+    # m_crit of each field from the oracle's Arnoldi run (tests/golden/mcrit.json)
     def crit_of(dims):
         key = "%dx%dx%dx%d_beta6.0_sweeps200_seed0" % dims
-        return (mc[key]["m_crit"], 0.005) if key in mc else (C3_MCRIT, 0.03)
+        return mc[key]["m_crit"], 0.005
 
     crit = {d: crit_of(d) for d in ((8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32))}
     two = wm.mg_default_params(n_levels=2, block=[(4, 4, 4, 4)], nv=[20], setup_sweeps=[300], mixed=1, seed=7)
@@ -847,7 +854,7 @@ def serve_workload(args):
     budget = int(0.5 * torch.cuda.get_device_properties(0).total_memory)
     rng = np.random.default_rng(4)
     out = {"workload": "serving: Poisson arrivals, fields 8^4 / 12^4 / 16^3x32 (beta=6.0 heatbath), masses "
-                       "U[m_crit+0.005, m_crit+0.1] (oracle m_crit; else the paper's -0.8049 and U[+0.03, +0.1]), "
+                       "U[m_crit+0.005, m_crit+0.1] (m_crit of each field from the oracle's Arnoldi run), "
                        "1-12 Gaussian RHS, tol 1e-10, 4 workers, waiting requests of a field merged into one "
                        "solve of up to 64 RHS (a mass per RHS), half of HBM as budget (resident hierarchies "
                        "included)",

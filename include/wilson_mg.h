@@ -330,6 +330,13 @@ int mg_get_prolongator(mg_handle* h, int level, double* out);
  * site itself, d = 1 + 2 mu the hop to n + mu, d = 2 + 2 mu to n - mu. */
 int mg_get_coarse_op(mg_handle* h, int level, double* out);
 
+/* Copy the dense inverse of the coarsest operator (Sec. 4: the coarsest
+ * level is solved exactly) to host memory as [N][N] complex, N = V_c ncomp_c,
+ * rows and columns in the external order (site-major, component fastest);
+ * FP64 or FP32 values as the handle stores them, widened to double.  Builds
+ * a deferred inverse first.  MG_EINVAL for a one-level handle. */
+int mg_get_coarsest_inverse(mg_handle* h, double* out);
+
 /* Same as mr_apply (for nrhs = 1), but allocates nothing, for callers that
  * cannot allocate device memory when they call it: a server that fixed its
  * device footprint at start-up, or a thread that must not enter the driver's
@@ -435,7 +442,17 @@ size_t mg_trim_cache(void);
  * buffers; capacities of its buffers), for admission by memory budget. */
 size_t mg_handle_bytes(const mg_handle* h);
 
-/* Device bytes that mg_setup + mg_solve(nrhs) need for these sizes. */
+/* Hand the handle's solve buffers (Krylov basis, work vectors of every
+ * level, the inverses of mg_solve_masses) back to the memory cache, keeping
+ * the hierarchy (links, prolongators, coarse operators, coarsest inverse);
+ * the next solve takes them again.  Synchronises `stream` (the stream of the
+ * handle's last solve; NULL: the legacy stream) first.  Returns the bytes
+ * released.  A server calls it after each batch so that a resident handle
+ * holds only its hierarchy between batches. */
+size_t mg_release_work(mg_handle* h, void* stream);
+
+/* Device bytes that mg_setup + mg_solve(nrhs) need for these sizes, with
+ * nrhs distinct masses for mg_solve_masses (one coarsest inverse each). */
 size_t mg_footprint(const int dims[4], const mg_params* p, int nrhs);
 
 #ifdef __cplusplus

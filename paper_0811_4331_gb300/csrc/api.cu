@@ -848,6 +848,32 @@ int mg_destroy(mg_handle* h) {
 
 size_t mg_trim_cache(void) { return wmg::dev_cache().trim(); }
 
+size_t mg_release_work(mg_handle* h, void* stream) {
+  if (!h) return 0;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess || cudaStreamSynchronize(h->st) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;  // work may still be queued on the buffers: keep them
+  }
+  DevIdleScope idle;  // both streams the handle's solves use are done
+  size_t freed = 0;
+  auto drop = [&](DevBuf& d) {
+    if (d.p) {
+      freed += d.bytes;
+      d.release();
+    }
+  };
+  for (auto& byprec : h->work)
+    for (auto& vecs : byprec)
+      for (auto& v : vecs)
+        if (v) drop(*v);
+  for (DevBuf* d : {&h->gr, &h->gW, &h->gZ, &h->gb64, &h->gx64, &h->gr64, &h->gtmp, &h->gH, &h->galpha, &h->gy,
+                    &h->mm_inv})
+    drop(*d);
+  h->mm_masses.clear();
+  ++h->buf_gen;  // captured cycles hold the released addresses
+  return freed;
+}
+
 size_t mg_handle_bytes(const mg_handle* h) {
   if (!h) return 0;
   size_t b = 0;
@@ -912,12 +938,13 @@ static int build_coarsest_many(mg_handle* const* hs, int count) {
     inv[z] = c.inv.p;
   }
   CK(cudaMemsetAsync(errflag.p, 0, sizeof(int) * count, st));
+  long long nl = 1;
   {
     Prof pf(h0, MG_K_INVERSE, prec);
     LK(dense_inverse_batch(prec, C.data(), c0.L, c0.ncomp, count, aug.p, col.p, errflag.as<int>(), inv.data(),
-                           blk.p, st));
+                           blk.p, st, &nl));
   }
-  count_launches(N + 3 * (size_t)count - 1);  // per matrix: stencil-to-dense, init, finish; one per pivot (or panel pair)
+  count_launches(nl - 1);
   std::vector<int> herr(count, 0);
   CK(cudaMemcpyAsync(herr.data(), errflag.p, sizeof(int) * count, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -968,12 +995,13 @@ static int build_mass_inverses(mg_handle* h, const std::vector<double>& ms) {
     inv[z] = (char*)h->mm_inv.p + N * N * eb * z;
   }
   CK(cudaMemsetAsync(errflag.p, 0, sizeof(int) * count, st));
+  long long nl = 1;
   {
     Prof pf(h, MG_K_INVERSE, prec);
     LK(dense_inverse_batch(prec, C.data(), c.L, c.ncomp, count, aug.p, col.p, errflag.as<int>(), inv.data(), blk.p,
-                           st));
+                           st, &nl));
   }
-  count_launches(N + 3 * (size_t)count - 1);
+  count_launches(nl - 1);
   std::vector<int> herr(count, 0);
   CK(cudaMemcpyAsync(herr.data(), errflag.p, sizeof(int) * count, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -1283,7 +1311,6 @@ const double kSu3Tolerance = 1e-10;
 static int setup_impl(mg_handle* h, const double* gauge, int gauge_on_device, const double* const* starts) {
   const mg_params& p = h->p;
   cudaStream_t st = h->st;
-  const int Lv = p.n_levels;
   // ---- level 0 and the gauge field
   h->lev.emplace_back(new Level());
   Level& f = *h->lev[0];
@@ -1742,6 +1769,32 @@ int mg_get_coarse_op(mg_handle* h, int level, double* out) {
   return MG_OK;
 }
 
+int mg_get_coarsest_inverse(mg_handle* h, double* out) {
+  if (!h || h->lev.size() < 2 || !out) return MG_EINVAL;
+  if (h->lev.back()->inv_pending) RET(build_coarsest(h));
+  Level& c = *h->lev.back();
+  const size_t n = c.ncomp, V = c.V, N = n * V;
+  const bool f64 = c.inv_prec == MG_F64;
+  std::vector<double> d(f64 ? N * N * 2 : 0);
+  std::vector<float> f(f64 ? 0 : N * N * 2);
+  if (f64)
+    CK(cudaMemcpyAsync(d.data(), c.inv.p, d.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  else
+    CK(cudaMemcpyAsync(f.data(), c.inv.p, f.size() * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  // internal order (i V + B) -> external order (B n + i), rows and columns
+  for (size_t i = 0; i < n; ++i)
+    for (size_t B = 0; B < V; ++B)
+      for (size_t j = 0; j < n; ++j)
+        for (size_t Bp = 0; Bp < V; ++Bp) {
+          const size_t src = ((i * V + B) * N + j * V + Bp) * 2;
+          const size_t dst = ((B * n + i) * N + Bp * n + j) * 2;
+          out[dst] = f64 ? d[src] : (double)f[src];
+          out[dst + 1] = f64 ? d[src + 1] : (double)f[src + 1];
+        }
+  return MG_OK;
+}
+
 unsigned long long mg_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 unsigned long long mg_alloc_count(void) { return wmg::g_dev_allocs.load(std::memory_order_relaxed); }
@@ -1829,7 +1882,11 @@ size_t mg_footprint(const int dims[4], const mg_params* p, int nrhs) {
     bytes += 9 * nc * nc * Vl * 16 * 2;            // coarse stencil
     bytes += Vl * nc * 16 * (size_t)nrhs * 10;     // coarse work vectors
   }
-  if (p->n_levels >= 2) bytes += (Vl * nc) * (Vl * nc) * 16 * 3;  // dense inverse + scratch
+  if (p->n_levels >= 2) {
+    const size_t N2 = (Vl * nc) * (Vl * nc);
+    bytes += N2 * 16 * 3;  // dense inverse + elimination scratch
+    if (nrhs > 1) bytes += N2 * (p->mixed ? 8 : 16) * 3 * (size_t)nrhs;  // mg_solve_masses: one per mass
+  }
   return bytes;
 }
 

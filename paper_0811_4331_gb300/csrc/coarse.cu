@@ -294,15 +294,16 @@ int launch_diag_shift(double2* C, int n, int V, double delta, cudaStream_t st) {
 // ------------------------------------------------------------------ coarsest: dense inverse
 // Dense matrix of a stencil operator in the internal vector order
 // (row i V + B, column j V + B'), written into the left half of an
-// augmented [N][2N] array (element type T) whose right half is the identity.
+// augmented [N][2N] array (element type T); with ncol = 2N the right half
+// is set to the identity, with ncol = N it is left alone.
 template <typename T>
-__global__ void stencil_to_dense_kernel(const double2* C, int L0, int L1, int L2, int L3, int n, T* aug) {
+__global__ void stencil_to_dense_kernel(const double2* C, int L0, int L1, int L2, int L3, int n, int ncol, T* aug) {
   const int L[4] = {L0, L1, L2, L3};
   const int V = L0 * L1 * L2 * L3;
   const int N = n * V;
-  const size_t tot = (size_t)N * 2 * N;
+  const size_t tot = (size_t)N * ncol;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-    const int row = (int)(e / (2 * (size_t)N)), col = (int)(e % (2 * (size_t)N));
+    const int row = (int)(e / ncol), col = (int)(e % ncol);
     cx<double> v = zero<double>();
     if (col < N) {
       const int i = row / V, B = row % V, j = col / V, Bp = col % V;
@@ -317,7 +318,7 @@ __global__ void stencil_to_dense_kernel(const double2* C, int L0, int L1, int L2
     } else if (col - N == row) {
       v.re = 1.0;
     }
-    stc(aug, e, v);
+    stc(aug, (size_t)row * 2 * N + col, v);
   }
 }
 
@@ -425,171 +426,200 @@ static unsigned grid_for(size_t tot, size_t cap) {
 
 // ------------------------------------------------------------------ blocked Gauss-Jordan
 // The same elimination (partial pivoting on the largest |a_ik|, rows kept in
-// place, every other row eliminated) grouped in panels of b columns.  For a
-// panel starting at column kb, the b steps act on the other columns as one
-// linear map C -> T C with T = prod_j (1 - l_j e_{p_j}^+); T = 1 - X E^+ for
-// E = [e_{p_0} .. e_{p_b-1}], so T C = C - E C_P + (T E) C_P, where C_P are
-// the b pivot rows of C before the panel.  One CTA per matrix runs the b
-// steps on the panel columns in shared memory and tracks T E by applying the
-// same steps to b extra columns (column j set to e_{p_j} just before step
-// j); a second kernel applies the rank-b update to the trailing columns (the
-// columns left of the panel are already zero off their pivot rows and do not
-// change).  The per-element arithmetic differs from the column-by-column
-// order only by rounding.
+// place, every other row eliminated) grouped in two levels.  A group of
+// steps acts on the columns it does not pivot on as one linear map
+// C -> T C with T = prod_j (1 - l_j e_{p_j}^+) (l_j zero at p_j); T = 1 - X E^+
+// for E = [e_{p_0} .. e_{p_m-1}], so
+//     T C = C - E C_P + (T E) C_P,
+// where C_P are the m pivot rows of C before the group: pivot rows take
+// (T E) C_P, every other row adds it.  The per-element arithmetic differs
+// from the column-by-column order only by rounding.
+//
+// Right half in pivot order.  T e_q = e_q for every row q that is not yet a
+// pivot, so the right half [A | 1] -> [T A | T] only ever holds, besides
+// untouched unit columns, the columns T e_{p_s} of the rows already used.
+// Slot s (column N + s) keeps T e_{p_s}: it is first written when row p_s
+// becomes the pivot of step s (as the column of T E for that step) and the
+// unit columns are never stored.  At the end column k of the left half is
+// a_k e_{p_k}, and row k of the inverse is row p_k of T over a_k:
+//     inv[k][p_s] = aug[p_k][N + s] / a_k.
+//
+// Outer blocks of kGjW steps: the columns outside the block's own columns
+// that still change, i.e. the left columns right of the block and the slots
+// of the earlier blocks' pivots, are the contiguous range
+// [kb0 + W, N + kb0); they take one rank-W update per block (a dense
+// product, gjb_outer_update_kernel).  Inside a block, panels of b columns:
+// one CTA per matrix runs a panel's b steps with the rows in registers
+// (gjb_panel_kernel) and a small rank-b update (gjb_inner_update_kernel)
+// brings the rest of the block's columns and the block's earlier slots
+// along.
+constexpr int kGjW = 64;     // steps per outer block (a multiple of every panel width)
+constexpr int kGjbRows = 16;  // rows per CTA of the inner update
 
-// Panel kernel: one CTA per matrix z (blockIdx.x), nt threads.  Shared:
-// panel [N][b] and tracker [N][b] of element type T.
-constexpr int kGjbBatch = 8;
+// Panel kernel: one CTA per matrix z (blockIdx.x), b <= B steps on columns
+// kb .. kb + b - 1.  Thread t owns rows t + m nt (m < RPT) and keeps their
+// panel values P and tracker values Tr (the rows of T E) in registers; bit m
+// of `mine` says whether its m-th row is already a pivot (or beyond N).
+// Each step: the largest |a_ij| over the unused rows (one key per warp, then
+// every warp reduces the warp keys itself), the owner of the pivot row
+// publishes that row's panel and tracker values to shared memory, and every
+// other row takes its multiple of it.  used[i] = step + 1 of the step that
+// made row i a pivot (0: not yet).  Writes the panel back (zero off its
+// pivot rows), T E into slots kb .. kb + b - 1, the pivots' keys, and the
+// pivot rows of the inner update's columns (ranges [c1, c1 + n1) and
+// [c2, c2 + n2)) into prow [8][kGjPRow] (rows b .. 7 unused).
+constexpr int kGjPRow = 2 * kGjW;
 
-template <typename T, int B>
-__global__ void __launch_bounds__(1024) gjb_panel_kernel(T* aug0, int N, int kb, int b, unsigned long long* keys0,
-                                                         int* used0, T* te0, T* prow0, int* err0) {
+template <typename T, int B, int RPT, int NT>
+__global__ void __launch_bounds__(NT) gjb_panel_kernel(T* aug0, int N, int kb, int b, int c1, int n1, int c2,
+                                                       int n2, unsigned long long* keys0, int* used0, T* prow0,
+                                                       int* err0) {
   typedef typename Store<T>::R R;
+  constexpr int LT = B + 1;  // padded row of a warp's staging tile
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ cx<R> pr_s[2 * B];  // the pivot row: panel values, then tracker values
+  __shared__ unsigned long long wkey[32];
   const int z = blockIdx.x;
   T* aug = aug0 + (size_t)z * N * 2 * N;
   unsigned long long* keys = keys0 + (size_t)z * (N + 1);
   int* used = used0 + (size_t)z * N;
-  T* te = te0 + (size_t)z * N * b;
-  T* prow = prow0 + (size_t)z * b * 2 * N;
+  T* prow = prow0 + (size_t)z * 8 * kGjPRow;
   int* err = err0 + z;
-  // column-major: thread i of a warp touches consecutive words.  Panel column
-  // j keeps its pre-step values (zeroed off the pivot row on write-back).
-  cx<R>* Ps = (cx<R>*)smem_raw;    // [b][N]
-  cx<R>* Ts = Ps + (size_t)B * N;  // [b][N]
-  __shared__ unsigned long long wkey[32];
-  __shared__ int piv_s[B];
-  const int nt = blockDim.x, t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int nt = blockDim.x, t = threadIdx.x, warp = t >> 5, lane = t & 31, nw = nt >> 5;
   const size_t ld = 2 * (size_t)N;
+  // the warp's 32 consecutive rows (thread t owns row t + m nt) pass through its tile
+  // [32][LT], so that global memory is read and written a row segment at a time
+  cx<R>* tile = (cx<R>*)smem_raw + (size_t)warp * 32 * LT;
   if (*err) return;
   auto warp_max = [&](unsigned long long v) {
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long other = __shfl_down_sync(0xffffffffu, v, o);
+      const unsigned long long other = __shfl_xor_sync(0xffffffffu, v, o);
       v = other > v ? other : v;
     }
     return v;
   };
-  unsigned long long best = 0;
-  // kGjbBatch independent loads per thread in flight at once: one CTA moves the whole panel, so its
-  // time is a chain of L2 round trips unless they overlap
-  for (int e0 = t; e0 < N * b; e0 += nt * kGjbBatch) {  // coalesced along the panel's row
-    cx<R> v[kGjbBatch];
-    int fresh[kGjbBatch];
+  cx<R> P[RPT][B], Tr[RPT][B];
+  unsigned mine = 0;
 #pragma unroll
-    for (int u = 0; u < kGjbBatch; ++u) {
-      const int e = e0 + u * nt;
-      if (e < N * b) {
-        const int i = e / b, j = e - i * b;
-        v[u] = ldc<R>(aug, (size_t)i * ld + kb + j);
-        fresh[u] = j == 0 && !used[i];
-      }
-    }
+  for (int m = 0; m < RPT; ++m) {
+    const int i = t + m * nt, r0 = i - lane;
+    if (i >= N || used[i]) mine |= 1u << m;
 #pragma unroll
-    for (int u = 0; u < kGjbBatch; ++u) {
-      const int e = e0 + u * nt;
-      if (e < N * b) {
-        const int i = e / b, j = e - i * b;
-        Ps[(size_t)j * N + i] = v[u];
-        Ts[(size_t)j * N + i] = zero<R>();
-        if (fresh[u]) {
-          const unsigned long long key = pivot_key((float)norm2(v[u]), i);
-          best = key > best ? key : best;
-        }
-      }
+    for (int q = 0; q < B; ++q) {
+      const int e = q * 32 + lane, r = e / B, j = e - r * B;
+      tile[r * LT + j] = (j < b && r0 + r < N) ? ldc<R>(aug, (size_t)(r0 + r) * ld + kb + j) : zero<R>();
     }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      P[m][j] = tile[lane * LT + j];
+      Tr[m][j] = zero<R>();
+    }
+    __syncwarp();
   }
-  best = warp_max(best);
-  if (lane == 0) wkey[warp] = best;
-#pragma unroll 1
-  for (int j = 0; j < b; ++j) {
-    __syncthreads();  // the column's candidate keys and the previous step's updates are complete
-    if (warp == 0) {
-      unsigned long long v = lane < nt / 32 ? wkey[lane] : 0ull;
-      v = warp_max(v);
-      if (lane == 0) {
-        const int p = v ? pivot_row(v) : -1;
-        const bool ok = p >= 0 && p < N && norm2(Ps[(size_t)j * N + p]) > (R)0;
-        piv_s[j] = ok ? p : -1;
-        if (ok) {
-          keys[kb + j] = v;
-          used[p] = 1;
-          Ts[(size_t)j * N + p] = mk<R>((R)1, (R)0);
-        } else {
-          *err = 1;
-        }
-      }
-    }
-    __syncthreads();
-    const int p = piv_s[j];
-    if (p < 0) return;
-    const cx<R> pv = Ps[(size_t)j * N + p];
-    const R den = norm2(pv);
-    const cx<R> pinv = mk<R>(pv.re / den, -pv.im / den);
-    // every other row: panel columns right of j, tracker columns up to j; the
-    // updated column j+1 yields the next step's pivot candidates
-    best = 0;
-    for (int i = t; i < N; i += nt) {
-      if (i == p) continue;
-      const cx<R> l = Ps[(size_t)j * N + i] * pinv;
+  int piv[B];
 #pragma unroll
-      for (int jj = 0; jj < B; ++jj) {
-        if (jj >= b) break;
-        if (jj > j) {
-          const cx<R> v = Ps[(size_t)jj * N + i] - l * Ps[(size_t)jj * N + p];
-          Ps[(size_t)jj * N + i] = v;
-          if (jj == j + 1 && !used[i]) {
-            const unsigned long long key = pivot_key((float)norm2(v), i);
-            best = key > best ? key : best;
-          }
-        } else {
-          Ts[(size_t)jj * N + i] = Ts[(size_t)jj * N + i] - l * Ts[(size_t)jj * N + p];
-        }
+  for (int j = 0; j < B; ++j) {
+    piv[j] = -1;
+    if (j >= b) break;
+    unsigned long long best = 0;
+#pragma unroll
+    for (int m = 0; m < RPT; ++m)
+      if (!((mine >> m) & 1u)) {
+        const unsigned long long key = pivot_key((float)norm2(P[m][j]), t + m * nt);
+        best = key > best ? key : best;
       }
-    }
     best = warp_max(best);
     if (lane == 0) wkey[warp] = best;
-  }
-  __syncthreads();
-  // the panel back (its columns zero off their pivot rows), T E for the
-  // trailing update, and the pivot rows of the trailing columns
-  for (int e = t; e < N * b; e += nt) {
-    const int i = e / b, j = e - i * b;
-    stc(aug, (size_t)i * ld + kb + j, i == piv_s[j] ? Ps[(size_t)j * N + i] : zero<R>());
-    stc(te, e, Ts[(size_t)j * N + i]);
-  }
-  const int c0 = kb + b, nc = 2 * N - c0;
-  for (int e0 = t; e0 < b * nc; e0 += nt * kGjbBatch) {
-    T v[kGjbBatch];
+    __syncthreads();  // every warp's key (and the previous step's reads of pr_s) are complete
+    const unsigned long long v = warp_max(lane < nw ? wkey[lane] : 0ull);
+    const int p = v ? pivot_row(v) : -1;
+    if (p < 0 || p >= N) {
+      if (t == 0) *err = 1;
+      return;  // the same decision in every thread
+    }
+    piv[j] = p;
+    if (p % nt == t) {  // the owner: row p's values, with its tracker unit set
+      const int mp = p / nt;
 #pragma unroll
-    for (int u = 0; u < kGjbBatch; ++u) {
-      const int e = e0 + u * nt;
-      if (e < b * nc) {
-        const int j = e / nc, c = e - j * nc;
-        v[u] = aug[(size_t)piv_s[j] * ld + c0 + c];
+      for (int m = 0; m < RPT; ++m)
+        if (m == mp) {
+          Tr[m][j] = mk<R>((R)1, (R)0);
+          mine |= 1u << m;
+#pragma unroll
+          for (int jj = 0; jj < B; ++jj) {
+            pr_s[jj] = P[m][jj];
+            pr_s[B + jj] = Tr[m][jj];
+          }
+        }
+      keys[kb + j] = v;
+      used[p] = kb + j + 1;
+    }
+    __syncthreads();  // the pivot row is published
+    const cx<R> pv = pr_s[j];
+    const R den = norm2(pv);
+    if (!(den > (R)0)) {
+      if (t == 0) *err = 1;
+      return;
+    }
+    const cx<R> pinv = mk<R>(pv.re / den, -pv.im / den);
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+      const int i = t + m * nt;
+      if (i >= N || i == p) continue;
+      const cx<R> l = P[m][j] * pinv;
+#pragma unroll
+      for (int jj = 0; jj < B; ++jj) {
+        if (jj > j) {
+          if (jj < b) P[m][jj] = P[m][jj] - l * pr_s[jj];
+        } else {
+          Tr[m][jj] = Tr[m][jj] - l * pr_s[B + jj];
+        }
       }
     }
+  }
+  // the panel back (its columns zero off their pivot rows) and T E into the step's slots
 #pragma unroll
-    for (int u = 0; u < kGjbBatch; ++u) {
-      const int e = e0 + u * nt;
-      if (e < b * nc) {
-        const int j = e / nc, c = e - j * nc;
-        prow[(size_t)j * 2 * N + c0 + c] = v[u];
+  for (int m = 0; m < RPT; ++m) {
+    const int i = t + m * nt, r0 = i - lane;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+#pragma unroll
+      for (int j = 0; j < B; ++j) tile[lane * LT + j] = half ? Tr[m][j] : (i == piv[j] ? P[m][j] : zero<R>());
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        const int e = q * 32 + lane, r = e / B, j = e - r * B;
+        if (j < b && r0 + r < N) stc(aug, (size_t)(r0 + r) * ld + (half ? N : 0) + kb + j, tile[r * LT + j]);
       }
+      __syncwarp();
     }
+  }
+  // the pivot rows of the inner update's columns, before that update
+  const int nc = n1 + n2;
+  for (int e = t; e < b * nc; e += nt) {
+    const int j = e / nc, c = e - j * nc;
+    const int col = c < n1 ? c1 + c : c2 + (c - n1);
+    int pj = piv[0];
+#pragma unroll
+    for (int jj = 1; jj < B; ++jj)
+      if (jj == j) pj = piv[jj];
+    prow[(size_t)j * kGjPRow + c] = aug[(size_t)pj * ld + col];
   }
 }
 
-// Trailing update of the columns right of the panel: for row i and column c,
-// a = (i a pivot row of the panel ? 0 : a) + sum_j TE[i][j] prow[j][c].
-// grid = (column tiles of 256, row groups of kGjbRows, batch): a thread keeps
-// its column's b pivot-row values in registers for kGjbRows rows, and the
-// group's TE rows and pivot flags sit in shared memory.
-constexpr int kGjbRows = 16;
-
+// Inner update of the block's other columns after a panel at kb (b steps):
+// column c of the ranges [c1, c1 + n1) and [c2, c2 + n2) (index c' < n1 + n2
+// in prow), row i:  a = (i a pivot of the panel ? 0 : a) + sum_j TE[i][j] prow[j][c'],
+// TE[i][j] = aug[i][N + kb + j].  grid = (column tiles, row groups of
+// kGjbRows, batch): a thread keeps its column's b pivot-row values in
+// registers for kGjbRows rows; the group's TE rows and pivot flags sit in
+// shared memory.
 template <typename T>
-__global__ void __launch_bounds__(256) gjb_update_kernel(T* aug0, int N, int kb, int b,
-                                                         const unsigned long long* keys0, const T* te0,
-                                                         const T* prow0, const int* err0) {
+__global__ void __launch_bounds__(128) gjb_inner_update_kernel(T* aug0, int N, int kb, int b, int c1, int n1, int c2,
+                                                               int n2, const unsigned long long* keys0,
+                                                               const T* prow0, const int* err0) {
   typedef typename Store<T>::R R;
   __shared__ cx<R> tes[kGjbRows][8];
   __shared__ int isp[kGjbRows];
@@ -597,12 +627,12 @@ __global__ void __launch_bounds__(256) gjb_update_kernel(T* aug0, int N, int kb,
   if (err0[z]) return;
   T* aug = aug0 + (size_t)z * N * 2 * N;
   const unsigned long long* keys = keys0 + (size_t)z * (N + 1);
-  const T* te = te0 + (size_t)z * N * b;
-  const T* prow = prow0 + (size_t)z * b * 2 * N;
+  const T* prow = prow0 + (size_t)z * 8 * kGjPRow;
+  const size_t ld = 2 * (size_t)N;
   const int i0 = blockIdx.y * kGjbRows;
   for (int e = threadIdx.x; e < kGjbRows * 8; e += blockDim.x) {  // all 8 slots: unused ones must be 0, not NaN
     const int r = e / 8, j = e % 8;
-    tes[r][j] = (i0 + r < N && j < b) ? ldc<R>(te, (size_t)(i0 + r) * b + j) : zero<R>();
+    tes[r][j] = (i0 + r < N && j < b) ? ldc<R>(aug, (size_t)(i0 + r) * ld + N + kb + j) : zero<R>();
   }
   if (threadIdx.x < kGjbRows) {
     int piv = 0;
@@ -610,17 +640,16 @@ __global__ void __launch_bounds__(256) gjb_update_kernel(T* aug0, int N, int kb,
     isp[threadIdx.x] = piv;
   }
   __syncthreads();
-  const int c = kb + b + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= 2 * N) return;
+  const int cc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cc >= n1 + n2) return;
+  const int c = cc < n1 ? c1 + cc : c2 + (cc - n1);
   cx<R> pr[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) pr[j] = j < b ? ldc<R>(prow, (size_t)j * 2 * N + c) : zero<R>();
+  for (int j = 0; j < 8; ++j) pr[j] = j < b ? ldc<R>(prow, (size_t)j * kGjPRow + cc) : zero<R>();
   const int rows = min(kGjbRows, N - i0);
-  // all the group's loads first (independent, in flight together), then the stores
   cx<R> av[kGjbRows];
 #pragma unroll
-  for (int r = 0; r < kGjbRows; ++r)
-    av[r] = r < rows ? ldc<R>(aug, (size_t)(i0 + r) * 2 * N + c) : zero<R>();
+  for (int r = 0; r < kGjbRows; ++r) av[r] = r < rows ? ldc<R>(aug, (size_t)(i0 + r) * ld + c) : zero<R>();
 #pragma unroll
   for (int r = 0; r < kGjbRows; ++r) {
     if (r >= rows) break;
@@ -628,82 +657,251 @@ __global__ void __launch_bounds__(256) gjb_update_kernel(T* aug0, int N, int kb,
 #pragma unroll
     for (int j = 0; j < 8; ++j)
       if (j < b) acc = cfma(tes[r][j], pr[j], acc);
-    stc(aug, (size_t)(i0 + r) * 2 * N + c, isp[r] ? acc : av[r] + acc);
+    stc(aug, (size_t)(i0 + r) * ld + c, isp[r] ? acc : av[r] + acc);
   }
 }
 
-// Panel width for N rows of element size eb: the panel and its tracker in
-// one CTA's shared memory; 0 = too large, use single steps.
-static int gjb_width(int N, size_t eb) {
-  for (int b = 8; b >= 2; b /= 2)
-    if (2 * (size_t)b * N * eb <= 200 * 1024) return b;
-  return 0;
+// Pivot rows of an outer block (steps kb0 .. kb0 + W - 1) over the columns
+// [kb0 + W, N + kb0) that its update changes: cp[j][c] = aug[p_{kb0+j}][kb0 + W + c]
+// (row stride N), taken before the update overwrites them.
+template <typename T>
+__global__ void gjb_gather_kernel(const T* aug0, int N, int kb0, int W, const unsigned long long* keys0, T* cp0,
+                                  const int* err0) {
+  const int z = blockIdx.z;
+  if (err0[z]) return;
+  const T* aug = aug0 + (size_t)z * N * 2 * N;
+  const unsigned long long* keys = keys0 + (size_t)z * (N + 1);
+  T* cp = cp0 + (size_t)z * kGjW * N;
+  const int j = blockIdx.y, nc = N - W;
+  const int p = pivot_row(keys[kb0 + j]);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+    cp[(size_t)j * N + c] = aug[(size_t)p * 2 * N + kb0 + W + c];
+}
+
+// Outer update after the block's W steps: rows i < N, columns c of
+// [kb0 + W, N + kb0):  a = (i a pivot of the block ? 0 : a) + sum_{j<W} TE[i][j] cp[j][c],
+// TE[i][j] = aug[i][N + kb0 + j] (the block's slots).  A dense product of
+// N x W by W x (N - W) per matrix: CTA = kGjTile x kGjTile outputs, 256
+// threads of 4 x 4 outputs each, both operand tiles in shared memory
+// (TE row-major and padded, cp column-contiguous), K = W <= kGjW.
+constexpr int kGjTile = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(256) gjb_outer_update_kernel(T* aug0, int N, int kb0, int W, const int* used0,
+                                                               const T* cp0, const int* err0) {
+  typedef typename Store<T>::R R;
+  constexpr int LA = kGjW + 1;  // padded row of the TE tile
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<R>* As = (cx<R>*)smem_raw;      // [kGjTile][LA]   TE rows
+  cx<R>* Bs = As + kGjTile * LA;     // [kGjW][kGjTile] cp columns
+  const int z = blockIdx.z;
+  if (err0[z]) return;
+  T* aug = aug0 + (size_t)z * N * 2 * N;
+  const int* used = used0 + (size_t)z * N;
+  const T* cp = cp0 + (size_t)z * kGjW * N;
+  const size_t ld = 2 * (size_t)N;
+  const int nc = N - W, cbase = kb0 + W;
+  const int r0 = blockIdx.y * kGjTile, q0 = blockIdx.x * kGjTile;
+  for (int e = threadIdx.x; e < kGjTile * kGjW; e += blockDim.x) {
+    const int r = e / kGjW, k = e - r * kGjW;  // consecutive threads: consecutive slots of one row
+    As[r * LA + k] = (r0 + r < N && k < W) ? ldc<R>(aug, (size_t)(r0 + r) * ld + N + kb0 + k) : zero<R>();
+  }
+  for (int e = threadIdx.x; e < kGjW * kGjTile; e += blockDim.x) {
+    const int k = e / kGjTile, q = e - k * kGjTile;
+    Bs[k * kGjTile + q] = (k < W && q0 + q < nc) ? ldc<R>(cp, (size_t)k * N + q0 + q) : zero<R>();
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  cx<R> acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = zero<R>();
+#pragma unroll 4
+  for (int k = 0; k < W; ++k) {
+    cx<R> av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = As[(ty * 4 + a) * LA + k];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) bv[c] = Bs[k * kGjTile + tx * 4 + c];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = cfma(av[a], bv[c], acc[a][c]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = r0 + ty * 4 + a;
+    if (i >= N) break;
+    const bool piv = (unsigned)(used[i] - 1 - kb0) < (unsigned)W;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int q = q0 + tx * 4 + c;
+      if (q >= nc) break;
+      const size_t o = (size_t)i * ld + cbase + q;
+      stc(aug, o, piv ? acc[a][c] : ldc<R>(aug, o) + acc[a][c]);
+    }
+  }
+}
+
+// inv[k][p_s] = aug[p_k][N + s] / aug[p_k][k]   (the right half in pivot order)
+template <typename T>
+__global__ void gjb_finish_kernel(const T* aug, int N, const unsigned long long* keys, T* inv) {
+  typedef typename Store<T>::R R;
+  const size_t tot = (size_t)N * N;
+  const size_t ld = 2 * (size_t)N;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / N), s = (int)(e % N);
+    const int p = pivot_row(keys[k]), ps = pivot_row(keys[s]);
+    if (p < 0 || p >= N || ps < 0 || ps >= N) continue;
+    const cx<R> piv = ldc<R>(aug, (size_t)p * ld + k);
+    const R den = norm2(piv);
+    const cx<R> pinv = mk<R>(piv.re / den, -piv.im / den);
+    stc(inv, (size_t)k * N + ps, ldc<R>(aug, (size_t)p * ld + N + s) * pinv);
+  }
+}
+
+// Panel shapes (width B, rows per thread RPT, threads NT), widest first: a
+// thread's rows of the panel and its tracker sit in registers, so RPT x B is
+// bounded by the register file (NT threads x the registers each needs).
+struct GjbShape {
+  int b, rpt, nt;
+};
+constexpr GjbShape kGjbF32[] = {{8, 1, 1024}, {8, 2, 640}, {8, 4, 384}, {4, 4, 640}, {4, 8, 384}, {2, 8, 640},
+                                {2, 16, 384}};
+constexpr GjbShape kGjbF64[] = {{8, 1, 512}, {4, 1, 1024}, {4, 2, 640}, {4, 4, 384}, {2, 4, 640}, {2, 8, 384}};
+
+// The first shape whose threads x rows cover N; b = 0: none (single steps).
+static GjbShape gjb_shape(int N, size_t eb) {
+  const GjbShape* s = eb == 8 ? kGjbF32 : kGjbF64;
+  const int n = eb == 8 ? (int)(sizeof(kGjbF32) / sizeof(GjbShape)) : (int)(sizeof(kGjbF64) / sizeof(GjbShape));
+  for (int k = 0; k < n; ++k)
+    if ((long long)s[k].nt * s[k].rpt >= N) return s[k];
+  return GjbShape{0, 0, 0};
 }
 
 size_t gjb_scratch_bytes(int N, size_t eb, int batch) {
-  const int b = gjb_width(N, eb);
-  return b ? (size_t)batch * ((size_t)N * b + (size_t)b * 2 * N) * eb + 256 : 0;
+  const int b = gjb_shape(N, eb).b;
+  return b ? (size_t)batch * ((size_t)8 * kGjPRow + (size_t)kGjW * N) * eb + 256 : 0;
+}
+
+template <typename T>
+using GjbPanel = void (*)(T*, int, int, int, int, int, int, int, unsigned long long*, int*, T*, int*);
+
+template <typename T>
+static GjbPanel<T> gjb_panel_for(const GjbShape& s) {
+  if constexpr (sizeof(T) == 8) {
+    if (s.b == 8 && s.rpt == 1) return gjb_panel_kernel<T, 8, 1, 1024>;
+    if (s.b == 8 && s.rpt == 2) return gjb_panel_kernel<T, 8, 2, 640>;
+    if (s.b == 8 && s.rpt == 4) return gjb_panel_kernel<T, 8, 4, 384>;
+    if (s.b == 4 && s.rpt == 4) return gjb_panel_kernel<T, 4, 4, 640>;
+    if (s.b == 4 && s.rpt == 8) return gjb_panel_kernel<T, 4, 8, 384>;
+    if (s.b == 2 && s.rpt == 8) return gjb_panel_kernel<T, 2, 8, 640>;
+    return gjb_panel_kernel<T, 2, 16, 384>;
+  } else {
+    if (s.b == 8 && s.rpt == 1) return gjb_panel_kernel<T, 8, 1, 512>;
+    if (s.b == 4 && s.rpt == 1) return gjb_panel_kernel<T, 4, 1, 1024>;
+    if (s.b == 4 && s.rpt == 2) return gjb_panel_kernel<T, 4, 2, 640>;
+    if (s.b == 4 && s.rpt == 4) return gjb_panel_kernel<T, 4, 4, 384>;
+    if (s.b == 2 && s.rpt == 4) return gjb_panel_kernel<T, 2, 4, 640>;
+    return gjb_panel_kernel<T, 2, 8, 384>;
+  }
 }
 
 template <typename T>
 static int dense_inverse_t(const double2* const* C, const int L[4], int n, int batch, T* aug, char* sc, int* err,
-                           void* const* inv, void* blk, cudaStream_t st) {
+                           void* const* inv, void* blk, cudaStream_t st, long long* launches) {
   const int V = L[0] * L[1] * L[2] * L[3];
   const int N = n * V;
   const size_t nn2 = (size_t)N * 2 * N;
   T* cols = (T*)sc;
   unsigned long long* keys = (unsigned long long*)(sc + (size_t)batch * 2 * N * sizeof(T));
   int* used = (int*)(keys + (size_t)batch * (N + 1));
+  long long nl = 0;
   cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (N + 1) * batch, st);
   cudaMemsetAsync(used, 0, sizeof(int) * N * batch, st);
+  const GjbShape shape = blk ? gjb_shape(N, sizeof(T)) : GjbShape{0, 0, 0};
+  const int b = shape.b;
   for (int z = 0; z < batch; ++z) {
-    stencil_to_dense_kernel<T><<<grid_for(nn2, 8192), 256, 0, st>>>(C[z], L[0], L[1], L[2], L[3], n, aug + z * nn2);
-    gj_init_kernel<T><<<grid_for(N, 1024), 256, 0, st>>>(aug + z * nn2, N, cols + (size_t)z * 2 * N,
-                                                         keys + (size_t)z * (N + 1));
+    // the blocked form never reads a unit column of the right half (slots are written when used)
+    const int ncol = b ? N : 2 * N;
+    stencil_to_dense_kernel<T><<<grid_for((size_t)N * ncol, 8192), 256, 0, st>>>(C[z], L[0], L[1], L[2], L[3], n,
+                                                                                 ncol, aug + z * nn2);
+    ++nl;
+    if (!b) {
+      gj_init_kernel<T><<<grid_for(N, 1024), 256, 0, st>>>(aug + z * nn2, N, cols + (size_t)z * 2 * N,
+                                                           keys + (size_t)z * (N + 1));
+      ++nl;
+    }
   }
   if (!launched()) return -1;
-  const int b = blk ? gjb_width(N, sizeof(T)) : 0;
   if (b) {
-    T* te = (T*)blk;
-    T* prow = te + (size_t)batch * N * b;
-    const size_t sm = 2 * (size_t)b * N * sizeof(T);
-    auto panel = b == 8 ? gjb_panel_kernel<T, 8> : (b == 4 ? gjb_panel_kernel<T, 4> : gjb_panel_kernel<T, 2>);
+    T* prow = (T*)blk;
+    T* cp = prow + (size_t)batch * 8 * kGjPRow;
+    const int pnt = ((N + shape.rpt - 1) / shape.rpt + 31) / 32 * 32;  // threads of a panel CTA
+    const size_t psm = (size_t)(pnt / 32) * 32 * (shape.b + 1) * sizeof(T);  // the warps' staging tiles
+    auto panel = gjb_panel_for<T>(shape);
     allow_big_smem(panel);
-    for (int kb = 0; kb < N; kb += b) {
-      const int bw = N - kb < b ? N - kb : b;
-      panel<<<batch, 1024, sm, st>>>(aug, N, kb, bw, keys, used, te, prow, err);
-      if (kb + bw < 2 * N) {
-        const dim3 grid((unsigned)((2 * N - kb - bw + 255) / 256), (unsigned)((N + kGjbRows - 1) / kGjbRows),
-                        (unsigned)batch);
-        gjb_update_kernel<T><<<grid, 256, 0, st>>>(aug, N, kb, bw, keys, te, prow, err);
+    const size_t smo = ((size_t)kGjTile * (kGjW + 1) + (size_t)kGjW * kGjTile) * sizeof(T);
+    allow_big_smem(gjb_outer_update_kernel<T>);
+    for (int kb0 = 0; kb0 < N; kb0 += kGjW) {
+      const int W = N - kb0 < kGjW ? N - kb0 : kGjW;
+      for (int kb = kb0; kb < kb0 + W; kb += b) {
+        const int bw = kb0 + W - kb < b ? kb0 + W - kb : b;
+        // the block's columns right of the panel, and the block's earlier slots
+        const int c1 = kb + bw, n1 = kb0 + W - c1, c2 = N + kb0, n2 = kb - kb0;
+        panel<<<batch, pnt, psm, st>>>(aug, N, kb, bw, c1, n1, c2, n2, keys, used, prow, err);
+        ++nl;
+        if (n1 + n2 > 0) {
+          const dim3 grid((unsigned)((n1 + n2 + 127) / 128), (unsigned)((N + kGjbRows - 1) / kGjbRows),
+                          (unsigned)batch);
+          gjb_inner_update_kernel<T><<<grid, 128, 0, st>>>(aug, N, kb, bw, c1, n1, c2, n2, keys, prow, err);
+          ++nl;
+        }
+      }
+      if (N - W > 0) {
+        const dim3 gg((unsigned)((N - W + 255) / 256 < 16 ? (N - W + 255) / 256 : 16), (unsigned)W, (unsigned)batch);
+        gjb_gather_kernel<T><<<gg, 256, 0, st>>>(aug, N, kb0, W, keys, cp, err);
+        const dim3 go((unsigned)((N - W + kGjTile - 1) / kGjTile), (unsigned)((N + kGjTile - 1) / kGjTile),
+                      (unsigned)batch);
+        gjb_outer_update_kernel<T><<<go, 256, smo, st>>>(aug, N, kb0, W, used, cp, err);
+        nl += 2;
       }
     }
+    for (int z = 0; z < batch; ++z)
+      gjb_finish_kernel<T><<<grid_for((size_t)N * N, 8192), 256, 0, st>>>(aug + z * nn2, N, keys + (size_t)z * (N + 1),
+                                                                          (T*)inv[z]);
   } else {
     for (int k = 0; k < N; ++k) {
       const dim3 grid((unsigned)((2 * N - k + 255) / 256), (unsigned)N, (unsigned)batch);
       gj_step_kernel<T><<<grid, 256, 0, st>>>(aug, N, k, cols, used, keys, err);
     }
+    nl += N;
+    for (int z = 0; z < batch; ++z)
+      gj_finish_kernel<T><<<grid_for((size_t)N * N, 8192), 256, 0, st>>>(aug + z * nn2, N, keys + (size_t)z * (N + 1),
+                                                                        (T*)inv[z]);
   }
-  for (int z = 0; z < batch; ++z)
-    gj_finish_kernel<T><<<grid_for((size_t)N * N, 8192), 256, 0, st>>>(aug + z * nn2, N, keys + (size_t)z * (N + 1),
-                                                                      (T*)inv[z]);
+  nl += batch;
+  if (launches) *launches = nl;
   return launched() ? 0 : -1;
 }
 
 int dense_inverse_batch(int prec, const double2* const* C, const int L[4], int n, int batch, void* aug, void* scratch,
-                        int* err, void* const* inv, void* blk, cudaStream_t st) {
+                        int* err, void* const* inv, void* blk, cudaStream_t st, long long* launches) {
   // scratch: per matrix two column snapshots [2][N] of the element type, then N + 1 pivot keys per
-  // matrix, then N used-row flags per matrix; blk (optional): the blocked form's tracker and pivot rows
+  // matrix, then N pivot-step flags per matrix; blk (optional): the blocked form's pivot rows
   if (batch < 1) return -1;
-  if (prec == 0) return dense_inverse_t<double2>(C, L, n, batch, (double2*)aug, (char*)scratch, err, inv, blk, st);
-  if (prec == 1) return dense_inverse_t<float2>(C, L, n, batch, (float2*)aug, (char*)scratch, err, inv, blk, st);
+  if (prec == 0)
+    return dense_inverse_t<double2>(C, L, n, batch, (double2*)aug, (char*)scratch, err, inv, blk, st, launches);
+  if (prec == 1)
+    return dense_inverse_t<float2>(C, L, n, batch, (float2*)aug, (char*)scratch, err, inv, blk, st, launches);
   return -1;
 }
 
 int dense_inverse(int prec, const double2* C, const int L[4], int n, void* aug, void* scratch, int* err, void* inv,
                   cudaStream_t st) {
   void* invs[1] = {inv};
-  return dense_inverse_batch(prec, &C, L, n, 1, aug, scratch, err, invs, nullptr, st);
+  return dense_inverse_batch(prec, &C, L, n, 1, aug, scratch, err, invs, nullptr, st, nullptr);
 }
 
 size_t dense_inverse_scratch_bytes(int prec, int N) {

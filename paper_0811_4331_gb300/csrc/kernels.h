@@ -239,9 +239,10 @@ size_t dense_inverse_scratch_bytes(int prec, int N);
 // matrices, scratch batch x dense_inverse_scratch_bytes(prec, N), err batch
 // flags.
 // With blk (gjb_scratch_bytes(N, element size, batch) bytes, 0 = not
-// available for this N) the elimination runs in panels (blocked form).
+// available for this N) the elimination runs in panels and rank-64 blocks
+// (blocked form).  *launches (optional) = the kernels it launched.
 int dense_inverse_batch(int prec, const double2* const* C, const int L[4], int n, int batch, void* aug, void* scratch,
-                        int* err, void* const* inv, void* blk, cudaStream_t st);
+                        int* err, void* const* inv, void* blk, cudaStream_t st, long long* launches);
 size_t gjb_scratch_bytes(int N, size_t eb, int batch);
 // y = inv x (+ y if acc); (matrix, in, out) precisions (0,0,0), (1,0,0), (1,1,1).
 // With scratch (dense_matvec_scratch_bytes(N), tickets zeroed once) 4..64

@@ -12,7 +12,9 @@ right-hand sides, and runs them as one ``mg_solve_masses`` call (a mass per
 right-hand side: every kernel of the solve processes the whole batch, and one
 coarsest inverse per distinct mass is built in shared launches).  A batch is
 admitted while the device bytes of the resident hierarchies, of the batches
-in flight (``mg_footprint``) and its own stay within the HBM budget; each
+in flight (``mg_footprint``) and its own stay within the HBM budget; after a
+batch the worker's copy hands its solve buffers back (``mg_release_work``),
+so between batches it holds only its hierarchy; each
 worker owns a CUDA stream, so batches overlap on the GPU.  All arithmetic
 runs in the library's kernels.  A request's result meets its tolerance
 whether it is solved alone or in a batch (the batch's outer solve stops when
@@ -76,6 +78,7 @@ class SolveServer:
         self.lock = threading.Condition()
         self.bases = {}
         self.copies = {}
+        self.copy_bytes = {}
         self.base_lock = threading.Lock()
         self.completed = []
         self.stop = False
@@ -139,9 +142,23 @@ class SolveServer:
             with self.base_lock:
                 h = wm.mg_retarget(base, self.fields[field][2], stream=stream)
             self.copies[key] = h
+            self.copy_bytes[key] = wm.mg_handle_bytes(h)
             with self.lock:
-                self.resident_bytes += wm.mg_handle_bytes(h)
+                self.resident_bytes += self.copy_bytes[key]
         return h
+
+    def _settle(self, wid, field, stream):
+        """After a batch: the copy hands its solve buffers back (only its hierarchy stays resident;
+        the batch's footprint covered the rest) and the resident count follows its real size."""
+        key = (wid, field)
+        h = self.copies.get(key)
+        if h is None:
+            return
+        wm.mg_release_work(h, stream)
+        now = wm.mg_handle_bytes(h)
+        with self.lock:
+            self.resident_bytes += now - self.copy_bytes[key]
+        self.copy_bytes[key] = now
 
     # ------------------------------------------------------------------ workers
     def _admit(self):
@@ -195,7 +212,10 @@ class SolveServer:
             n = b.shape[0]
             r.x = X[k:k + n] if r.b.ndim == 7 else X[k]
             r.stats = st[k:k + n]
-            if status != wm.MG_OK:
+            # a batch that ran out of iterations fails only the requests with a right-hand side
+            # above its own tolerance
+            if status != wm.MG_OK and (status != wm.MG_ENOCONV or
+                                       any(s["true_rel_residual"] > r.tol for s in r.stats)):
                 r.error = wm.STATUS_NAMES[status]
             k += n
 
@@ -219,6 +239,7 @@ class SolveServer:
             except Exception as e:  # a failed batch must not stop the server
                 for req in batch:
                     req.error = str(e)
+            self._settle(wid, batch[0].field, stream)
             t = time.perf_counter()
             with self.lock:
                 for req in batch:
@@ -251,7 +272,9 @@ def run_stream(server, requests, arrivals):
     t1 = time.perf_counter()
     lat = np.array([r.done - r.arrival for r in requests if r.error is None])
     nrhs = sum((r.b.shape[0] if r.b.ndim == 7 else 1) for r in requests if r.error is None)
+    errors = collections.Counter(r.error[:120] for r in requests if r.error is not None)
     return {"requests": len(requests), "failed": sum(r.error is not None for r in requests),
+            "errors": dict(errors.most_common(4)),
             "wall_s": t1 - t0, "solves_per_s": len(lat) / (t1 - t0), "rhs_per_s": nrhs / (t1 - t0),
             "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_s": float(np.percentile(lat, 99)) if len(lat) else None}

@@ -109,12 +109,14 @@ def _load():
         "mg_level_info": (I, [VP, I, P(I), P(I), P(I)]),
         "mg_get_prolongator": (I, [VP, I, VP]),
         "mg_get_coarse_op": (I, [VP, I, VP]),
+        "mg_get_coarsest_inverse": (I, [VP, VP]),
         "mg_footprint": (ctypes.c_size_t, [P(I), P(mg_params), I]),
         "mg_profile": (I, [VP, ctypes.c_uint]),
         "mg_launch_count": (ctypes.c_ulonglong, []),
         "mg_alloc_count": (ctypes.c_ulonglong, []),
         "mg_trim_cache": (ctypes.c_size_t, []),
         "mg_handle_bytes": (ctypes.c_size_t, [VP]),
+        "mg_release_work": (ctypes.c_size_t, [VP, VP]),
         "mg_profile_read": (I, [VP, I, I, P(ctypes.c_longlong), P(D)]),
         "mg_profile_bytes": (I, [VP, I, I, P(D)]),
         "mg_tune": (I, [I]),
@@ -133,9 +135,9 @@ LIB = _load()
 EXPORTS = ["mg_last_error", "mg_default_params", "mg_setup", "mg_retarget", "mg_destroy", "mg_solve", "dslash_apply",
            "coarse_apply", "restrict_apply", "prolong_apply", "mr_apply", "vcycle_apply", "mg_field_to_internal",
            "mg_field_from_internal", "mg_level_info", "mg_get_prolongator", "mg_get_coarse_op",
-           "mg_footprint", "mg_profile", "mg_profile_read", "mg_profile_bytes",
-           "mg_launch_count", "mg_alloc_count", "mg_trim_cache", "mg_handle_bytes", "mr_apply_noalloc", "mg_tune",
-           "mg_tune_report", "krylov_solve", "mg_retarget_batch", "eo_split", "eo_merge", "dslash_eo_apply",
+           "mg_get_coarsest_inverse", "mg_footprint", "mg_profile", "mg_profile_read", "mg_profile_bytes",
+           "mg_launch_count", "mg_alloc_count", "mg_trim_cache", "mg_handle_bytes", "mg_release_work",
+           "mr_apply_noalloc", "mg_tune", "mg_tune_report", "krylov_solve", "mg_retarget_batch", "eo_split", "eo_merge", "dslash_eo_apply",
            "schur_apply", "mg_solve_many", "mg_solve_masses"]
 
 (MG_K_DSLASH, MG_K_COARSE, MG_K_RESTRICT, MG_K_PROLONG, MG_K_VECTOR, MG_K_COARSEST, MG_K_SETUP, MG_K_GALERKIN,
@@ -435,6 +437,20 @@ def mg_get_coarse_op(h, level):
     return out
 
 
+def mg_get_coarsest_inverse(h):
+    """Dense inverse of the coarsest operator, [N][N] complex in the external order (site-major,
+    component fastest), N = sites x components of the coarsest level."""
+    last = 0
+    while LIB.mg_level_info(h.ptr, last + 1, (ctypes.c_int * 4)(), ctypes.byref(ctypes.c_int()),
+                            ctypes.byref(ctypes.c_int())) == MG_OK:
+        last += 1
+    dims, nc, _ = mg_level_info(h, last)
+    N = int(np.prod(dims)) * nc
+    out = np.empty((N, N), dtype=np.complex128)
+    _check(LIB.mg_get_coarsest_inverse(h.ptr, ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
 def mg_footprint(dims, params, nrhs):
     d = (ctypes.c_int * 4)(*[int(x) for x in dims])
     return int(LIB.mg_footprint(d, ctypes.byref(params), int(nrhs)))
@@ -452,6 +468,12 @@ def mg_alloc_count():
 def mg_handle_bytes(h):
     """Device bytes the handle holds now."""
     return int(LIB.mg_handle_bytes(h.ptr))
+
+
+def mg_release_work(h, stream=None):
+    """Hand the handle's solve buffers back to the library's cache (the hierarchy stays); returns the
+    bytes released."""
+    return int(LIB.mg_release_work(h.ptr, _stream(stream)))
 
 
 def mg_trim_cache():

@@ -202,3 +202,34 @@ def test_mixed_coarsest_solve_in_fp64():
         assert _true_rel(U, mass, x, b) <= 1e-10
         its[f64] = st[0]["iters"]
     assert abs(its[1] - its[0]) <= 2, its
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_release_work_keeps_the_hierarchy(mixed):
+    """mg_release_work hands the solve buffers back (the handle shrinks to its hierarchy) and the next
+    solve, which takes fresh buffers and recaptures its cycle, returns the same x; a mass-per-RHS solve
+    after it rebuilds its inverses."""
+    wm = require_gpu()
+    dims = (8, 4, 4, 8)
+    U = inputs.random_gauge(dims, 5)
+    p = wm.mg_default_params(n_levels=3, block=[(2, 2, 2, 2), (2, 2, 1, 2)], nv=[8, 6], setup_sweeps=[20, 20],
+                             mixed=mixed)
+    h = wm.mg_setup(U, dims, 0.1, p)
+    b = np.stack([inputs.gaussian_spinor(dims, 20 + r) for r in range(3)])
+    x1 = np.zeros_like(b)
+    wm.mg_solve(h, b, x1, 1e-10)
+    big = wm.mg_handle_bytes(h)
+    freed = wm.mg_release_work(h)
+    assert freed > 0 and wm.mg_handle_bytes(h) == big - freed
+    x2 = np.zeros_like(b)
+    wm.mg_solve(h, b, x2, 1e-10)
+    assert rel_err(x2, x1) <= 1e-12
+    masses = [0.1, 0.15, 0.2]
+    xm = np.zeros_like(b)
+    wm.mg_solve_masses(h, masses, b, xm, 1e-10)
+    wm.mg_release_work(h)
+    xm2 = np.zeros_like(b)
+    wm.mg_solve_masses(h, masses, b, xm2, 1e-10)
+    assert rel_err(xm2, xm) <= 1e-12
+    for r, m in enumerate(masses):
+        assert _true_rel(U, m, xm2[r], b[r]) <= 1e-10
