@@ -250,7 +250,10 @@ def native(args, rank, world, U, b):
             assert rel <= TOL * 1.0001, ("even-odd smoother solve missed the tolerance", m, rel)
             pm.append({"dm": round(m - mc, 4), "iters": st["iters"], "fine_dslash": st["fine_dslash"],
                        "true_rel_residual": rel})
-        out["mixed_eo_smoother"] = {"value": float(np.median(t_eo)), "unit": "s per 4-mass sweep", "per_mass": pm}
+        out["mixed_eo_smoother"] = {"value": float(np.median(t_eo)), "unit": "s per 4-mass sweep", "per_mass": pm,
+                                    # mg_solve_masses needs the MR fine smoother, so this row always runs
+                                    # the masses as concurrent handles
+                                    "sweep": "concurrent handles (retarget batch + mg_solve_many)"}
     # the unpreconditioned baseline the paper compares against (Secs. 4-5): FP64 BiCGstab per mass, on the
     # full system and on its even-odd Schur complement
     if not args.no_plain:
@@ -689,6 +692,11 @@ def reference_arm(args, rank, world):
 C3_DIMS = (16, 16, 16, 32)
 
 
+# MR setup sweeps of the two 16^3 x 32 levels: at m_crit + 0.02 the mixed solve needs 450 iterations with
+# 300/100, 250 with 1000/300 and 300 with 2000/500 (the candidates then crowd onto the lowest modes)
+C3_SWEEPS = (1000, 300)
+
+
 def c3_mcrit():
     """m_crit of the 16^3 x 32 beta = 6.0 field: minus the smallest real part of the spectrum of D(m = 0),
     from the oracle's Arnoldi run (tests/golden/mcrit.json)."""
@@ -710,13 +718,13 @@ def c3_workload(args):
     B = torch.from_numpy(np.stack(srcs)).cuda()
     mass = c3_mcrit() + args.c3_dm
     out = {"workload": "16^3x32 beta=6.0 heatbath (200 sweeps, seed 0), 3-level MG 4^4 then 2^4 blocks, Nv=24/24, "
-                       "m = m_crit + %g (m_crit = %.4f from Arnoldi), 12 point + 12 Gaussian sources, tol 1e-10"
-                       % (args.c3_dm, c3_mcrit())}
+                       "%d/%d MR setup sweeps, m = m_crit + %g (m_crit = %.4f from Arnoldi), 12 point + 12 Gaussian "
+                       "sources, tol 1e-10" % (C3_SWEEPS[0], C3_SWEEPS[1], args.c3_dm, c3_mcrit())}
     res = {}
     for mixed in ((1,) if args.no_plain else (1, 0)):
         # the mixed form applies the level-1 stencil to all right-hand sides on tensor cores
         p = wm.mg_default_params(n_levels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 24],
-                                 setup_sweeps=[300, 100], mixed=mixed, seed=7, coarse_mma=mixed)
+                                 setup_sweeps=list(C3_SWEEPS), mixed=mixed, seed=7, coarse_mma=mixed)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = wm.mg_setup(Ud, C3_DIMS, mass, p, stream=stream)
@@ -746,7 +754,7 @@ def c3_workload(args):
         out["speedup_solve"] = round(res["fp64_single_rhs"]["solve_s"] / res["mixed_multi_rhs"]["solve_s"], 3)
     # class shares and the dominant class's roofline of the mixed multi-RHS solve (one profiled run)
     p = wm.mg_default_params(n_levels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 24],
-                             setup_sweeps=[300, 100], mixed=1, seed=7, coarse_mma=1)
+                             setup_sweeps=list(C3_SWEEPS), mixed=1, seed=7, coarse_mma=1)
 
     def run(collect):
         h = wm.mg_setup(Ud, C3_DIMS, mass, p, stream=stream)
@@ -845,7 +853,7 @@ def serve_workload(args):
     crit = {d: crit_of(d) for d in ((8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32))}
     two = wm.mg_default_params(n_levels=2, block=[(4, 4, 4, 4)], nv=[20], setup_sweeps=[300], mixed=1, seed=7)
     three = wm.mg_default_params(n_levels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 24],
-                                 setup_sweeps=[300, 100], mixed=1, seed=7, coarse_mma=1)
+                                 setup_sweeps=list(C3_SWEEPS), mixed=1, seed=7, coarse_mma=1)
     fields = {}
     for dims, p in (((8, 8, 8, 8), two), ((12, 12, 12, 12), two), ((16, 16, 16, 32), three)):
         U = inputs.heatbath_gauge(dims, BETA, HB_SWEEPS, HB_SEED)

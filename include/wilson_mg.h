@@ -78,7 +78,8 @@ typedef struct {
   int block[MG_MAX_LEVELS - 1][4];    /* aggregate of level l -> l+1, {bx, by, bz, bt} */
   int nv[MG_MAX_LEVELS - 1];          /* null vectors of level l (coarse ncomp = 2 nv) */
   int setup_sweeps[MG_MAX_LEVELS - 1];/* MR steps on A x = 0 per candidate (Sec. 2, "l") */
-  int coarse_cycles[MG_MAX_LEVELS - 1];/* next-level V-cycles per coarse correction of level l */
+  int coarse_cycles[MG_MAX_LEVELS - 1];/* next-level V-cycles per coarse correction of level l (at most 8
+                                         with the flexible coarse solver) */
   int nu_pre, nu_post;                /* MR smoothing steps before / after the coarse correction */
   double omega;                       /* MR under-relaxation */
   int gcr_restart;                    /* outer flexible GCR restart length */

@@ -28,7 +28,12 @@ void set_error(const std::string& msg) { g_err = msg; }
 static unsigned long long g_launches = 0;
 // profiler mask that new handles start with (mg_profile(NULL, mask))
 static unsigned g_default_prof_mask = 0;
-inline void count_launches(unsigned long long n) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
+// the same count for the calling thread only (what a graph capture on this thread recorded)
+static thread_local unsigned long long tl_launches = 0;
+inline void count_launches(unsigned long long n) {
+  __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED);
+  tl_launches += n;
+}
 
 }  // namespace wmg
 
@@ -574,7 +579,15 @@ int coarse_gcr(mg_handle* h, int l, int prec, const void* b, void* e, int iters,
   char* Z = (char*)work(h, l, prec, WV_KZ, nrhs, kInnerBasis);
   void* rl = pl == prec ? nullptr : work(h, l, pl, WV_PR, nrhs);
   void* el = pl == prec ? nullptr : work(h, l, pl, WV_PE, nrhs);
-  if (!r || !W || !Z || iters > kInnerBasis || (pl != prec && (!rl || !el))) return MG_ENOMEM;
+  if (iters > kInnerBasis) {
+    set_error("coarse_cycles above the flexible coarse solver's basis");
+    return MG_EINVAL;
+  }
+  if (!r || !W || !Z || (pl != prec && (!rl || !el))) {
+    set_error(h->capturing ? "coarse solver work buffer missing during a graph capture"
+                           : "device allocation failed for the coarse solver's work vectors");
+    return MG_ENOMEM;
+  }
   const size_t swr = slot_inner(l), srn = swr + 4 * kMaxRhs, sbeta = srn + 4 * kMaxRhs;
   CK(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, h->st));
   CK(cudaMemsetAsync(e, 0, vb, h->st));
@@ -706,7 +719,7 @@ int vcycle_graph(mg_handle* h, const void* r, void* e, int nrhs) {
   CK(cudaStreamSynchronize(h->st));
   cudaStream_t keep = h->st;
   const unsigned long long gen = h->buf_gen;
-  const unsigned long long n0 = mg_launch_count();
+  const unsigned long long n0 = tl_launches;  // this thread's: other threads launch meanwhile
   h->st = h->cap_st;
   h->capturing = true;
   cudaGraph_t graph = nullptr;
@@ -723,7 +736,10 @@ int vcycle_graph(mg_handle* h, const void* r, void* e, int nrhs) {
   }
   h->capturing = false;
   h->st = keep;
-  const unsigned long long nodes = mg_launch_count() - n0;
+  const unsigned long long nodes = tl_launches - n0;
+  // a capture launches nothing: its kernels count when the graph is replayed
+  __atomic_fetch_sub(&g_launches, nodes, __ATOMIC_RELAXED);
+  tl_launches = n0;
   if (ce != cudaSuccess || rc != MG_OK || gen != h->buf_gen) {
     // the eager run above already produced e; a capture that failed only costs the graph
     if (graph) cudaGraphDestroy(graph);
@@ -1401,6 +1417,12 @@ int mg_setup(mg_handle** hout, const double* gauge, int gauge_on_device, const i
     set_error("fine_smoother must be 0 (MR) or 1 (even-odd)");
     return MG_EINVAL;
   }
+  for (int l = 0; l + 2 < p->n_levels; ++l)
+    if (p->coarse_solver == 0 && p->coarse_cycles[l] > kInnerBasis) {
+      set_error("coarse_cycles above " + std::to_string(kInnerBasis) +
+                " (the flexible coarse solver keeps that many directions)");
+      return MG_EINVAL;
+    }
   if (p->fine_smoother == 1 && (dims[0] % 2 || dims[1] % 2 || dims[2] % 2 || dims[3] % 2)) {
     set_error("the even-odd smoother needs every lattice extent even");
     return MG_EINVAL;

@@ -454,7 +454,7 @@ static unsigned grid_for(size_t tot, size_t cap) {
 // brings the rest of the block's columns and the block's earlier slots
 // along.
 constexpr int kGjW = 64;     // steps per outer block (a multiple of every panel width)
-constexpr int kGjbRows = 16;  // rows per CTA of the inner update
+constexpr int kGjbRows = 4;  // rows per CTA of the inner update (many CTAs: the update is short)
 
 // Panel kernel: one CTA per matrix z (blockIdx.x), b <= B steps on columns
 // kb .. kb + b - 1.  Thread t owns rows t + m nt (m < RPT) and keeps their

@@ -249,9 +249,14 @@ __global__ void __launch_bounds__(NT) galerkin_kernel(const Agg g, Op op, const 
       const TP* pr = P + ((size_t)B * 2 * g.nv + row) * len;
       const cx<R>* hv = h + (size_t)chi * len;
       cx<R> in = zero<R>(), out = zero<R>();
-      for (int e = lane; e < len; e += 32) {
-        const int s = e % g.bsites;
-        const cx<R> t = cmul_conj(ldc<R>(pr, e), hv[e]);
+      // site-major: the site's crossing test once, its nhalf components' loads in flight together
+      for (int s = lane; s < g.bsites; s += 32) {
+        cx<R> t = zero<R>();
+#pragma unroll 6
+        for (int c = 0; c < g.nhalf; ++c) {
+          const int e = c * g.bsites + s;
+          t = t + cmul_conj(ldc<R>(pr, e), hv[e]);
+        }
         if (crosses(g, s, d))
           out = out + t;
         else

@@ -58,6 +58,13 @@ def test_host_only_entry_points(lib):
     st = wm.LIB.mg_setup(ctypes.byref(h), ctypes.c_void_p(1), 0, (ctypes.c_int * 4)(4, 4, 4, 4), 0.1,
                          ctypes.byref(p), None, None)
     assert st == wm.MG_EINVAL and "fine_smoother" in wm.mg_last_error()
+    p.fine_smoother = 0
+    p.n_levels = 3
+    p.coarse_cycles[0] = 9  # the flexible coarse solver keeps 8 directions
+    st = wm.LIB.mg_setup(ctypes.byref(h), ctypes.c_void_p(1), 0, (ctypes.c_int * 4)(8, 8, 8, 8), 0.1,
+                         ctypes.byref(p), None, None)
+    assert st == wm.MG_EINVAL and "coarse_cycles" in wm.mg_last_error()
+    assert wm.LIB.mg_release_work(None, None) == 0
     # null handles and empty batches are refused without touching a device
     assert wm.LIB.mg_solve_many(None, 0, None, None, 1, 1, 1e-10, None, None) == wm.MG_EINVAL
     assert wm.LIB.eo_split(None, 0, None, None, None, 1, None) == wm.MG_EINVAL
