@@ -57,14 +57,30 @@ __global__ void __launch_bounds__(NT) coarse_apply_kernel(const CoarseArgs<S> A)
     const int terms = 9 * n;
     int d = q / n, j = q - (q / n) * n;
     int nb = (q < terms) ? neighbor(c, A.L, d) : 0;
-    for (int p = q; p < terms; p += G) {
-      acc = cfma(ldc<R>(A.C, (((size_t)(d * n + i) * n) + j) * V + B), ldc<R>(A.in, voff + (size_t)j * V + nb), acc);
+    auto next = [&]() {
       j += G;
       while (j >= n) {
         j -= n;
         ++d;
         if (d < 9) nb = neighbor(c, A.L, d);
       }
+    };
+    int p = q;
+    // four terms' loads in flight per lane (the sum keeps its order)
+    for (; p + 3 * G < terms; p += 4 * G) {
+      cx<R> cv[4], xv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cv[u] = ldc<R>(A.C, (((size_t)(d * n + i) * n) + j) * V + B);
+        xv[u] = ldc<R>(A.in, voff + (size_t)j * V + nb);
+        next();
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc = cfma(cv[u], xv[u], acc);
+    }
+    for (; p < terms; p += G) {
+      acc = cfma(ldc<R>(A.C, (((size_t)(d * n + i) * n) + j) * V + B), ldc<R>(A.in, voff + (size_t)j * V + nb), acc);
+      next();
     }
   }
   if (G > 1) {
@@ -182,7 +198,16 @@ __global__ void __launch_bounds__(NT) restrict_kernel(const Agg g, const SP* P, 
     const SP* pr = P + ((size_t)B * 2 * g.nv + row) * len;
     const cx<R>* v = sm + (size_t)chi * len;
     cx<R> acc = zero<R>();
-    for (int e = lane; e < len; e += 32) acc = cfma_conj(ldc<R>(pr, e), v[e], acc);
+    int e = lane;
+    // eight loads of P in flight per lane (the sum keeps its order)
+    for (; e + 7 * 32 < len; e += 8 * 32) {
+      cx<R> pv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) pv[u] = ldc<R>(pr, e + u * 32);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc = cfma_conj(pv[u], v[e + u * 32], acc);
+    }
+    for (; e < len; e += 32) acc = cfma_conj(ldc<R>(pr, e), v[e], acc);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       acc.re += __shfl_down_sync(0xffffffffu, acc.re, o);
@@ -212,7 +237,16 @@ __global__ void __launch_bounds__(NT) prolong_kernel(const Agg g, const SP* P, c
     const int chi = c / nh, cl = c - chi * nh;
     const SP* pc = P + ((size_t)B * 2 + chi) * nv * len + (size_t)cl * bs + s;
     cx<R> acc = zero<R>();
-    for (int k = 0; k < nv; ++k) acc = cfma(ldc<R>(pc, (size_t)k * len), xc[chi * nv + k], acc);
+    int k = 0;
+    // four loads of P in flight per thread (the sum keeps its order)
+    for (; k + 3 < nv; k += 4) {
+      cx<R> pv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pv[u] = ldc<R>(pc, (size_t)(k + u) * len);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc = cfma(pv[u], xc[chi * nv + k + u], acc);
+    }
+    for (; k < nv; ++k) acc = cfma(ldc<R>(pc, (size_t)k * len), xc[chi * nv + k], acc);
     stc(out, (size_t)rhs * g.ncomp * g.V + fidx_q(c, agg_site(g, B, s), g.V, g.q), acc);
   }
 }
@@ -1013,6 +1047,15 @@ __global__ void __launch_bounds__(32 * kMvWarps) dense_matvec4_kernel(int N, con
   const SI* xr = x + (size_t)rhs * N;
   cx<R> a = zero<R>(), b = zero<R>();
   int j = c0 + lane;
+  // eight loads in flight per lane; chain a takes columns j, j + 64, ..., chain b j + 32, j + 96, ...
+  for (; j + 96 < c1; j += 128) {
+    const cx<R> m0 = ldc<R>(rp, j), m1 = ldc<R>(rp, j + 32), m2 = ldc<R>(rp, j + 64), m3 = ldc<R>(rp, j + 96);
+    const cx<R> x0 = ldc<R>(xr, j), x1 = ldc<R>(xr, j + 32), x2 = ldc<R>(xr, j + 64), x3 = ldc<R>(xr, j + 96);
+    a = cfma(m0, x0, a);
+    b = cfma(m1, x1, b);
+    a = cfma(m2, x2, a);
+    b = cfma(m3, x3, b);
+  }
   for (; j + 32 < c1; j += 64) {
     a = cfma(ldc<R>(rp, j), ldc<R>(xr, j), a);
     b = cfma(ldc<R>(rp, j + 32), ldc<R>(xr, j + 32), b);

@@ -3,7 +3,7 @@
 // * blockwise Gram-Schmidt of the candidate vectors into P (Sec. 2, adaptive
 //   step 3 and Eq. 2.3: P V_c = V with P^+ P = 1), one aggregate and
 //   chirality per CTA (chirality kept intact, Sec. 3 after Eq. 3.2 and the
-//   blocking of Sec. 5), modified Gram-Schmidt applied twice in candidate
+//   blocking of Sec. 5), classical Gram-Schmidt applied twice in candidate
 //   order;
 // * the Galerkin coarse operator A_c = P^+ A P (Sec. 2) as a 9-point stencil:
 //   column j of every block C_d'(B) comes from one CTA per aggregate that
@@ -13,6 +13,8 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "wilson_hop.cuh"
+
+#include <cooperative_groups.h>
 
 namespace wmg {
 
@@ -44,54 +46,119 @@ __device__ __forceinline__ cx<double> block_csum(cx<double> v, double* sm) {
 }
 
 // ------------------------------------------------------------------ block Gram-Schmidt
+constexpr int kGsMaxNv = 128;  // candidates per level the block Gram-Schmidt takes
+constexpr int kGsCluster = 2;  // CTAs (SMs) per aggregate and chirality: FP64 is this part's scarce pipe
+
+// Sum of NV values over the block, then over the CTAs of the cluster in rank
+// order (the same total in every CTA and thread).  part: NV doubles of this
+// CTA's shared memory, sm: NV * NT / 32 doubles of scratch.
+template <int NV, int NT>
+__device__ __forceinline__ void cluster_sum(double (&a)[NV], double* sm, double* part) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  block_sum<NV, NT, double>(a, sm);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int u = 0; u < NV; ++u) part[u] = a[u];
+  cl.sync();  // every CTA's partial is written
+#pragma unroll
+  for (int u = 0; u < NV; ++u) {
+    double t = 0.0;
+    for (int r = 0; r < (int)cl.num_blocks(); ++r) t += cl.map_shared_rank(part, r)[u];
+    a[u] = t;
+  }
+  cl.sync();  // every CTA has read every partial before any is overwritten
+}
+
+// One classical Gram-Schmidt pass of q (this CTA's elements e in [e0, e1),
+// this thread's e0 + tid + m NT) against the k earlier vectors
+// p_j = base + j len: all k overlaps first (eight per reduction), then one
+// combined update.
 template <int NT>
-__global__ void __launch_bounds__(NT) block_gs_kernel(const Agg g, const double2* cand, double2* P, int* err) {
-  __shared__ double sm[2 * (NT / 32)];
-  const int B = blockIdx.x >> 1, chi = blockIdx.x & 1;
+__device__ __forceinline__ void cgs_pass(const double2* base, int k, int len, int e0, int e1, double2* q, double* sm,
+                                         double* part, cx<double>* dots) {
+  for (int j0 = 0; j0 < k; j0 += 8) {
+    double a[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) a[u] = 0.0;
+    for (int e = e0 + threadIdx.x; e < e1; e += NT) {
+      const cx<double> qe = mk<double>(q[e].x, q[e].y);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < k) {  // a += conj(p) q: four FP64 FMAs
+          const double2 pv = base[(size_t)(j0 + u) * len + e];
+          a[2 * u] = fma(pv.x, qe.re, fma(pv.y, qe.im, a[2 * u]));
+          a[2 * u + 1] = fma(pv.x, qe.im, fma(-pv.y, qe.re, a[2 * u + 1]));
+        }
+    }
+    cluster_sum<16, NT>(a, sm, part);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if ((int)threadIdx.x == u && j0 + u < k) dots[j0 + u] = mk<double>(a[2 * u], a[2 * u + 1]);
+    __syncthreads();
+  }
+  for (int e = e0 + threadIdx.x; e < e1; e += NT) {
+    cx<double> v = mk<double>(q[e].x, q[e].y);
+    for (int j = 0; j < k; ++j) {  // v -= d_j p_j, four FP64 FMAs
+      const double2 pv = base[(size_t)j * len + e];
+      const cx<double> d = dots[j];
+      v.re = fma(-d.re, pv.x, fma(d.im, pv.y, v.re));
+      v.im = fma(-d.re, pv.y, fma(-d.im, pv.x, v.im));
+    }
+    q[e] = make_double2(v.re, v.im);
+  }
+  __syncthreads();
+}
+
+// One cluster of kGsCluster CTAs per (aggregate B, chirality chi), each CTA a
+// contiguous share of the block's elements: the candidates restricted to the
+// block, orthonormalised in candidate order by classical Gram-Schmidt applied
+// twice (each pass removes the overlaps with all earlier vectors at once).
+template <int NT>
+__global__ void __cluster_dims__(kGsCluster, 1, 1) __launch_bounds__(NT)
+    block_gs_kernel(const Agg g, const double2* cand, double2* P, int* err) {
+  __shared__ double sm[16 * (NT / 32)];
+  __shared__ double part[16];
+  __shared__ cx<double> dots[kGsMaxNv];
+  const int pair = blockIdx.x / kGsCluster, rank = blockIdx.x % kGsCluster;
+  const int B = pair >> 1, chi = pair & 1;
   const int nv = g.nv, nh = g.nhalf, bs = g.bsites;
   const int len = nh * bs;
+  const int e0 = (int)((long)rank * len / kGsCluster), e1 = (int)((long)(rank + 1) * len / kGsCluster);
   double2* base = P + ((size_t)B * 2 + chi) * nv * len;
   for (int k = 0; k < nv; ++k) {
     double2* q = base + (size_t)k * len;
     // gather candidate k restricted to (B, chi)
-    double nrm0 = 0.0;
-    for (int e = threadIdx.x; e < len; e += NT) {
+    double nrm[1] = {0.0};
+    for (int e = e0 + threadIdx.x; e < e1; e += NT) {
       const int c = e / bs, s = e - c * bs;
       const double2 v = cand[(size_t)k * g.ncomp * g.V + fidx_q(chi * nh + c, agg_site2(g, B, s), g.V, g.q)];
       q[e] = v;
-      nrm0 += v.x * v.x + v.y * v.y;
+      nrm[0] += v.x * v.x + v.y * v.y;
     }
-    const double orig = block_csum<NT>(mk<double>(nrm0, 0.0), sm).re;
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int j = 0; j < k; ++j) {
-        const double2* pj = base + (size_t)j * len;
-        cx<double> d = zero<double>();
-        for (int e = threadIdx.x; e < len; e += NT)
-          d = cfma_conj(mk<double>(pj[e].x, pj[e].y), mk<double>(q[e].x, q[e].y), d);
-        d = block_csum<NT>(d, sm);
-        for (int e = threadIdx.x; e < len; e += NT) {
-          const cx<double> v = mk<double>(q[e].x, q[e].y) - d * mk<double>(pj[e].x, pj[e].y);
-          q[e] = make_double2(v.re, v.im);
-        }
-        __syncthreads();
-      }
+    cluster_sum<1, NT>(nrm, sm, part);
+    const double orig = nrm[0];
+    if (k > 0) {
+      cgs_pass<NT>(base, k, len, e0, e1, q, sm, part, dots);
+      cgs_pass<NT>(base, k, len, e0, e1, q, sm, part, dots);
     }
-    double nrm = 0.0;
-    for (int e = threadIdx.x; e < len; e += NT) nrm += q[e].x * q[e].x + q[e].y * q[e].y;
-    nrm = block_csum<NT>(mk<double>(nrm, 0.0), sm).re;
-    const double nq = sqrt(nrm);
-    if (!(nq > 1e-12 * sqrt(orig))) {
-      if (threadIdx.x == 0) atomicExch(err, 2);
+    nrm[0] = 0.0;
+    for (int e = e0 + threadIdx.x; e < e1; e += NT) nrm[0] += q[e].x * q[e].x + q[e].y * q[e].y;
+    cluster_sum<1, NT>(nrm, sm, part);
+    const double nq = sqrt(nrm[0]);
+    if (!(nq > 1e-12 * sqrt(orig))) {  // the same decision in every CTA of the cluster
+      if (threadIdx.x == 0 && rank == 0) atomicExch(err, 2);
       return;
     }
     const double inv = 1.0 / nq;
-    for (int e = threadIdx.x; e < len; e += NT) q[e] = make_double2(q[e].x * inv, q[e].y * inv);
+    for (int e = e0 + threadIdx.x; e < e1; e += NT) q[e] = make_double2(q[e].x * inv, q[e].y * inv);
     __syncthreads();
   }
 }
 
 int launch_block_gs(const Agg& g, const double2* cand, double2* P, int* err, cudaStream_t st) {
-  block_gs_kernel<256><<<g.Vc * 2, 256, 0, st>>>(g, cand, P, err);
+  if (g.nv > kGsMaxNv) return -1;
+  block_gs_kernel<256><<<g.Vc * 2 * kGsCluster, 256, 0, st>>>(g, cand, P, err);
   return launched() ? 0 : -1;
 }
 
