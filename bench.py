@@ -692,9 +692,16 @@ def reference_arm(args, rank, world):
 C3_DIMS = (16, 16, 16, 32)
 
 
-# MR setup sweeps of the two 16^3 x 32 levels: at m_crit + 0.02 the mixed solve needs 450 iterations with
-# 300/100, 250 with 1000/300 and 300 with 2000/500 (the candidates then crowd onto the lowest modes)
-C3_SWEEPS = (1000, 300)
+# Setup of the 16^3 x 32 hierarchy (Nv = 24/24): 4 + 16 candidates of each level from 300 MR sweeps, the
+# rest from two adaptive steps of 64 solver iterations each (Sec. 2).  At m_crit + 0.02 the mixed solve
+# needs 100 iterations this way, against 250 with 1000/300 relaxation sweeps alone and 450 with 300/100.
+C3_SWEEPS = (300, 300)
+C3_ADAPT = dict(adapt_steps=2, adapt_nv=[20, 8], adapt_cycles=64)
+
+
+def c3_params(wm, mixed):
+    return wm.mg_default_params(n_levels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 24],
+                                setup_sweeps=list(C3_SWEEPS), mixed=mixed, seed=7, coarse_mma=mixed, **C3_ADAPT)
 
 
 def c3_mcrit():
@@ -718,13 +725,13 @@ def c3_workload(args):
     B = torch.from_numpy(np.stack(srcs)).cuda()
     mass = c3_mcrit() + args.c3_dm
     out = {"workload": "16^3x32 beta=6.0 heatbath (200 sweeps, seed 0), 3-level MG 4^4 then 2^4 blocks, Nv=24/24, "
-                       "%d/%d MR setup sweeps, m = m_crit + %g (m_crit = %.4f from Arnoldi), 12 point + 12 Gaussian "
-                       "sources, tol 1e-10" % (C3_SWEEPS[0], C3_SWEEPS[1], args.c3_dm, c3_mcrit())}
+                       "setup %d/%d MR sweeps + 2 adaptive steps (20/8 of the candidates, 64 solver iterations each), "
+                       "m = m_crit + %g (m_crit = %.4f from Arnoldi), 12 point + 12 Gaussian sources, tol 1e-10"
+                       % (C3_SWEEPS[0], C3_SWEEPS[1], args.c3_dm, c3_mcrit())}
     res = {}
     for mixed in ((1,) if args.no_plain else (1, 0)):
         # the mixed form applies the level-1 stencil to all right-hand sides on tensor cores
-        p = wm.mg_default_params(n_levels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 24],
-                                 setup_sweeps=list(C3_SWEEPS), mixed=mixed, seed=7, coarse_mma=mixed)
+        p = c3_params(wm, mixed)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = wm.mg_setup(Ud, C3_DIMS, mass, p, stream=stream)
@@ -753,8 +760,7 @@ def c3_workload(args):
     if "fp64_single_rhs" in res:
         out["speedup_solve"] = round(res["fp64_single_rhs"]["solve_s"] / res["mixed_multi_rhs"]["solve_s"], 3)
     # class shares and the dominant class's roofline of the mixed multi-RHS solve (one profiled run)
-    p = wm.mg_default_params(n_levels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 24],
-                             setup_sweeps=list(C3_SWEEPS), mixed=1, seed=7, coarse_mma=1)
+    p = c3_params(wm, 1)
 
     def run(collect):
         h = wm.mg_setup(Ud, C3_DIMS, mass, p, stream=stream)
@@ -770,6 +776,10 @@ def c3_workload(args):
 
 # ---------------------------------------------------------------------------- large lattice
 C5_DIMS = (32, 32, 32, 64)
+
+
+# the 16^3 x 32 setup's adaptive steps, on the first two of the three coarsenings
+C5_ADAPT = dict(adapt_steps=2, adapt_nv=[20, 8, 0], adapt_cycles=64)
 
 
 def tile_gauge(U, reps):
@@ -798,7 +808,9 @@ def c5_workload(args):
     nrhs = args.c5_rhs
     B = torch.from_numpy(np.stack([inputs.gaussian_spinor(C5_DIMS, 200 + r) for r in range(nrhs)])).cuda()
     out = {"workload": "32^3x64: the 16^3x32 beta=6.0 heatbath field (200 sweeps, seed 0) tiled 2x2x2x2, "
-                       "4-level MG 4^4, 2^4, 2^4 blocks, Nv=24/32/24, %d Gaussian sources, tol 1e-10, GCR(%d)"
+                       "4-level MG 4^4, 2^4, 2^4 blocks, Nv=24/32/24, setup 300 MR sweeps + 2 adaptive steps "
+                       "(20/8 candidates of the first two levels, 64 solver iterations each), %d Gaussian sources, "
+                       "tol 1e-10, GCR(%d)"
                        % (nrhs, args.c5_restart), "masses": []}
     for dm in args.c5_dm:
         mass = c3_mcrit() + dm
@@ -807,8 +819,8 @@ def c5_workload(args):
             # the third level (4^3 x 8 sites x 64 components = 32768 unknowns) is too large for the
             # exact dense coarsest solve, so a fourth level (2^4 blocks, Nv = 24: 1536 unknowns) takes it
             p = wm.mg_default_params(n_levels=4, block=[(4, 4, 4, 4), (2, 2, 2, 2), (2, 2, 2, 2)], nv=[24, 32, 24],
-                                     setup_sweeps=[300, 100, 100], mixed=mixed, seed=7, coarse_mma=mixed,
-                                     gcr_restart=args.c5_restart, max_iter=4000)
+                                     setup_sweeps=[300, 300, 300], mixed=mixed, seed=7, coarse_mma=mixed,
+                                     gcr_restart=args.c5_restart, max_iter=4000, **C5_ADAPT)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = wm.mg_setup(Ud, C5_DIMS, mass, p, stream=stream)
@@ -852,8 +864,7 @@ def serve_workload(args):
 
     crit = {d: crit_of(d) for d in ((8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32))}
     two = wm.mg_default_params(n_levels=2, block=[(4, 4, 4, 4)], nv=[20], setup_sweeps=[300], mixed=1, seed=7)
-    three = wm.mg_default_params(n_levels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 24],
-                                 setup_sweeps=list(C3_SWEEPS), mixed=1, seed=7, coarse_mma=1)
+    three = c3_params(wm, 1)
     fields = {}
     for dims, p in (((8, 8, 8, 8), two), ((12, 12, 12, 12), two), ((16, 16, 16, 32), three)):
         U = inputs.heatbath_gauge(dims, BETA, HB_SWEEPS, HB_SEED)
