@@ -51,9 +51,10 @@ NV, BLOCK, SETUP_SWEEPS = 20, (4, 4, 4, 4), 300
 TOL = 1e-10
 RHS_SEED = 1
 BW_DIMS = (32, 32, 32, 64)
-WORKLOAD = "8^3x16 beta=6.0 heatbath (200 sweeps, seed 0), 2-level MG 4^4 blocks Nv=20 (300 MR setup sweeps), " \
-           "mass sweep m_crit+{0.1,0.03,0.01,0.003} (setup at the lightest, one batched retarget to all four), " \
-           "1 Gaussian RHS, tol 1e-10"
+# no commas inside: a reader that splits the line's values at commas keeps the whole string
+WORKLOAD = "8^3x16 beta=6.0 heatbath (200 sweeps; seed 0); 2-level MG 4^4 blocks Nv=20 (300 MR setup sweeps); " \
+           "mass sweep m_crit + 0.1/0.03/0.01/0.003 (setup at the lightest; one batched retarget to all four); " \
+           "1 Gaussian RHS; tol 1e-10"
 
 
 def mcrit():
@@ -239,6 +240,7 @@ def native(args, rank, world, U, b):
                                            "fine_dslash": st["fine_dslash"],
                                            "true_rel_residual": st["true_rel_residual"]} for m, st, _ in chk]}
         out["speedup_mixed_vs_fp64"] = float(np.median(t_plain) / np.median(t_mixed))
+        out["fp64_plain_s"] = float(np.median(t_plain))
         # plain FP64 MG with the adaptive setup of Sec. 2 (16 of the 20 candidates from two adaptive
         # steps of 64 solver iterations), for the operator-application count against BiCGstab
         pa = wm.mg_default_params(n_levels=2, block=[BLOCK], nv=[NV], setup_sweeps=[SETUP_SWEEPS], mixed=0, seed=7,
@@ -701,7 +703,8 @@ def reference_arm(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(float(np.median(walls)) * 1e3, 1),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded beta=6.0 heatbath gauge field, Gaussian source)",
-            "config": {"workload": WORKLOAD, "l2": "n/a (host)",
+            "config": {"workload": WORKLOAD, "lattice": "8^3x16", "mg": "2 levels; 4^4 blocks; Nv=20",
+                       "masses": "m_crit + 0.1/0.03/0.01/0.003", "tol": 1e-10, "l2": "n/a (host)",
                        "step": "one sampled oracle step per timed step (ms_per_step is its wall time)"},
             "cpu_baseline": {"value": round(v, 3), "unit": "s per 4-mass sweep", "cores": nproc, "kind": "oracle",
                              "sample": ORACLE_SAMPLE, "parts": parts},
@@ -1019,12 +1022,14 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 3),
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded beta=6.0 heatbath gauge field, Gaussian source)",
-                "config": {"workload": WORKLOAD, "l2": "256 MB buffer written between timed steps",
+                "config": {"workload": WORKLOAD, "lattice": "8^3x16", "mg": "2 levels; 4^4 blocks; Nv=20",
+                           "masses": "m_crit + 0.1/0.03/0.01/0.003", "tol": 1e-10,
+                           "l2": "256 MB buffer written between timed steps",
                            "sweep": ("the four masses as concurrent handles (retarget batch + mg_solve_many)"
                                      if args.sweep == "many" else
                                      "one solve with a mass per right-hand side (mg_solve_masses)"),
-                           "precision": "fine smoother FP16 storage / FP32 math, Krylov FP32, FP64 reliable "
-                                        "updates, Gram-Schmidt and coarsest solve"},
+                           "precision": "fine smoother FP16 storage / FP32 math; Krylov FP32; FP64 reliable "
+                                        "updates / Gram-Schmidt / coarsest solve"},
                 "solves_per_s": round(world * len(DMASSES) / v, 3)}
         line.update(r)
         line["cpu_baseline"] = cpu
