@@ -903,7 +903,7 @@ def serve_workload(args):
                        "included)",
            "m_crit": {"x".join(map(str, d)): v[0] for d, v in crit.items()},
            "rates": []}
-    srv = serve.SolveServer(fields, None, budget, workers=4)
+    srv = serve.SolveServer(fields, None, budget, workers=4, keep_results=False)
     for name in names:  # warm the per-field hierarchies (setup once per field)
         srv.base(name)
     n_per_rate = args.serve_requests // len(args.serve_rates)
@@ -913,11 +913,17 @@ def serve_workload(args):
             f = names[int(rng.integers(0, len(names)))]
             dims = fields[f][1]
             nrhs = int(rng.integers(1, 13))
-            g = np.random.default_rng(int(rng.integers(1 << 30)))
-            shp = (nrhs,) + (dims[3], dims[2], dims[1], dims[0], 4, 3)
-            b = g.standard_normal(shp) + 1j * g.standard_normal(shp)
+            seed = int(rng.integers(1 << 30))
             m = crit[dims][0] + float(rng.uniform(crit[dims][1], 0.1))
-            reqs.append(serve.Request(i, f, m, b, TOL, 0.0))
+
+            def make(i=i, f=f, dims=dims, nrhs=nrhs, seed=seed, m=m):
+                # the right-hand sides are drawn when the request arrives: a 16^3 x 32 request holds up
+                # to 300 MB, too much to keep a whole stream of them in host memory
+                g = np.random.default_rng(seed)
+                shp = (nrhs,) + (dims[3], dims[2], dims[1], dims[0], 4, 3)
+                return serve.Request(i, f, m, g.standard_normal(shp) + 1j * g.standard_normal(shp), TOL, 0.0)
+
+            reqs.append(make)
         nb0 = len(srv.batches)
         st = serve.run_stream(srv, reqs, serve.poisson_arrivals(rate, len(reqs), int(rng.integers(1 << 30))))
         bt = srv.batches[nb0:]

@@ -31,7 +31,7 @@ from . import wilson_mg as wm
 
 
 class Request:
-    __slots__ = ("rid", "field", "mass", "b", "tol", "arrival", "admitted", "done", "x", "stats", "error",
+    __slots__ = ("rid", "field", "mass", "b", "nrhs", "tol", "arrival", "admitted", "done", "x", "stats", "error",
                  "footprint", "event")
 
     def __init__(self, rid, field, mass, b, tol, arrival):
@@ -39,6 +39,7 @@ class Request:
         self.field = field
         self.mass = mass
         self.b = b
+        self.nrhs = b.shape[0] if b.ndim == 7 else 1
         self.tol = tol
         self.arrival = arrival
         self.admitted = None
@@ -57,10 +58,11 @@ class SolveServer:
     the mg_params of fields that bring none; hbm_budget: device bytes for the
     resident hierarchies plus the batches in flight; workers: maximum number
     of concurrent batches (one CUDA stream each); max_batch_rhs: right-hand
-    sides per batch (1..64); merge: False serves every request alone.
+    sides per batch (1..64); merge: False serves every request alone; keep_results: False drops each
+    request's right-hand sides and solution once its batch is done (its statistics stay), for long streams.
     """
 
-    def __init__(self, fields, params, hbm_budget, workers=4, max_batch_rhs=64, merge=True):
+    def __init__(self, fields, params, hbm_budget, workers=4, max_batch_rhs=64, merge=True, keep_results=True):
         import torch
         self.torch = torch
         self.fields = fields
@@ -68,6 +70,7 @@ class SolveServer:
         self.budget = int(hbm_budget)
         self.max_batch_rhs = int(max_batch_rhs)
         self.merge = merge
+        self.keep_results = keep_results
         self.inflight_bytes = 0
         self.inflight = 0
         self.max_inflight = 0
@@ -94,7 +97,7 @@ class SolveServer:
 
     @staticmethod
     def nrhs_of(req):
-        return req.b.shape[0] if req.b.ndim == 7 else 1
+        return req.nrhs
 
     def footprint(self, field, nrhs):
         return wm.mg_footprint(self.fields[field][1], self.params_of(field), nrhs)
@@ -240,6 +243,10 @@ class SolveServer:
                 for req in batch:
                     req.error = str(e)
             self._settle(wid, batch[0].field, stream)
+            if not self.keep_results:
+                for req in batch:
+                    req.b = None
+                    req.x = None
             t = time.perf_counter()
             with self.lock:
                 for req in batch:
@@ -259,19 +266,26 @@ def poisson_arrivals(rate, n, seed):
 
 
 def run_stream(server, requests, arrivals):
-    """Submit requests at their arrival times (relative to now); wait for all; return latency stats."""
+    """Submit requests at their arrival times (relative to now); wait for all; return latency stats.
+    An entry of `requests` may be a function that makes the Request when it arrives (so that a long
+    stream does not hold every right-hand side at once)."""
     t0 = time.perf_counter()
+    made = []
     for req, ta in zip(requests, arrivals):
         delay = t0 + ta - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
+        if callable(req):
+            req = req()
+        made.append(req)
         req.arrival = time.perf_counter()
         server.submit(req)
+    requests = made
     for req in requests:
         req.event.wait()
     t1 = time.perf_counter()
     lat = np.array([r.done - r.arrival for r in requests if r.error is None])
-    nrhs = sum((r.b.shape[0] if r.b.ndim == 7 else 1) for r in requests if r.error is None)
+    nrhs = sum(r.nrhs for r in requests if r.error is None)
     errors = collections.Counter(r.error[:120] for r in requests if r.error is not None)
     return {"requests": len(requests), "failed": sum(r.error is not None for r in requests),
             "errors": dict(errors.most_common(4)),

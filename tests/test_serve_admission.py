@@ -100,3 +100,29 @@ def test_same_field_requests_merge_into_one_batch(serve_mod):
                 resident=wm.mg_footprint(dims, p, 4) - wm.mg_footprint(dims, p, 1) + 1)
     t.submit(_req(serve_mod, 5, "a", 1, dims))
     assert t._admit() is None
+
+
+def test_stream_makes_requests_on_arrival(serve_mod):
+    """run_stream takes functions that make each request when it arrives (a long stream then never holds
+    every right-hand side at once); latency and right-hand-side counts come from the made requests."""
+    made = []
+
+    class Instant:  # completes every submission at once, with no device work
+        def submit(self, req):
+            req.done = req.arrival + 0.001
+            req.stats = [{}] * req.nrhs
+            req.event.set()
+            return req
+
+    def factory(i, nrhs):
+        def make():
+            made.append(i)
+            return serve_mod.Request(i, "a", 0.1, np.zeros((nrhs, 1, 1, 1, 1, 4, 3), np.complex128), 1e-10, 0.0)
+        return make
+
+    fs = [factory(i, 1 + i % 3) for i in range(6)]
+    st = serve_mod.run_stream(Instant(), fs, np.zeros(6))
+    assert made == list(range(6))
+    assert st["requests"] == 6 and st["failed"] == 0
+    assert abs(st["rhs_per_s"] * st["wall_s"] - sum(1 + i % 3 for i in range(6))) < 1e-9
+    assert abs(st["p50_s"] - 0.001) < 1e-12
