@@ -57,6 +57,17 @@ WORKLOAD = "8^3x16 beta=6.0 heatbath (200 sweeps; seed 0); 2-level MG 4^4 blocks
            "1 Gaussian RHS; tol 1e-10"
 
 
+def bench_config(args):
+    """The step's configuration (the same dict in the library's line and the oracle's)."""
+    return {"workload": WORKLOAD, "lattice": "8^3x16", "mg": "2 levels; 4^4 blocks; Nv=20",
+            "masses": "m_crit + 0.1/0.03/0.01/0.003", "tol": 1e-10,
+            "l2": "256 MB buffer written between timed steps (GPU)",
+            "sweep": ("the four masses as concurrent handles (retarget batch + mg_solve_many)"
+                      if args.sweep == "many" else "one solve with a mass per right-hand side (mg_solve_masses)"),
+            "precision": "fine smoother FP16 storage / FP32 math; Krylov FP32; FP64 reliable updates / "
+                         "Gram-Schmidt / coarsest solve (the oracle: FP64 throughout)"}
+
+
 def mcrit():
     key = "%dx%dx%dx%d_beta%.1f_sweeps%d_seed%d" % (*DIMS, BETA, HB_SWEEPS, HB_SEED)
     with open(os.path.join(ROOT, "tests", "golden", "mcrit.json")) as f:
@@ -703,9 +714,7 @@ def reference_arm(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(float(np.median(walls)) * 1e3, 1),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded beta=6.0 heatbath gauge field, Gaussian source)",
-            "config": {"workload": WORKLOAD, "lattice": "8^3x16", "mg": "2 levels; 4^4 blocks; Nv=20",
-                       "masses": "m_crit + 0.1/0.03/0.01/0.003", "tol": 1e-10, "l2": "n/a (host)",
-                       "step": "one sampled oracle step per timed step (ms_per_step is its wall time)"},
+            "config": bench_config(args),
             "cpu_baseline": {"value": round(v, 3), "unit": "s per 4-mass sweep", "cores": nproc, "kind": "oracle",
                              "sample": ORACLE_SAMPLE, "parts": parts},
             "e2e": {"value": round(v, 3), "unit": "s per 4-mass sweep", "h2d_bytes_per_step": 0,
@@ -1028,14 +1037,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 3),
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded beta=6.0 heatbath gauge field, Gaussian source)",
-                "config": {"workload": WORKLOAD, "lattice": "8^3x16", "mg": "2 levels; 4^4 blocks; Nv=20",
-                           "masses": "m_crit + 0.1/0.03/0.01/0.003", "tol": 1e-10,
-                           "l2": "256 MB buffer written between timed steps",
-                           "sweep": ("the four masses as concurrent handles (retarget batch + mg_solve_many)"
-                                     if args.sweep == "many" else
-                                     "one solve with a mass per right-hand side (mg_solve_masses)"),
-                           "precision": "fine smoother FP16 storage / FP32 math; Krylov FP32; FP64 reliable "
-                                        "updates / Gram-Schmidt / coarsest solve"},
+                "config": bench_config(args),
                 "solves_per_s": round(world * len(DMASSES) / v, 3)}
         line.update(r)
         line["cpu_baseline"] = cpu
